@@ -1,0 +1,167 @@
+"""CPU oracle for the cyclic-group RAID-6 code (arXiv cs/0611109).
+
+TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The product package never imports this
+module and this module never imports the product package.
+
+This file is a thin ctypes binding over ``rcg_oracle.c`` (compiled with gcc into
+``oracle/_build/``).  All arithmetic lives in the C file: bit-level polynomial
+arithmetic in R = F2[x]/(1 + x + ... + x^(p-1)), one codeword per bit position,
+following Corollary 3.2.4 (encode) and Lemma 3.1.2 (the four erasure-pair
+cases).  Buffers are numpy uint8 arrays in the stripe layout
+``[stripe][strip 0..N+1][row 0..p-2][C bytes]`` (strip N = P, strip N+1 = Q),
+with optional explicit byte strides.
+
+Parity pins: every function here is checked against facts the paper and the
+mathematics fix (tests/test_oracle_pins.py); no function is unpinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rcg_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "librcg_oracle.so")
+
+_u64 = ctypes.c_uint64
+_uint = ctypes.c_uint
+_vp = ctypes.c_void_p
+
+
+def build(src: str = _SRC, out: str = _LIB) -> str:
+    """Compile the oracle with gcc (portable C, no target-specific flags)."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if (not os.path.exists(out)) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, src])
+        os.replace(tmp, out)
+    return out
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    lib = ctypes.CDLL(path or build())
+    lib.oracle_ring_mul.restype = _u64
+    lib.oracle_ring_mul.argtypes = [_uint, _u64, _u64]
+    lib.oracle_ring_xpow.restype = _u64
+    lib.oracle_ring_xpow.argtypes = [_uint, _uint]
+    lib.oracle_ring_inv.restype = _u64
+    lib.oracle_ring_inv.argtypes = [_uint, _u64]
+    lib.oracle_mul_xpow_array.restype = None
+    lib.oracle_mul_xpow_array.argtypes = [_uint, _uint, _vp, _vp, ctypes.c_size_t]
+    lib.oracle_encode.restype = ctypes.c_int
+    lib.oracle_encode.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _u64]
+    lib.oracle_recover.restype = ctypes.c_int
+    lib.oracle_recover.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _u64, _uint, _uint, _vp]
+    lib.oracle_update.restype = ctypes.c_int
+    lib.oracle_update.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _u64, _uint, _vp, _u64]
+    lib.oracle_degraded_read.restype = ctypes.c_int
+    lib.oracle_degraded_read.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _u64, _uint, _vp, _u64]
+    return lib
+
+
+_lib: ctypes.CDLL | None = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded oracle.  RCG_ORACLE_LIB, when set, names another build of
+    rcg_oracle.c to load instead (the mutation tests use it)."""
+    global _lib
+    if _lib is None:
+        _lib = load(os.environ.get("RCG_ORACLE_LIB") or None)
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _strides(p, N, C, row_stride, strip_stride, stripe_stride):
+    row_stride = C if row_stride is None else row_stride
+    strip_stride = (p - 1) * row_stride if strip_stride is None else strip_stride
+    stripe_stride = (N + 2) * strip_stride if stripe_stride is None else stripe_stride
+    return row_stride, strip_stride, stripe_stride
+
+
+def _check_buf(buf: np.ndarray):
+    if buf.dtype != np.uint8 or not buf.flags["C_CONTIGUOUS"] or not buf.flags["WRITEABLE"]:
+        raise ValueError("oracle buffers must be writeable C-contiguous uint8 arrays")
+
+
+# ------------------------------------------------------------------ ring ops
+
+def ring_mul(p: int, a: int, b: int) -> int:
+    """Product in R = F2[x]/(1+...+x^(p-1)); bit r of an int = coefficient of x^r."""
+    return int(lib().oracle_ring_mul(p, a, b))
+
+
+def ring_xpow(p: int, k: int) -> int:
+    """x^k in R (0 <= k < 128)."""
+    return int(lib().oracle_ring_xpow(p, k))
+
+
+def ring_inv(p: int, a: int) -> int:
+    """Inverse in R by extended Euclid; 0 if a is not invertible."""
+    return int(lib().oracle_ring_inv(p, a))
+
+
+def mul_xpow_array(p: int, k: int, a: np.ndarray) -> np.ndarray:
+    """x^k * a[t] in R for every element of a uint64 array."""
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    out = np.empty_like(a)
+    lib().oracle_mul_xpow_array(p, k, _ptr(a), _ptr(out), a.size)
+    return out
+
+
+# ------------------------------------------------------------- stripe ops
+
+def encode(p, N, C, buf, n_stripes, row_stride=None, strip_stride=None, stripe_stride=None):
+    """Write P and Q of every stripe (Corollary 3.2.4, equation znparity)."""
+    _check_buf(buf)
+    rs, ss, st = _strides(p, N, C, row_stride, strip_stride, stripe_stride)
+    rc = lib().oracle_encode(p, N, C, _ptr(buf), n_stripes, rs, ss, st)
+    if rc:
+        raise ValueError("oracle_encode: invalid arguments")
+
+
+def recover(p, N, C, buf, n_stripes, i=0, j=1, pairs=None, row_stride=None,
+            strip_stride=None, stripe_stride=None):
+    """Rebuild strips i < j (or per-stripe pairs, uint8 [n_stripes, 2]) in place
+    by the case analysis of Lemma 3.1.2."""
+    _check_buf(buf)
+    rs, ss, st = _strides(p, N, C, row_stride, strip_stride, stripe_stride)
+    pp = None
+    if pairs is not None:
+        pairs = np.ascontiguousarray(pairs, dtype=np.uint8)
+        pp = _ptr(pairs)
+    rc = lib().oracle_recover(p, N, C, _ptr(buf), n_stripes, rs, ss, st, i, j, pp)
+    if rc:
+        raise ValueError("oracle_recover: invalid arguments (rc=%d)" % rc)
+
+
+def update(p, N, C, buf, stripe, i, new_strip, row_stride=None, strip_stride=None,
+           stripe_stride=None):
+    """Store new_strip ((p-1) x C uint8) as data strip i of one stripe and
+    re-encode that stripe."""
+    _check_buf(buf)
+    rs, ss, st = _strides(p, N, C, row_stride, strip_stride, stripe_stride)
+    new_strip = np.ascontiguousarray(new_strip, dtype=np.uint8).reshape(p - 1, -1)
+    rc = lib().oracle_update(p, N, C, _ptr(buf), stripe, rs, ss, st, i, _ptr(new_strip),
+                             new_strip.shape[1])
+    if rc:
+        raise ValueError("oracle_update: invalid arguments")
+
+
+def degraded_read(p, N, C, buf, stripe, j, row_stride=None, strip_stride=None,
+                  stripe_stride=None) -> np.ndarray:
+    """Strip j of one stripe rebuilt from the others, as a (p-1) x C array."""
+    _check_buf(buf)
+    rs, ss, st = _strides(p, N, C, row_stride, strip_stride, stripe_stride)
+    out = np.zeros((p - 1, C), dtype=np.uint8)
+    rc = lib().oracle_degraded_read(p, N, C, _ptr(buf), stripe, rs, ss, st, j, _ptr(out), C)
+    if rc:
+        raise ValueError("oracle_degraded_read: invalid arguments")
+    return out

@@ -1,0 +1,371 @@
+/*
+ * rcg_oracle.c -- bit-level CPU oracle for the cyclic-group RAID-6 code of
+ * Jackson, Rumynin and Zaboronski, "An approach to RAID-6 based on cyclic
+ * groups" (arXiv cs/0611109).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file.  The product library never
+ * links, includes or calls it, and it shares no code, table or helper with the
+ * CUDA path.
+ *
+ * What it computes.  A strip is an element of the ring
+ *     R = F2[x] / (f),   f = 1 + x + ... + x^(p-1),   p an odd prime,
+ * i.e. a polynomial of degree <= p-2 (Lemma 3.4.1: the Sylvester matrix S_p is
+ * the companion matrix of f, so multiplying by S_p is multiplying by x in R).
+ * The code is the one of Corollary 3.2.4, equation (znparity), with generator
+ * g = S_p and 0-based data indices as in Section 4.1 (data strip k is weighted
+ * by g^k):
+ *     P = sum_k d_k,            Q = sum_k x^k d_k   (mod f).
+ *
+ * Storage (bit slicing).  A strip is p-1 rows of C bytes.  Bit b of the row
+ * region (byte b/8, bit b%8) of row r holds the coefficient of x^r of the b-th
+ * independent codeword of the strip.  So a strip of C-byte rows carries 8*C
+ * ring elements, one per bit position, and every function below works one bit
+ * position at a time: gather the polynomial, do the ring arithmetic with a
+ * generic carry-less multiply and a long-division remainder, scatter it back.
+ *
+ * Ring arithmetic is deliberately generic: multiplication is schoolbook
+ * carry-less multiplication followed by polynomial long division by f, and
+ * inverses come from the extended Euclidean algorithm against f.  None of the
+ * rotate-and-fold shortcuts or the closed-form inverse of Section 4.6 appear
+ * here; the tests check those closed forms against this file.
+ *
+ * Stripe layout: stripe s starts at buf + s*stripe_stride; strip k (data
+ * 0..N-1, then P = strip N and Q = strip N+1) at + k*strip_stride; row r at
+ * + r*row_stride; the row is C bytes.
+ */
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+typedef uint64_t u64;
+
+/* ---------------------------------------------------------------- F2[x] */
+
+static int poly_degree(u128 a)
+{
+    int d = -1;
+    while (a) {
+        a >>= 1;
+        d++;
+    }
+    return d;
+}
+
+/* Carry-less (F2[x]) product.  The caller keeps deg(a)+deg(b) < 128. */
+static u128 poly_mul(u128 a, u128 b)
+{
+    u128 r = 0;
+    int sh = 0;
+    while (b) {
+        if (b & 1)
+            r ^= a << sh;
+        b >>= 1;
+        sh++;
+    }
+    return r;
+}
+
+/* Quotient and remainder of polynomial long division a = q*m + r. */
+static void poly_divmod(u128 a, u128 m, u128 *q, u128 *r)
+{
+    int dm = poly_degree(m);
+    u128 quo = 0;
+    int da = poly_degree(a);
+    while (da >= dm) {
+        quo ^= (u128)1 << (da - dm);
+        a ^= m << (da - dm);
+        da = poly_degree(a);
+    }
+    if (q)
+        *q = quo;
+    if (r)
+        *r = a;
+}
+
+/* f = 1 + x + ... + x^(p-1): the characteristic (and minimal) polynomial of
+ * the Sylvester matrix S_p, Lemma 3.4.1(ii). */
+static u128 poly_f(unsigned p)
+{
+    return (((u128)1) << p) - 1;
+}
+
+/* ------------------------------------------------------------------ R */
+
+/* Product in R = F2[x]/(f).  Operands are reduced (degree <= p-2). */
+u64 oracle_ring_mul(unsigned p, u64 a, u64 b)
+{
+    u128 r;
+    poly_divmod(poly_mul(a, b), poly_f(p), NULL, &r);
+    return (u64)r;
+}
+
+/* x^k in R, for 0 <= k < 128. */
+u64 oracle_ring_xpow(unsigned p, unsigned k)
+{
+    u128 r;
+    poly_divmod(((u128)1) << k, poly_f(p), NULL, &r);
+    return (u64)r;
+}
+
+/* Inverse in R by the extended Euclidean algorithm against f.  Returns 0 when
+ * gcd(a, f) != 1 (a not invertible). */
+u64 oracle_ring_inv(unsigned p, u64 a)
+{
+    u128 f = poly_f(p);
+    u128 r0 = f, r1, s0 = 0, s1 = 1;
+    poly_divmod(a, f, NULL, &r1);
+    if (r1 == 0)
+        return 0;
+    while (r1 != 0) {
+        u128 q, rem, s2;
+        poly_divmod(r0, r1, &q, &rem);
+        s2 = s0 ^ poly_mul(q, s1);
+        r0 = r1;
+        r1 = rem;
+        s0 = s1;
+        s1 = s2;
+    }
+    if (r0 != 1)
+        return 0;
+    poly_divmod(s0, f, NULL, &r1);
+    return (u64)r1;
+}
+
+/* out[t] = x^k * in[t] in R, for n elements. */
+void oracle_mul_xpow_array(unsigned p, unsigned k, const u64 *in, u64 *out, size_t n)
+{
+    u64 g = oracle_ring_xpow(p, k);
+    for (size_t t = 0; t < n; t++)
+        out[t] = oracle_ring_mul(p, g, in[t]);
+}
+
+/* ------------------------------------------------------ bit slicing */
+
+typedef struct {
+    uint8_t *base;
+    u64 row_stride, strip_stride, stripe_stride;
+    unsigned rows; /* p - 1 */
+} layout_t;
+
+static uint8_t *row_ptr(const layout_t *L, u64 s, unsigned k, unsigned r)
+{
+    return L->base + s * L->stripe_stride + (u64)k * L->strip_stride + (u64)r * L->row_stride;
+}
+
+/* Polynomial of codeword (bit position) b of strip k of stripe s. */
+static u64 gather(const layout_t *L, u64 s, unsigned k, u64 b)
+{
+    u64 a = 0;
+    for (unsigned r = 0; r < L->rows; r++) {
+        const uint8_t *row = row_ptr(L, s, k, r);
+        a |= (u64)((row[b >> 3] >> (b & 7)) & 1u) << r;
+    }
+    return a;
+}
+
+static void scatter(const layout_t *L, u64 s, unsigned k, u64 b, u64 a)
+{
+    for (unsigned r = 0; r < L->rows; r++) {
+        uint8_t *row = row_ptr(L, s, k, r);
+        uint8_t m = (uint8_t)(1u << (b & 7));
+        if ((a >> r) & 1u)
+            row[b >> 3] |= m;
+        else
+            row[b >> 3] &= (uint8_t)~m;
+    }
+}
+
+static int check_args(unsigned p, unsigned N)
+{
+    if (p < 3 || p > 61 || (p % 2) == 0)
+        return -1;
+    for (unsigned t = 3; t * t <= p; t += 2)
+        if (p % t == 0)
+            return -1;
+    if (N < 1 || N > p)
+        return -1;
+    return 0;
+}
+
+/* ------------------------------------------------------------- encode */
+
+/* Equation (znparity) of Corollary 3.2.4 with g = S_p and g_k = g^k:
+ * P = sum_k d_k, Q = sum_k g^k d_k.  Writes strips N and N+1. */
+int oracle_encode(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
+                  u64 row_stride, u64 strip_stride, u64 stripe_stride)
+{
+    if (check_args(p, N))
+        return -1;
+    layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1};
+    u64 g[64];
+    for (unsigned k = 0; k < N; k++)
+        g[k] = oracle_ring_xpow(p, k);
+    for (u64 s = 0; s < n_stripes; s++) {
+        for (u64 b = 0; b < 8 * C; b++) {
+            u64 P = 0, Q = 0;
+            for (unsigned k = 0; k < N; k++) {
+                u64 d = gather(&L, s, k, b);
+                P ^= d;
+                Q ^= oracle_ring_mul(p, g[k], d);
+            }
+            scatter(&L, s, N, b, P);
+            scatter(&L, s, N + 1, b, Q);
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------ recover */
+
+/* Solve the parity equations (cone) of Lemma 3.1.2 for the pair of lost
+ * strips i < j (0-based; strip N is P = d_{N+1} of the lemma and strip N+1
+ * is Q = d_{N+2}), following the four cases of its proof:
+ *   (P, Q):          recompute both parities;
+ *   (d_i, P):        d_i = g_i^{-1} (Q + sum_{k != i} g_k d_k), then P;
+ *   (d_i, Q):        d_i = P + sum_{k != i} d_k (RAID-5), then Q;
+ *   (d_i, d_j):      d_j = (g_i + g_j)^{-1} (g_i P + Q + sum_{k != i,j} (g_k + g_i) d_k),
+ *                    then d_i = P + sum_{k != i} d_k.
+ * Inverses come from the extended Euclidean algorithm.  The erased strips'
+ * contents are never read. */
+static void recover_one(const layout_t *L, unsigned p, unsigned N, u64 s, u64 b,
+                        unsigned i, unsigned j, const u64 *g)
+{
+    u64 d[64];
+    if (i == N && j == N + 1) {
+        u64 P = 0, Q = 0;
+        for (unsigned k = 0; k < N; k++) {
+            d[k] = gather(L, s, k, b);
+            P ^= d[k];
+            Q ^= oracle_ring_mul(p, g[k], d[k]);
+        }
+        scatter(L, s, N, b, P);
+        scatter(L, s, N + 1, b, Q);
+        return;
+    }
+    if (j == N) { /* d_i and P lost */
+        u64 Q = gather(L, s, N + 1, b);
+        u64 acc = Q;
+        for (unsigned k = 0; k < N; k++) {
+            if (k == i)
+                continue;
+            d[k] = gather(L, s, k, b);
+            acc ^= oracle_ring_mul(p, g[k], d[k]);
+        }
+        d[i] = oracle_ring_mul(p, oracle_ring_inv(p, g[i]), acc);
+        u64 P = 0;
+        for (unsigned k = 0; k < N; k++)
+            P ^= d[k];
+        scatter(L, s, i, b, d[i]);
+        scatter(L, s, N, b, P);
+        return;
+    }
+    if (j == N + 1) { /* d_i and Q lost */
+        u64 P = gather(L, s, N, b);
+        u64 acc = P;
+        for (unsigned k = 0; k < N; k++) {
+            if (k == i)
+                continue;
+            d[k] = gather(L, s, k, b);
+            acc ^= d[k];
+        }
+        d[i] = acc;
+        u64 Q = 0;
+        for (unsigned k = 0; k < N; k++)
+            Q ^= oracle_ring_mul(p, g[k], d[k]);
+        scatter(L, s, i, b, d[i]);
+        scatter(L, s, N + 1, b, Q);
+        return;
+    }
+    /* two data strips lost */
+    u64 P = gather(L, s, N, b);
+    u64 Q = gather(L, s, N + 1, b);
+    u64 rhs = oracle_ring_mul(p, g[i], P) ^ Q;
+    for (unsigned k = 0; k < N; k++) {
+        if (k == i || k == j)
+            continue;
+        d[k] = gather(L, s, k, b);
+        rhs ^= oracle_ring_mul(p, g[k] ^ g[i], d[k]);
+    }
+    d[j] = oracle_ring_mul(p, oracle_ring_inv(p, g[i] ^ g[j]), rhs);
+    u64 di = P ^ d[j];
+    for (unsigned k = 0; k < N; k++)
+        if (k != i && k != j)
+            di ^= d[k];
+    scatter(L, s, i, b, di);
+    scatter(L, s, j, b, d[j]);
+}
+
+/* Recover strips i < j of stripes [0, n_stripes) in place.  pairs, when not
+ * NULL, gives a per-stripe (i, j) as two bytes per stripe and overrides i, j. */
+int oracle_recover(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
+                   u64 row_stride, u64 strip_stride, u64 stripe_stride,
+                   unsigned i, unsigned j, const uint8_t *pairs)
+{
+    if (check_args(p, N))
+        return -1;
+    layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1};
+    u64 g[64];
+    for (unsigned k = 0; k < N; k++)
+        g[k] = oracle_ring_xpow(p, k);
+    for (u64 s = 0; s < n_stripes; s++) {
+        unsigned a = pairs ? pairs[2 * s] : i;
+        unsigned c = pairs ? pairs[2 * s + 1] : j;
+        if (!(a < c && c < N + 2))
+            return -2;
+        for (u64 b = 0; b < 8 * C; b++)
+            recover_one(&L, p, N, s, b, a, c, g);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------- update */
+
+/* Small write: replace data strip i of stripe `stripe` with new_strip (p-1
+ * rows of C bytes, rows new_row_stride apart) and bring P and Q back to the
+ * values equation (znparity) gives for the new data.  The oracle does this by
+ * its definition -- store the new strip, re-encode the stripe -- rather than
+ * by the incremental rule P += delta, Q += g^i delta. */
+int oracle_update(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 stripe,
+                  u64 row_stride, u64 strip_stride, u64 stripe_stride,
+                  unsigned i, const uint8_t *new_strip, u64 new_row_stride)
+{
+    if (check_args(p, N) || i >= N)
+        return -1;
+    layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1};
+    for (unsigned r = 0; r < p - 1; r++)
+        memmove(row_ptr(&L, stripe, i, r), new_strip + (u64)r * new_row_stride, C);
+    return oracle_encode(p, N, C, buf + stripe * stripe_stride, 1, row_stride, strip_stride,
+                         stripe_stride);
+}
+
+/* -------------------------------------------------------- degraded read */
+
+/* Read strip j of stripe `stripe` as if it were lost, rebuilding it from the
+ * other strips with the equation that does not involve the other parity:
+ * a data strip or P from the first equation of (znparity) (the RAID-5 rule),
+ * Q from the second.  The result goes to out (p-1 rows, out_row_stride apart);
+ * strip j itself is not read. */
+int oracle_degraded_read(unsigned p, unsigned N, u64 C, const uint8_t *buf, u64 stripe,
+                         u64 row_stride, u64 strip_stride, u64 stripe_stride, unsigned j,
+                         uint8_t *out, u64 out_row_stride)
+{
+    if (check_args(p, N) || j >= N + 2)
+        return -1;
+    layout_t L = {(uint8_t *)buf, row_stride, strip_stride, stripe_stride, p - 1};
+    layout_t O = {out, out_row_stride, 0, 0, p - 1};
+    for (u64 b = 0; b < 8 * C; b++) {
+        u64 v = 0;
+        if (j == N + 1) {
+            for (unsigned k = 0; k < N; k++)
+                v ^= oracle_ring_mul(p, oracle_ring_xpow(p, k), gather(&L, stripe, k, b));
+        } else {
+            for (unsigned k = 0; k <= N; k++)
+                if (k != j)
+                    v ^= gather(&L, stripe, k, b);
+        }
+        scatter(&O, 0, 0, b, v);
+    }
+    return 0;
+}
