@@ -1,0 +1,205 @@
+/*
+ * rcg.h -- C ABI of librcg, a GB300 (sm_103a) implementation of the
+ * cyclic-group RAID-6 code of Jackson, Rumynin and Zaboronski, "An approach to
+ * RAID-6 based on cyclic groups" (arXiv cs/0611109).
+ *
+ * The code.  A strip is an element of R = F2[x]/(1 + x + ... + x^(p-1)) for an
+ * odd prime p: multiplication by x is multiplication by the Sylvester matrix
+ * S_p of Lemma 3.4.1, which has order p (Section 3.4).  For N data strips
+ * d_0..d_{N-1} the two parity strips are (Corollary 3.2.4, equation
+ * (znparity), 0-based data indices as in Section 4.1)
+ *     P = d_0 + d_1 + ... + d_{N-1},      Q = d_0 + x d_1 + ... + x^(N-1) d_{N-1},
+ * and any two lost strips are rebuilt by the case analysis of Lemma 3.1.2,
+ * the two-data case by the elimination of Sections 4.3 and 4.6 with the
+ * precomputed inverses (1 + x^z)^(-1).  Everything is XOR over GF(2): results
+ * are exact and the solution of every erasure pair is unique (Lemma 3.1.2).
+ *
+ * Storage (bit-sliced).  A strip is p-1 rows of C bytes; row r holds the
+ * coefficient of x^r of 8*C independent codewords, one per bit position.
+ * Byte order, word width and bit order inside a row are irrelevant: every
+ * operation is a row-level XOR plus a row-index remap.
+ *
+ * Stripe layout.  rcg_layout describes stripes in device memory: stripe s at
+ * base + s*stripe_stride, its strip k (data k < N, P = strip N, Q = strip
+ * N+1) at + k*strip_stride, row r at + r*row_stride; each row is row_bytes
+ * bytes.  A zero stride means "packed".  base, strides and row_bytes must be
+ * multiples of 16 bytes.
+ *
+ * Ownership and asynchrony.  The caller owns every stripe buffer (device
+ * memory, e.g. from PyTorch) and every output buffer.  Calls enqueue work on
+ * the caller's CUDA stream (a cudaStream_t passed as void*; NULL = legacy
+ * default stream) and return before it runs; the library keeps no pointer
+ * past the call except as stated for rcg_batch_submit.  Argument errors are
+ * returned synchronously and enqueue nothing.  Errors a kernel finds (an
+ * invalid per-stripe erasure pair read from device memory, a bounded wait
+ * that expired) are recorded in the context's device status word, read with
+ * rcg_last_device_status.  No call aborts the process, traps on the device or
+ * waits without a time limit.
+ *
+ * Overlap.  Work inside one call must not write memory another part of the
+ * same call reads, except in place as documented (a recovery writes only the
+ * erased strips, which it never reads).
+ */
+#ifndef RCG_H
+#define RCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RCG_ABI_VERSION 1u
+
+typedef enum rcg_status {
+    RCG_OK = 0,
+    RCG_EINVAL = 1,       /* invalid argument; nothing was enqueued */
+    RCG_ENOMEM = 2,       /* a library allocation failed */
+    RCG_ECUDA = 3,        /* a CUDA runtime call failed */
+    RCG_ETIMEOUT = 4,     /* a bounded wait expired */
+    RCG_EBUSY = 5,        /* a queue or slot table is full; retry later */
+    RCG_EUNSUPPORTED = 6, /* the device is not sm_103 or a parameter is out of range */
+    RCG_EDEVICE = 7       /* a kernel reported an error in the device status word */
+} rcg_status;
+
+/* Bits of the device status word (rcg_last_device_status). */
+#define RCG_DEV_TIMEOUT 0x1u  /* a kernel's bounded wait on an mbarrier expired */
+#define RCG_DEV_BADPAIR 0x2u  /* a per-stripe erasure pair read from device memory was invalid;
+                                 that stripe was skipped */
+#define RCG_DEV_BADJOB 0x4u   /* a batch descriptor failed the device-side check; skipped */
+
+typedef struct rcg_ctx rcg_ctx;
+
+typedef struct rcg_layout {
+    void *base;             /* device address of stripe 0 */
+    uint32_t p;             /* odd prime, 3 <= p <= 61; strips have p-1 rows */
+    uint32_t n_data;        /* N, 1 <= N <= p (Corollary 3.2.4); strip N = P, N+1 = Q */
+    uint64_t row_bytes;     /* C, bytes per row, a positive multiple of 16 */
+    uint64_t row_stride;    /* bytes between rows of a strip; 0 = row_bytes */
+    uint64_t strip_stride;  /* bytes between strips; 0 = (p-1)*row_stride */
+    uint64_t stripe_stride; /* bytes between stripes; 0 = (N+2)*strip_stride */
+} rcg_layout;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (must be compute capability 10.3).
+ * The context owns the per-p inverse tables (uploaded to the device), a
+ * device status word and the batch descriptor buffers.  One context may be
+ * used from one host thread at a time. */
+rcg_status rcg_create(int device, rcg_ctx **out);
+rcg_status rcg_destroy(rcg_ctx *ctx);
+
+/* Upper limit, in nanoseconds, of every wait a kernel of this context makes
+ * (default 2e9).  A wait that runs out sets RCG_DEV_TIMEOUT and the kernel
+ * returns. */
+rcg_status rcg_set_timeout(rcg_ctx *ctx, uint64_t timeout_ns);
+
+/* Synchronise the device and read, then clear, the device status word.
+ * Returns RCG_EDEVICE when any bit was set (then *code holds the bits). */
+rcg_status rcg_last_device_status(rcg_ctx *ctx, uint32_t *code);
+
+const char *rcg_status_str(rcg_status s);
+uint32_t rcg_abi_version(void);
+
+/* ------------------------------------------------------------ stripe ops */
+
+/* Encode: write P and Q of stripes [first_stripe, first_stripe + n_stripes)
+ * from their data strips (Corollary 3.2.4, equation (znparity)).  One launch
+ * for all stripes.  n_stripes == 0 is a no-op. */
+rcg_status rcg_encode(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe,
+                      uint64_t n_stripes, void *stream);
+
+/* Recover strips i < j (0 <= i < j <= N+1) of one stripe in place from the
+ * other N strips (Lemma 3.1.2): two data strips by Section 4.6's solve,
+ * data + P through x^(-i) = x^(p-i), data + Q as in RAID-5, P + Q by
+ * re-encoding.  The contents of strips i and j are not read. */
+rcg_status rcg_recover(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32_t i,
+                       uint32_t j, void *stream);
+
+/* Recover a per-stripe erasure pair for stripes [first_stripe, first_stripe +
+ * n_stripes) in one launch.  pairs is a DEVICE array of 2*n_stripes bytes:
+ * (i, j) of stripe first_stripe + s at pairs[2s], pairs[2s+1].  A stripe whose
+ * pair is not 0 <= i < j <= N+1 is left untouched and sets RCG_DEV_BADPAIR. */
+rcg_status rcg_recover_many(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe,
+                            uint64_t n_stripes, const uint8_t *pairs, void *stream);
+
+/* Small write (Section 3.4: updating Q needs no special instructions):
+ * replace data strip i (< N) of one stripe by new_strip (device, p-1 rows of
+ * C bytes, new_row_stride bytes apart; 0 = C) and update the parities by
+ * P += d_i + new, Q += x^i (d_i + new).  Reads 4 strips, writes 3.  new_strip
+ * must not overlap the stripe. */
+rcg_status rcg_update(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32_t i,
+                      const void *new_strip, uint64_t new_row_stride, void *stream);
+
+/* Degraded read: rebuild strip j (0 <= j <= N+1) of one stripe without
+ * reading it -- a data strip or P from the first parity equation (RAID-5),
+ * Q from the second -- into out (device, p-1 rows of C bytes, out_row_stride
+ * apart; 0 = C).  The stripe is not modified. */
+rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32_t j,
+                             void *out, uint64_t out_row_stride, void *stream);
+
+/* ------------------------------------------------------------ batches */
+
+typedef enum rcg_op {
+    RCG_OP_ENCODE = 0,        /* encode n_stripes stripes */
+    RCG_OP_RECOVER = 1,       /* recover pair (i, j) of n_stripes stripes */
+    RCG_OP_DEGRADED_READ = 2, /* rebuild strip j of n_stripes stripes into aux */
+    RCG_OP_UPDATE = 3         /* replace data strip i of n_stripes stripes by aux */
+} rcg_op;
+
+typedef struct rcg_job {
+    rcg_layout layout;          /* stripes of this job (device memory) */
+    uint64_t first_stripe;      /* first stripe of the layout this job touches */
+    uint64_t n_stripes;         /* stripes in this job */
+    uint32_t op;                /* rcg_op */
+    uint32_t i, j;              /* recover: pair i < j; update: i; degraded read: j */
+    const void *aux;            /* update: new strips; degraded read: output (device) */
+    uint64_t aux_row_stride;    /* bytes between rows of aux; 0 = row_bytes */
+    uint64_t aux_stripe_stride; /* bytes between stripes of aux; 0 = (p-1)*aux_row_stride */
+} rcg_job;
+
+/* Run a list of jobs of mixed p, N, C and op in ONE persistent-kernel launch
+ * with dynamic tile scheduling (a global tile counter), so CTAs that finish
+ * small stripes take tiles of large ones.  The job list is validated on the
+ * host, copied into a context-owned device descriptor table and replayed
+ * through a CUDA graph captured once per context.  Jobs must not overlap in
+ * memory.  On return *ticket identifies the batch for rcg_batch_wait.  The
+ * context keeps no pointer into `jobs`.  Up to 4 batches may be in flight;
+ * a fifth waits (bounded) for the oldest, or returns RCG_EBUSY. */
+rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, void *stream,
+                            uint64_t *ticket);
+
+/* Wait at most timeout_ns for batch `ticket`; RCG_ETIMEOUT if it has not
+ * finished (the batch keeps running). */
+rcg_status rcg_batch_wait(rcg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns);
+
+/* ----------------------------------------------------------- utilities */
+
+/* Fill nbytes of device memory with the seeded test-data stream: word w (8
+ * bytes little-endian) of stream `seed` is the (w+1)-th output of SplitMix64
+ * started from state seed * 2^40; the buffer holds bytes [byte_offset,
+ * byte_offset + nbytes) of that stream (byte_offset a multiple of 8). */
+rcg_status rcg_fill_random(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte_offset,
+                           void *stream);
+
+/* Host: the per-p table of Section 4.6, (1 + x^z)^(-1) = sum_{j=0}^{(p-1)/2}
+ * x^(2jz), for z = 1..p-1, as exponent sets modulo x^p - 1: bit m of masks[z]
+ * set means the term x^m (0 <= m < p; x^(p-1) stands for its residue mod f).
+ * masks[0] is set to 0.  masks must hold p entries. */
+rcg_status rcg_inverse_table(uint32_t p, uint64_t *masks);
+
+/* Host: the tiling the library uses for one stripe geometry. */
+typedef struct rcg_plan_info {
+    uint32_t tile_bytes;       /* W: column-tile width in bytes (multiple of 16) */
+    uint32_t tiles_per_stripe; /* ceil(C / W) */
+    uint32_t slot_bytes;       /* shared-memory ring slot: (p-1) rows x W */
+    uint32_t n_slots;          /* ring depth */
+} rcg_plan_info;
+rcg_status rcg_plan(uint32_t p, uint64_t row_bytes, rcg_plan_info *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RCG_H */

@@ -1,0 +1,529 @@
+// rcg_api.cu -- host side of librcg: the C ABI declared in include/rcg.h.
+// Argument validation, tiling plans, per-context device state (status word,
+// inverse tables, batch descriptor tables and their CUDA graphs) and kernel
+// launches.  All stripe arithmetic runs in rcg_engine.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+#include <time.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/rcg.h"
+#include "rcg_internal.h"
+
+using namespace rcg;
+
+namespace {
+
+constexpr int kBatchRing = 4;
+
+struct BatchSlot {
+    uint8_t *host = nullptr;  // pinned descriptor table (header + jobs)
+    uint8_t *dev = nullptr;   // device copy read by the kernel
+    unsigned long long *counter = nullptr;
+    size_t cap_jobs = 0;
+    size_t bytes = 0;          // bytes the captured memcpy node copies
+    cudaStream_t capture = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t copy_node = nullptr;
+    cudaEvent_t done = nullptr;
+    uint64_t ticket = 0;
+    bool used = false;
+};
+
+}  // namespace
+
+struct rcg_ctx {
+    int device = 0;
+    int sm_count = 0;
+    uint32_t *status = nullptr;
+    uint64_t timeout_ns = 2000000000ull;
+    uint64_t next_ticket = 1;
+    BatchSlot slots[kBatchRing];
+};
+
+namespace {
+
+// Switch to the context's device for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+rcg_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return RCG_OK;
+    if (e == cudaErrorMemoryAllocation) return RCG_ENOMEM;
+    return RCG_ECUDA;
+}
+
+bool is_odd_prime(uint32_t p) {
+    if (p < 3 || (p & 1) == 0) return false;
+    for (uint32_t d = 3; d * d <= p; d += 2)
+        if (p % d == 0) return false;
+    return true;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+struct Geo {
+    uint32_t p, N;
+    uint64_t C, rs, ss, st;
+};
+
+rcg_status check_layout(const rcg_layout *L, Geo *g) {
+    if (!L || !L->base || !aligned16(L->base)) return RCG_EINVAL;
+    if (!is_odd_prime(L->p) || L->p > static_cast<uint32_t>(kMaxP)) return RCG_EINVAL;
+    if (L->n_data < 1 || L->n_data > L->p) return RCG_EINVAL;
+    const uint64_t C = L->row_bytes;
+    if (C == 0 || (C & 15) || C > 0xffffffffull) return RCG_EINVAL;
+    g->p = L->p;
+    g->N = L->n_data;
+    g->C = C;
+    g->rs = L->row_stride ? L->row_stride : C;
+    g->ss = L->strip_stride ? L->strip_stride : (L->p - 1) * g->rs;
+    g->st = L->stripe_stride ? L->stripe_stride : (L->n_data + 2) * g->ss;
+    if (g->rs < C || (g->rs & 15) || (g->ss & 15) || (g->st & 15)) return RCG_EINVAL;
+    return RCG_OK;
+}
+
+Job base_job(const rcg_layout *L, const Geo &g, uint64_t first_stripe, uint64_t n_stripes,
+             const Plan &pl) {
+    Job J;
+    memset(&J, 0, sizeof(J));
+    J.base = static_cast<uint8_t *>(L->base) + first_stripe * g.st;
+    J.row_stride = g.rs;
+    J.strip_stride = g.ss;
+    J.stripe_stride = g.st;
+    J.n_stripes = static_cast<uint32_t>(n_stripes);
+    J.C = static_cast<uint32_t>(g.C);
+    J.W = pl.W;
+    J.tiles_per_stripe = pl.tiles_per_stripe;
+    J.p = static_cast<uint8_t>(g.p);
+    J.n = static_cast<uint8_t>(g.N);
+    return J;
+}
+
+rcg_status launch_single(rcg_ctx *ctx, const Job &J, const Plan &pl, cudaStream_t stream) {
+    LaunchParams prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.jobs = nullptr;
+    prm.job0 = J;
+    prm.n_jobs = 1;
+    prm.slot_bytes = pl.slot_bytes;
+    prm.n_slots = pl.n_slots;
+    prm.dynamic_sched = 0;
+    prm.total_tiles = static_cast<uint64_t>(J.n_stripes) * J.tiles_per_stripe;
+    prm.status = ctx->status;
+    prm.timeout_ns = ctx->timeout_ns;
+    if (prm.total_tiles == 0) return RCG_OK;
+    const uint64_t grid = std::min<uint64_t>(prm.total_tiles, static_cast<uint64_t>(ctx->sm_count));
+    return from_cuda(launch_engine(prm, static_cast<int>(grid), stream));
+}
+
+uint64_t now_ns() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return static_cast<uint64_t>(ts.tv_sec) * 1000000000ull + ts.tv_nsec;
+}
+
+void sleep_us(long us) {
+    timespec ts = {0, us * 1000};
+    nanosleep(&ts, nullptr);
+}
+
+// Poll an event until it completes or timeout_ns passes.
+rcg_status wait_event(cudaEvent_t ev, uint64_t timeout_ns) {
+    const uint64_t t0 = now_ns();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return RCG_OK;
+        if (e != cudaErrorNotReady) return from_cuda(e);
+        if (now_ns() - t0 > timeout_ns) return RCG_ETIMEOUT;
+        sleep_us(20);
+    }
+}
+
+void free_slot(BatchSlot &s) {
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.host) cudaFreeHost(s.host);
+    if (s.dev) cudaFree(s.dev);
+    if (s.counter) cudaFree(s.counter);
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.capture) cudaStreamDestroy(s.capture);
+    s = BatchSlot();
+}
+
+}  // namespace
+
+// ====================================================================== plan
+
+bool rcg::make_plan(uint32_t p, uint64_t C, Plan *out) {
+    if (!is_odd_prime(p) || p > static_cast<uint32_t>(kMaxP) || C == 0 || (C & 15)) return false;
+    const uint64_t nvec_total = C / 16;
+    uint64_t nvec_max = static_cast<uint64_t>(kMaxItems) / p;
+    nvec_max = std::min<uint64_t>(nvec_max, kMaxSlotBytes / ((p - 1) * 16ull));
+    nvec_max = std::min<uint64_t>(nvec_max, kFoldBytes / 16);
+    const uint64_t tiles = (nvec_total + nvec_max - 1) / nvec_max;
+    if (tiles > 0xffffffffull) return false;
+    const uint64_t nvec = (nvec_total + tiles - 1) / tiles;
+    out->W = static_cast<uint32_t>(nvec * 16);
+    out->tiles_per_stripe = static_cast<uint32_t>(tiles);
+    out->slot_bytes = static_cast<uint32_t>(((p - 1) * out->W + 127) & ~127u);
+    out->n_slots = std::min<uint32_t>(kMaxSlots, kRingBytes / out->slot_bytes);
+    return out->n_slots >= 2;
+}
+
+// =================================================================== C ABI
+
+extern "C" {
+
+uint32_t rcg_abi_version(void) { return RCG_ABI_VERSION; }
+
+const char *rcg_status_str(rcg_status s) {
+    switch (s) {
+        case RCG_OK: return "ok";
+        case RCG_EINVAL: return "invalid argument";
+        case RCG_ENOMEM: return "out of memory";
+        case RCG_ECUDA: return "CUDA runtime error";
+        case RCG_ETIMEOUT: return "timed out";
+        case RCG_EBUSY: return "busy";
+        case RCG_EUNSUPPORTED: return "unsupported device or parameter";
+        case RCG_EDEVICE: return "device-side error";
+    }
+    return "unknown status";
+}
+
+rcg_status rcg_inverse_table(uint32_t p, uint64_t *masks) {
+    if (!masks || !is_odd_prime(p) || p > static_cast<uint32_t>(kMaxP)) return RCG_EINVAL;
+    inverse_masks(p, masks);
+    return RCG_OK;
+}
+
+rcg_status rcg_plan(uint32_t p, uint64_t row_bytes, rcg_plan_info *out) {
+    Plan pl;
+    if (!out || !make_plan(p, row_bytes, &pl)) return RCG_EINVAL;
+    out->tile_bytes = pl.W;
+    out->tiles_per_stripe = pl.tiles_per_stripe;
+    out->slot_bytes = pl.slot_bytes;
+    out->n_slots = pl.n_slots;
+    return RCG_OK;
+}
+
+rcg_status rcg_create(int device, rcg_ctx **out) {
+    if (!out) return RCG_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return RCG_EUNSUPPORTED;
+    DeviceGuard guard(device);
+    if (!guard.ok) return RCG_ECUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return RCG_ECUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return RCG_EUNSUPPORTED;
+    rcg_ctx *ctx = new (std::nothrow) rcg_ctx();
+    if (!ctx) return RCG_ENOMEM;
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    rcg_status st = from_cuda(upload_inverse_tables());
+    if (st == RCG_OK) st = from_cuda(engine_init_attributes());
+    if (st == RCG_OK) st = from_cuda(cudaMalloc(&ctx->status, 256));
+    if (st == RCG_OK) st = from_cuda(cudaMemset(ctx->status, 0, 256));
+    if (st == RCG_OK) st = from_cuda(cudaDeviceSynchronize());
+    if (st != RCG_OK) {
+        if (ctx->status) cudaFree(ctx->status);
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return RCG_OK;
+}
+
+rcg_status rcg_destroy(rcg_ctx *ctx) {
+    if (!ctx) return RCG_EINVAL;
+    DeviceGuard guard(ctx->device);
+    for (auto &s : ctx->slots) {
+        if (s.done) cudaEventSynchronize(s.done);
+        free_slot(s);
+    }
+    if (ctx->status) cudaFree(ctx->status);
+    delete ctx;
+    return RCG_OK;
+}
+
+rcg_status rcg_set_timeout(rcg_ctx *ctx, uint64_t timeout_ns) {
+    if (!ctx || timeout_ns == 0) return RCG_EINVAL;
+    ctx->timeout_ns = timeout_ns;
+    return RCG_OK;
+}
+
+rcg_status rcg_last_device_status(rcg_ctx *ctx, uint32_t *code) {
+    if (!ctx || !code) return RCG_EINVAL;
+    DeviceGuard guard(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return from_cuda(e);
+    uint32_t v = 0;
+    e = cudaMemcpy(&v, ctx->status, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(v));
+    if (e != cudaSuccess) return from_cuda(e);
+    *code = v;
+    return v ? RCG_EDEVICE : RCG_OK;
+}
+
+rcg_status rcg_encode(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe, uint64_t n_stripes,
+                      void *stream) {
+    Geo g;
+    if (!ctx) return RCG_EINVAL;
+    rcg_status st = check_layout(L, &g);
+    if (st) return st;
+    if (n_stripes == 0) return RCG_OK;
+    if (n_stripes > 0xffffffffull) return RCG_EINVAL;
+    Plan pl;
+    if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
+    Job J = base_job(L, g, first_stripe, n_stripes, pl);
+    J.op = OP_ENCODE;
+    DeviceGuard guard(ctx->device);
+    return launch_single(ctx, J, pl, static_cast<cudaStream_t>(stream));
+}
+
+rcg_status rcg_recover(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32_t i, uint32_t j,
+                       void *stream) {
+    Geo g;
+    if (!ctx) return RCG_EINVAL;
+    rcg_status st = check_layout(L, &g);
+    if (st) return st;
+    if (!(i < j && j <= g.N + 1)) return RCG_EINVAL;
+    Plan pl;
+    if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
+    Job J = base_job(L, g, stripe, 1, pl);
+    J.op = OP_RECOVER;
+    J.i = static_cast<uint8_t>(i);
+    J.j = static_cast<uint8_t>(j);
+    DeviceGuard guard(ctx->device);
+    return launch_single(ctx, J, pl, static_cast<cudaStream_t>(stream));
+}
+
+rcg_status rcg_recover_many(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe,
+                            uint64_t n_stripes, const uint8_t *pairs, void *stream) {
+    Geo g;
+    if (!ctx || !pairs) return RCG_EINVAL;
+    rcg_status st = check_layout(L, &g);
+    if (st) return st;
+    if (n_stripes == 0) return RCG_OK;
+    if (n_stripes > 0xffffffffull) return RCG_EINVAL;
+    Plan pl;
+    if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
+    Job J = base_job(L, g, first_stripe, n_stripes, pl);
+    J.op = OP_RECOVER;
+    J.pairs = pairs;
+    DeviceGuard guard(ctx->device);
+    return launch_single(ctx, J, pl, static_cast<cudaStream_t>(stream));
+}
+
+rcg_status rcg_update(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32_t i,
+                      const void *new_strip, uint64_t new_row_stride, void *stream) {
+    Geo g;
+    if (!ctx || !new_strip || !aligned16(new_strip)) return RCG_EINVAL;
+    rcg_status st = check_layout(L, &g);
+    if (st) return st;
+    if (i >= g.N) return RCG_EINVAL;
+    const uint64_t ars = new_row_stride ? new_row_stride : g.C;
+    if (ars < g.C || (ars & 15)) return RCG_EINVAL;
+    Plan pl;
+    if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
+    Job J = base_job(L, g, stripe, 1, pl);
+    J.op = OP_UPDATE;
+    J.i = static_cast<uint8_t>(i);
+    J.aux = static_cast<uint8_t *>(const_cast<void *>(new_strip));
+    J.aux_row_stride = ars;
+    J.aux_stripe_stride = (g.p - 1) * ars;
+    DeviceGuard guard(ctx->device);
+    return launch_single(ctx, J, pl, static_cast<cudaStream_t>(stream));
+}
+
+rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32_t j,
+                             void *out, uint64_t out_row_stride, void *stream) {
+    Geo g;
+    if (!ctx || !out || !aligned16(out)) return RCG_EINVAL;
+    rcg_status st = check_layout(L, &g);
+    if (st) return st;
+    if (j > g.N + 1) return RCG_EINVAL;
+    const uint64_t ors = out_row_stride ? out_row_stride : g.C;
+    if (ors < g.C || (ors & 15)) return RCG_EINVAL;
+    Plan pl;
+    if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
+    Job J = base_job(L, g, stripe, 1, pl);
+    J.op = OP_DEGRADED;
+    J.j = static_cast<uint8_t>(j);
+    J.aux = static_cast<uint8_t *>(out);
+    J.aux_row_stride = ors;
+    J.aux_stripe_stride = (g.p - 1) * ors;
+    DeviceGuard guard(ctx->device);
+    return launch_single(ctx, J, pl, static_cast<cudaStream_t>(stream));
+}
+
+// ================================================================= batches
+
+static rcg_status build_job(const rcg_job &in, Job *out, Plan *pl) {
+    Geo g;
+    rcg_status st = check_layout(&in.layout, &g);
+    if (st) return st;
+    if (in.n_stripes == 0 || in.n_stripes > 0xffffffffull) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, pl)) return RCG_EINVAL;
+    Job J = base_job(&in.layout, g, in.first_stripe, in.n_stripes, *pl);
+    const uint64_t ars = in.aux_row_stride ? in.aux_row_stride : g.C;
+    const uint64_t ass = in.aux_stripe_stride ? in.aux_stripe_stride : (g.p - 1) * ars;
+    switch (in.op) {
+        case RCG_OP_ENCODE:
+            J.op = OP_ENCODE;
+            break;
+        case RCG_OP_RECOVER:
+            if (!(in.i < in.j && in.j <= g.N + 1)) return RCG_EINVAL;
+            J.op = OP_RECOVER;
+            J.i = static_cast<uint8_t>(in.i);
+            J.j = static_cast<uint8_t>(in.j);
+            break;
+        case RCG_OP_DEGRADED_READ:
+        case RCG_OP_UPDATE:
+            if (in.op == RCG_OP_DEGRADED_READ ? in.j > g.N + 1 : in.i >= g.N) return RCG_EINVAL;
+            if (!in.aux || !aligned16(in.aux) || ars < g.C || (ars & 15) || (ass & 15)) return RCG_EINVAL;
+            J.op = in.op == RCG_OP_UPDATE ? OP_UPDATE : OP_DEGRADED;
+            J.i = static_cast<uint8_t>(in.i);
+            J.j = static_cast<uint8_t>(in.j);
+            J.aux = static_cast<uint8_t *>(const_cast<void *>(in.aux));
+            J.aux_row_stride = ars;
+            J.aux_stripe_stride = ass;
+            break;
+        default:
+            return RCG_EINVAL;
+    }
+    *out = J;
+    return RCG_OK;
+}
+
+// (Re)allocate a batch slot for `jobs` descriptors and capture its graph:
+// descriptor-table copy -> tile-counter reset -> persistent kernel.
+static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t jobs) {
+    if (s.cap_jobs >= jobs && s.exec) return RCG_OK;
+    free_slot(s);
+    const size_t cap = std::max<size_t>(jobs, 256);
+    const size_t bytes = sizeof(BatchHeader) + cap * sizeof(Job);
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&s.host), bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s.dev), bytes);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s.counter), sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        free_slot(s);
+        return from_cuda(e);
+    }
+    memset(s.host, 0, bytes);
+    s.cap_jobs = cap;
+    s.bytes = bytes;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(s.capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemcpyAsync(s.dev, s.host, bytes, cudaMemcpyHostToDevice, s.capture);
+        cudaMemsetAsync(s.counter, 0, sizeof(unsigned long long), s.capture);
+        launch_batch(s.dev, ctx->status, s.counter, ctx->timeout_ns, ctx->sm_count, s.capture);
+        e = cudaStreamEndCapture(s.capture, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s.exec, graph, 0);
+    if (e == cudaSuccess) {
+        size_t n = 0;
+        cudaGraphGetNodes(graph, nullptr, &n);
+        std::vector<cudaGraphNode_t> nodes(n);
+        cudaGraphGetNodes(graph, nodes.data(), &n);
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeMemcpy) s.copy_node = nd;
+        }
+        if (!s.copy_node) e = cudaErrorUnknown;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        free_slot(s);
+        return from_cuda(e);
+    }
+    return RCG_OK;
+}
+
+rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, void *stream,
+                            uint64_t *ticket) {
+    if (!ctx || !ticket || (n_jobs && !jobs)) return RCG_EINVAL;
+    *ticket = 0;
+    if (n_jobs == 0) return RCG_OK;
+    std::vector<Job> table(n_jobs);
+    uint64_t total = 0;
+    uint32_t slot_bytes = 0;
+    for (uint32_t k = 0; k < n_jobs; ++k) {
+        Plan pl;
+        rcg_status st = build_job(jobs[k], &table[k], &pl);
+        if (st) return st;
+        table[k].tile_begin = total;
+        total += static_cast<uint64_t>(table[k].n_stripes) * table[k].tiles_per_stripe;
+        slot_bytes = std::max(slot_bytes, pl.slot_bytes);
+    }
+    BatchHeader hdr;
+    memset(&hdr, 0, sizeof(hdr));
+    hdr.total_tiles = total;
+    hdr.n_jobs = n_jobs;
+    hdr.slot_bytes = slot_bytes;
+    hdr.n_slots = std::min<uint32_t>(kMaxSlots, kRingBytes / slot_bytes);
+
+    DeviceGuard guard(ctx->device);
+    const uint64_t tk = ctx->next_ticket;
+    BatchSlot &s = ctx->slots[tk % kBatchRing];
+    if (s.used && s.done) {
+        rcg_status st = wait_event(s.done, ctx->timeout_ns);
+        if (st == RCG_ETIMEOUT) return RCG_EBUSY;
+        if (st) return st;
+    }
+    rcg_status st = prepare_slot(ctx, s, n_jobs);
+    if (st) return st;
+    const size_t bytes = sizeof(BatchHeader) + static_cast<size_t>(n_jobs) * sizeof(Job);
+    memcpy(s.host, &hdr, sizeof(hdr));
+    memcpy(s.host + sizeof(hdr), table.data(), static_cast<size_t>(n_jobs) * sizeof(Job));
+    cudaError_t e = cudaSuccess;
+    if (bytes != s.bytes) {
+        e = cudaGraphExecMemcpyNodeSetParams1D(s.exec, s.copy_node, s.dev, s.host, bytes,
+                                               cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) s.bytes = bytes;
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(s.exec, static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) e = cudaEventRecord(s.done, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return from_cuda(e);
+    s.used = true;
+    s.ticket = tk;
+    ctx->next_ticket = tk + 1;
+    *ticket = tk;
+    return RCG_OK;
+}
+
+rcg_status rcg_batch_wait(rcg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns) {
+    if (!ctx || ticket == 0 || ticket >= ctx->next_ticket) return RCG_EINVAL;
+    DeviceGuard guard(ctx->device);
+    BatchSlot &s = ctx->slots[ticket % kBatchRing];
+    if (!s.used || s.ticket != ticket) return RCG_OK;  // slot reused: that batch finished
+    return wait_event(s.done, timeout_ns);
+}
+
+// =============================================================== utilities
+
+rcg_status rcg_fill_random(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte_offset,
+                           void *stream) {
+    if ((!dev && nbytes) || !aligned16(dev) || (byte_offset & 7))
+        return RCG_EINVAL;
+    return from_cuda(launch_fill(dev, nbytes, seed, byte_offset, static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,721 @@
+// rcg_engine.cu -- the tile engine: one persistent, warp-specialised kernel
+// that runs every stripe operation of the cyclic-group RAID-6 code
+// (Corollary 3.2.4 encode; Lemma 3.1.2 recovery classes; the degraded read and
+// the small write) on GB300 (sm_103a).
+//
+// Data path.  A work unit is a tile: W bytes of columns of one stripe (all
+// p-1 rows of every strip it needs).  The producer warp streams the tile's
+// strips, one strip per shared-memory ring slot, with 1-D bulk asynchronous
+// copies (cp.async.bulk global->shared, one per row, completion counted on an
+// mbarrier).  Consumer warps XOR each slot into register accumulators:
+//   accP[r]            ^= strip[r]                      (P, first equation of (znparity))
+//   accQ[(r + k) mod p] ^= strip_k[r]                   (x^k d_k in F2[x]/(x^p - 1))
+// A consumer owns fixed accumulator rows, so x^k is a read of the slot at the
+// row rotated by k: an index remap, no data movement.  Row p-1 of the lift is
+// the imaginary row; reducing modulo f = 1 + ... + x^(p-1) XORs it into every
+// other row (the "conditional all-ones fold" of Lemma 3.4.1's (powers); the
+// EVENODD adjuster).  The epilogue of each tile exchanges rows through shared
+// memory and writes the results straight to global memory.
+//
+// Two-data recovery (Sections 4.3, 4.6): with z = j - i,
+//   T   = dP + x^(-i) dQ,     D_j = (1 + x^z)^(-1) T,     D_i = D_j + dP,
+// where (1 + x^z)^(-1) = sum_{t=0}^{(p-1)/2} x^(2tz) is read from a per-p
+// table precomputed on the host and kept in constant memory.
+//
+// Every wait is bounded (mbarrier try_wait against %globaltimer); an expired
+// wait sets RCG_DEV_TIMEOUT in the status word and the thread returns after
+// the copies it issued have landed.  No trap, no unbounded spin.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rcg.h"
+#include "rcg_internal.h"
+
+namespace rcg {
+
+__constant__ uint64_t c_inv[kMaxP + 1][kMaxP + 1];
+
+namespace {
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `bar` with the given parity to complete, for at most
+// timeout_ns.  try_wait itself suspends for a hardware-chosen interval, so
+// the loop does not spin hot.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t timeout_ns) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(bar, parity)) {
+        if (global_ns() - t0 > timeout_ns) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// 1-D bulk copy global -> shared; completion (bytes) counted on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
+    return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
+}
+
+__device__ __forceinline__ uint4 lds(const uint8_t *p) {
+    return *reinterpret_cast<const uint4 *>(p);
+}
+
+__device__ __forceinline__ void sts(uint8_t *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
+
+__device__ __forceinline__ void stg(uint8_t *p, uint4 v) {
+    asm volatile("st.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+// --------------------------------------------------------- slot protocol
+
+enum : uint8_t {
+    F_P = 1,      // XOR the slot into the P accumulators
+    F_Q = 2,      // XOR the slot, rotated by `rot`, into the lifted Q accumulators
+    F_COPY = 4,   // also store the slot to the job's data strip i (small write)
+    F_FIRST = 8,  // first slot of a tile
+    F_LAST = 16,  // last slot of a tile: run the epilogue after it
+    F_END = 128   // no more tiles for this CTA
+};
+
+// Epilogue classes.
+enum : uint8_t {
+    E_ENC = 0,   // write P = accP, Q = fold(accQ)  (encode, P+Q recovery, small write)
+    E_DD = 1,    // two data strips (Section 4.6)
+    E_DP = 2,    // data strip i and P
+    E_DQ = 3,    // data strip i and Q
+    E_DEGP = 4,  // degraded read of a data strip or P: out = accP
+    E_DEGQ = 5   // degraded read of Q: out = fold(accQ)
+};
+
+struct SlotHdr {
+    uint32_t job;
+    uint32_t stripe;
+    uint32_t c0;    // first column byte of the tile
+    uint16_t w;     // tile width, bytes
+    uint8_t flags;
+    uint8_t rot;    // x^rot for F_Q
+    uint8_t cls;    // epilogue class
+    uint8_t a, b;   // the erased pair (a < b), or i / j of the op
+    uint8_t p;
+    uint8_t pad[12];
+};
+static_assert(sizeof(SlotHdr) == 32, "slot header is 32 bytes");
+
+struct Smem {
+    uint64_t *full;   // [kMaxSlots] producer -> consumers (tx-counted)
+    uint64_t *empty;  // [kMaxSlots] consumers -> producer
+    uint64_t *ep;     // epilogue barrier among consumer warps
+    SlotHdr *hdr;     // [kMaxSlots]
+    uint8_t *xp;      // exchange buffer [p][nvec] x 16 B
+    uint8_t *xq;      // exchange buffer [p][nvec] x 16 B
+    uint8_t *fold;    // one row [nvec] x 16 B
+    uint8_t *ring;    // n_slots x slot_bytes
+};
+
+__device__ __forceinline__ Smem carve(uint8_t *smem) {
+    Smem s;
+    s.full = reinterpret_cast<uint64_t *>(smem);
+    s.empty = s.full + kMaxSlots;
+    s.ep = s.empty + kMaxSlots;
+    s.hdr = reinterpret_cast<SlotHdr *>(smem + 1024);
+    s.xp = smem + kCtlBytes;
+    s.xq = s.xp + kXBytes;
+    s.fold = s.xq + kXBytes;
+    s.ring = s.fold + kFoldBytes;
+    return s;
+}
+
+__device__ __forceinline__ void set_status(uint32_t *status, uint32_t bits) {
+    if (status) atomicOr(status, bits);
+}
+
+// Role of strip k (0..N-1 data, N = P, N+1 = Q, N+2 = the small write's new
+// strip) in a tile of class `cls` with pair (a, b): returns flags (0 = not
+// read) and the rotation for Q.
+__device__ __forceinline__ uint8_t strip_role(uint8_t cls, bool update, uint32_t k, uint32_t N,
+                                              uint32_t a, uint32_t b, uint32_t *rot) {
+    *rot = 0;
+    const bool data = k < N;
+    if (update) {  // old d_a, P, Q, new d_a (last, so d_a is read before it is overwritten)
+        if (k == a) { *rot = a; return F_P | F_Q; }
+        if (k == N) return F_P;
+        if (k == N + 1) return F_Q;
+        if (k == N + 2) { *rot = a; return F_P | F_Q | F_COPY; }
+        return 0;
+    }
+    switch (cls) {
+        case E_ENC:
+            if (data) { *rot = k; return F_P | F_Q; }
+            return 0;
+        case E_DD:
+            if (data && k != a && k != b) { *rot = k; return F_P | F_Q; }
+            if (k == N) return F_P;
+            if (k == N + 1) return F_Q;
+            return 0;
+        case E_DP:
+            if (data && k != a) { *rot = k; return F_P | F_Q; }
+            if (k == N + 1) return F_Q;
+            return 0;
+        case E_DQ:
+            if (data && k != a) { *rot = k; return F_P | F_Q; }
+            if (k == N) return F_P;
+            return 0;
+        case E_DEGP:  // strip b (data or P) from the first equation
+            if (k <= N && k != b) return F_P;
+            return 0;
+        case E_DEGQ:
+            if (data) { *rot = k; return F_Q; }
+            return 0;
+    }
+    return 0;
+}
+
+__device__ __forceinline__ const Job &job_ref(const LaunchParams &prm, uint32_t idx) {
+    return prm.jobs ? prm.jobs[idx] : prm.job0;
+}
+
+// ---------------------------------------------------------------- producer
+
+__device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_jobs,
+                         uint64_t total_tiles, uint32_t slot_bytes, uint32_t n_slots) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t policy = l2_evict_first();
+    uint32_t it = 0;  // slots issued
+    bool ok = true;
+    uint64_t next_static = blockIdx.x;
+
+    for (;;) {
+        uint64_t t;
+        if (prm.dynamic_sched) {
+            unsigned long long v = 0;
+            if (lane == 0) v = atomicAdd(prm.tile_counter, 1ull);
+            t = __shfl_sync(0xffffffffu, v, 0);
+        } else {
+            t = next_static;
+            next_static += gridDim.x;
+        }
+        if (t >= total_tiles) break;
+
+        // job of this tile: last job with tile_begin <= t
+        uint32_t ji = 0;
+        if (prm.jobs && n_jobs > 1) {
+            uint32_t lo = 0, hi = n_jobs - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (prm.jobs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+            }
+            ji = lo;
+        }
+        const Job &J = job_ref(prm, ji);
+        const uint32_t p = J.p, N = J.n, rows = p - 1;
+        const uint64_t local = t - J.tile_begin;
+        const uint32_t stripe = static_cast<uint32_t>(local / J.tiles_per_stripe);
+        const uint32_t c0 = static_cast<uint32_t>(local % J.tiles_per_stripe) * J.W;
+        const uint32_t w = min(J.W, J.C - c0);
+        // device-side guard: a tile must fit its slot and the item budget
+        if (p < 3 || p > kMaxP || N < 1 || N > p || (w & 15) || w == 0 ||
+            rows * w > slot_bytes || p * (w >> 4) > static_cast<uint32_t>(kMaxItems) ||
+            stripe >= J.n_stripes) {
+            if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
+            continue;
+        }
+
+        uint8_t cls = E_ENC;
+        uint32_t a = J.i, b = J.j;
+        const bool update = J.op == OP_UPDATE;
+        if (J.op == OP_RECOVER) {
+            if (J.pairs) {
+                a = J.pairs[2ull * stripe];
+                b = J.pairs[2ull * stripe + 1];
+            }
+            if (!(a < b && b <= N + 1)) {
+                if (lane == 0) set_status(prm.status, RCG_DEV_BADPAIR);
+                continue;
+            }
+            cls = (b < N) ? E_DD : (a == N) ? E_ENC : (b == N) ? E_DP : E_DQ;
+        } else if (J.op == OP_DEGRADED) {
+            cls = (b == N + 1) ? E_DEGQ : E_DEGP;
+        } else if (update) {
+            if (a >= N) {
+                if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
+                continue;
+            }
+        }
+
+        uint32_t count = 0, rot;
+        for (uint32_t k = 0; k < N + 3; ++k)
+            if (strip_role(cls, update, k, N, a, b, &rot)) ++count;
+
+        const uint8_t *stripe_base = J.base + stripe * J.stripe_stride + c0;
+        uint32_t emitted = 0;
+        for (uint32_t k = 0; k < N + 3 && ok; ++k) {
+            const uint8_t fl = strip_role(cls, update, k, N, a, b, &rot);
+            if (!fl) continue;
+            const uint32_t slot = it % n_slots;
+            const uint32_t ph = (it / n_slots) & 1u;
+            if (!mbar_wait(smem_addr(&sm.empty[slot]), ph ^ 1u, prm.timeout_ns)) {
+                ok = false;
+                break;
+            }
+            const uint32_t full = smem_addr(&sm.full[slot]);
+            if (lane == 0) {
+                SlotHdr h;
+                h.job = ji;
+                h.stripe = stripe;
+                h.c0 = c0;
+                h.w = static_cast<uint16_t>(w);
+                h.flags = fl | (emitted == 0 ? F_FIRST : 0) | (emitted + 1 == count ? F_LAST : 0);
+                h.rot = static_cast<uint8_t>(rot);
+                h.cls = cls;
+                h.a = static_cast<uint8_t>(a);
+                h.b = static_cast<uint8_t>(b);
+                h.p = static_cast<uint8_t>(p);
+                sm.hdr[slot] = h;
+                mbar_arrive_tx(full, rows * w);
+            }
+            __syncwarp();
+            const uint8_t *src;
+            uint64_t rs;
+            if (k == N + 2) {
+                src = J.aux + stripe * J.aux_stripe_stride + c0;
+                rs = J.aux_row_stride;
+            } else {
+                src = stripe_base + k * J.strip_stride;
+                rs = J.row_stride;
+            }
+            const uint32_t dst = smem_addr(sm.ring + static_cast<size_t>(slot) * slot_bytes);
+            for (uint32_t r = lane; r < rows; r += 32) bulk_load(dst + r * w, src + r * rs, w, full, policy);
+            ++it;
+            ++emitted;
+        }
+        if (!ok) break;
+    }
+
+    if (ok) {  // end marker
+        const uint32_t slot = it % n_slots;
+        const uint32_t ph = (it / n_slots) & 1u;
+        if (mbar_wait(smem_addr(&sm.empty[slot]), ph ^ 1u, prm.timeout_ns)) {
+            if (lane == 0) {
+                SlotHdr h = {};
+                h.flags = F_END;
+                sm.hdr[slot] = h;
+                mbar_arrive(smem_addr(&sm.full[slot]));
+            }
+            ++it;
+        } else {
+            ok = false;
+        }
+    }
+    if (!ok && lane == 0) set_status(prm.status, RCG_DEV_TIMEOUT);
+    // Do not leave while a bulk copy may still be writing this CTA's shared
+    // memory: wait (bounded) for the last use of every slot to complete.
+    const uint32_t first = it > n_slots ? it - n_slots : 0;
+    for (uint32_t s = first; s < it; ++s)
+        if (!mbar_wait(smem_addr(&sm.full[s % n_slots]), (s / n_slots) & 1u, prm.timeout_ns)) {
+            if (lane == 0) set_status(prm.status, RCG_DEV_TIMEOUT);
+            break;
+        }
+}
+
+// ---------------------------------------------------------------- consumers
+
+struct Tile {
+    uint8_t *base;      // stripe base + c0
+    uint8_t *out;       // degraded read output + c0 (stripe applied)
+    uint64_t strip_stride, row_stride, out_row_stride;
+    uint32_t p, nvec, w;
+    uint8_t cls, a, b;
+};
+
+// Epilogue barrier among the consumer warps (bounded).
+__device__ __forceinline__ bool ep_sync(const Smem &sm, uint32_t &phase, uint64_t timeout_ns) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(sm.ep));
+    const bool ok = mbar_wait(smem_addr(sm.ep), phase, timeout_ns);
+    phase ^= 1u;
+    return ok;
+}
+
+__device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kItems],
+                         uint4 (&accQ)[kItems], const int (&row)[kItems],
+                         const int (&col)[kItems], uint32_t &ep_phase, uint64_t timeout_ns) {
+    const int p = static_cast<int>(T.p);
+    const uint32_t nv = T.nvec;
+    auto X = [&](uint8_t *buf, int r, int c) { return buf + (static_cast<size_t>(r) * nv + c) * 16; };
+    auto strip_row = [&](uint32_t k, int r, int c) {
+        return T.base + k * T.strip_stride + static_cast<uint64_t>(r) * T.row_stride + c * 16;
+    };
+    // previous tile's readers of the exchange buffers are done
+    if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+
+    switch (T.cls) {
+        case E_ENC:
+        case E_DEGQ: {
+            for (int t = 0; t < kItems; ++t)
+                if (row[t] == p - 1) sts(sm.fold + col[t] * 16, accQ[t]);
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            for (int t = 0; t < kItems; ++t) {
+                if (row[t] >= p - 1) continue;
+                const uint4 q = xor4(accQ[t], lds(sm.fold + col[t] * 16));
+                if (T.cls == E_ENC) {
+                    stg(strip_row(T.b, row[t], col[t]), accP[t]);      // P = strip N
+                    stg(strip_row(T.b + 1, row[t], col[t]), q);        // Q = strip N+1
+                } else {
+                    stg(T.out + static_cast<uint64_t>(row[t]) * T.out_row_stride + col[t] * 16, q);
+                }
+            }
+            break;
+        }
+        case E_DEGP: {
+            for (int t = 0; t < kItems; ++t)
+                if (row[t] < p - 1)
+                    stg(T.out + static_cast<uint64_t>(row[t]) * T.out_row_stride + col[t] * 16, accP[t]);
+            break;
+        }
+        case E_DP: {  // D_a = x^(-a) dQ (reduced), P = accP + D_a
+            for (int t = 0; t < kItems; ++t)
+                if (row[t] < p) sts(X(sm.xq, row[t], col[t]), accQ[t]);
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            const int a = T.a;
+            for (int t = 0; t < kItems; ++t) {
+                if (row[t] >= p - 1) continue;
+                int s = row[t] + a;
+                if (s >= p) s -= p;
+                int f = p - 1 + a;
+                if (f >= p) f -= p;
+                const uint4 d = xor4(lds(X(sm.xq, s, col[t])), lds(X(sm.xq, f, col[t])));
+                stg(strip_row(T.a, row[t], col[t]), d);
+                stg(strip_row(T.b, row[t], col[t]), xor4(accP[t], d));
+            }
+            break;
+        }
+        case E_DQ: {  // D_a = accP; Q = fold(accQ + x^a D_a)
+            const uint4 zero = make_uint4(0, 0, 0, 0);
+            for (int t = 0; t < kItems; ++t)
+                if (row[t] < p) sts(X(sm.xp, row[t], col[t]), row[t] < p - 1 ? accP[t] : zero);
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            const int a = T.a;
+            for (int t = 0; t < kItems; ++t) {
+                if (row[t] >= p) continue;
+                int s = row[t] - a;
+                if (s < 0) s += p;
+                accQ[t] = xor4(accQ[t], lds(X(sm.xp, s, col[t])));
+                if (row[t] == p - 1) sts(sm.fold + col[t] * 16, accQ[t]);
+            }
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            for (int t = 0; t < kItems; ++t) {
+                if (row[t] >= p - 1) continue;
+                stg(strip_row(T.a, row[t], col[t]), accP[t]);
+                stg(strip_row(T.b, row[t], col[t]), xor4(accQ[t], lds(sm.fold + col[t] * 16)));
+            }
+            break;
+        }
+        case E_DD: {
+            const uint4 zero = make_uint4(0, 0, 0, 0);
+            for (int t = 0; t < kItems; ++t) {
+                if (row[t] >= p) continue;
+                sts(X(sm.xp, row[t], col[t]), row[t] < p - 1 ? accP[t] : zero);
+                sts(X(sm.xq, row[t], col[t]), accQ[t]);
+            }
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            const int a = T.a;
+            // T = dP + x^(-a) dQ, written over xp (each thread touches only its own rows)
+            for (int t = 0; t < kItems; ++t) {
+                if (row[t] >= p) continue;
+                int s = row[t] + a;
+                if (s >= p) s -= p;
+                sts(X(sm.xp, row[t], col[t]), xor4(lds(X(sm.xp, row[t], col[t])), lds(X(sm.xq, s, col[t]))));
+            }
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            // D_b (lifted) = (1 + x^z)^(-1) T: sum of x^m T over the table's exponent set
+            const uint64_t mask = c_inv[p][T.b - T.a];
+            for (int t = 0; t < kItems; ++t) {
+                if (row[t] >= p) continue;
+                uint4 d = zero;
+                uint64_t m = mask;
+                while (m) {
+                    const int e = __ffsll(static_cast<long long>(m)) - 1;
+                    m &= m - 1;
+                    int s = row[t] - e;
+                    if (s < 0) s += p;
+                    d = xor4(d, lds(X(sm.xp, s, col[t])));
+                }
+                accQ[t] = d;
+                if (row[t] == p - 1) sts(sm.fold + col[t] * 16, d);
+            }
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            for (int t = 0; t < kItems; ++t) {
+                if (row[t] >= p - 1) continue;
+                const uint4 dj = xor4(accQ[t], lds(sm.fold + col[t] * 16));
+                stg(strip_row(T.b, row[t], col[t]), dj);
+                stg(strip_row(T.a, row[t], col[t]), xor4(dj, accP[t]));
+            }
+            break;
+        }
+    }
+    return true;
+}
+
+__device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_bytes,
+                         uint32_t n_slots) {
+    const int ctid = static_cast<int>(threadIdx.x) - 32;
+    const uint32_t lane = threadIdx.x & 31;
+    uint4 accP[kItems], accQ[kItems];
+    int row[kItems], col[kItems];
+    Tile T = {};
+    uint8_t *copy_dst = nullptr;  // small write: data strip a of the tile
+    uint32_t ep_phase = 0;
+    uint32_t it = 0;
+
+    for (;;) {
+        const uint32_t slot = it % n_slots;
+        const uint32_t ph = (it / n_slots) & 1u;
+        if (!mbar_wait(smem_addr(&sm.full[slot]), ph, prm.timeout_ns)) {
+            if (lane == 0) set_status(prm.status, RCG_DEV_TIMEOUT);
+            return;
+        }
+        const SlotHdr h = sm.hdr[slot];
+        if (h.flags & F_END) break;
+        if (h.flags & F_FIRST) {
+            const Job &J = job_ref(prm, h.job);
+            T.p = h.p;
+            T.w = h.w;
+            T.nvec = h.w >> 4;
+            T.cls = h.cls;
+            T.a = h.a;
+            T.b = h.b;
+            T.strip_stride = J.strip_stride;
+            T.row_stride = J.row_stride;
+            T.base = J.base + h.stripe * J.stripe_stride + h.c0;
+            T.out = J.aux + h.stripe * J.aux_stripe_stride + h.c0;
+            T.out_row_stride = J.aux_row_stride;
+            copy_dst = T.base + static_cast<uint64_t>(h.a) * J.strip_stride;
+            if (T.cls == E_ENC) {  // P and Q are strips N and N+1: pass N through b
+                T.b = J.n;
+            }
+            for (int t = 0; t < kItems; ++t) {
+                const int item = ctid + t * kConsumers;
+                const int r = item / static_cast<int>(T.nvec);
+                row[t] = r < static_cast<int>(T.p) ? r : 0x7fff;
+                col[t] = item - r * static_cast<int>(T.nvec);
+                accP[t] = make_uint4(0, 0, 0, 0);
+                accQ[t] = make_uint4(0, 0, 0, 0);
+            }
+        }
+        const uint8_t *stage = sm.ring + static_cast<size_t>(slot) * slot_bytes;
+        const int p = static_cast<int>(T.p);
+        const int rot = h.rot;
+        const uint32_t w = T.w;
+#pragma unroll
+        for (int t = 0; t < kItems; ++t) {
+            const int r = row[t];
+            if (r >= p) continue;
+            if ((h.flags & F_P) && r < p - 1) {
+                const uint4 v = lds(stage + r * w + col[t] * 16);
+                accP[t] = xor4(accP[t], v);
+                if (h.flags & F_COPY)
+                    stg(copy_dst + static_cast<uint64_t>(r) * T.row_stride + col[t] * 16, v);
+            }
+            if (h.flags & F_Q) {
+                int s = r - rot;
+                if (s < 0) s += p;
+                if (s < p - 1) accQ[t] = xor4(accQ[t], lds(stage + s * w + col[t] * 16));
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&sm.empty[slot]));
+        ++it;
+        if (h.flags & F_LAST) {
+            if (!epilogue(sm, T, accP, accQ, row, col, ep_phase, prm.timeout_ns)) {
+                if (lane == 0) set_status(prm.status, RCG_DEV_TIMEOUT);
+                return;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ kernel
+
+__global__ void __launch_bounds__(kThreads, 1)
+    rcg_tile_engine(const __grid_constant__ LaunchParams prm, const BatchHeader *bh) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const Smem sm = carve(smem_raw);
+
+    uint32_t n_jobs = prm.n_jobs, slot_bytes = prm.slot_bytes, n_slots = prm.n_slots;
+    uint64_t total = prm.total_tiles;
+    if (bh) {
+        n_jobs = bh->n_jobs;
+        slot_bytes = bh->slot_bytes;
+        n_slots = bh->n_slots;
+        total = bh->total_tiles;
+    }
+    if (n_slots == 0 || n_slots > kMaxSlots || slot_bytes == 0 ||
+        static_cast<uint64_t>(n_slots) * slot_bytes > kRingBytes || (slot_bytes & 127)) {
+        if (threadIdx.x == 0) set_status(prm.status, RCG_DEV_BADJOB);
+        return;
+    }
+
+    if (threadIdx.x == 0) {
+        for (uint32_t s = 0; s < n_slots; ++s) {
+            mbar_init(smem_addr(&sm.full[s]), 1);
+            mbar_init(smem_addr(&sm.empty[s]), kConsumerWarps);
+        }
+        mbar_init(smem_addr(sm.ep), kConsumerWarps);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (threadIdx.x < 32)
+        producer(prm, sm, n_jobs, total, slot_bytes, n_slots);
+    else
+        consumer(prm, sm, slot_bytes, n_slots);
+}
+
+// ------------------------------------------------------ test-data generator
+
+__device__ __forceinline__ uint64_t splitmix_word(uint64_t seed, uint64_t w) {
+    uint64_t z = (seed << 40) + (w + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void rcg_fill_kernel(uint8_t *dst, uint64_t nbytes, uint64_t seed, uint64_t word0) {
+    const uint64_t n_pairs = (nbytes + 15) / 16;
+    for (uint64_t q = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; q < n_pairs;
+         q += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t w0 = splitmix_word(seed, word0 + 2 * q);
+        const uint64_t w1 = splitmix_word(seed, word0 + 2 * q + 1);
+        const uint64_t off = 16 * q;
+        if (off + 16 <= nbytes) {
+            uint4 v = make_uint4(static_cast<uint32_t>(w0), static_cast<uint32_t>(w0 >> 32),
+                                 static_cast<uint32_t>(w1), static_cast<uint32_t>(w1 >> 32));
+            *reinterpret_cast<uint4 *>(dst + off) = v;
+        } else {
+            for (uint64_t b = off; b < nbytes; ++b) {
+                const uint64_t w = (b - off) < 8 ? w0 : w1;
+                dst[b] = static_cast<uint8_t>(w >> (8 * ((b - off) & 7)));
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+void inverse_masks(uint32_t p, uint64_t *masks) {
+    // Section 4.6: (1 + x^z)^(-1) = sum_{t=0}^{(p-1)/2} x^(2tz), exponents mod p.
+    masks[0] = 0;
+    for (uint32_t z = 1; z < p; ++z) {
+        uint64_t m = 0;
+        for (uint32_t t = 0; t <= (p - 1) / 2; ++t) m |= 1ull << ((2ull * t * z) % p);
+        masks[z] = m;
+    }
+}
+
+static bool is_odd_prime(uint32_t p) {
+    if (p < 3 || (p & 1) == 0) return false;
+    for (uint32_t d = 3; d * d <= p; d += 2)
+        if (p % d == 0) return false;
+    return true;
+}
+
+cudaError_t upload_inverse_tables() {
+    static uint64_t table[kMaxP + 1][kMaxP + 1];
+    for (uint32_t p = 0; p <= static_cast<uint32_t>(kMaxP); ++p) {
+        for (uint32_t z = 0; z <= static_cast<uint32_t>(kMaxP); ++z) table[p][z] = 0;
+        if (is_odd_prime(p)) inverse_masks(p, table[p]);
+    }
+    return cudaMemcpyToSymbol(c_inv, table, sizeof(table));
+}
+
+cudaError_t engine_init_attributes() {
+    return cudaFuncSetAttribute(rcg_tile_engine, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kSmemLimit));
+}
+
+cudaError_t launch_engine(const LaunchParams &prm, int grid, cudaStream_t stream) {
+    const size_t smem = kFixedSmem + static_cast<size_t>(prm.n_slots) * prm.slot_bytes;
+    rcg_tile_engine<<<grid, kThreads, smem, stream>>>(prm, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const uint8_t *table_dev, uint32_t *status, unsigned long long *counter,
+                         uint64_t timeout_ns, int grid, cudaStream_t stream) {
+    LaunchParams prm = {};
+    prm.jobs = reinterpret_cast<const Job *>(table_dev + sizeof(BatchHeader));
+    prm.dynamic_sched = 1;
+    prm.tile_counter = counter;
+    prm.status = status;
+    prm.timeout_ns = timeout_ns;
+    rcg_tile_engine<<<grid, kThreads, kSmemLimit, stream>>>(
+        prm, reinterpret_cast<const BatchHeader *>(table_dev));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte_offset,
+                        cudaStream_t stream) {
+    if (nbytes == 0) return cudaSuccess;
+    const uint64_t pairs = (nbytes + 15) / 16;
+    const int threads = 256;
+    uint64_t blocks = (pairs + threads - 1) / threads;
+    if (blocks > 152ull * 16) blocks = 152ull * 16;
+    rcg_fill_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
+        static_cast<uint8_t *>(dev), nbytes, seed, byte_offset / 8);
+    return cudaGetLastError();
+}
+
+}  // namespace rcg

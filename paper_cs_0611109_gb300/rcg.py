@@ -1,0 +1,263 @@
+"""Python binding of librcg (include/rcg.h): ctypes argument marshalling only.
+
+Every function here has the name and the semantics of the C call it wraps;
+all stripe arithmetic runs in the CUDA kernels of librcg.so.  Device buffers
+are passed as PyTorch CUDA tensors (their data_ptr) or raw integer addresses;
+streams as torch.cuda.Stream, a raw cudaStream_t integer, or None for the
+current PyTorch stream.  There is no CPU fallback: if librcg.so has not been
+built, importing the library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB
+
+RCG_OK, RCG_EINVAL, RCG_ENOMEM, RCG_ECUDA, RCG_ETIMEOUT, RCG_EBUSY, RCG_EUNSUPPORTED, RCG_EDEVICE = range(8)
+RCG_DEV_TIMEOUT, RCG_DEV_BADPAIR, RCG_DEV_BADJOB = 1, 2, 4
+RCG_OP_ENCODE, RCG_OP_RECOVER, RCG_OP_DEGRADED_READ, RCG_OP_UPDATE = range(4)
+
+_u32, _u64, _vp, _int = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+
+
+class RcgError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s: %s (status %d)" % (what, rcg_status_str(status), status))
+        self.status = status
+
+
+class rcg_layout(ctypes.Structure):
+    _fields_ = [("base", _vp), ("p", _u32), ("n_data", _u32), ("row_bytes", _u64),
+                ("row_stride", _u64), ("strip_stride", _u64), ("stripe_stride", _u64)]
+
+
+class rcg_job(ctypes.Structure):
+    _fields_ = [("layout", rcg_layout), ("first_stripe", _u64), ("n_stripes", _u64), ("op", _u32),
+                ("i", _u32), ("j", _u32), ("aux", _vp), ("aux_row_stride", _u64),
+                ("aux_stripe_stride", _u64)]
+
+
+class rcg_plan_info(ctypes.Structure):
+    _fields_ = [("tile_bytes", _u32), ("tiles_per_stripe", _u32), ("slot_bytes", _u32), ("n_slots", _u32)]
+
+
+EXPORTS = {
+    "rcg_create": (_int, [_int, ctypes.POINTER(_vp)]),
+    "rcg_destroy": (_int, [_vp]),
+    "rcg_set_timeout": (_int, [_vp, _u64]),
+    "rcg_last_device_status": (_int, [_vp, ctypes.POINTER(_u32)]),
+    "rcg_status_str": (ctypes.c_char_p, [_int]),
+    "rcg_abi_version": (_u32, []),
+    "rcg_encode": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u64, _vp]),
+    "rcg_recover": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u32, _u32, _vp]),
+    "rcg_recover_many": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u64, _vp, _vp]),
+    "rcg_update": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u32, _vp, _u64, _vp]),
+    "rcg_degraded_read": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u32, _vp, _u64, _vp]),
+    "rcg_batch_submit": (_int, [_vp, ctypes.POINTER(rcg_job), _u32, _vp, ctypes.POINTER(_u64)]),
+    "rcg_batch_wait": (_int, [_vp, _u64, _u64]),
+    "rcg_fill_random": (_int, [_vp, _u64, _u64, _u64, _vp]),
+    "rcg_inverse_table": (_int, [_u32, ctypes.POINTER(_u64)]),
+    "rcg_plan": (_int, [_u32, _u64, ctypes.POINTER(rcg_plan_info)]),
+}
+
+_lib: ctypes.CDLL | None = None
+
+
+def lib(path: str | None = None) -> ctypes.CDLL:
+    """Load librcg.so (built by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = path or LIB
+        if not os.path.exists(path):
+            raise ImportError("librcg.so is not built (%s); run paper_cs_0611109_gb300.build.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != RCG_OK:
+        raise RcgError(st, what)
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def make_layout(base, p: int, n_data: int, row_bytes: int, row_stride: int = 0,
+                strip_stride: int = 0, stripe_stride: int = 0) -> rcg_layout:
+    """Describe stripes at device address `base` (tensor or int); zero strides = packed."""
+    return rcg_layout(_ptr(base), p, n_data, row_bytes, row_stride, strip_stride, stripe_stride)
+
+
+# ------------------------------------------------------------- the C calls
+
+def rcg_status_str(st: int) -> str:
+    try:
+        return lib().rcg_status_str(st).decode()
+    except ImportError:
+        return "status %d" % st
+
+
+def rcg_abi_version() -> int:
+    return int(lib().rcg_abi_version())
+
+
+def rcg_create(device: int = 0) -> int:
+    h = _vp()
+    _check(lib().rcg_create(device, ctypes.byref(h)), "rcg_create")
+    return h.value
+
+
+def rcg_destroy(ctx: int):
+    _check(lib().rcg_destroy(ctx), "rcg_destroy")
+
+
+def rcg_set_timeout(ctx: int, timeout_ns: int):
+    _check(lib().rcg_set_timeout(ctx, timeout_ns), "rcg_set_timeout")
+
+
+def rcg_last_device_status(ctx: int) -> int:
+    """Synchronise, return and clear the device status word (RCG_DEV_* bits)."""
+    code = _u32(0)
+    st = lib().rcg_last_device_status(ctx, ctypes.byref(code))
+    if st not in (RCG_OK, RCG_EDEVICE):
+        _check(st, "rcg_last_device_status")
+    return int(code.value)
+
+
+def rcg_encode(ctx: int, layout: rcg_layout, first_stripe: int, n_stripes: int, stream=None):
+    _check(lib().rcg_encode(ctx, ctypes.byref(layout), first_stripe, n_stripes, _stream(stream)),
+           "rcg_encode")
+
+
+def rcg_recover(ctx: int, layout: rcg_layout, stripe: int, i: int, j: int, stream=None):
+    _check(lib().rcg_recover(ctx, ctypes.byref(layout), stripe, i, j, _stream(stream)), "rcg_recover")
+
+
+def rcg_recover_many(ctx: int, layout: rcg_layout, first_stripe: int, n_stripes: int, pairs,
+                     stream=None):
+    """pairs: device uint8 tensor [n_stripes, 2] (or address) of per-stripe (i, j)."""
+    _check(lib().rcg_recover_many(ctx, ctypes.byref(layout), first_stripe, n_stripes, _ptr(pairs),
+                                  _stream(stream)), "rcg_recover_many")
+
+
+def rcg_update(ctx: int, layout: rcg_layout, stripe: int, i: int, new_strip, new_row_stride: int = 0,
+               stream=None):
+    _check(lib().rcg_update(ctx, ctypes.byref(layout), stripe, i, _ptr(new_strip), new_row_stride,
+                            _stream(stream)), "rcg_update")
+
+
+def rcg_degraded_read(ctx: int, layout: rcg_layout, stripe: int, j: int, out, out_row_stride: int = 0,
+                      stream=None):
+    _check(lib().rcg_degraded_read(ctx, ctypes.byref(layout), stripe, j, _ptr(out), out_row_stride,
+                                   _stream(stream)), "rcg_degraded_read")
+
+
+def make_job(layout: rcg_layout, first_stripe: int, n_stripes: int, op: int, i: int = 0, j: int = 0,
+             aux=None, aux_row_stride: int = 0, aux_stripe_stride: int = 0) -> rcg_job:
+    return rcg_job(layout, first_stripe, n_stripes, op, i, j, _ptr(aux), aux_row_stride,
+                   aux_stripe_stride)
+
+
+def rcg_batch_submit(ctx: int, jobs, stream=None) -> int:
+    arr = (rcg_job * len(jobs))(*jobs)
+    ticket = _u64(0)
+    _check(lib().rcg_batch_submit(ctx, arr, len(jobs), _stream(stream), ctypes.byref(ticket)),
+           "rcg_batch_submit")
+    return int(ticket.value)
+
+
+def rcg_batch_wait(ctx: int, ticket: int, timeout_ns: int = 10 ** 10) -> bool:
+    """True when the batch finished, False on RCG_ETIMEOUT."""
+    st = lib().rcg_batch_wait(ctx, ticket, timeout_ns)
+    if st == RCG_ETIMEOUT:
+        return False
+    _check(st, "rcg_batch_wait")
+    return True
+
+
+def rcg_fill_random(dev, nbytes: int, seed: int, byte_offset: int = 0, stream=None):
+    _check(lib().rcg_fill_random(_ptr(dev), nbytes, seed, byte_offset, _stream(stream)),
+           "rcg_fill_random")
+
+
+def rcg_inverse_table(p: int) -> list[int]:
+    masks = (_u64 * p)()
+    _check(lib().rcg_inverse_table(p, masks), "rcg_inverse_table")
+    return [int(m) for m in masks]
+
+
+def rcg_plan(p: int, row_bytes: int) -> dict:
+    info = rcg_plan_info()
+    _check(lib().rcg_plan(p, row_bytes, ctypes.byref(info)), "rcg_plan")
+    return {f: int(getattr(info, f)) for f, _ in rcg_plan_info._fields_}
+
+
+class Context:
+    """Owns an rcg_ctx; methods forward to the C calls above."""
+
+    def __init__(self, device: int = 0):
+        self.handle = rcg_create(device)
+
+    def close(self):
+        if self.handle:
+            rcg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def encode(self, layout, first_stripe, n_stripes, stream=None):
+        rcg_encode(self.handle, layout, first_stripe, n_stripes, stream)
+
+    def recover(self, layout, stripe, i, j, stream=None):
+        rcg_recover(self.handle, layout, stripe, i, j, stream)
+
+    def recover_many(self, layout, first_stripe, n_stripes, pairs, stream=None):
+        rcg_recover_many(self.handle, layout, first_stripe, n_stripes, pairs, stream)
+
+    def update(self, layout, stripe, i, new_strip, new_row_stride=0, stream=None):
+        rcg_update(self.handle, layout, stripe, i, new_strip, new_row_stride, stream)
+
+    def degraded_read(self, layout, stripe, j, out, out_row_stride=0, stream=None):
+        rcg_degraded_read(self.handle, layout, stripe, j, out, out_row_stride, stream)
+
+    def batch_submit(self, jobs, stream=None) -> int:
+        return rcg_batch_submit(self.handle, jobs, stream)
+
+    def batch_wait(self, ticket, timeout_ns=10 ** 10) -> bool:
+        return rcg_batch_wait(self.handle, ticket, timeout_ns)
+
+    def set_timeout(self, timeout_ns):
+        rcg_set_timeout(self.handle, timeout_ns)
+
+    def last_device_status(self) -> int:
+        return rcg_last_device_status(self.handle)

@@ -1,0 +1,107 @@
+"""CPU-only checks of librcg: it builds for sm_103a, loads, exports every
+symbol include/rcg.h declares, and its host logic (the per-p inverse table,
+the tiling plan, argument validation) is right.  No kernel is launched."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rcg.h")
+PRIMES = [3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61]
+
+
+@pytest.fixture(scope="module")
+def rcg():
+    from paper_cs_0611109_gb300 import build
+    build.build()
+    from paper_cs_0611109_gb300 import rcg as R
+    return R
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rcg_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(rcg):
+    names = declared_functions()
+    assert "rcg_encode" in names and "rcg_recover" in names and "rcg_update" in names
+    assert "rcg_batch_submit" in names
+    lib = ctypes.CDLL(rcg.LIB)
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding wraps every one of them under the same name
+    for n in names:
+        assert n in rcg.EXPORTS, n
+        assert callable(getattr(rcg, n)), n
+
+
+def test_abi_version_and_status_strings(rcg):
+    assert rcg.rcg_abi_version() == 1
+    for st in range(8):
+        assert rcg.rcg_status_str(st) != "unknown status"
+    assert rcg.rcg_status_str(99) == "unknown status"
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_inverse_table_matches_oracle(rcg, oracle, p):
+    # Section 4.6 closed form, as the library tabulates it, against the
+    # oracle's extended-Euclid inverse of 1 + x^z.
+    masks = rcg.rcg_inverse_table(p)
+    assert masks[0] == 0
+    full = (1 << (p - 1)) - 1
+    for z in range(1, p):
+        m = masks[z]
+        assert m < (1 << p)
+        assert bin(m).count("1") == (p + 1) // 2
+        reduced = m & full
+        if (m >> (p - 1)) & 1:  # x^(p-1) = 1 + x + ... + x^(p-2) mod f
+            reduced ^= full
+        assert reduced == oracle.ring_inv(p, 1 ^ oracle.ring_xpow(p, z)), (p, z)
+
+
+def test_inverse_table_rejects_non_primes(rcg):
+    for p in (1, 2, 9, 15, 63, 67):
+        with pytest.raises(rcg.RcgError):
+            rcg.rcg_inverse_table(p)
+
+
+@pytest.mark.parametrize("p", PRIMES)
+@pytest.mark.parametrize("C", [16, 48, 1024, 1040, 2048, 4096, 65536, 65536 - 16])
+def test_plan_covers_the_row(rcg, p, C):
+    pl = rcg.rcg_plan(p, C)
+    W, T = pl["tile_bytes"], pl["tiles_per_stripe"]
+    assert W % 16 == 0 and W > 0
+    assert (T - 1) * W < C <= T * W          # tiles cover the row, the last one is non-empty
+    assert p * (W // 16) <= 1024              # items per tile fit the consumers
+    assert (p - 1) * W <= pl["slot_bytes"] and pl["slot_bytes"] % 128 == 0
+    assert 2 <= pl["n_slots"] <= 32
+    assert pl["n_slots"] * pl["slot_bytes"] <= 227 * 1024 - (2048 + 2 * 16384 + 8192)
+
+
+def test_plan_rejects_bad_geometry(rcg):
+    for p, C in ((5, 0), (5, 24), (9, 64), (2, 64), (67, 64)):
+        with pytest.raises(rcg.RcgError):
+            rcg.rcg_plan(p, C)
+
+
+def test_null_context_rejected_without_touching_the_gpu(rcg):
+    lib = rcg.lib()
+    L = rcg.make_layout(0x1000, 5, 4, 16)
+    assert lib.rcg_encode(None, ctypes.byref(L), 0, 1, None) == rcg.RCG_EINVAL
+    assert lib.rcg_recover(None, ctypes.byref(L), 0, 0, 1, None) == rcg.RCG_EINVAL
+    assert lib.rcg_destroy(None) == rcg.RCG_EINVAL
+    assert lib.rcg_batch_wait(None, 1, 0) == rcg.RCG_EINVAL
+
+
+def test_create_without_a_gpu_is_an_error_not_a_crash(rcg):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = rcg.lib().rcg_create(0, ctypes.byref(h))
+    assert st in (rcg.RCG_EUNSUPPORTED, rcg.RCG_ECUDA)
+    assert not h.value
