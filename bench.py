@@ -1,0 +1,385 @@
+"""Benchmark: encode + two-erasure recovery throughput of the cyclic-group
+RAID-6 code on GB300, in user-data GB/s, with the HBM roofline of the tile
+engine kernel.
+
+Workload (one step): 8192 stripes of p = 13, N = 12 data strips, rows of
+4 KiB (4.5 GiB of user data, 5.25 GiB moved per operation), seeded random
+bytes generated on the device.  A step runs, each as ONE launch over all
+stripes: encode (P and Q), then recovery of a uniformly drawn erasure pair
+per stripe for each class of Lemma 3.1.2 -- two data strips, data + P,
+data + Q, P + Q.  User bytes per step = 5 x N x (p-1) x C x stripes.  Every
+operation moves (N+2)(p-1)C bytes per stripe; each operation's inputs (5.25
+GiB) are far larger than the 129 MB L2, so no flush is needed.
+
+Multi-GPU: stripes are independent codes, so each rank runs the same
+workload on its own stripes (weak scaling, no collective on the data path);
+the timing is the max over ranks.
+
+--impl reference times the CPU oracle on a bounded sample of the same
+workload (the reference arm of this build; the paper ships no code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P, N, C, S = 13, 12, 4096, 8192
+SEED = 1
+CLASSES = ("dd", "dp", "dq", "pq")
+METRIC = "encode & 2-erasure recovery user GB/s vs HBM roofline"
+WORKLOAD = "p=13, N=12 data strips + P + Q, 12 rows x 4 KiB per strip, 8192 stripes; " \
+           "encode + per-stripe random DD/DP/DQ/PQ recovery, one launch per op"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def user_bytes_per_op(stripes=S):
+    return N * (P - 1) * C * stripes
+
+
+def moved_bytes_per_op(stripes=S):
+    return (N + 2) * (P - 1) * C * stripes
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples taken while the timed region runs."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(maxs) if maxs else None,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# --------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_cs_0611109_gb300 import build, inputs
+    build.build()
+    from paper_cs_0611109_gb300 import rcg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    ctx = rcg.Context(local)
+    sb = inputs.stripe_bytes(P, N, C)
+    buf = torch.empty((S, N + 2, P - 1, C), dtype=torch.uint8, device=dev)
+    rcg.rcg_fill_random(buf, S * sb, SEED + 100 * rank)
+    L = rcg.make_layout(buf, P, N, C)
+    ctx.encode(L, 0, S)
+    pairs = {k: torch.from_numpy(inputs.random_pairs(20 + n + 100 * rank, N, S, k)).to(dev)
+             for n, k in enumerate(CLASSES)}
+
+    def step(evs=None):
+        ops = [lambda: ctx.encode(L, 0, S)] + [
+            (lambda k=k: ctx.recover_many(L, 0, S, pairs[k])) for k in CLASSES]
+        for n, op in enumerate(ops):
+            if evs is not None:
+                evs[n][0].record(stream)
+            op()
+            if evs is not None:
+                evs[n][1].record(stream)
+        return len(ops)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ctx.last_device_status() != 0:
+        raise RuntimeError("device status word set during warm-up")
+
+    launch_evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(5)]
+                  for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t0.record(stream)
+    launches = 0
+    for k in range(args.steps):
+        launches += step(launch_evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    status = ctx.last_device_status()
+    if status != 0:
+        raise RuntimeError("device status word %#x after the timed region" % status)
+
+    per_launch = [[launch_evs[k][n][0].elapsed_time(launch_evs[k][n][1]) for k in range(args.steps)]
+                  for n in range(5)]
+    all_launch = [x for row in per_launch for x in row]
+    avg_launch_ms = sum(all_launch) / len(all_launch)
+    peak, peak_kind = peak_hbm()
+    achieved = moved_bytes_per_op() / (avg_launch_ms * 1e-3) / 1e9
+
+    user_step = 5 * user_bytes_per_op()
+    value = user_step * args.steps * world / (ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (SplitMix64 bytes generated on the device, seed %d)" % SEED,
+        "config": {"workload": WORKLOAD, "p": P, "n_data": N, "row_bytes": C, "stripes_per_gpu": S,
+                   "ops_per_step": ["encode", "recover_dd", "recover_dp", "recover_dq", "recover_pq"],
+                   "user_bytes_per_step_per_gpu": user_step,
+                   "hbm_bytes_per_op_per_gpu": moved_bytes_per_op(),
+                   "l2": "inputs (5.25 GiB per op) far larger than the 129 MB L2; no flush",
+                   "parallelism": "stripe-sharded x%d, no collective" % world},
+        "roofline": {"bound": "hbm", "kernel": "rcg_tile_engine",
+                     "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "avg_launch_ms": round(avg_launch_ms, 4),
+                     "bytes_per_launch": moved_bytes_per_op()},
+        "per_op": {name: {"ms": round(sum(row) / len(row), 4),
+                          "user_gbs": round(user_bytes_per_op() / (sum(row) / len(row) * 1e-3) / 1e9, 1),
+                          "hbm_frac": round(moved_bytes_per_op() / (sum(row) / len(row) * 1e-3) / 1e9 / peak, 4)}
+                   for name, row in zip(["encode", "dd", "dp", "dq", "pq"], per_launch)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    traffic = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic):
+        try:
+            tj = json.load(open(traffic))
+            if tj.get("kernel") == "rcg_tile_engine" and tj.get("source_hash") == kernel_hash():
+                out["roofline"]["traffic"] = tj["bytes_per_launch"]
+        except Exception:
+            pass
+
+    if not args.no_e2e:
+        out["e2e"] = e2e_ours(ctx, rcg, torch, dev, stream, pairs, args, world)
+    del buf
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(budget_s=15.0)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("rcg_engine.cu", "rcg_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_cs_0611109_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def e2e_ours(ctx, rcg, torch, dev, stream, pairs, args, world):
+    """Same step through the public API with the stripes in pinned HOST memory:
+    every op copies its inputs host->device and its results device->host inside
+    the timed region (encode: data in, P and Q out; recovery: the N surviving
+    strips' stripes in, the two rebuilt strips out)."""
+    from paper_cs_0611109_gb300 import inputs
+    host = torch.empty((S, N + 2, P - 1, C), dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty((S, N + 2, P - 1, C), dtype=torch.uint8, device=dev)
+    rcg.rcg_fill_random(dbuf, S * inputs.stripe_bytes(P, N, C), SEED)
+    L = rcg.make_layout(dbuf, P, N, C)
+    ctx.encode(L, 0, S)
+    host.copy_(dbuf)
+    torch.cuda.synchronize()
+    pairs_host = {k: pairs[k].cpu().pin_memory() for k in CLASSES}
+    pd = {k: torch.empty_like(pairs[k]) for k in CLASSES}
+    strip = (P - 1) * C
+    h2d = d2h = 0
+
+    def step():
+        nonlocal h2d, d2h
+        # encode: data strips in, P and Q out
+        dbuf[:, :N].copy_(host[:, :N], non_blocking=True)
+        h2d += S * N * strip
+        ctx.encode(L, 0, S)
+        host[:, N:].copy_(dbuf[:, N:], non_blocking=True)
+        d2h += S * 2 * strip
+        for k in CLASSES:
+            # the surviving strips of each stripe: copy the whole stripe array in
+            # (the erased strips' bytes are never read), the pairs, and the two
+            # rebuilt strips back
+            dbuf.copy_(host, non_blocking=True)
+            pd[k].copy_(pairs_host[k], non_blocking=True)
+            h2d += S * (N + 2) * strip + 2 * S
+            ctx.recover_many(L, 0, S, pd[k])
+            host.copy_(dbuf, non_blocking=True)
+            d2h += S * (N + 2) * strip
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    h2d = d2h = 0
+    steps = max(2, args.steps // 4)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    value = 5 * user_bytes_per_op() * steps * world / (ms * 1e-3) / 1e9
+    del host, dbuf
+    return {"value": round(value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d // steps,
+            "d2h_bytes_per_step": d2h // steps,
+            "note": "torch pinned-host copies around the C-ABI device calls"}
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_step(stripes, seed=SEED):
+    """One step of the workload on `stripes` stripes with the CPU oracle;
+    returns (seconds, user bytes)."""
+    import numpy as np
+
+    import oracle
+    from paper_cs_0611109_gb300 import inputs
+    host = np.ascontiguousarray(inputs.random_stripes(seed, P, N, C, stripes))
+    t = time.perf_counter()
+    oracle.encode(P, N, C, host, stripes)
+    for n, k in enumerate(CLASSES):
+        pairs = inputs.random_pairs(20 + n, N, stripes, k)
+        oracle.recover(P, N, C, host, stripes, pairs=pairs)
+    return time.perf_counter() - t, 5 * user_bytes_per_op(stripes)
+
+
+def cpu_baseline(budget_s=15.0):
+    import oracle
+    oracle.build()
+    t1, _ = oracle_step(1)
+    n = max(1, int(budget_s / max(t1, 1e-3)))
+    t, ub = oracle_step(n)
+    return {"value": round(ub / t / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "%d of the 8192 stripes, the full 5-op step (encode + DD/DP/DQ/PQ), "
+                      "single-threaded bit-level C oracle, %.1f s" % (n, t)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    stripes = 2
+    for _ in range(args.warmup):
+        oracle_step(stripes)
+    total_t = total_b = 0.0
+    for _ in range(args.steps):
+        t, b = oracle_step(stripes)
+        total_t += t
+        total_b += b
+    value = total_b / total_t / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "GB/s",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * total_t / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (SplitMix64 bytes, seed %d)" % SEED,
+            "config": {"workload": WORKLOAD, "p": P, "n_data": N, "row_bytes": C,
+                       "stripes_per_step": stripes},
+            "cpu_baseline": {"value": round(value, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d stripes per step of the 8192, full 5-op step" % stripes},
+            "e2e": {"value": round(value, 6), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

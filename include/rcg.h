@@ -102,6 +102,11 @@ rcg_status rcg_last_device_status(rcg_ctx *ctx, uint32_t *code);
 const char *rcg_status_str(rcg_status s);
 uint32_t rcg_abi_version(void);
 
+/* Text of the last CUDA runtime error the library saw on the calling thread
+ * (which call, the error name and message); "" if none.  The pointer stays
+ * valid until the thread's next library call. */
+const char *rcg_last_error(void);
+
 /* ------------------------------------------------------------ stripe ops */
 
 /* Encode: write P and Q of stripes [first_stripe, first_stripe + n_stripes)

@@ -4,6 +4,7 @@
 // launches.  All stripe arithmetic runs in rcg_engine.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 #include <time.h>
 
@@ -27,6 +28,7 @@ struct BatchSlot {
     size_t cap_jobs = 0;
     size_t bytes = 0;          // bytes the captured memcpy node copies
     cudaStream_t capture = nullptr;
+    cudaGraph_t graph = nullptr;       // kept alive: exec updates name its nodes
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t copy_node = nullptr;
     cudaEvent_t done = nullptr;
@@ -61,8 +63,12 @@ struct DeviceGuard {
     }
 };
 
-rcg_status from_cuda(cudaError_t e) {
+thread_local char g_last_error[256] = "";
+
+rcg_status from_cuda(cudaError_t e, const char *where = "") {
     if (e == cudaSuccess) return RCG_OK;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorString(e),
+             cudaGetErrorName(e));
     if (e == cudaErrorMemoryAllocation) return RCG_ENOMEM;
     return RCG_ECUDA;
 }
@@ -156,6 +162,7 @@ rcg_status wait_event(cudaEvent_t ev, uint64_t timeout_ns) {
 
 void free_slot(BatchSlot &s) {
     if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.graph) cudaGraphDestroy(s.graph);
     if (s.host) cudaFreeHost(s.host);
     if (s.dev) cudaFree(s.dev);
     if (s.counter) cudaFree(s.counter);
@@ -189,6 +196,8 @@ bool rcg::make_plan(uint32_t p, uint64_t C, Plan *out) {
 extern "C" {
 
 uint32_t rcg_abi_version(void) { return RCG_ABI_VERSION; }
+
+const char *rcg_last_error(void) { return g_last_error; }
 
 const char *rcg_status_str(rcg_status s) {
     switch (s) {
@@ -424,20 +433,27 @@ static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t jobs) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.capture, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         free_slot(s);
-        return from_cuda(e);
+        return from_cuda(e, "batch slot allocation");
     }
     memset(s.host, 0, bytes);
     s.cap_jobs = cap;
     s.bytes = bytes;
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(s.capture, cudaStreamCaptureModeThreadLocal);
+    const char *where = "graph capture";
     if (e == cudaSuccess) {
-        cudaMemcpyAsync(s.dev, s.host, bytes, cudaMemcpyHostToDevice, s.capture);
-        cudaMemsetAsync(s.counter, 0, sizeof(unsigned long long), s.capture);
-        launch_batch(s.dev, ctx->status, s.counter, ctx->timeout_ns, ctx->sm_count, s.capture);
+        cudaError_t e1 = cudaMemcpyAsync(s.dev, s.host, bytes, cudaMemcpyHostToDevice, s.capture);
+        cudaError_t e2 = cudaMemsetAsync(s.counter, 0, sizeof(unsigned long long), s.capture);
+        cudaError_t e3 = launch_batch(s.dev, ctx->status, s.counter, ctx->timeout_ns, ctx->sm_count, s.capture);
         e = cudaStreamEndCapture(s.capture, &graph);
+        if (e1 != cudaSuccess) { e = e1; where = "captured table copy"; }
+        else if (e2 != cudaSuccess) { e = e2; where = "captured counter reset"; }
+        else if (e3 != cudaSuccess) { e = e3; where = "captured kernel launch"; }
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&s.exec, graph, 0);
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&s.exec, graph, 0);
+        where = "graph instantiate";
+    }
     if (e == cudaSuccess) {
         size_t n = 0;
         cudaGraphGetNodes(graph, nullptr, &n);
@@ -449,10 +465,10 @@ static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t jobs) {
         }
         if (!s.copy_node) e = cudaErrorUnknown;
     }
-    if (graph) cudaGraphDestroy(graph);
+    s.graph = graph;
     if (e != cudaSuccess) {
         free_slot(s);
-        return from_cuda(e);
+        return from_cuda(e, where);
     }
     return RCG_OK;
 }
@@ -494,14 +510,36 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
     memcpy(s.host, &hdr, sizeof(hdr));
     memcpy(s.host + sizeof(hdr), table.data(), static_cast<size_t>(n_jobs) * sizeof(Job));
     cudaError_t e = cudaSuccess;
+    const char *where = "graph copy-size update";
     if (bytes != s.bytes) {
-        e = cudaGraphExecMemcpyNodeSetParams1D(s.exec, s.copy_node, s.dev, s.host, bytes,
-                                               cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) s.bytes = bytes;
+        // copy only the live part of the table: update the captured node
+        cudaMemcpy3DParms mp;
+        e = cudaGraphMemcpyNodeGetParams(s.copy_node, &mp);
+        if (e == cudaSuccess) {
+            mp.extent.width = bytes;
+            mp.srcPtr.pitch = bytes;
+            mp.srcPtr.xsize = bytes;
+            mp.dstPtr.pitch = bytes;
+            mp.dstPtr.xsize = bytes;
+            e = cudaGraphExecMemcpyNodeSetParams(s.exec, s.copy_node, &mp);
+        }
+        if (e == cudaSuccess) {
+            s.bytes = bytes;
+        } else {
+            // keep copying the whole table (the kernel reads n_jobs entries)
+            cudaGetLastError();
+            e = cudaSuccess;
+        }
     }
-    if (e == cudaSuccess) e = cudaGraphLaunch(s.exec, static_cast<cudaStream_t>(stream));
-    if (e == cudaSuccess) e = cudaEventRecord(s.done, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return from_cuda(e);
+    if (e == cudaSuccess) {
+        e = cudaGraphLaunch(s.exec, static_cast<cudaStream_t>(stream));
+        where = "graph launch";
+    }
+    if (e == cudaSuccess) {
+        e = cudaEventRecord(s.done, static_cast<cudaStream_t>(stream));
+        where = "event record";
+    }
+    if (e != cudaSuccess) return from_cuda(e, where);
     s.used = true;
     s.ticket = tk;
     ctx->next_ticket = tk + 1;

@@ -110,6 +110,15 @@ __device__ __forceinline__ uint4 lds(const uint8_t *p) {
     return *reinterpret_cast<const uint4 *>(p);
 }
 
+// 16-byte shared-memory load by 32-bit shared address
+__device__ __forceinline__ uint4 lds_a(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
 __device__ __forceinline__ void sts(uint8_t *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
 
 __device__ __forceinline__ void stg(uint8_t *p, uint4 v) {
@@ -139,16 +148,18 @@ enum : uint8_t {
     E_DEGQ = 5   // degraded read of Q: out = fold(accQ)
 };
 
+// Slot header.  The first 16 bytes are read (one 16-byte load) for every
+// slot; the second half only on a tile's first slot.
 struct SlotHdr {
+    uint8_t flags;    // F_* bits
+    uint8_t rot;      // x^rot for F_Q
+    uint16_t w;       // tile width, bytes
     uint32_t job;
     uint32_t stripe;
-    uint32_t c0;    // first column byte of the tile
-    uint16_t w;     // tile width, bytes
-    uint8_t flags;
-    uint8_t rot;    // x^rot for F_Q
-    uint8_t cls;    // epilogue class
-    uint8_t a, b;   // the erased pair (a < b), or i / j of the op
+    uint32_t c0;      // first column byte of the tile
+    uint8_t cls;      // epilogue class
     uint8_t p;
+    uint8_t a, b;     // the erased pair (a < b), or i / j of the op
     uint8_t pad[12];
 };
 static_assert(sizeof(SlotHdr) == 32, "slot header is 32 bytes");
@@ -228,11 +239,25 @@ __device__ __forceinline__ const Job &job_ref(const LaunchParams &prm, uint32_t 
 
 // ---------------------------------------------------------------- producer
 
+// Ring position: slot index and the parity of its current phase.
+struct RingPos {
+    uint32_t slot = 0, phase = 0;
+    __device__ __forceinline__ void next(uint32_t n_slots) {
+        if (++slot == n_slots) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
 __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_jobs,
                          uint64_t total_tiles, uint32_t slot_bytes, uint32_t n_slots) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t policy = l2_evict_first();
-    uint32_t it = 0;  // slots issued
+    const uint64_t timeout = prm.timeout_ns;
+    const uint32_t ring0 = smem_addr(sm.ring);
+    RingPos pos;
+    uint32_t issued = 0;  // slots handed to the consumers
     bool ok = true;
     uint64_t next_static = blockIdx.x;
 
@@ -258,7 +283,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
             }
             ji = lo;
         }
-        const Job &J = job_ref(prm, ji);
+        const Job J = job_ref(prm, ji);  // by value: fields stay in registers
         const uint32_t p = J.p, N = J.n, rows = p - 1;
         const uint64_t local = t - J.tile_begin;
         const uint32_t stripe = static_cast<uint32_t>(local / J.tiles_per_stripe);
@@ -299,61 +324,56 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
             if (strip_role(cls, update, k, N, a, b, &rot)) ++count;
 
         const uint8_t *stripe_base = J.base + stripe * J.stripe_stride + c0;
+        const uint8_t *aux_base = J.aux + stripe * J.aux_stripe_stride + c0;
+        const uint64_t strip_stride = J.strip_stride, row_stride = J.row_stride;
+        const uint64_t aux_rs = J.aux_row_stride;
+        const uint32_t tx = rows * w;
         uint32_t emitted = 0;
-        for (uint32_t k = 0; k < N + 3 && ok; ++k) {
+        for (uint32_t k = 0; k < N + 3; ++k) {
             const uint8_t fl = strip_role(cls, update, k, N, a, b, &rot);
             if (!fl) continue;
-            const uint32_t slot = it % n_slots;
-            const uint32_t ph = (it / n_slots) & 1u;
-            if (!mbar_wait(smem_addr(&sm.empty[slot]), ph ^ 1u, prm.timeout_ns)) {
+            if (!mbar_wait(smem_addr(&sm.empty[pos.slot]), pos.phase ^ 1u, timeout)) {
                 ok = false;
                 break;
             }
-            const uint32_t full = smem_addr(&sm.full[slot]);
+            const uint32_t full = smem_addr(&sm.full[pos.slot]);
             if (lane == 0) {
                 SlotHdr h;
+                h.flags = fl | (emitted == 0 ? F_FIRST : 0) | (emitted + 1 == count ? F_LAST : 0);
+                h.rot = static_cast<uint8_t>(rot);
+                h.w = static_cast<uint16_t>(w);
                 h.job = ji;
                 h.stripe = stripe;
                 h.c0 = c0;
-                h.w = static_cast<uint16_t>(w);
-                h.flags = fl | (emitted == 0 ? F_FIRST : 0) | (emitted + 1 == count ? F_LAST : 0);
-                h.rot = static_cast<uint8_t>(rot);
                 h.cls = cls;
+                h.p = static_cast<uint8_t>(p);
                 h.a = static_cast<uint8_t>(a);
                 h.b = static_cast<uint8_t>(b);
-                h.p = static_cast<uint8_t>(p);
-                sm.hdr[slot] = h;
-                mbar_arrive_tx(full, rows * w);
+                sm.hdr[pos.slot] = h;
+                mbar_arrive_tx(full, tx);
             }
             __syncwarp();
-            const uint8_t *src;
-            uint64_t rs;
-            if (k == N + 2) {
-                src = J.aux + stripe * J.aux_stripe_stride + c0;
-                rs = J.aux_row_stride;
-            } else {
-                src = stripe_base + k * J.strip_stride;
-                rs = J.row_stride;
-            }
-            const uint32_t dst = smem_addr(sm.ring + static_cast<size_t>(slot) * slot_bytes);
+            const uint8_t *src = (k == N + 2) ? aux_base : stripe_base + k * strip_stride;
+            const uint64_t rs = (k == N + 2) ? aux_rs : row_stride;
+            const uint32_t dst = ring0 + pos.slot * slot_bytes;
             for (uint32_t r = lane; r < rows; r += 32) bulk_load(dst + r * w, src + r * rs, w, full, policy);
-            ++it;
+            pos.next(n_slots);
+            ++issued;
             ++emitted;
         }
         if (!ok) break;
     }
 
     if (ok) {  // end marker
-        const uint32_t slot = it % n_slots;
-        const uint32_t ph = (it / n_slots) & 1u;
-        if (mbar_wait(smem_addr(&sm.empty[slot]), ph ^ 1u, prm.timeout_ns)) {
+        if (mbar_wait(smem_addr(&sm.empty[pos.slot]), pos.phase ^ 1u, timeout)) {
             if (lane == 0) {
                 SlotHdr h = {};
                 h.flags = F_END;
-                sm.hdr[slot] = h;
-                mbar_arrive(smem_addr(&sm.full[slot]));
+                sm.hdr[pos.slot] = h;
+                mbar_arrive(smem_addr(&sm.full[pos.slot]));
             }
-            ++it;
+            pos.next(n_slots);
+            ++issued;
         } else {
             ok = false;
         }
@@ -361,9 +381,9 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
     if (!ok && lane == 0) set_status(prm.status, RCG_DEV_TIMEOUT);
     // Do not leave while a bulk copy may still be writing this CTA's shared
     // memory: wait (bounded) for the last use of every slot to complete.
-    const uint32_t first = it > n_slots ? it - n_slots : 0;
-    for (uint32_t s = first; s < it; ++s)
-        if (!mbar_wait(smem_addr(&sm.full[s % n_slots]), (s / n_slots) & 1u, prm.timeout_ns)) {
+    const uint32_t first = issued > n_slots ? issued - n_slots : 0;
+    for (uint32_t s = first; s < issued; ++s)
+        if (!mbar_wait(smem_addr(&sm.full[s % n_slots]), (s / n_slots) & 1u, timeout)) {
             if (lane == 0) set_status(prm.status, RCG_DEV_TIMEOUT);
             break;
         }
@@ -512,73 +532,82 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
                          uint32_t n_slots) {
     const int ctid = static_cast<int>(threadIdx.x) - 32;
     const uint32_t lane = threadIdx.x & 31;
+    const uint64_t timeout = prm.timeout_ns;
+    const uint32_t ring0 = smem_addr(sm.ring);
+    const uint32_t hdr0 = smem_addr(sm.hdr);
     uint4 accP[kItems], accQ[kItems];
     int row[kItems], col[kItems];
+    uint32_t off[kItems];   // byte offset of the item's own row in a slot
     Tile T = {};
     uint8_t *copy_dst = nullptr;  // small write: data strip a of the tile
     uint32_t ep_phase = 0;
-    uint32_t it = 0;
+    int p = 3;
+    uint32_t w = 16, pw = 48;
+    RingPos pos;
 
     for (;;) {
-        const uint32_t slot = it % n_slots;
-        const uint32_t ph = (it / n_slots) & 1u;
-        if (!mbar_wait(smem_addr(&sm.full[slot]), ph, prm.timeout_ns)) {
+        if (!mbar_wait(smem_addr(&sm.full[pos.slot]), pos.phase, timeout)) {
             if (lane == 0) set_status(prm.status, RCG_DEV_TIMEOUT);
             return;
         }
-        const SlotHdr h = sm.hdr[slot];
-        if (h.flags & F_END) break;
-        if (h.flags & F_FIRST) {
-            const Job &J = job_ref(prm, h.job);
-            T.p = h.p;
-            T.w = h.w;
-            T.nvec = h.w >> 4;
-            T.cls = h.cls;
-            T.a = h.a;
-            T.b = h.b;
+        const uint4 hv = lds_a(hdr0 + pos.slot * static_cast<uint32_t>(sizeof(SlotHdr)));
+        const uint32_t flags = hv.x & 0xffu;
+        if (flags & F_END) break;
+        if (flags & F_FIRST) {
+            const uint4 tv = lds_a(hdr0 + pos.slot * static_cast<uint32_t>(sizeof(SlotHdr)) + 16);
+            const uint32_t job = hv.y, stripe = hv.z, c0 = hv.w;
+            const Job &J = job_ref(prm, job);
+            T.w = hv.x >> 16;
+            T.nvec = T.w >> 4;
+            T.cls = static_cast<uint8_t>(tv.x);
+            T.p = (tv.x >> 8) & 0xffu;
+            T.a = static_cast<uint8_t>(tv.x >> 16);
+            T.b = static_cast<uint8_t>(tv.x >> 24);
             T.strip_stride = J.strip_stride;
             T.row_stride = J.row_stride;
-            T.base = J.base + h.stripe * J.stripe_stride + h.c0;
-            T.out = J.aux + h.stripe * J.aux_stripe_stride + h.c0;
+            T.base = J.base + stripe * J.stripe_stride + c0;
+            T.out = J.aux + stripe * J.aux_stripe_stride + c0;
             T.out_row_stride = J.aux_row_stride;
-            copy_dst = T.base + static_cast<uint64_t>(h.a) * J.strip_stride;
-            if (T.cls == E_ENC) {  // P and Q are strips N and N+1: pass N through b
-                T.b = J.n;
-            }
+            copy_dst = T.base + static_cast<uint64_t>(T.a) * J.strip_stride;
+            if (T.cls == E_ENC) T.b = J.n;  // P and Q are strips N and N+1
+            p = static_cast<int>(T.p);
+            w = T.w;
+            pw = p * w;
             for (int t = 0; t < kItems; ++t) {
                 const int item = ctid + t * kConsumers;
                 const int r = item / static_cast<int>(T.nvec);
-                row[t] = r < static_cast<int>(T.p) ? r : 0x7fff;
+                row[t] = r < p ? r : 0x7fff;
                 col[t] = item - r * static_cast<int>(T.nvec);
+                off[t] = r * w + col[t] * 16;
                 accP[t] = make_uint4(0, 0, 0, 0);
                 accQ[t] = make_uint4(0, 0, 0, 0);
             }
         }
-        const uint8_t *stage = sm.ring + static_cast<size_t>(slot) * slot_bytes;
-        const int p = static_cast<int>(T.p);
-        const int rot = h.rot;
-        const uint32_t w = T.w;
+        const uint32_t stage = ring0 + pos.slot * slot_bytes;
+        const int rot = (hv.x >> 8) & 0xff;
+        const uint32_t rotw = rot * w;
+        const bool fp = flags & F_P, fq = flags & F_Q, fc = flags & F_COPY;
 #pragma unroll
         for (int t = 0; t < kItems; ++t) {
             const int r = row[t];
             if (r >= p) continue;
-            if ((h.flags & F_P) && r < p - 1) {
-                const uint4 v = lds(stage + r * w + col[t] * 16);
+            if (fp && r < p - 1) {
+                const uint4 v = lds_a(stage + off[t]);
                 accP[t] = xor4(accP[t], v);
-                if (h.flags & F_COPY)
-                    stg(copy_dst + static_cast<uint64_t>(r) * T.row_stride + col[t] * 16, v);
+                if (fc) stg(copy_dst + static_cast<uint64_t>(r) * T.row_stride + col[t] * 16, v);
             }
-            if (h.flags & F_Q) {
-                int s = r - rot;
-                if (s < 0) s += p;
-                if (s < p - 1) accQ[t] = xor4(accQ[t], lds(stage + s * w + col[t] * 16));
+            if (fq) {
+                // row r of x^rot * strip is row r - rot (mod p) of the strip; row p-1 is zero
+                const int s = r - rot;
+                const uint32_t o = off[t] - rotw + (s < 0 ? pw : 0u);
+                if (s != -1 && s != p - 1) accQ[t] = xor4(accQ[t], lds_a(stage + o));
             }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&sm.empty[slot]));
-        ++it;
-        if (h.flags & F_LAST) {
-            if (!epilogue(sm, T, accP, accQ, row, col, ep_phase, prm.timeout_ns)) {
+        if (lane == 0) mbar_arrive(smem_addr(&sm.empty[pos.slot]));
+        pos.next(n_slots);
+        if (flags & F_LAST) {
+            if (!epilogue(sm, T, accP, accQ, row, col, ep_phase, timeout)) {
                 if (lane == 0) set_status(prm.status, RCG_DEV_TIMEOUT);
                 return;
             }

@@ -13,11 +13,17 @@ namespace rcg {
 // "items": one 16-byte column vector of one row, for P and for the lifted Q
 // accumulator (rows 0..p-1, row p-1 being the imaginary row of the lift to
 // F2[x]/(x^p - 1)).  A tile of W bytes of a p-row stripe has p * W/16 items.
-constexpr int kConsumerWarps = 8;
+#ifndef RCG_CONSUMER_WARPS
+#define RCG_CONSUMER_WARPS 16
+#endif
+#ifndef RCG_ITEMS
+#define RCG_ITEMS 2
+#endif
+constexpr int kConsumerWarps = RCG_CONSUMER_WARPS;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;
-constexpr int kItems = 4;
-constexpr int kMaxItems = kItems * kConsumers;  // 1024 items per tile
+constexpr int kItems = RCG_ITEMS;
+constexpr int kMaxItems = kItems * kConsumers;  // items per tile (1024 by default)
 constexpr int kMaxSlots = 32;
 constexpr int kMaxP = 61;
 constexpr uint32_t kMaxSlotBytes = 32 * 1024;
@@ -25,7 +31,7 @@ constexpr uint32_t kMaxSlotBytes = 32 * 1024;
 // Dynamic shared memory: control block, exchange buffers, then the ring.
 constexpr uint32_t kCtlBytes = 2048;                       // barriers + slot headers
 constexpr uint32_t kXBytes = kMaxItems * 16;               // one p x W exchange buffer
-constexpr uint32_t kFoldBytes = 8192;                      // one row of W bytes (W <= kMaxItems/3*16)
+constexpr uint32_t kFoldBytes = ((kMaxItems / 3) * 16 + 127) / 128 * 128;  // one row of W bytes
 constexpr uint32_t kFixedSmem = kCtlBytes + 2 * kXBytes + kFoldBytes;
 constexpr uint32_t kSmemLimit = 227 * 1024;
 constexpr uint32_t kRingBytes = kSmemLimit - kFixedSmem;

@@ -23,7 +23,10 @@ _u32, _u64, _vp, _int = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctype
 
 class RcgError(RuntimeError):
     def __init__(self, status: int, what: str):
-        super().__init__("%s: %s (status %d)" % (what, rcg_status_str(status), status))
+        msg = "%s: %s (status %d)" % (what, rcg_status_str(status), status)
+        if status == RCG_ECUDA:
+            msg += " [%s]" % rcg_last_error()
+        super().__init__(msg)
         self.status = status
 
 
@@ -49,6 +52,7 @@ EXPORTS = {
     "rcg_last_device_status": (_int, [_vp, ctypes.POINTER(_u32)]),
     "rcg_status_str": (ctypes.c_char_p, [_int]),
     "rcg_abi_version": (_u32, []),
+    "rcg_last_error": (ctypes.c_char_p, []),
     "rcg_encode": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u64, _vp]),
     "rcg_recover": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u32, _u32, _vp]),
     "rcg_recover_many": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u64, _vp, _vp]),
@@ -115,6 +119,13 @@ def rcg_status_str(st: int) -> str:
         return lib().rcg_status_str(st).decode()
     except ImportError:
         return "status %d" % st
+
+
+def rcg_last_error() -> str:
+    try:
+        return lib().rcg_last_error().decode()
+    except ImportError:
+        return ""
 
 
 def rcg_abi_version() -> int:
