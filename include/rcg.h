@@ -196,10 +196,12 @@ rcg_status rcg_inverse_table(uint32_t p, uint64_t *masks);
 
 /* Host: the tiling the library uses for one stripe geometry. */
 typedef struct rcg_plan_info {
-    uint32_t tile_bytes;       /* W: column-tile width in bytes (multiple of 16) */
+    uint32_t tile_bytes;       /* W: column-tile width in bytes (multiple of 16, <= 2048) */
     uint32_t tiles_per_stripe; /* ceil(C / W) */
     uint32_t slot_bytes;       /* shared-memory ring slot: (p-1) rows x W */
     uint32_t n_slots;          /* ring depth */
+    uint32_t max_items;        /* the engine's limit on p x W/16 per tile */
+    uint32_t smem_bytes;       /* dynamic shared memory of one CTA for this plan */
 } rcg_plan_info;
 rcg_status rcg_plan(uint32_t p, uint64_t row_bytes, rcg_plan_info *out);
 

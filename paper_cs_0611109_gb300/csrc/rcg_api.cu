@@ -2,6 +2,8 @@
 // Argument validation, tiling plans, per-context device state (status word,
 // inverse tables, batch descriptor tables and their CUDA graphs) and kernel
 // launches.  All stripe arithmetic runs in rcg_engine.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -103,6 +105,37 @@ rcg_status check_layout(const rcg_layout *L, Geo *g) {
     return RCG_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once (no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// 4-D tiled tensor map over (8-byte column, row, strip, stripe) with a
+// (W/8) x (p-1) x 1 x 1 box.  A layout the driver refuses (e.g. strides it
+// does not accept) keeps use_tmap = 0 and is served by per-row bulk copies.
+void attach_tensor_map(Job &J, const Geo &g) {
+    J.use_tmap = 0;
+    auto encode = tensor_map_encoder();
+    if (!encode || J.W > kMaxTileBytes || J.n_stripes == 0) return;
+    const cuuint64_t dims[4] = {g.C / 8, g.p - 1, g.N + 2, J.n_stripes};
+    const cuuint64_t strides[3] = {g.rs, g.ss, g.st};
+    const cuuint32_t box[4] = {J.W / 8, g.p - 1, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(&J.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, J.base, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    J.use_tmap = r == CUDA_SUCCESS ? 1 : 0;
+}
+
 Job base_job(const rcg_layout *L, const Geo &g, uint64_t first_stripe, uint64_t n_stripes,
              const Plan &pl) {
     Job J;
@@ -117,6 +150,7 @@ Job base_job(const rcg_layout *L, const Geo &g, uint64_t first_stripe, uint64_t 
     J.tiles_per_stripe = pl.tiles_per_stripe;
     J.p = static_cast<uint8_t>(g.p);
     J.n = static_cast<uint8_t>(g.N);
+    attach_tensor_map(J, g);
     return J;
 }
 
@@ -180,7 +214,7 @@ bool rcg::make_plan(uint32_t p, uint64_t C, Plan *out) {
     const uint64_t nvec_total = C / 16;
     uint64_t nvec_max = static_cast<uint64_t>(kMaxItems) / p;
     nvec_max = std::min<uint64_t>(nvec_max, kMaxSlotBytes / ((p - 1) * 16ull));
-    nvec_max = std::min<uint64_t>(nvec_max, kFoldBytes / 16);
+    nvec_max = std::min<uint64_t>(nvec_max, kMaxTileBytes / 16);
     const uint64_t tiles = (nvec_total + nvec_max - 1) / nvec_max;
     if (tiles > 0xffffffffull) return false;
     const uint64_t nvec = (nvec_total + tiles - 1) / tiles;
@@ -226,6 +260,8 @@ rcg_status rcg_plan(uint32_t p, uint64_t row_bytes, rcg_plan_info *out) {
     out->tiles_per_stripe = pl.tiles_per_stripe;
     out->slot_bytes = pl.slot_bytes;
     out->n_slots = pl.n_slots;
+    out->max_items = kMaxItems;
+    out->smem_bytes = kFixedSmem + pl.n_slots * pl.slot_bytes;
     return RCG_OK;
 }
 
@@ -295,7 +331,7 @@ rcg_status rcg_encode(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe, 
     rcg_status st = check_layout(L, &g);
     if (st) return st;
     if (n_stripes == 0) return RCG_OK;
-    if (n_stripes > 0xffffffffull) return RCG_EINVAL;
+    if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
     Plan pl;
     if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
     Job J = base_job(L, g, first_stripe, n_stripes, pl);
@@ -328,7 +364,7 @@ rcg_status rcg_recover_many(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_st
     rcg_status st = check_layout(L, &g);
     if (st) return st;
     if (n_stripes == 0) return RCG_OK;
-    if (n_stripes > 0xffffffffull) return RCG_EINVAL;
+    if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
     Plan pl;
     if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
     Job J = base_job(L, g, first_stripe, n_stripes, pl);
@@ -386,7 +422,7 @@ static rcg_status build_job(const rcg_job &in, Job *out, Plan *pl) {
     Geo g;
     rcg_status st = check_layout(&in.layout, &g);
     if (st) return st;
-    if (in.n_stripes == 0 || in.n_stripes > 0xffffffffull) return RCG_EINVAL;
+    if (in.n_stripes == 0 || in.n_stripes > 0x7fffffffull) return RCG_EINVAL;
     if (!make_plan(g.p, g.C, pl)) return RCG_EINVAL;
     Job J = base_job(&in.layout, g, in.first_stripe, in.n_stripes, *pl);
     const uint64_t ars = in.aux_row_stride ? in.aux_row_stride : g.C;

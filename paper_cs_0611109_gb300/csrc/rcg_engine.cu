@@ -102,6 +102,17 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
         : "memory");
 }
 
+// 4-D tiled tensor copy global -> shared (box given by the tensor map),
+// completion counted on `bar`.  Coordinates innermost first.
+__device__ __forceinline__ void tensor_load_4d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                               int z, int w, uint32_t bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar), "l"(policy)
+        : "memory");
+}
+
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }
@@ -160,7 +171,8 @@ struct SlotHdr {
     uint8_t cls;      // epilogue class
     uint8_t p;
     uint8_t a, b;     // the erased pair (a < b), or i / j of the op
-    uint8_t pad[12];
+    uint16_t pitch;   // bytes between rows in the slot (the job's tile width W)
+    uint8_t pad[10];
 };
 static_assert(sizeof(SlotHdr) == 32, "slot header is 32 bytes");
 
@@ -169,8 +181,7 @@ struct Smem {
     uint64_t *empty;  // [kMaxSlots] consumers -> producer
     uint64_t *ep;     // epilogue barrier among consumer warps
     SlotHdr *hdr;     // [kMaxSlots]
-    uint8_t *xp;      // exchange buffer [p][nvec] x 16 B
-    uint8_t *xq;      // exchange buffer [p][nvec] x 16 B
+    uint8_t *xb;      // exchange buffer [p][nvec] x 16 B
     uint8_t *fold;    // one row [nvec] x 16 B
     uint8_t *ring;    // n_slots x slot_bytes
 };
@@ -181,9 +192,8 @@ __device__ __forceinline__ Smem carve(uint8_t *smem) {
     s.empty = s.full + kMaxSlots;
     s.ep = s.empty + kMaxSlots;
     s.hdr = reinterpret_cast<SlotHdr *>(smem + 1024);
-    s.xp = smem + kCtlBytes;
-    s.xq = s.xp + kXBytes;
-    s.fold = s.xq + kXBytes;
+    s.xb = smem + kCtlBytes;
+    s.fold = s.xb + kXBytes;
     s.ring = s.fold + kFoldBytes;
     return s;
 }
@@ -283,24 +293,27 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
             }
             ji = lo;
         }
-        const Job J = job_ref(prm, ji);  // by value: fields stay in registers
+        const Job &J = job_ref(prm, ji);  // the tensor map is used in place
+        // the fields this tile needs, loaded once into registers
         const uint32_t p = J.p, N = J.n, rows = p - 1;
+        const uint32_t tps = J.tiles_per_stripe, W = J.W, C = J.C, n_stripes = J.n_stripes;
+        const uint32_t op = J.op, use_tmap = J.use_tmap;
         const uint64_t local = t - J.tile_begin;
-        const uint32_t stripe = static_cast<uint32_t>(local / J.tiles_per_stripe);
-        const uint32_t c0 = static_cast<uint32_t>(local % J.tiles_per_stripe) * J.W;
-        const uint32_t w = min(J.W, J.C - c0);
+        const uint32_t stripe = static_cast<uint32_t>(local / tps);
+        const uint32_t c0 = static_cast<uint32_t>(local % tps) * W;
+        const uint32_t w = min(W, C - c0);
         // device-side guard: a tile must fit its slot and the item budget
-        if (p < 3 || p > kMaxP || N < 1 || N > p || (w & 15) || w == 0 ||
-            rows * w > slot_bytes || p * (w >> 4) > static_cast<uint32_t>(kMaxItems) ||
-            stripe >= J.n_stripes) {
+        if (p < 3 || p > kMaxP || N < 1 || N > p || (w & 15) || w == 0 || W > kMaxTileBytes ||
+            (W & 15) || rows * W > slot_bytes || p * (w >> 4) > static_cast<uint32_t>(kMaxItems) ||
+            stripe >= n_stripes) {
             if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
             continue;
         }
 
         uint8_t cls = E_ENC;
         uint32_t a = J.i, b = J.j;
-        const bool update = J.op == OP_UPDATE;
-        if (J.op == OP_RECOVER) {
+        const bool update = op == OP_UPDATE;
+        if (op == OP_RECOVER) {
             if (J.pairs) {
                 a = J.pairs[2ull * stripe];
                 b = J.pairs[2ull * stripe + 1];
@@ -310,7 +323,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
                 continue;
             }
             cls = (b < N) ? E_DD : (a == N) ? E_ENC : (b == N) ? E_DP : E_DQ;
-        } else if (J.op == OP_DEGRADED) {
+        } else if (op == OP_DEGRADED) {
             cls = (b == N + 1) ? E_DEGQ : E_DEGP;
         } else if (update) {
             if (a >= N) {
@@ -327,7 +340,9 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
         const uint8_t *aux_base = J.aux + stripe * J.aux_stripe_stride + c0;
         const uint64_t strip_stride = J.strip_stride, row_stride = J.row_stride;
         const uint64_t aux_rs = J.aux_row_stride;
-        const uint32_t tx = rows * w;
+        // rows sit W bytes apart in a slot; a tensor copy always lands the full
+        // W-wide box (columns past C are zero-filled), row copies land w bytes
+        const uint32_t tx = use_tmap ? rows * W : rows * w;
         uint32_t emitted = 0;
         for (uint32_t k = 0; k < N + 3; ++k) {
             const uint8_t fl = strip_role(cls, update, k, N, a, b, &rot);
@@ -349,14 +364,23 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
                 h.p = static_cast<uint8_t>(p);
                 h.a = static_cast<uint8_t>(a);
                 h.b = static_cast<uint8_t>(b);
+                h.pitch = static_cast<uint16_t>(W);
                 sm.hdr[pos.slot] = h;
                 mbar_arrive_tx(full, tx);
             }
             __syncwarp();
-            const uint8_t *src = (k == N + 2) ? aux_base : stripe_base + k * strip_stride;
-            const uint64_t rs = (k == N + 2) ? aux_rs : row_stride;
             const uint32_t dst = ring0 + pos.slot * slot_bytes;
-            for (uint32_t r = lane; r < rows; r += 32) bulk_load(dst + r * w, src + r * rs, w, full, policy);
+            if (use_tmap && k < N + 2) {
+                // one tensor copy: box (W/8 x p-1) at column c0, strip k, stripe
+                if (lane == 0)
+                    tensor_load_4d(dst, &J.tmap, static_cast<int>(c0 >> 3), 0, static_cast<int>(k),
+                                   static_cast<int>(stripe), full, policy);
+            } else {
+                const uint8_t *src = (k == N + 2) ? aux_base : stripe_base + k * strip_stride;
+                const uint64_t rs = (k == N + 2) ? aux_rs : row_stride;
+                for (uint32_t r = lane; r < rows; r += 32)
+                    bulk_load(dst + r * W, src + r * rs, w, full, policy);
+            }
             pos.next(n_slots);
             ++issued;
             ++emitted;
@@ -423,9 +447,11 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
     switch (T.cls) {
         case E_ENC:
         case E_DEGQ: {
+            #pragma unroll
             for (int t = 0; t < kItems; ++t)
                 if (row[t] == p - 1) sts(sm.fold + col[t] * 16, accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            #pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p - 1) continue;
                 const uint4 q = xor4(accQ[t], lds(sm.fold + col[t] * 16));
@@ -439,23 +465,26 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
             break;
         }
         case E_DEGP: {
+            #pragma unroll
             for (int t = 0; t < kItems; ++t)
                 if (row[t] < p - 1)
                     stg(T.out + static_cast<uint64_t>(row[t]) * T.out_row_stride + col[t] * 16, accP[t]);
             break;
         }
         case E_DP: {  // D_a = x^(-a) dQ (reduced), P = accP + D_a
+            #pragma unroll
             for (int t = 0; t < kItems; ++t)
-                if (row[t] < p) sts(X(sm.xq, row[t], col[t]), accQ[t]);
+                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             const int a = T.a;
+            #pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p - 1) continue;
                 int s = row[t] + a;
                 if (s >= p) s -= p;
                 int f = p - 1 + a;
                 if (f >= p) f -= p;
-                const uint4 d = xor4(lds(X(sm.xq, s, col[t])), lds(X(sm.xq, f, col[t])));
+                const uint4 d = xor4(lds(X(sm.xb, s, col[t])), lds(X(sm.xb, f, col[t])));
                 stg(strip_row(T.a, row[t], col[t]), d);
                 stg(strip_row(T.b, row[t], col[t]), xor4(accP[t], d));
             }
@@ -463,18 +492,21 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
         }
         case E_DQ: {  // D_a = accP; Q = fold(accQ + x^a D_a)
             const uint4 zero = make_uint4(0, 0, 0, 0);
+            #pragma unroll
             for (int t = 0; t < kItems; ++t)
-                if (row[t] < p) sts(X(sm.xp, row[t], col[t]), row[t] < p - 1 ? accP[t] : zero);
+                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), row[t] < p - 1 ? accP[t] : zero);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             const int a = T.a;
+            #pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p) continue;
                 int s = row[t] - a;
                 if (s < 0) s += p;
-                accQ[t] = xor4(accQ[t], lds(X(sm.xp, s, col[t])));
+                accQ[t] = xor4(accQ[t], lds(X(sm.xb, s, col[t])));
                 if (row[t] == p - 1) sts(sm.fold + col[t] * 16, accQ[t]);
             }
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            #pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p - 1) continue;
                 stg(strip_row(T.a, row[t], col[t]), accP[t]);
@@ -484,23 +516,28 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
         }
         case E_DD: {
             const uint4 zero = make_uint4(0, 0, 0, 0);
-            for (int t = 0; t < kItems; ++t) {
-                if (row[t] >= p) continue;
-                sts(X(sm.xp, row[t], col[t]), row[t] < p - 1 ? accP[t] : zero);
-                sts(X(sm.xq, row[t], col[t]), accQ[t]);
-            }
-            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             const int a = T.a;
-            // T = dP + x^(-a) dQ, written over xp (each thread touches only its own rows)
+            #pragma unroll
+            for (int t = 0; t < kItems; ++t)
+                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), accQ[t]);
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            // T = dP + x^(-a) dQ (lifted; row p-1 of dP is zero)
+            uint4 tv[kItems];
+            #pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p) continue;
                 int s = row[t] + a;
                 if (s >= p) s -= p;
-                sts(X(sm.xp, row[t], col[t]), xor4(lds(X(sm.xp, row[t], col[t])), lds(X(sm.xq, s, col[t]))));
+                tv[t] = xor4(row[t] < p - 1 ? accP[t] : zero, lds(X(sm.xb, s, col[t])));
             }
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            #pragma unroll
+            for (int t = 0; t < kItems; ++t)
+                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), tv[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             // D_b (lifted) = (1 + x^z)^(-1) T: sum of x^m T over the table's exponent set
             const uint64_t mask = c_inv[p][T.b - T.a];
+            #pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p) continue;
                 uint4 d = zero;
@@ -510,12 +547,13 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
                     m &= m - 1;
                     int s = row[t] - e;
                     if (s < 0) s += p;
-                    d = xor4(d, lds(X(sm.xp, s, col[t])));
+                    d = xor4(d, lds(X(sm.xb, s, col[t])));
                 }
                 accQ[t] = d;
                 if (row[t] == p - 1) sts(sm.fold + col[t] * 16, d);
             }
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            #pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p - 1) continue;
                 const uint4 dj = xor4(accQ[t], lds(sm.fold + col[t] * 16));
@@ -542,7 +580,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
     uint8_t *copy_dst = nullptr;  // small write: data strip a of the tile
     uint32_t ep_phase = 0;
     int p = 3;
-    uint32_t w = 16, pw = 48;
+    uint32_t pitch = 16, pw = 48;
     RingPos pos;
 
     for (;;) {
@@ -571,21 +609,21 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
             copy_dst = T.base + static_cast<uint64_t>(T.a) * J.strip_stride;
             if (T.cls == E_ENC) T.b = J.n;  // P and Q are strips N and N+1
             p = static_cast<int>(T.p);
-            w = T.w;
-            pw = p * w;
+            pitch = tv.y & 0xffffu;
+            pw = p * pitch;
             for (int t = 0; t < kItems; ++t) {
                 const int item = ctid + t * kConsumers;
                 const int r = item / static_cast<int>(T.nvec);
                 row[t] = r < p ? r : 0x7fff;
                 col[t] = item - r * static_cast<int>(T.nvec);
-                off[t] = r * w + col[t] * 16;
+                off[t] = r * pitch + col[t] * 16;
                 accP[t] = make_uint4(0, 0, 0, 0);
                 accQ[t] = make_uint4(0, 0, 0, 0);
             }
         }
         const uint32_t stage = ring0 + pos.slot * slot_bytes;
         const int rot = (hv.x >> 8) & 0xff;
-        const uint32_t rotw = rot * w;
+        const uint32_t rotw = rot * pitch;
         const bool fp = flags & F_P, fq = flags & F_Q, fc = flags & F_COPY;
 #pragma unroll
         for (int t = 0; t < kItems; ++t) {

@@ -2,6 +2,7 @@
 // tile engine (rcg_engine.cu) of librcg.  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,32 +15,37 @@ namespace rcg {
 // accumulator (rows 0..p-1, row p-1 being the imaginary row of the lift to
 // F2[x]/(x^p - 1)).  A tile of W bytes of a p-row stripe has p * W/16 items.
 #ifndef RCG_CONSUMER_WARPS
-#define RCG_CONSUMER_WARPS 16
+#define RCG_CONSUMER_WARPS 15
 #endif
 #ifndef RCG_ITEMS
-#define RCG_ITEMS 2
+#define RCG_ITEMS 4
 #endif
 constexpr int kConsumerWarps = RCG_CONSUMER_WARPS;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;
 constexpr int kItems = RCG_ITEMS;
-constexpr int kMaxItems = kItems * kConsumers;  // items per tile (1024 by default)
+constexpr int kMaxItems = kItems * kConsumers;  // items per tile (2048 by default)
+constexpr uint32_t kMaxTileBytes = 2048;        // a TMA box row is at most 256 8-byte elements
 constexpr int kMaxSlots = 32;
 constexpr int kMaxP = 61;
 constexpr uint32_t kMaxSlotBytes = 32 * 1024;
 
 // Dynamic shared memory: control block, exchange buffers, then the ring.
 constexpr uint32_t kCtlBytes = 2048;                       // barriers + slot headers
-constexpr uint32_t kXBytes = kMaxItems * 16;               // one p x W exchange buffer
-constexpr uint32_t kFoldBytes = ((kMaxItems / 3) * 16 + 127) / 128 * 128;  // one row of W bytes
-constexpr uint32_t kFixedSmem = kCtlBytes + 2 * kXBytes + kFoldBytes;
+constexpr uint32_t kXBytes = kMaxItems * 16;               // the p x W exchange buffer
+constexpr uint32_t kFoldBytes = kMaxTileBytes;             // one row of W bytes
+constexpr uint32_t kFixedSmem = kCtlBytes + kXBytes + kFoldBytes;
 constexpr uint32_t kSmemLimit = 227 * 1024;
 constexpr uint32_t kRingBytes = kSmemLimit - kFixedSmem;
 
 enum Op : uint8_t { OP_ENCODE = 0, OP_RECOVER = 1, OP_DEGRADED = 2, OP_UPDATE = 3 };
 
 // Device-side job: a run of stripes with one geometry and one operation.
-struct Job {
+// tmap is a 4-D tiled TMA descriptor over (8-byte column, row, strip, stripe)
+// of the job's stripes with a (W/8) x (p-1) x 1 x 1 box: one tensor copy
+// brings a whole strip tile into a ring slot.
+struct alignas(128) Job {
+    CUtensorMap tmap;
     uint8_t *base;           // stripe 0 of this job (first_stripe already applied)
     uint8_t *aux;            // update: new strips (read); degraded read: output (written)
     const uint8_t *pairs;    // recover: per-stripe (i, j) bytes, or nullptr
@@ -51,7 +57,8 @@ struct Job {
     uint32_t W;              // tile width, bytes
     uint32_t tiles_per_stripe;
     uint8_t p, n, op, i, j;
-    uint8_t pad[3];
+    uint8_t use_tmap;        // 0: the driver refused this layout; fall back to row copies
+    uint8_t pad[2];
 };
 
 struct LaunchParams {
@@ -69,13 +76,15 @@ struct LaunchParams {
 
 // Header of a batch descriptor table: the graph-replayed batch kernel reads
 // its sizes from here so the captured kernel node never changes.
-struct BatchHeader {
+struct alignas(128) BatchHeader {
     uint64_t total_tiles;
     uint32_t n_jobs;
     uint32_t slot_bytes;
     uint32_t n_slots;
-    uint32_t pad[3];
+    uint32_t pad[27];
 };
+static_assert(sizeof(BatchHeader) == 128, "the job table after the header stays 128-byte aligned");
+static_assert(sizeof(Job) % 128 == 0, "jobs keep their tensor maps 128-byte aligned");
 
 struct Plan {
     uint32_t W, tiles_per_stripe, slot_bytes, n_slots;

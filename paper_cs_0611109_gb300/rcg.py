@@ -42,7 +42,8 @@ class rcg_job(ctypes.Structure):
 
 
 class rcg_plan_info(ctypes.Structure):
-    _fields_ = [("tile_bytes", _u32), ("tiles_per_stripe", _u32), ("slot_bytes", _u32), ("n_slots", _u32)]
+    _fields_ = [("tile_bytes", _u32), ("tiles_per_stripe", _u32), ("slot_bytes", _u32), ("n_slots", _u32),
+                ("max_items", _u32), ("smem_bytes", _u32)]
 
 
 EXPORTS = {

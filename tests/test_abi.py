@@ -74,14 +74,12 @@ def test_inverse_table_rejects_non_primes(rcg):
 def test_plan_covers_the_row(rcg, p, C):
     pl = rcg.rcg_plan(p, C)
     W, T = pl["tile_bytes"], pl["tiles_per_stripe"]
-    assert W % 16 == 0 and W > 0
+    assert W % 16 == 0 and 0 < W <= 2048      # a TMA box row is at most 256 8-byte elements
     assert (T - 1) * W < C <= T * W          # tiles cover the row, the last one is non-empty
-    assert p * (W // 16) <= 1024              # items per tile fit the consumers
+    assert p * (W // 16) <= pl["max_items"]   # items per tile fit the consumers
     assert (p - 1) * W <= pl["slot_bytes"] and pl["slot_bytes"] % 128 == 0
     assert 2 <= pl["n_slots"] <= 32
-    # shared memory: control block, two p x W exchange buffers, one fold row, the ring
-    fixed = 2048 + 2 * 1024 * 16 + ((1024 // 3) * 16 + 127) // 128 * 128
-    assert pl["n_slots"] * pl["slot_bytes"] + fixed <= 227 * 1024
+    assert pl["n_slots"] * pl["slot_bytes"] < pl["smem_bytes"] <= 227 * 1024
 
 
 def test_plan_rejects_bad_geometry(rcg):
