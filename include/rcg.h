@@ -95,6 +95,14 @@ rcg_status rcg_destroy(rcg_ctx *ctx);
  * returns. */
 rcg_status rcg_set_timeout(rcg_ctx *ctx, uint64_t timeout_ns);
 
+/* How the engine moves strip tiles into shared memory.  RCG_COPY_AUTO (the
+ * default): one 4-D tensor copy per strip tile wherever the driver accepts a
+ * tensor map for the layout, per-row 1-D bulk copies otherwise.
+ * RCG_COPY_ROWS: always per-row bulk copies.  Results are identical. */
+#define RCG_COPY_AUTO 0
+#define RCG_COPY_ROWS 1
+rcg_status rcg_set_copy_mode(rcg_ctx *ctx, int mode);
+
 /* Synchronise the device and read, then clear, the device status word.
  * Returns RCG_EDEVICE when any bit was set (then *code holds the bits). */
 rcg_status rcg_last_device_status(rcg_ctx *ctx, uint32_t *code);

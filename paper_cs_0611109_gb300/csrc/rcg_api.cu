@@ -45,6 +45,7 @@ struct rcg_ctx {
     int sm_count = 0;
     uint32_t *status = nullptr;
     uint64_t timeout_ns = 2000000000ull;
+    int copy_mode = RCG_COPY_AUTO;
     uint64_t next_ticket = 1;
     BatchSlot slots[kBatchRing];
 };
@@ -136,8 +137,8 @@ void attach_tensor_map(Job &J, const Geo &g) {
     J.use_tmap = r == CUDA_SUCCESS ? 1 : 0;
 }
 
-Job base_job(const rcg_layout *L, const Geo &g, uint64_t first_stripe, uint64_t n_stripes,
-             const Plan &pl) {
+Job base_job(const rcg_ctx *ctx, const rcg_layout *L, const Geo &g, uint64_t first_stripe,
+             uint64_t n_stripes, const Plan &pl) {
     Job J;
     memset(&J, 0, sizeof(J));
     J.base = static_cast<uint8_t *>(L->base) + first_stripe * g.st;
@@ -150,7 +151,7 @@ Job base_job(const rcg_layout *L, const Geo &g, uint64_t first_stripe, uint64_t 
     J.tiles_per_stripe = pl.tiles_per_stripe;
     J.p = static_cast<uint8_t>(g.p);
     J.n = static_cast<uint8_t>(g.N);
-    attach_tensor_map(J, g);
+    if (ctx->copy_mode == RCG_COPY_AUTO) attach_tensor_map(J, g);
     return J;
 }
 
@@ -305,6 +306,12 @@ rcg_status rcg_destroy(rcg_ctx *ctx) {
     return RCG_OK;
 }
 
+rcg_status rcg_set_copy_mode(rcg_ctx *ctx, int mode) {
+    if (!ctx || (mode != RCG_COPY_AUTO && mode != RCG_COPY_ROWS)) return RCG_EINVAL;
+    ctx->copy_mode = mode;
+    return RCG_OK;
+}
+
 rcg_status rcg_set_timeout(rcg_ctx *ctx, uint64_t timeout_ns) {
     if (!ctx || timeout_ns == 0) return RCG_EINVAL;
     ctx->timeout_ns = timeout_ns;
@@ -334,7 +341,7 @@ rcg_status rcg_encode(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe, 
     if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
     Plan pl;
     if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
-    Job J = base_job(L, g, first_stripe, n_stripes, pl);
+    Job J = base_job(ctx, L, g, first_stripe, n_stripes, pl);
     J.op = OP_ENCODE;
     DeviceGuard guard(ctx->device);
     return launch_single(ctx, J, pl, static_cast<cudaStream_t>(stream));
@@ -349,7 +356,7 @@ rcg_status rcg_recover(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint3
     if (!(i < j && j <= g.N + 1)) return RCG_EINVAL;
     Plan pl;
     if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
-    Job J = base_job(L, g, stripe, 1, pl);
+    Job J = base_job(ctx, L, g, stripe, 1, pl);
     J.op = OP_RECOVER;
     J.i = static_cast<uint8_t>(i);
     J.j = static_cast<uint8_t>(j);
@@ -367,7 +374,7 @@ rcg_status rcg_recover_many(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_st
     if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
     Plan pl;
     if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
-    Job J = base_job(L, g, first_stripe, n_stripes, pl);
+    Job J = base_job(ctx, L, g, first_stripe, n_stripes, pl);
     J.op = OP_RECOVER;
     J.pairs = pairs;
     DeviceGuard guard(ctx->device);
@@ -385,7 +392,7 @@ rcg_status rcg_update(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32
     if (ars < g.C || (ars & 15)) return RCG_EINVAL;
     Plan pl;
     if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
-    Job J = base_job(L, g, stripe, 1, pl);
+    Job J = base_job(ctx, L, g, stripe, 1, pl);
     J.op = OP_UPDATE;
     J.i = static_cast<uint8_t>(i);
     J.aux = static_cast<uint8_t *>(const_cast<void *>(new_strip));
@@ -406,7 +413,7 @@ rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe,
     if (ors < g.C || (ors & 15)) return RCG_EINVAL;
     Plan pl;
     if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
-    Job J = base_job(L, g, stripe, 1, pl);
+    Job J = base_job(ctx, L, g, stripe, 1, pl);
     J.op = OP_DEGRADED;
     J.j = static_cast<uint8_t>(j);
     J.aux = static_cast<uint8_t *>(out);
@@ -418,13 +425,13 @@ rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe,
 
 // ================================================================= batches
 
-static rcg_status build_job(const rcg_job &in, Job *out, Plan *pl) {
+static rcg_status build_job(const rcg_ctx *ctx, const rcg_job &in, Job *out, Plan *pl) {
     Geo g;
     rcg_status st = check_layout(&in.layout, &g);
     if (st) return st;
     if (in.n_stripes == 0 || in.n_stripes > 0x7fffffffull) return RCG_EINVAL;
     if (!make_plan(g.p, g.C, pl)) return RCG_EINVAL;
-    Job J = base_job(&in.layout, g, in.first_stripe, in.n_stripes, *pl);
+    Job J = base_job(ctx, &in.layout, g, in.first_stripe, in.n_stripes, *pl);
     const uint64_t ars = in.aux_row_stride ? in.aux_row_stride : g.C;
     const uint64_t ass = in.aux_stripe_stride ? in.aux_stripe_stride : (g.p - 1) * ars;
     switch (in.op) {
@@ -519,7 +526,7 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
     uint32_t slot_bytes = 0;
     for (uint32_t k = 0; k < n_jobs; ++k) {
         Plan pl;
-        rcg_status st = build_job(jobs[k], &table[k], &pl);
+        rcg_status st = build_job(ctx, jobs[k], &table[k], &pl);
         if (st) return st;
         table[k].tile_begin = total;
         total += static_cast<uint64_t>(table[k].n_stripes) * table[k].tiles_per_stripe;

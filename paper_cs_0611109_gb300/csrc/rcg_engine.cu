@@ -342,7 +342,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
         const uint64_t aux_rs = J.aux_row_stride;
         // rows sit W bytes apart in a slot; a tensor copy always lands the full
         // W-wide box (columns past C are zero-filled), row copies land w bytes
-        const uint32_t tx = use_tmap ? rows * W : rows * w;
+        const uint32_t tx_tensor = rows * W, tx_rows = rows * w;
         uint32_t emitted = 0;
         for (uint32_t k = 0; k < N + 3; ++k) {
             const uint8_t fl = strip_role(cls, update, k, N, a, b, &rot);
@@ -352,6 +352,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
                 break;
             }
             const uint32_t full = smem_addr(&sm.full[pos.slot]);
+            const bool tensor = use_tmap && k < N + 2;
             if (lane == 0) {
                 SlotHdr h;
                 h.flags = fl | (emitted == 0 ? F_FIRST : 0) | (emitted + 1 == count ? F_LAST : 0);
@@ -366,11 +367,11 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
                 h.b = static_cast<uint8_t>(b);
                 h.pitch = static_cast<uint16_t>(W);
                 sm.hdr[pos.slot] = h;
-                mbar_arrive_tx(full, tx);
+                mbar_arrive_tx(full, tensor ? tx_tensor : tx_rows);
             }
             __syncwarp();
             const uint32_t dst = ring0 + pos.slot * slot_bytes;
-            if (use_tmap && k < N + 2) {
+            if (tensor) {
                 // one tensor copy: box (W/8 x p-1) at column c0, strip k, stripe
                 if (lane == 0)
                     tensor_load_4d(dst, &J.tmap, static_cast<int>(c0 >> 3), 0, static_cast<int>(k),

@@ -17,6 +17,7 @@ from .build import LIB
 RCG_OK, RCG_EINVAL, RCG_ENOMEM, RCG_ECUDA, RCG_ETIMEOUT, RCG_EBUSY, RCG_EUNSUPPORTED, RCG_EDEVICE = range(8)
 RCG_DEV_TIMEOUT, RCG_DEV_BADPAIR, RCG_DEV_BADJOB = 1, 2, 4
 RCG_OP_ENCODE, RCG_OP_RECOVER, RCG_OP_DEGRADED_READ, RCG_OP_UPDATE = range(4)
+RCG_COPY_AUTO, RCG_COPY_ROWS = 0, 1
 
 _u32, _u64, _vp, _int = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
 
@@ -50,6 +51,7 @@ EXPORTS = {
     "rcg_create": (_int, [_int, ctypes.POINTER(_vp)]),
     "rcg_destroy": (_int, [_vp]),
     "rcg_set_timeout": (_int, [_vp, _u64]),
+    "rcg_set_copy_mode": (_int, [_vp, _int]),
     "rcg_last_device_status": (_int, [_vp, ctypes.POINTER(_u32)]),
     "rcg_status_str": (ctypes.c_char_p, [_int]),
     "rcg_abi_version": (_u32, []),
@@ -145,6 +147,10 @@ def rcg_destroy(ctx: int):
 
 def rcg_set_timeout(ctx: int, timeout_ns: int):
     _check(lib().rcg_set_timeout(ctx, timeout_ns), "rcg_set_timeout")
+
+
+def rcg_set_copy_mode(ctx: int, mode: int):
+    _check(lib().rcg_set_copy_mode(ctx, mode), "rcg_set_copy_mode")
 
 
 def rcg_last_device_status(ctx: int) -> int:
@@ -270,6 +276,9 @@ class Context:
 
     def set_timeout(self, timeout_ns):
         rcg_set_timeout(self.handle, timeout_ns)
+
+    def set_copy_mode(self, mode):
+        rcg_set_copy_mode(self.handle, mode)
 
     def last_device_status(self) -> int:
         return rcg_last_device_status(self.handle)

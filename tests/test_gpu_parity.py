@@ -216,6 +216,29 @@ def test_degraded_read_matches_oracle(rcg, ctx, oracle, p, N, C):
     check_clean(ctx)
 
 
+@pytest.mark.parametrize("p,N,C,S", [(59, 58, 528, 2), (13, 12, 4096 + 48, 2), (5, 4, 1024, 3)])
+def test_row_copy_path_matches_oracle(rcg, oracle, p, N, C, S):
+    # the per-row bulk-copy path (used where the driver refuses a tensor map)
+    host = host_stripes(950 + p, p, N, C, S)
+    want = host.copy()
+    oracle.encode(p, N, C, want, S)
+    with rcg.Context(0) as c:
+        c.set_copy_mode(rcg.RCG_COPY_ROWS)
+        buf = dev(host)
+        L = rcg.make_layout(buf, p, N, C)
+        c.encode(L, 0, S)
+        torch.cuda.synchronize()
+        assert np.array_equal(buf.cpu().numpy(), want)
+        pairs = inputs.random_pairs(3, N, S, "any")
+        buf[0, pairs[0, 0]] = POISON_I
+        c.recover_many(L, 0, S, dev(pairs))
+        new = inputs.random_bytes(77, (p - 1) * C).reshape(p - 1, C)
+        c.update(L, S - 1, N - 1, dev(new))
+        oracle.update(p, N, C, want, S - 1, N - 1, new)
+        assert c.last_device_status() == 0
+        assert np.array_equal(buf.cpu().numpy(), want)
+
+
 # ------------------------------------------------------------------ batches
 
 def test_batch_mixed_jobs_alone_and_in_the_mix(rcg, ctx, oracle):
