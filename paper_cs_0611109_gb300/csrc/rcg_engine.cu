@@ -182,7 +182,7 @@ struct Smem {
     uint64_t *ep;     // epilogue barrier among consumer warps
     SlotHdr *hdr;     // [kMaxSlots]
     uint8_t *xb;      // exchange buffer [p][nvec] x 16 B
-    uint8_t *fold;    // one row [nvec] x 16 B
+    uint8_t *fold;    // two rows [2][nvec] x 16 B, used alternately by successive tiles
     uint8_t *ring;    // n_slots x slot_bytes
 };
 
@@ -194,7 +194,7 @@ __device__ __forceinline__ Smem carve(uint8_t *smem) {
     s.hdr = reinterpret_cast<SlotHdr *>(smem + 1024);
     s.xb = smem + kCtlBytes;
     s.fold = s.xb + kXBytes;
-    s.ring = s.fold + kFoldBytes;
+    s.ring = s.fold + 2 * kFoldBytes;
     return s;
 }
 
@@ -204,9 +204,12 @@ __device__ __forceinline__ void set_status(uint32_t *status, uint32_t bits) {
 
 // Role of strip k (0..N-1 data, N = P, N+1 = Q, N+2 = the small write's new
 // strip) in a tile of class `cls` with pair (a, b): returns flags (0 = not
-// read) and the rotation for Q.
+// read) and the rotation for Q.  For the two classes whose result involves
+// x^(-a) dQ (two data strips, data + P) the rotation is applied while
+// accumulating: strip k is weighted by x^(k-a) and Q by x^(-a) = x^(p-a), so
+// the lifted accumulator holds x^(-a) dQ directly.
 __device__ __forceinline__ uint8_t strip_role(uint8_t cls, bool update, uint32_t k, uint32_t N,
-                                              uint32_t a, uint32_t b, uint32_t *rot) {
+                                              uint32_t a, uint32_t b, uint32_t p, uint32_t *rot) {
     *rot = 0;
     const bool data = k < N;
     if (update) {  // old d_a, P, Q, new d_a (last, so d_a is read before it is overwritten)
@@ -216,18 +219,19 @@ __device__ __forceinline__ uint8_t strip_role(uint8_t cls, bool update, uint32_t
         if (k == N + 2) { *rot = a; return F_P | F_Q | F_COPY; }
         return 0;
     }
+    const uint32_t back = (k + p - a) % p;  // k - a (mod p)
     switch (cls) {
         case E_ENC:
             if (data) { *rot = k; return F_P | F_Q; }
             return 0;
         case E_DD:
-            if (data && k != a && k != b) { *rot = k; return F_P | F_Q; }
+            if (data && k != a && k != b) { *rot = back; return F_P | F_Q; }
             if (k == N) return F_P;
-            if (k == N + 1) return F_Q;
+            if (k == N + 1) { *rot = (p - a) % p; return F_Q; }
             return 0;
         case E_DP:
-            if (data && k != a) { *rot = k; return F_P | F_Q; }
-            if (k == N + 1) return F_Q;
+            if (data && k != a) { *rot = back; return F_P | F_Q; }
+            if (k == N + 1) { *rot = (p - a) % p; return F_Q; }
             return 0;
         case E_DQ:
             if (data && k != a) { *rot = k; return F_P | F_Q; }
@@ -334,7 +338,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
 
         uint32_t count = 0, rot;
         for (uint32_t k = 0; k < N + 3; ++k)
-            if (strip_role(cls, update, k, N, a, b, &rot)) ++count;
+            if (strip_role(cls, update, k, N, a, b, p, &rot)) ++count;
 
         const uint8_t *stripe_base = J.base + stripe * J.stripe_stride + c0;
         const uint8_t *aux_base = J.aux + stripe * J.aux_stripe_stride + c0;
@@ -345,7 +349,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
         const uint32_t tx_tensor = rows * W, tx_rows = rows * w;
         uint32_t emitted = 0;
         for (uint32_t k = 0; k < N + 3; ++k) {
-            const uint8_t fl = strip_role(cls, update, k, N, a, b, &rot);
+            const uint8_t fl = strip_role(cls, update, k, N, a, b, p, &rot);
             if (!fl) continue;
             if (!mbar_wait(smem_addr(&sm.empty[pos.slot]), pos.phase ^ 1u, timeout)) {
                 ok = false;
@@ -433,29 +437,34 @@ __device__ __forceinline__ bool ep_sync(const Smem &sm, uint32_t &phase, uint64_
     return ok;
 }
 
+// Buffer discipline (no barrier on entry): every read of the exchange buffer
+// happens before a barrier all consumers pass before the next tile's writes;
+// the fold row alternates between two buffers, so a tile's fold writes never
+// meet the previous fold-using tile's reads, which sit after its own barrier.
 __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kItems],
                          uint4 (&accQ)[kItems], const int (&row)[kItems],
-                         const int (&col)[kItems], uint32_t &ep_phase, uint64_t timeout_ns) {
+                         const int (&col)[kItems], uint32_t &ep_phase, uint32_t &fold_par,
+                         uint64_t timeout_ns) {
     const int p = static_cast<int>(T.p);
     const uint32_t nv = T.nvec;
     auto X = [&](uint8_t *buf, int r, int c) { return buf + (static_cast<size_t>(r) * nv + c) * 16; };
     auto strip_row = [&](uint32_t k, int r, int c) {
         return T.base + k * T.strip_stride + static_cast<uint64_t>(r) * T.row_stride + c * 16;
     };
-    // previous tile's readers of the exchange buffers are done
-    if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+    uint8_t *const fold = sm.fold + fold_par * kFoldBytes;
+    if (T.cls != E_DEGP) fold_par ^= 1u;
 
     switch (T.cls) {
         case E_ENC:
         case E_DEGQ: {
             #pragma unroll
             for (int t = 0; t < kItems; ++t)
-                if (row[t] == p - 1) sts(sm.fold + col[t] * 16, accQ[t]);
+                if (row[t] == p - 1) sts(fold + col[t] * 16, accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             #pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p - 1) continue;
-                const uint4 q = xor4(accQ[t], lds(sm.fold + col[t] * 16));
+                const uint4 q = xor4(accQ[t], lds(fold + col[t] * 16));
                 if (T.cls == E_ENC) {
                     stg(strip_row(T.b, row[t], col[t]), accP[t]);      // P = strip N
                     stg(strip_row(T.b + 1, row[t], col[t]), q);        // Q = strip N+1
@@ -472,20 +481,15 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
                     stg(T.out + static_cast<uint64_t>(row[t]) * T.out_row_stride + col[t] * 16, accP[t]);
             break;
         }
-        case E_DP: {  // D_a = x^(-a) dQ (reduced), P = accP + D_a
-            #pragma unroll
+        case E_DP: {  // accQ = x^(-a) dQ (lifted): D_a = fold(accQ), P = accP + D_a
+#pragma unroll
             for (int t = 0; t < kItems; ++t)
-                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), accQ[t]);
+                if (row[t] == p - 1) sts(fold + col[t] * 16, accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
-            const int a = T.a;
-            #pragma unroll
+#pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p - 1) continue;
-                int s = row[t] + a;
-                if (s >= p) s -= p;
-                int f = p - 1 + a;
-                if (f >= p) f -= p;
-                const uint4 d = xor4(lds(X(sm.xb, s, col[t])), lds(X(sm.xb, f, col[t])));
+                const uint4 d = xor4(accQ[t], lds(fold + col[t] * 16));
                 stg(strip_row(T.a, row[t], col[t]), d);
                 stg(strip_row(T.b, row[t], col[t]), xor4(accP[t], d));
             }
@@ -504,41 +508,28 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
                 int s = row[t] - a;
                 if (s < 0) s += p;
                 accQ[t] = xor4(accQ[t], lds(X(sm.xb, s, col[t])));
-                if (row[t] == p - 1) sts(sm.fold + col[t] * 16, accQ[t]);
+                if (row[t] == p - 1) sts(fold + col[t] * 16, accQ[t]);
             }
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             #pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p - 1) continue;
                 stg(strip_row(T.a, row[t], col[t]), accP[t]);
-                stg(strip_row(T.b, row[t], col[t]), xor4(accQ[t], lds(sm.fold + col[t] * 16)));
+                stg(strip_row(T.b, row[t], col[t]), xor4(accQ[t], lds(fold + col[t] * 16)));
             }
             break;
         }
         case E_DD: {
+            // accQ = x^(-a) dQ (lifted), so T = dP + x^(-a) dQ is formed in place
+            // (row p-1 of dP is zero); D_b = (1 + x^z)^(-1) T needs every row of T.
             const uint4 zero = make_uint4(0, 0, 0, 0);
-            const int a = T.a;
-            #pragma unroll
+#pragma unroll
             for (int t = 0; t < kItems; ++t)
-                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), accQ[t]);
+                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), row[t] < p - 1 ? xor4(accP[t], accQ[t]) : accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
-            // T = dP + x^(-a) dQ (lifted; row p-1 of dP is zero)
-            uint4 tv[kItems];
-            #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
-                if (row[t] >= p) continue;
-                int s = row[t] + a;
-                if (s >= p) s -= p;
-                tv[t] = xor4(row[t] < p - 1 ? accP[t] : zero, lds(X(sm.xb, s, col[t])));
-            }
-            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
-            #pragma unroll
-            for (int t = 0; t < kItems; ++t)
-                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), tv[t]);
-            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
-            // D_b (lifted) = (1 + x^z)^(-1) T: sum of x^m T over the table's exponent set
+            // D_b (lifted) = sum over the table's exponent set of x^m T
             const uint64_t mask = c_inv[p][T.b - T.a];
-            #pragma unroll
+#pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p) continue;
                 uint4 d = zero;
@@ -551,13 +542,13 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
                     d = xor4(d, lds(X(sm.xb, s, col[t])));
                 }
                 accQ[t] = d;
-                if (row[t] == p - 1) sts(sm.fold + col[t] * 16, d);
+                if (row[t] == p - 1) sts(fold + col[t] * 16, d);
             }
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
-            #pragma unroll
+#pragma unroll
             for (int t = 0; t < kItems; ++t) {
                 if (row[t] >= p - 1) continue;
-                const uint4 dj = xor4(accQ[t], lds(sm.fold + col[t] * 16));
+                const uint4 dj = xor4(accQ[t], lds(fold + col[t] * 16));
                 stg(strip_row(T.b, row[t], col[t]), dj);
                 stg(strip_row(T.a, row[t], col[t]), xor4(dj, accP[t]));
             }
@@ -579,7 +570,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
     uint32_t off[kItems];   // byte offset of the item's own row in a slot
     Tile T = {};
     uint8_t *copy_dst = nullptr;  // small write: data strip a of the tile
-    uint32_t ep_phase = 0;
+    uint32_t ep_phase = 0, fold_par = 0;
     int p = 3;
     uint32_t pitch = 16, pw = 48;
     RingPos pos;
@@ -646,7 +637,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
         if (lane == 0) mbar_arrive(smem_addr(&sm.empty[pos.slot]));
         pos.next(n_slots);
         if (flags & F_LAST) {
-            if (!epilogue(sm, T, accP, accQ, row, col, ep_phase, timeout)) {
+            if (!epilogue(sm, T, accP, accQ, row, col, ep_phase, fold_par, timeout)) {
                 if (lane == 0) set_status(prm.status, RCG_DEV_TIMEOUT);
                 return;
             }

@@ -34,7 +34,7 @@ constexpr uint32_t kMaxSlotBytes = 32 * 1024;
 constexpr uint32_t kCtlBytes = 2048;                       // barriers + slot headers
 constexpr uint32_t kXBytes = kMaxItems * 16;               // the p x W exchange buffer
 constexpr uint32_t kFoldBytes = kMaxTileBytes;             // one row of W bytes
-constexpr uint32_t kFixedSmem = kCtlBytes + kXBytes + kFoldBytes;
+constexpr uint32_t kFixedSmem = kCtlBytes + kXBytes + 2 * kFoldBytes;  // two fold rows
 constexpr uint32_t kSmemLimit = 227 * 1024;
 constexpr uint32_t kRingBytes = kSmemLimit - kFixedSmem;
 
