@@ -168,7 +168,8 @@ rcg_status launch_single(rcg_ctx *ctx, const Job &J, const Plan &pl, cudaStream_
     prm.status = ctx->status;
     prm.timeout_ns = ctx->timeout_ns;
     if (prm.total_tiles == 0) return RCG_OK;
-    const uint64_t grid = std::min<uint64_t>(prm.total_tiles, static_cast<uint64_t>(ctx->sm_count));
+    const uint64_t grid =
+        std::min<uint64_t>(prm.total_tiles, static_cast<uint64_t>(ctx->sm_count) * kCtasPerSm);
     return from_cuda(launch_engine(prm, static_cast<int>(grid), stream));
 }
 
@@ -487,7 +488,8 @@ static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t jobs) {
     if (e == cudaSuccess) {
         cudaError_t e1 = cudaMemcpyAsync(s.dev, s.host, bytes, cudaMemcpyHostToDevice, s.capture);
         cudaError_t e2 = cudaMemsetAsync(s.counter, 0, sizeof(unsigned long long), s.capture);
-        cudaError_t e3 = launch_batch(s.dev, ctx->status, s.counter, ctx->timeout_ns, ctx->sm_count, s.capture);
+        cudaError_t e3 = launch_batch(s.dev, ctx->status, s.counter, ctx->timeout_ns,
+                                      ctx->sm_count * kCtasPerSm, s.capture);
         e = cudaStreamEndCapture(s.capture, &graph);
         if (e1 != cudaSuccess) { e = e1; where = "captured table copy"; }
         else if (e2 != cudaSuccess) { e = e2; where = "captured counter reset"; }

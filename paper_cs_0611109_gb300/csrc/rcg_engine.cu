@@ -68,6 +68,20 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes or the hint (ns) passes, instead of polling.
+__device__ __forceinline__ bool mbar_test_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -80,7 +94,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t timeout_ns) {
     if (mbar_test(bar, parity)) return true;
     const uint64_t t0 = global_ns();
-    while (!mbar_test(bar, parity)) {
+    while (!mbar_test_sleep(bar, parity, 100000u)) {
         if (global_ns() - t0 > timeout_ns) return false;
     }
     return true;
@@ -647,7 +661,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
 
 // ------------------------------------------------------------------ kernel
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
     rcg_tile_engine(const __grid_constant__ LaunchParams prm, const BatchHeader *bh) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const Smem sm = carve(smem_raw);

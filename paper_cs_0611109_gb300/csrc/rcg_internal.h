@@ -20,6 +20,10 @@ namespace rcg {
 #ifndef RCG_ITEMS
 #define RCG_ITEMS 4
 #endif
+#ifndef RCG_CTAS_PER_SM
+#define RCG_CTAS_PER_SM 1
+#endif
+constexpr int kCtasPerSm = RCG_CTAS_PER_SM;
 constexpr int kConsumerWarps = RCG_CONSUMER_WARPS;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;
@@ -35,7 +39,8 @@ constexpr uint32_t kCtlBytes = 2048;                       // barriers + slot he
 constexpr uint32_t kXBytes = kMaxItems * 16;               // the p x W exchange buffer
 constexpr uint32_t kFoldBytes = kMaxTileBytes;             // one row of W bytes
 constexpr uint32_t kFixedSmem = kCtlBytes + kXBytes + 2 * kFoldBytes;  // two fold rows
-constexpr uint32_t kSmemLimit = 227 * 1024;
+// 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
+constexpr uint32_t kSmemLimit = (228 / kCtasPerSm - 1) * 1024;
 constexpr uint32_t kRingBytes = kSmemLimit - kFixedSmem;
 
 enum Op : uint8_t { OP_ENCODE = 0, OP_RECOVER = 1, OP_DEGRADED = 2, OP_UPDATE = 3 };
