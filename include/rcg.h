@@ -103,6 +103,17 @@ rcg_status rcg_set_timeout(rcg_ctx *ctx, uint64_t timeout_ns);
 #define RCG_COPY_ROWS 1
 rcg_status rcg_set_copy_mode(rcg_ctx *ctx, int mode);
 
+/* How a two-data-strip erasure solves (1 + x^z) D_j = T, z = j - i, where
+ * T = dP + x^(-i) dQ (Section 4.6).  The solution is unique (Lemma 3.1.2), so
+ * both give identical bytes.
+ * RCG_SOLVE_CHAIN (default): lift to F2[x]/(x^p - 1) and walk the rows
+ * p-1, p-1+z, p-1+2z, ... (mod p) once, O(p) row XORs per column.
+ * RCG_SOLVE_TABLE: the paper's closed form D_j = (1 + x^z)^(-1) T with the
+ * per-p table (1 + x^z)^(-1) = sum_{t=0}^{(p-1)/2} x^(2tz), O(p^2/2). */
+#define RCG_SOLVE_CHAIN 0
+#define RCG_SOLVE_TABLE 1
+rcg_status rcg_set_dd_solve(rcg_ctx *ctx, int solve);
+
 /* Synchronise the device and read, then clear, the device status word.
  * Returns RCG_EDEVICE when any bit was set (then *code holds the bits). */
 rcg_status rcg_last_device_status(rcg_ctx *ctx, uint32_t *code);

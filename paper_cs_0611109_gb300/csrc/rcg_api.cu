@@ -46,6 +46,7 @@ struct rcg_ctx {
     uint32_t *status = nullptr;
     uint64_t timeout_ns = 2000000000ull;
     int copy_mode = RCG_COPY_AUTO;
+    int dd_solve = RCG_SOLVE_CHAIN;
     uint64_t next_ticket = 1;
     BatchSlot slots[kBatchRing];
 };
@@ -152,6 +153,7 @@ Job base_job(const rcg_ctx *ctx, const rcg_layout *L, const Geo &g, uint64_t fir
     J.p = static_cast<uint8_t>(g.p);
     J.n = static_cast<uint8_t>(g.N);
     if (ctx->copy_mode == RCG_COPY_AUTO) attach_tensor_map(J, g);
+    J.dd_solve = ctx->dd_solve == RCG_SOLVE_TABLE ? 1 : 0;
     return J;
 }
 
@@ -310,6 +312,12 @@ rcg_status rcg_destroy(rcg_ctx *ctx) {
 rcg_status rcg_set_copy_mode(rcg_ctx *ctx, int mode) {
     if (!ctx || (mode != RCG_COPY_AUTO && mode != RCG_COPY_ROWS)) return RCG_EINVAL;
     ctx->copy_mode = mode;
+    return RCG_OK;
+}
+
+rcg_status rcg_set_dd_solve(rcg_ctx *ctx, int solve) {
+    if (!ctx || (solve != RCG_SOLVE_CHAIN && solve != RCG_SOLVE_TABLE)) return RCG_EINVAL;
+    ctx->dd_solve = solve;
     return RCG_OK;
 }
 

@@ -170,7 +170,8 @@ enum : uint8_t {
     E_DP = 2,    // data strip i and P
     E_DQ = 3,    // data strip i and Q
     E_DEGP = 4,  // degraded read of a data strip or P: out = accP
-    E_DEGQ = 5   // degraded read of Q: out = fold(accQ)
+    E_DEGQ = 5,  // degraded read of Q: out = fold(accQ)
+    E_DDC = 6    // two data strips, solved by the chain along x^z (same result as E_DD)
 };
 
 // Slot header.  The first 16 bytes are read (one 16-byte load) for every
@@ -186,7 +187,8 @@ struct SlotHdr {
     uint8_t p;
     uint8_t a, b;     // the erased pair (a < b), or i / j of the op
     uint16_t pitch;   // bytes between rows in the slot (the job's tile width W)
-    uint8_t pad[10];
+    uint8_t zinv;     // two-data tiles: (b - a)^(-1) mod p
+    uint8_t pad[9];
 };
 static_assert(sizeof(SlotHdr) == 32, "slot header is 32 bytes");
 
@@ -239,6 +241,7 @@ __device__ __forceinline__ uint8_t strip_role(uint8_t cls, bool update, uint32_t
             if (data) { *rot = k; return F_P | F_Q; }
             return 0;
         case E_DD:
+        case E_DDC:
             if (data && k != a && k != b) { *rot = back; return F_P | F_Q; }
             if (k == N) return F_P;
             if (k == N + 1) { *rot = (p - a) % p; return F_Q; }
@@ -340,7 +343,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
                 if (lane == 0) set_status(prm.status, RCG_DEV_BADPAIR);
                 continue;
             }
-            cls = (b < N) ? E_DD : (a == N) ? E_ENC : (b == N) ? E_DP : E_DQ;
+            cls = (b < N) ? (J.dd_solve ? E_DD : E_DDC) : (a == N) ? E_ENC : (b == N) ? E_DP : E_DQ;
         } else if (op == OP_DEGRADED) {
             cls = (b == N + 1) ? E_DEGQ : E_DEGP;
         } else if (update) {
@@ -348,6 +351,12 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
                 if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
                 continue;
             }
+        }
+
+        uint32_t zinv = 0;
+        if (cls == E_DDC) {  // (b - a)^(p-2) mod p, the inverse in Z/p
+            zinv = 1;
+            for (uint32_t e = 0; e + 2 < p; ++e) zinv = zinv * (b - a) % p;
         }
 
         uint32_t count = 0, rot;
@@ -384,6 +393,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
                 h.a = static_cast<uint8_t>(a);
                 h.b = static_cast<uint8_t>(b);
                 h.pitch = static_cast<uint16_t>(W);
+                h.zinv = static_cast<uint8_t>(zinv);
                 sm.hdr[pos.slot] = h;
                 mbar_arrive_tx(full, tensor ? tx_tensor : tx_rows);
             }
@@ -439,7 +449,7 @@ struct Tile {
     uint8_t *out;       // degraded read output + c0 (stripe applied)
     uint64_t strip_stride, row_stride, out_row_stride;
     uint32_t p, nvec, w;
-    uint8_t cls, a, b;
+    uint8_t cls, a, b, zinv;
 };
 
 // Epilogue barrier among the consumer warps (bounded).
@@ -533,6 +543,45 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
             }
             break;
         }
+        case E_DDC: {
+            // (1 + x^z) D = T in R, z = b - a.  Lifted to F2[x]/(x^p - 1) the
+            // solution with D[p-1] = 0 satisfies D[r] + D[r-z] = T[r] + c, where
+            // c (the XOR of all p rows of T) makes T + c*f vanish at x = 1.
+            // One thread per column walks r_t = p-1 + t z (t = 1..p-1), turning
+            // T into its prefix XOR E_t in place; then D[r_t] = E_t + (t odd) c.
+            const uint4 zero = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int t = 0; t < kItems; ++t)
+                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), row[t] < p - 1 ? xor4(accP[t], accQ[t]) : accQ[t]);
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            const int z = T.b - T.a;
+            const int ctid = static_cast<int>(threadIdx.x) - 32;
+            if (ctid < static_cast<int>(nv)) {
+                uint4 e = zero;
+                int r = p - 1;
+                for (int t = 1; t < p; ++t) {
+                    r += z;
+                    if (r >= p) r -= p;
+                    uint8_t *cell = X(sm.xb, r, ctid);
+                    e = xor4(e, lds(cell));
+                    sts(cell, e);
+                }
+                sts(fold + ctid * 16, xor4(e, lds(X(sm.xb, p - 1, ctid))));  // c
+            }
+            if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
+            // chain position of row r: r = p-1 + t z (mod p)  =>  t = (r+1) z^-1 (mod p)
+            const int zinv = T.zinv;
+#pragma unroll
+            for (int t = 0; t < kItems; ++t) {
+                if (row[t] >= p - 1) continue;
+                const int pos = ((row[t] + 1) * zinv) % p;
+                uint4 dj = lds(X(sm.xb, row[t], col[t]));
+                if (pos & 1) dj = xor4(dj, lds(fold + col[t] * 16));
+                stg(strip_row(T.b, row[t], col[t]), dj);
+                stg(strip_row(T.a, row[t], col[t]), xor4(dj, accP[t]));
+            }
+            break;
+        }
         case E_DD: {
             // accQ = x^(-a) dQ (lifted), so T = dP + x^(-a) dQ is formed in place
             // (row p-1 of dP is zero); D_b = (1 + x^z)^(-1) T needs every row of T.
@@ -616,6 +665,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
             if (T.cls == E_ENC) T.b = J.n;  // P and Q are strips N and N+1
             p = static_cast<int>(T.p);
             pitch = tv.y & 0xffffu;
+            T.zinv = static_cast<uint8_t>(tv.y >> 16);
             pw = p * pitch;
             for (int t = 0; t < kItems; ++t) {
                 const int item = ctid + t * kConsumers;

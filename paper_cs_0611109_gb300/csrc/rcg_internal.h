@@ -63,7 +63,8 @@ struct alignas(128) Job {
     uint32_t tiles_per_stripe;
     uint8_t p, n, op, i, j;
     uint8_t use_tmap;        // 0: the driver refused this layout; fall back to row copies
-    uint8_t pad[2];
+    uint8_t dd_solve;        // two-data solve: 0 = chain along x^z, 1 = Section 4.6 table
+    uint8_t pad[1];
 };
 
 struct LaunchParams {

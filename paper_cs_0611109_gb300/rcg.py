@@ -18,6 +18,7 @@ RCG_OK, RCG_EINVAL, RCG_ENOMEM, RCG_ECUDA, RCG_ETIMEOUT, RCG_EBUSY, RCG_EUNSUPPO
 RCG_DEV_TIMEOUT, RCG_DEV_BADPAIR, RCG_DEV_BADJOB = 1, 2, 4
 RCG_OP_ENCODE, RCG_OP_RECOVER, RCG_OP_DEGRADED_READ, RCG_OP_UPDATE = range(4)
 RCG_COPY_AUTO, RCG_COPY_ROWS = 0, 1
+RCG_SOLVE_CHAIN, RCG_SOLVE_TABLE = 0, 1
 
 _u32, _u64, _vp, _int = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
 
@@ -52,6 +53,7 @@ EXPORTS = {
     "rcg_destroy": (_int, [_vp]),
     "rcg_set_timeout": (_int, [_vp, _u64]),
     "rcg_set_copy_mode": (_int, [_vp, _int]),
+    "rcg_set_dd_solve": (_int, [_vp, _int]),
     "rcg_last_device_status": (_int, [_vp, ctypes.POINTER(_u32)]),
     "rcg_status_str": (ctypes.c_char_p, [_int]),
     "rcg_abi_version": (_u32, []),
@@ -151,6 +153,10 @@ def rcg_set_timeout(ctx: int, timeout_ns: int):
 
 def rcg_set_copy_mode(ctx: int, mode: int):
     _check(lib().rcg_set_copy_mode(ctx, mode), "rcg_set_copy_mode")
+
+
+def rcg_set_dd_solve(ctx: int, solve: int):
+    _check(lib().rcg_set_dd_solve(ctx, solve), "rcg_set_dd_solve")
 
 
 def rcg_last_device_status(ctx: int) -> int:
@@ -279,6 +285,9 @@ class Context:
 
     def set_copy_mode(self, mode):
         rcg_set_copy_mode(self.handle, mode)
+
+    def set_dd_solve(self, solve):
+        rcg_set_dd_solve(self.handle, solve)
 
     def last_device_status(self) -> int:
         return rcg_last_device_status(self.handle)

@@ -145,6 +145,28 @@ def test_recover_many_per_stripe_pairs(rcg, ctx, oracle, kind, p, N, C, S):
     assert np.array_equal(got, host)
 
 
+@pytest.mark.parametrize("p,N,C,S", [(13, 12, 4096, 4), (59, 58, 528, 2), (3, 3, 16, 2), (61, 61, 96, 2), (5, 4, 1024, 3)])
+def test_two_data_solves_agree(rcg, oracle, p, N, C, S):
+    # the chain solve and the Section 4.6 table solve give the oracle's bytes
+    host = host_stripes(330 + p, p, N, C, S)
+    oracle.encode(p, N, C, host, S)
+    pairs = inputs.random_pairs(8, N, S, "dd")
+    lost = host.copy()
+    for s, (i, j) in enumerate(pairs):
+        lost[s, i] = POISON_I
+        lost[s, j] = POISON_J
+    want = lost.copy()
+    oracle.recover(p, N, C, want, S, pairs=pairs)
+    assert np.array_equal(want, host)
+    for solve in (rcg.RCG_SOLVE_CHAIN, rcg.RCG_SOLVE_TABLE):
+        with rcg.Context(0) as c:
+            c.set_dd_solve(solve)
+            buf = dev(lost)
+            c.recover_many(rcg.make_layout(buf, p, N, C), 0, S, dev(pairs))
+            assert c.last_device_status() == 0
+            assert np.array_equal(buf.cpu().numpy(), want), solve
+
+
 def test_recover_many_rejects_bad_pairs_on_device(rcg, ctx, oracle):
     p, N, C, S = 5, 4, 64, 4
     host = host_stripes(9, p, N, C, S)
