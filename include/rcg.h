@@ -198,6 +198,39 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
  * finished (the batch keeps running). */
 rcg_status rcg_batch_wait(rcg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns);
 
+/* ------------------------------------------------ no-allocation batches */
+
+/* The paper has no counterpart to this call: it exists for callers that may
+ * not allocate device memory -- a framework whose caching allocator owns all
+ * of the GPU's memory, or a submit path that cannot afford the implicit
+ * device synchronisation of cudaMalloc/cudaFree.
+ *
+ * Runs jobs exactly as rcg_batch_submit does (one persistent launch, same
+ * kernel, same results), but needs no rcg_ctx and allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  Its scratch (the
+ * descriptor table, the tile counter and a fallback status word, about 66 KB)
+ * is one file-scope device array that every GPU loading librcg holds until
+ * the process exits.  The caller passes the inputs and outputs as in
+ * rcg_job, plus optionally status_dev: a caller-owned device word that
+ * receives the RCG_DEV_* bits of this call (OR-ed in; clear it first).  With
+ * status_dev == NULL device-side errors are not reported.
+ *
+ * Limits and behaviour:
+ *  - at most RCG_NOALLOC_MAX_JOBS jobs per call; more is RCG_EINVAL;
+ *  - runs on the current device and the given stream, asynchronously;
+ *  - the first call on a device also sets that device up (looks up the
+ *    scratch array's device address, uploads the inverse tables, sets the
+ *    kernel's shared-memory limit); make that first call before any stream
+ *    capture;
+ *  - every call reuses the same scratch, which keeps the previous call's
+ *    contents (the tile counter is cleared on the stream before each launch):
+ *    calls whose work overlaps on the GPU race on it, so keep them ordered
+ *    (one stream, or events), and do not call it from two host threads at
+ *    once. */
+#define RCG_NOALLOC_MAX_JOBS 256u
+rcg_status rcg_batch_submit_noalloc(const rcg_job *jobs, uint32_t n_jobs, uint32_t *status_dev,
+                                    void *stream);
+
 /* ----------------------------------------------------------- utilities */
 
 /* Fill nbytes of device memory with the seeded test-data stream: word w (8

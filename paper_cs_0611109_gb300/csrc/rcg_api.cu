@@ -618,3 +618,10 @@ rcg_status rcg_fill_random(void *dev, uint64_t nbytes, uint64_t seed, uint64_t b
 }
 
 }  // extern "C"
+
+// Job validation and descriptor for rcg_batch_submit_noalloc (default copy
+// mode and two-data solve; no context).
+bool rcg::noalloc_build_job(const rcg_job &in, Job *out, Plan *pl) {
+    static const rcg_ctx defaults;
+    return build_job(&defaults, in, out, pl) == RCG_OK;
+}

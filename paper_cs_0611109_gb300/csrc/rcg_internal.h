@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/rcg.h"
+
 namespace rcg {
 
 // ---------------------------------------------------------------- geometry
@@ -111,5 +113,9 @@ cudaError_t launch_fill(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte
                         cudaStream_t stream);
 
 void inverse_masks(uint32_t p, uint64_t *masks);
+
+// Host: validate one public job and build its device descriptor with the
+// default copy mode and two-data solve (used by rcg_batch_submit_noalloc).
+bool noalloc_build_job(const rcg_job &in, Job *out, Plan *pl);
 
 }  // namespace rcg

@@ -19,6 +19,7 @@ RCG_DEV_TIMEOUT, RCG_DEV_BADPAIR, RCG_DEV_BADJOB = 1, 2, 4
 RCG_OP_ENCODE, RCG_OP_RECOVER, RCG_OP_DEGRADED_READ, RCG_OP_UPDATE = range(4)
 RCG_COPY_AUTO, RCG_COPY_ROWS = 0, 1
 RCG_SOLVE_CHAIN, RCG_SOLVE_TABLE = 0, 1
+RCG_NOALLOC_MAX_JOBS = 256
 
 _u32, _u64, _vp, _int = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
 
@@ -65,6 +66,7 @@ EXPORTS = {
     "rcg_degraded_read": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u32, _vp, _u64, _vp]),
     "rcg_batch_submit": (_int, [_vp, ctypes.POINTER(rcg_job), _u32, _vp, ctypes.POINTER(_u64)]),
     "rcg_batch_wait": (_int, [_vp, _u64, _u64]),
+    "rcg_batch_submit_noalloc": (_int, [ctypes.POINTER(rcg_job), _u32, _vp, _vp]),
     "rcg_fill_random": (_int, [_vp, _u64, _u64, _u64, _vp]),
     "rcg_inverse_table": (_int, [_u32, ctypes.POINTER(_u64)]),
     "rcg_plan": (_int, [_u32, _u64, ctypes.POINTER(rcg_plan_info)]),
@@ -208,6 +210,15 @@ def rcg_batch_submit(ctx: int, jobs, stream=None) -> int:
     _check(lib().rcg_batch_submit(ctx, arr, len(jobs), _stream(stream), ctypes.byref(ticket)),
            "rcg_batch_submit")
     return int(ticket.value)
+
+
+def rcg_batch_submit_noalloc(jobs, status_dev=None, stream=None):
+    """rcg_batch_submit without a context and without allocating device memory
+    (scratch in a fixed device array; at most RCG_NOALLOC_MAX_JOBS jobs).
+    status_dev: optional caller-owned device uint32 that receives RCG_DEV_* bits."""
+    arr = (rcg_job * max(1, len(jobs)))(*jobs)
+    _check(lib().rcg_batch_submit_noalloc(arr, len(jobs), _ptr(status_dev), _stream(stream)),
+           "rcg_batch_submit_noalloc")
 
 
 def rcg_batch_wait(ctx: int, ticket: int, timeout_ns: int = 10 ** 10) -> bool:
