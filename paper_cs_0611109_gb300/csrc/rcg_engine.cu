@@ -679,22 +679,30 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
         }
         const uint32_t stage = ring0 + pos.slot * slot_bytes;
         const int rot = (hv.x >> 8) & 0xff;
-        const uint32_t rotw = rot * pitch;
-        const bool fp = flags & F_P, fq = flags & F_Q, fc = flags & F_COPY;
+        // row r of x^rot * strip is row r - rot (mod p) of the strip; the item
+        // row whose source is the imaginary row p-1 is vrow = (p-1+rot) mod p
+        const uint32_t qbase = stage - rot * pitch;  // + p*pitch for rows r < rot
+        const int vrow = rot == 0 ? p - 1 : rot - 1;
+        if ((flags & (F_P | F_Q | F_COPY)) == (F_P | F_Q)) {
+            // a data strip feeding both accumulators: the common case
 #pragma unroll
-        for (int t = 0; t < kItems; ++t) {
-            const int r = row[t];
-            if (r >= p) continue;
-            if (fp && r < p - 1) {
-                const uint4 v = lds_a(stage + off[t]);
-                accP[t] = xor4(accP[t], v);
-                if (fc) stg(copy_dst + static_cast<uint64_t>(r) * T.row_stride + col[t] * 16, v);
+            for (int t = 0; t < kItems; ++t) {
+                const int r = row[t];  // invalid items carry a row >= p
+                if (r < p - 1) accP[t] = xor4(accP[t], lds_a(stage + off[t]));
+                if (r < p && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
             }
-            if (fq) {
-                // row r of x^rot * strip is row r - rot (mod p) of the strip; row p-1 is zero
-                const int s = r - rot;
-                const uint32_t o = off[t] - rotw + (s < 0 ? pw : 0u);
-                if (s != -1 && s != p - 1) accQ[t] = xor4(accQ[t], lds_a(stage + o));
+        } else {
+            const bool fp = flags & F_P, fq = flags & F_Q, fc = flags & F_COPY;
+#pragma unroll
+            for (int t = 0; t < kItems; ++t) {
+                const int r = row[t];
+                if (r >= p) continue;
+                if (fp && r < p - 1) {
+                    const uint4 v = lds_a(stage + off[t]);
+                    accP[t] = xor4(accP[t], v);
+                    if (fc) stg(copy_dst + static_cast<uint64_t>(r) * T.row_stride + col[t] * 16, v);
+                }
+                if (fq && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
             }
         }
         __syncwarp();
