@@ -114,6 +114,17 @@ rcg_status rcg_set_copy_mode(rcg_ctx *ctx, int mode);
 #define RCG_SOLVE_TABLE 1
 rcg_status rcg_set_dd_solve(rcg_ctx *ctx, int solve);
 
+/* Engine shape.  RCG_SHAPE_WIDE: one CTA per SM, 15 consumer warps, the
+ * deepest shared-memory ring (best for large p such as 59).  RCG_SHAPE_PAIR:
+ * two CTAs per SM, 6 consumer warps each, so one CTA's epilogue overlaps the
+ * other's streaming (best for small and medium p).  RCG_SHAPE_AUTO (default)
+ * picks pair unless its ring would force tiles narrower than 512 bytes.
+ * Results are identical. */
+#define RCG_SHAPE_AUTO 0
+#define RCG_SHAPE_WIDE 1
+#define RCG_SHAPE_PAIR 2
+rcg_status rcg_set_engine_shape(rcg_ctx *ctx, int shape);
+
 /* Synchronise the device and read, then clear, the device status word.
  * Returns RCG_EDEVICE when any bit was set (then *code holds the bits). */
 rcg_status rcg_last_device_status(rcg_ctx *ctx, uint32_t *code);
@@ -254,6 +265,8 @@ typedef struct rcg_plan_info {
     uint32_t n_slots;          /* ring depth */
     uint32_t max_items;        /* the engine's limit on p x W/16 per tile */
     uint32_t smem_bytes;       /* dynamic shared memory of one CTA for this plan */
+    uint32_t ctas_per_sm;      /* resident CTAs per SM of the engine shape */
+    uint32_t shape;            /* 0 = wide, 1 = pair (the shape RCG_SHAPE_AUTO picks) */
 } rcg_plan_info;
 rcg_status rcg_plan(uint32_t p, uint64_t row_bytes, rcg_plan_info *out);
 

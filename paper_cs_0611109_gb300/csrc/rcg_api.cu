@@ -34,6 +34,7 @@ struct BatchSlot {
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t copy_node = nullptr;
     cudaEvent_t done = nullptr;
+    uint32_t shape = 0;  // engine shape the graph's kernel node was captured with
     uint64_t ticket = 0;
     bool used = false;
 };
@@ -47,6 +48,7 @@ struct rcg_ctx {
     uint64_t timeout_ns = 2000000000ull;
     int copy_mode = RCG_COPY_AUTO;
     int dd_solve = RCG_SOLVE_CHAIN;
+    int shape = RCG_SHAPE_AUTO;
     uint64_t next_ticket = 1;
     BatchSlot slots[kBatchRing];
 };
@@ -170,9 +172,9 @@ rcg_status launch_single(rcg_ctx *ctx, const Job &J, const Plan &pl, cudaStream_
     prm.status = ctx->status;
     prm.timeout_ns = ctx->timeout_ns;
     if (prm.total_tiles == 0) return RCG_OK;
-    const uint64_t grid =
-        std::min<uint64_t>(prm.total_tiles, static_cast<uint64_t>(ctx->sm_count) * kCtasPerSm);
-    return from_cuda(launch_engine(prm, static_cast<int>(grid), stream));
+    const uint64_t grid = std::min<uint64_t>(
+        prm.total_tiles, static_cast<uint64_t>(ctx->sm_count) * shape_info(pl.shape).ctas_per_sm);
+    return from_cuda(launch_engine(prm, pl.shape, static_cast<int>(grid), stream));
 }
 
 uint64_t now_ns() {
@@ -213,20 +215,39 @@ void free_slot(BatchSlot &s) {
 
 // ====================================================================== plan
 
-bool rcg::make_plan(uint32_t p, uint64_t C, Plan *out) {
+bool rcg::make_plan(uint32_t p, uint64_t C, uint32_t shape, Plan *out) {
     if (!is_odd_prime(p) || p > static_cast<uint32_t>(kMaxP) || C == 0 || (C & 15)) return false;
+    const ShapeInfo si = shape_info(shape);
     const uint64_t nvec_total = C / 16;
-    uint64_t nvec_max = static_cast<uint64_t>(kMaxItems) / p;
+    uint64_t nvec_max = si.max_items / p;                                  // items per tile
     nvec_max = std::min<uint64_t>(nvec_max, kMaxSlotBytes / ((p - 1) * 16ull));
-    nvec_max = std::min<uint64_t>(nvec_max, kMaxTileBytes / 16);
-    const uint64_t tiles = (nvec_total + nvec_max - 1) / nvec_max;
-    if (tiles > 0xffffffffull) return false;
-    const uint64_t nvec = (nvec_total + tiles - 1) / tiles;
-    out->W = static_cast<uint32_t>(nvec * 16);
-    out->tiles_per_stripe = static_cast<uint32_t>(tiles);
-    out->slot_bytes = static_cast<uint32_t>(((p - 1) * out->W + 127) & ~127u);
-    out->n_slots = std::min<uint32_t>(kMaxSlots, kRingBytes / out->slot_bytes);
-    return out->n_slots >= 2;
+    nvec_max = std::min<uint64_t>(nvec_max, kMaxTileBytes / 16);           // TMA box row
+    nvec_max = std::min<uint64_t>(nvec_max, si.ring_bytes / si.min_slots / ((p - 1) * 16ull));
+    if (nvec_max == 0) return false;
+    for (;;) {
+        const uint64_t tiles = (nvec_total + nvec_max - 1) / nvec_max;
+        if (tiles > 0xffffffffull) return false;
+        const uint64_t nvec = (nvec_total + tiles - 1) / tiles;  // balanced tile widths
+        out->W = static_cast<uint32_t>(nvec * 16);
+        out->tiles_per_stripe = static_cast<uint32_t>(tiles);
+        out->slot_bytes = static_cast<uint32_t>(((p - 1) * out->W + 127) & ~127u);
+        out->n_slots = std::min<uint32_t>(kMaxSlots, si.ring_bytes / out->slot_bytes);
+        out->shape = shape;
+        if (out->n_slots >= si.min_slots) return true;
+        if (--nvec_max == 0) return false;  // rounding of the slot size: narrow the tile
+    }
+}
+
+// The engine shape for a geometry: an explicit choice of the context, else
+// the pair shape (two CTAs per SM, epilogues overlap streaming) unless its
+// ring would force tiles narrower than 512 bytes, where the wide shape's
+// deep ring wins.
+uint32_t choose_shape(const rcg_ctx *ctx, uint32_t p, uint64_t C) {
+    if (ctx->shape == RCG_SHAPE_WIDE) return SHAPE_WIDE;
+    if (ctx->shape == RCG_SHAPE_PAIR) return SHAPE_PAIR;
+    Plan pl;
+    if (make_plan(p, C, SHAPE_PAIR, &pl) && (pl.W >= 512 || pl.W >= C)) return SHAPE_PAIR;
+    return SHAPE_WIDE;
 }
 
 // =================================================================== C ABI
@@ -259,13 +280,18 @@ rcg_status rcg_inverse_table(uint32_t p, uint64_t *masks) {
 
 rcg_status rcg_plan(uint32_t p, uint64_t row_bytes, rcg_plan_info *out) {
     Plan pl;
-    if (!out || !make_plan(p, row_bytes, &pl)) return RCG_EINVAL;
+    static const rcg_ctx defaults;
+    if (!out || !is_odd_prime(p) || p > static_cast<uint32_t>(kMaxP)) return RCG_EINVAL;
+    if (!make_plan(p, row_bytes, choose_shape(&defaults, p, row_bytes), &pl)) return RCG_EINVAL;
+    const ShapeInfo si = shape_info(pl.shape);
     out->tile_bytes = pl.W;
     out->tiles_per_stripe = pl.tiles_per_stripe;
     out->slot_bytes = pl.slot_bytes;
     out->n_slots = pl.n_slots;
-    out->max_items = kMaxItems;
-    out->smem_bytes = kFixedSmem + pl.n_slots * pl.slot_bytes;
+    out->max_items = si.max_items;
+    out->smem_bytes = si.fixed_smem + pl.n_slots * pl.slot_bytes;
+    out->ctas_per_sm = si.ctas_per_sm;
+    out->shape = pl.shape;
     return RCG_OK;
 }
 
@@ -321,6 +347,13 @@ rcg_status rcg_set_dd_solve(rcg_ctx *ctx, int solve) {
     return RCG_OK;
 }
 
+rcg_status rcg_set_engine_shape(rcg_ctx *ctx, int shape) {
+    if (!ctx || (shape != RCG_SHAPE_AUTO && shape != RCG_SHAPE_WIDE && shape != RCG_SHAPE_PAIR))
+        return RCG_EINVAL;
+    ctx->shape = shape;
+    return RCG_OK;
+}
+
 rcg_status rcg_set_timeout(rcg_ctx *ctx, uint64_t timeout_ns) {
     if (!ctx || timeout_ns == 0) return RCG_EINVAL;
     ctx->timeout_ns = timeout_ns;
@@ -349,7 +382,7 @@ rcg_status rcg_encode(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe, 
     if (n_stripes == 0) return RCG_OK;
     if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
     Plan pl;
-    if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, choose_shape(ctx, g.p, g.C), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, first_stripe, n_stripes, pl);
     J.op = OP_ENCODE;
     DeviceGuard guard(ctx->device);
@@ -364,7 +397,7 @@ rcg_status rcg_recover(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint3
     if (st) return st;
     if (!(i < j && j <= g.N + 1)) return RCG_EINVAL;
     Plan pl;
-    if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, choose_shape(ctx, g.p, g.C), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, stripe, 1, pl);
     J.op = OP_RECOVER;
     J.i = static_cast<uint8_t>(i);
@@ -382,7 +415,7 @@ rcg_status rcg_recover_many(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_st
     if (n_stripes == 0) return RCG_OK;
     if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
     Plan pl;
-    if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, choose_shape(ctx, g.p, g.C), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, first_stripe, n_stripes, pl);
     J.op = OP_RECOVER;
     J.pairs = pairs;
@@ -400,7 +433,7 @@ rcg_status rcg_update(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32
     const uint64_t ars = new_row_stride ? new_row_stride : g.C;
     if (ars < g.C || (ars & 15)) return RCG_EINVAL;
     Plan pl;
-    if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, choose_shape(ctx, g.p, g.C), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, stripe, 1, pl);
     J.op = OP_UPDATE;
     J.i = static_cast<uint8_t>(i);
@@ -421,7 +454,7 @@ rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe,
     const uint64_t ors = out_row_stride ? out_row_stride : g.C;
     if (ors < g.C || (ors & 15)) return RCG_EINVAL;
     Plan pl;
-    if (!make_plan(g.p, g.C, &pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, choose_shape(ctx, g.p, g.C), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, stripe, 1, pl);
     J.op = OP_DEGRADED;
     J.j = static_cast<uint8_t>(j);
@@ -434,12 +467,12 @@ rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe,
 
 // ================================================================= batches
 
-static rcg_status build_job(const rcg_ctx *ctx, const rcg_job &in, Job *out, Plan *pl) {
+static rcg_status build_job(const rcg_ctx *ctx, const rcg_job &in, uint32_t shape, Job *out, Plan *pl) {
     Geo g;
     rcg_status st = check_layout(&in.layout, &g);
     if (st) return st;
     if (in.n_stripes == 0 || in.n_stripes > 0x7fffffffull) return RCG_EINVAL;
-    if (!make_plan(g.p, g.C, pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, shape, pl)) return RCG_EINVAL;
     Job J = base_job(ctx, &in.layout, g, in.first_stripe, in.n_stripes, *pl);
     const uint64_t ars = in.aux_row_stride ? in.aux_row_stride : g.C;
     const uint64_t ass = in.aux_stripe_stride ? in.aux_stripe_stride : (g.p - 1) * ars;
@@ -471,33 +504,25 @@ static rcg_status build_job(const rcg_ctx *ctx, const rcg_job &in, Job *out, Pla
     return RCG_OK;
 }
 
-// (Re)allocate a batch slot for `jobs` descriptors and capture its graph:
-// descriptor-table copy -> tile-counter reset -> persistent kernel.
-static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t jobs) {
-    if (s.cap_jobs >= jobs && s.exec) return RCG_OK;
-    free_slot(s);
-    const size_t cap = std::max<size_t>(jobs, 256);
-    const size_t bytes = sizeof(BatchHeader) + cap * sizeof(Job);
-    cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&s.host), bytes, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s.dev), bytes);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s.counter), sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.capture, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-        free_slot(s);
-        return from_cuda(e, "batch slot allocation");
-    }
-    memset(s.host, 0, bytes);
-    s.cap_jobs = cap;
+// Capture the slot's graph: descriptor-table copy -> tile-counter reset ->
+// persistent kernel of the given engine shape.
+static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.graph) cudaGraphDestroy(s.graph);
+    s.exec = nullptr;
+    s.graph = nullptr;
+    s.copy_node = nullptr;
+    const size_t bytes = sizeof(BatchHeader) + s.cap_jobs * sizeof(Job);
     s.bytes = bytes;
     cudaGraph_t graph = nullptr;
-    e = cudaStreamBeginCapture(s.capture, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(s.capture, cudaStreamCaptureModeThreadLocal);
     const char *where = "graph capture";
     if (e == cudaSuccess) {
         cudaError_t e1 = cudaMemcpyAsync(s.dev, s.host, bytes, cudaMemcpyHostToDevice, s.capture);
         cudaError_t e2 = cudaMemsetAsync(s.counter, 0, sizeof(unsigned long long), s.capture);
-        cudaError_t e3 = launch_batch(s.dev, ctx->status, s.counter, ctx->timeout_ns,
-                                      ctx->sm_count * kCtasPerSm, s.capture);
+        cudaError_t e3 = launch_batch(s.dev, ctx->status, s.counter, ctx->timeout_ns, shape,
+                                      ctx->sm_count * static_cast<int>(shape_info(shape).ctas_per_sm),
+                                      s.capture);
         e = cudaStreamEndCapture(s.capture, &graph);
         if (e1 != cudaSuccess) { e = e1; where = "captured table copy"; }
         else if (e2 != cudaSuccess) { e = e2; where = "captured counter reset"; }
@@ -523,6 +548,58 @@ static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t jobs) {
         free_slot(s);
         return from_cuda(e, where);
     }
+    s.shape = shape;
+    return RCG_OK;
+}
+
+// (Re)allocate a batch slot for `jobs` descriptors; recapture its graph when
+// the engine shape changes.
+static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t jobs, uint32_t shape) {
+    if (s.cap_jobs >= jobs && s.exec) return s.shape == shape ? RCG_OK : capture_slot(ctx, s, shape);
+    free_slot(s);
+    const size_t cap = std::max<size_t>(jobs, 256);
+    const size_t bytes = sizeof(BatchHeader) + cap * sizeof(Job);
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&s.host), bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s.dev), bytes);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s.counter), sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        free_slot(s);
+        return from_cuda(e, "batch slot allocation");
+    }
+    memset(s.host, 0, bytes);
+    s.cap_jobs = cap;
+    return capture_slot(ctx, s, shape);
+}
+
+// One engine shape for a whole batch: the context's explicit choice, else
+// pair when every job's geometry prefers it.
+static uint32_t batch_shape(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs) {
+    for (uint32_t k = 0; k < n_jobs; ++k)
+        if (choose_shape(ctx, jobs[k].layout.p, jobs[k].layout.row_bytes) != SHAPE_PAIR) return SHAPE_WIDE;
+    return SHAPE_PAIR;
+}
+
+// The descriptor table of a batch (header + jobs) for one engine shape.
+static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, uint32_t shape,
+                              BatchHeader *hdr, Job *table) {
+    uint64_t total = 0;
+    uint32_t slot_bytes = 0;
+    for (uint32_t k = 0; k < n_jobs; ++k) {
+        Plan pl;
+        rcg_status st = build_job(ctx, jobs[k], shape, &table[k], &pl);
+        if (st) return st;
+        table[k].tile_begin = total;
+        total += static_cast<uint64_t>(table[k].n_stripes) * table[k].tiles_per_stripe;
+        slot_bytes = std::max(slot_bytes, pl.slot_bytes);
+    }
+    memset(hdr, 0, sizeof(*hdr));
+    hdr->total_tiles = total;
+    hdr->n_jobs = n_jobs;
+    hdr->slot_bytes = slot_bytes;
+    hdr->n_slots = std::min<uint32_t>(kMaxSlots, shape_info(shape).ring_bytes / slot_bytes);
+    hdr->shape = shape;
     return RCG_OK;
 }
 
@@ -532,22 +609,10 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
     *ticket = 0;
     if (n_jobs == 0) return RCG_OK;
     std::vector<Job> table(n_jobs);
-    uint64_t total = 0;
-    uint32_t slot_bytes = 0;
-    for (uint32_t k = 0; k < n_jobs; ++k) {
-        Plan pl;
-        rcg_status st = build_job(ctx, jobs[k], &table[k], &pl);
-        if (st) return st;
-        table[k].tile_begin = total;
-        total += static_cast<uint64_t>(table[k].n_stripes) * table[k].tiles_per_stripe;
-        slot_bytes = std::max(slot_bytes, pl.slot_bytes);
-    }
     BatchHeader hdr;
-    memset(&hdr, 0, sizeof(hdr));
-    hdr.total_tiles = total;
-    hdr.n_jobs = n_jobs;
-    hdr.slot_bytes = slot_bytes;
-    hdr.n_slots = std::min<uint32_t>(kMaxSlots, kRingBytes / slot_bytes);
+    const uint32_t shape = batch_shape(ctx, jobs, n_jobs);
+    rcg_status st0 = build_table(ctx, jobs, n_jobs, shape, &hdr, table.data());
+    if (st0) return st0;
 
     DeviceGuard guard(ctx->device);
     const uint64_t tk = ctx->next_ticket;
@@ -557,7 +622,7 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
         if (st == RCG_ETIMEOUT) return RCG_EBUSY;
         if (st) return st;
     }
-    rcg_status st = prepare_slot(ctx, s, n_jobs);
+    rcg_status st = prepare_slot(ctx, s, n_jobs, shape);
     if (st) return st;
     const size_t bytes = sizeof(BatchHeader) + static_cast<size_t>(n_jobs) * sizeof(Job);
     memcpy(s.host, &hdr, sizeof(hdr));
@@ -619,9 +684,11 @@ rcg_status rcg_fill_random(void *dev, uint64_t nbytes, uint64_t seed, uint64_t b
 
 }  // extern "C"
 
-// Job validation and descriptor for rcg_batch_submit_noalloc (default copy
-// mode and two-data solve; no context).
-bool rcg::noalloc_build_job(const rcg_job &in, Job *out, Plan *pl) {
+// Descriptor table for rcg_batch_submit_noalloc (default copy mode, solve and
+// shape; no context).  Returns the engine shape through *shape.
+bool rcg::noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, BatchHeader *hdr, Job *table,
+                              uint32_t *shape) {
     static const rcg_ctx defaults;
-    return build_job(&defaults, in, out, pl) == RCG_OK;
+    *shape = batch_shape(&defaults, jobs, n_jobs);
+    return build_table(&defaults, jobs, n_jobs, *shape, hdr, table) == RCG_OK;
 }

@@ -202,6 +202,7 @@ struct Smem {
     uint8_t *ring;    // n_slots x slot_bytes
 };
 
+template <class S>
 __device__ __forceinline__ Smem carve(uint8_t *smem) {
     Smem s;
     s.full = reinterpret_cast<uint64_t *>(smem);
@@ -209,7 +210,7 @@ __device__ __forceinline__ Smem carve(uint8_t *smem) {
     s.ep = s.empty + kMaxSlots;
     s.hdr = reinterpret_cast<SlotHdr *>(smem + 1024);
     s.xb = smem + kCtlBytes;
-    s.fold = s.xb + kXBytes;
+    s.fold = s.xb + S::kXBytes;
     s.ring = s.fold + 2 * kFoldBytes;
     return s;
 }
@@ -281,6 +282,7 @@ struct RingPos {
     }
 };
 
+template <class S>
 __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_jobs,
                          uint64_t total_tiles, uint32_t slot_bytes, uint32_t n_slots) {
     const uint32_t lane = threadIdx.x & 31;
@@ -325,7 +327,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_job
         const uint32_t w = min(W, C - c0);
         // device-side guard: a tile must fit its slot and the item budget
         if (p < 3 || p > kMaxP || N < 1 || N > p || (w & 15) || w == 0 || W > kMaxTileBytes ||
-            (W & 15) || rows * W > slot_bytes || p * (w >> 4) > static_cast<uint32_t>(kMaxItems) ||
+            (W & 15) || rows * W > slot_bytes || p * (w >> 4) > static_cast<uint32_t>(S::kMaxItems) ||
             stripe >= n_stripes) {
             if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
             continue;
@@ -465,10 +467,15 @@ __device__ __forceinline__ bool ep_sync(const Smem &sm, uint32_t &phase, uint64_
 // happens before a barrier all consumers pass before the next tile's writes;
 // the fold row alternates between two buffers, so a tile's fold writes never
 // meet the previous fold-using tile's reads, which sit after its own barrier.
-__device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kItems],
-                         uint4 (&accQ)[kItems], const int (&row)[kItems],
-                         const int (&col)[kItems], uint32_t &ep_phase, uint32_t &fold_par,
-                         uint64_t timeout_ns) {
+template <class S>
+__device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[S::kItems],
+                         uint4 (&accQ)[S::kItems], const int (&row)[S::kItems], uint32_t &ep_phase,
+                         uint32_t &fold_par, uint64_t timeout_ns) {
+    // column of item t: item index minus row * nvec (recomputed, not kept in registers)
+    const int ctid = static_cast<int>(threadIdx.x) - 32;
+    int col[S::kItems];
+#pragma unroll
+    for (int t = 0; t < S::kItems; ++t) col[t] = ctid + t * S::kConsumers - row[t] * static_cast<int>(T.nvec);
     const int p = static_cast<int>(T.p);
     const uint32_t nv = T.nvec;
     auto X = [&](uint8_t *buf, int r, int c) { return buf + (static_cast<size_t>(r) * nv + c) * 16; };
@@ -482,11 +489,11 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
         case E_ENC:
         case E_DEGQ: {
             #pragma unroll
-            for (int t = 0; t < kItems; ++t)
+            for (int t = 0; t < S::kItems; ++t)
                 if (row[t] == p - 1) sts(fold + col[t] * 16, accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
+            for (int t = 0; t < S::kItems; ++t) {
                 if (row[t] >= p - 1) continue;
                 const uint4 q = xor4(accQ[t], lds(fold + col[t] * 16));
                 if (T.cls == E_ENC) {
@@ -500,18 +507,18 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
         }
         case E_DEGP: {
             #pragma unroll
-            for (int t = 0; t < kItems; ++t)
+            for (int t = 0; t < S::kItems; ++t)
                 if (row[t] < p - 1)
                     stg(T.out + static_cast<uint64_t>(row[t]) * T.out_row_stride + col[t] * 16, accP[t]);
             break;
         }
         case E_DP: {  // accQ = x^(-a) dQ (lifted): D_a = fold(accQ), P = accP + D_a
 #pragma unroll
-            for (int t = 0; t < kItems; ++t)
+            for (int t = 0; t < S::kItems; ++t)
                 if (row[t] == p - 1) sts(fold + col[t] * 16, accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
 #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
+            for (int t = 0; t < S::kItems; ++t) {
                 if (row[t] >= p - 1) continue;
                 const uint4 d = xor4(accQ[t], lds(fold + col[t] * 16));
                 stg(strip_row(T.a, row[t], col[t]), d);
@@ -522,12 +529,12 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
         case E_DQ: {  // D_a = accP; Q = fold(accQ + x^a D_a)
             const uint4 zero = make_uint4(0, 0, 0, 0);
             #pragma unroll
-            for (int t = 0; t < kItems; ++t)
+            for (int t = 0; t < S::kItems; ++t)
                 if (row[t] < p) sts(X(sm.xb, row[t], col[t]), row[t] < p - 1 ? accP[t] : zero);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             const int a = T.a;
             #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
+            for (int t = 0; t < S::kItems; ++t) {
                 if (row[t] >= p) continue;
                 int s = row[t] - a;
                 if (s < 0) s += p;
@@ -536,7 +543,7 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
             }
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
+            for (int t = 0; t < S::kItems; ++t) {
                 if (row[t] >= p - 1) continue;
                 stg(strip_row(T.a, row[t], col[t]), accP[t]);
                 stg(strip_row(T.b, row[t], col[t]), xor4(accQ[t], lds(fold + col[t] * 16)));
@@ -551,11 +558,10 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
             // T into its prefix XOR E_t in place; then D[r_t] = E_t + (t odd) c.
             const uint4 zero = make_uint4(0, 0, 0, 0);
 #pragma unroll
-            for (int t = 0; t < kItems; ++t)
+            for (int t = 0; t < S::kItems; ++t)
                 if (row[t] < p) sts(X(sm.xb, row[t], col[t]), row[t] < p - 1 ? xor4(accP[t], accQ[t]) : accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             const int z = T.b - T.a;
-            const int ctid = static_cast<int>(threadIdx.x) - 32;
             if (ctid < static_cast<int>(nv)) {
                 uint4 e = zero;
                 int r = p - 1;
@@ -572,7 +578,7 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
             // chain position of row r: r = p-1 + t z (mod p)  =>  t = (r+1) z^-1 (mod p)
             const int zinv = T.zinv;
 #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
+            for (int t = 0; t < S::kItems; ++t) {
                 if (row[t] >= p - 1) continue;
                 const int pos = ((row[t] + 1) * zinv) % p;
                 uint4 dj = lds(X(sm.xb, row[t], col[t]));
@@ -587,13 +593,13 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
             // (row p-1 of dP is zero); D_b = (1 + x^z)^(-1) T needs every row of T.
             const uint4 zero = make_uint4(0, 0, 0, 0);
 #pragma unroll
-            for (int t = 0; t < kItems; ++t)
+            for (int t = 0; t < S::kItems; ++t)
                 if (row[t] < p) sts(X(sm.xb, row[t], col[t]), row[t] < p - 1 ? xor4(accP[t], accQ[t]) : accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             // D_b (lifted) = sum over the table's exponent set of x^m T
             const uint64_t mask = c_inv[p][T.b - T.a];
 #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
+            for (int t = 0; t < S::kItems; ++t) {
                 if (row[t] >= p) continue;
                 uint4 d = zero;
                 uint64_t m = mask;
@@ -609,7 +615,7 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
             }
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
 #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
+            for (int t = 0; t < S::kItems; ++t) {
                 if (row[t] >= p - 1) continue;
                 const uint4 dj = xor4(accQ[t], lds(fold + col[t] * 16));
                 stg(strip_row(T.b, row[t], col[t]), dj);
@@ -621,6 +627,7 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[kIte
     return true;
 }
 
+template <class S>
 __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_bytes,
                          uint32_t n_slots) {
     const int ctid = static_cast<int>(threadIdx.x) - 32;
@@ -628,9 +635,9 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
     const uint64_t timeout = prm.timeout_ns;
     const uint32_t ring0 = smem_addr(sm.ring);
     const uint32_t hdr0 = smem_addr(sm.hdr);
-    uint4 accP[kItems], accQ[kItems];
-    int row[kItems], col[kItems];
-    uint32_t off[kItems];   // byte offset of the item's own row in a slot
+    uint4 accP[S::kItems], accQ[S::kItems];
+    int row[S::kItems];
+    uint32_t off[S::kItems];   // byte offset of the item's own row in a slot
     Tile T = {};
     uint8_t *copy_dst = nullptr;  // small write: data strip a of the tile
     uint32_t ep_phase = 0, fold_par = 0;
@@ -667,12 +674,11 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
             pitch = tv.y & 0xffffu;
             T.zinv = static_cast<uint8_t>(tv.y >> 16);
             pw = p * pitch;
-            for (int t = 0; t < kItems; ++t) {
-                const int item = ctid + t * kConsumers;
+            for (int t = 0; t < S::kItems; ++t) {
+                const int item = ctid + t * S::kConsumers;
                 const int r = item / static_cast<int>(T.nvec);
                 row[t] = r < p ? r : 0x7fff;
-                col[t] = item - r * static_cast<int>(T.nvec);
-                off[t] = r * pitch + col[t] * 16;
+                off[t] = r * pitch + (item - r * static_cast<int>(T.nvec)) * 16;
                 accP[t] = make_uint4(0, 0, 0, 0);
                 accQ[t] = make_uint4(0, 0, 0, 0);
             }
@@ -686,7 +692,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
         if ((flags & (F_P | F_Q | F_COPY)) == (F_P | F_Q)) {
             // a data strip feeding both accumulators: the common case
 #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
+            for (int t = 0; t < S::kItems; ++t) {
                 const int r = row[t];  // invalid items carry a row >= p
                 if (r < p - 1) accP[t] = xor4(accP[t], lds_a(stage + off[t]));
                 if (r < p && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
@@ -694,13 +700,13 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
         } else {
             const bool fp = flags & F_P, fq = flags & F_Q, fc = flags & F_COPY;
 #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
+            for (int t = 0; t < S::kItems; ++t) {
                 const int r = row[t];
                 if (r >= p) continue;
                 if (fp && r < p - 1) {
                     const uint4 v = lds_a(stage + off[t]);
                     accP[t] = xor4(accP[t], v);
-                    if (fc) stg(copy_dst + static_cast<uint64_t>(r) * T.row_stride + col[t] * 16, v);
+                    if (fc) stg(copy_dst + static_cast<uint64_t>(r) * T.row_stride + (off[t] - r * pitch), v);
                 }
                 if (fq && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
             }
@@ -709,7 +715,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
         if (lane == 0) mbar_arrive(smem_addr(&sm.empty[pos.slot]));
         pos.next(n_slots);
         if (flags & F_LAST) {
-            if (!epilogue(sm, T, accP, accQ, row, col, ep_phase, fold_par, timeout)) {
+            if (!epilogue<S>(sm, T, accP, accQ, row, ep_phase, fold_par, timeout)) {
                 if (lane == 0) set_status(prm.status, RCG_DEV_TIMEOUT);
                 return;
             }
@@ -719,10 +725,11 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
 
 // ------------------------------------------------------------------ kernel
 
-__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+template <class S>
+__global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
     rcg_tile_engine(const __grid_constant__ LaunchParams prm, const BatchHeader *bh) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    const Smem sm = carve(smem_raw);
+    const Smem sm = carve<S>(smem_raw);
 
     uint32_t n_jobs = prm.n_jobs, slot_bytes = prm.slot_bytes, n_slots = prm.n_slots;
     uint64_t total = prm.total_tiles;
@@ -732,8 +739,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         n_slots = bh->n_slots;
         total = bh->total_tiles;
     }
-    if (n_slots == 0 || n_slots > kMaxSlots || slot_bytes == 0 ||
-        static_cast<uint64_t>(n_slots) * slot_bytes > kRingBytes || (slot_bytes & 127)) {
+    const uint32_t my_shape = S::kCtasPerSm == 2 ? SHAPE_PAIR : SHAPE_WIDE;
+    if ((bh && bh->shape != my_shape) || n_slots == 0 || n_slots > kMaxSlots || slot_bytes == 0 ||
+        static_cast<uint64_t>(n_slots) * slot_bytes > S::kRingBytes || (slot_bytes & 127)) {
         if (threadIdx.x == 0) set_status(prm.status, RCG_DEV_BADJOB);
         return;
     }
@@ -741,17 +749,17 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < n_slots; ++s) {
             mbar_init(smem_addr(&sm.full[s]), 1);
-            mbar_init(smem_addr(&sm.empty[s]), kConsumerWarps);
+            mbar_init(smem_addr(&sm.empty[s]), S::kConsumerWarps);
         }
-        mbar_init(smem_addr(sm.ep), kConsumerWarps);
+        mbar_init(smem_addr(sm.ep), S::kConsumerWarps);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
     if (threadIdx.x < 32)
-        producer(prm, sm, n_jobs, total, slot_bytes, n_slots);
+        producer<S>(prm, sm, n_jobs, total, slot_bytes, n_slots);
     else
-        consumer(prm, sm, slot_bytes, n_slots);
+        consumer<S>(prm, sm, slot_bytes, n_slots);
 }
 
 // ------------------------------------------------------ test-data generator
@@ -814,27 +822,41 @@ cudaError_t upload_inverse_tables() {
 }
 
 cudaError_t engine_init_attributes() {
-    return cudaFuncSetAttribute(rcg_tile_engine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(kSmemLimit));
+    cudaError_t e = cudaFuncSetAttribute(rcg_tile_engine<ShapeWide>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(ShapeWide::kSmemLimit));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rcg_tile_engine<ShapePair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(ShapePair::kSmemLimit));
+    return e;
 }
 
-cudaError_t launch_engine(const LaunchParams &prm, int grid, cudaStream_t stream) {
-    const size_t smem = kFixedSmem + static_cast<size_t>(prm.n_slots) * prm.slot_bytes;
-    rcg_tile_engine<<<grid, kThreads, smem, stream>>>(prm, nullptr);
+template <class S>
+static cudaError_t launch_shape(const LaunchParams &prm, const BatchHeader *bh, size_t smem, int grid,
+                                cudaStream_t stream) {
+    rcg_tile_engine<S><<<grid, S::kThreads, smem, stream>>>(prm, bh);
     return cudaGetLastError();
 }
 
+cudaError_t launch_engine(const LaunchParams &prm, uint32_t shape, int grid, cudaStream_t stream) {
+    const ShapeInfo si = shape_info(shape);
+    const size_t smem = si.fixed_smem + static_cast<size_t>(prm.n_slots) * prm.slot_bytes;
+    return shape == SHAPE_PAIR ? launch_shape<ShapePair>(prm, nullptr, smem, grid, stream)
+                               : launch_shape<ShapeWide>(prm, nullptr, smem, grid, stream);
+}
+
 cudaError_t launch_batch(const uint8_t *table_dev, uint32_t *status, unsigned long long *counter,
-                         uint64_t timeout_ns, int grid, cudaStream_t stream) {
+                         uint64_t timeout_ns, uint32_t shape, int grid, cudaStream_t stream) {
     LaunchParams prm = {};
     prm.jobs = reinterpret_cast<const Job *>(table_dev + sizeof(BatchHeader));
     prm.dynamic_sched = 1;
     prm.tile_counter = counter;
     prm.status = status;
     prm.timeout_ns = timeout_ns;
-    rcg_tile_engine<<<grid, kThreads, kSmemLimit, stream>>>(
-        prm, reinterpret_cast<const BatchHeader *>(table_dev));
-    return cudaGetLastError();
+    const auto *bh = reinterpret_cast<const BatchHeader *>(table_dev);
+    const ShapeInfo si = shape_info(shape);
+    return shape == SHAPE_PAIR ? launch_shape<ShapePair>(prm, bh, si.smem_limit, grid, stream)
+                               : launch_shape<ShapeWide>(prm, bh, si.smem_limit, grid, stream);
 }
 
 cudaError_t launch_fill(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte_offset,

@@ -11,39 +11,54 @@
 namespace rcg {
 
 // ---------------------------------------------------------------- geometry
-// A CTA of the tile engine is one producer warp (issues the bulk copies) and
-// kConsumerWarps consumer warps.  A consumer thread owns up to kItems
-// "items": one 16-byte column vector of one row, for P and for the lifted Q
-// accumulator (rows 0..p-1, row p-1 being the imaginary row of the lift to
-// F2[x]/(x^p - 1)).  A tile of W bytes of a p-row stripe has p * W/16 items.
-#ifndef RCG_CONSUMER_WARPS
-#define RCG_CONSUMER_WARPS 15
-#endif
-#ifndef RCG_ITEMS
-#define RCG_ITEMS 4
-#endif
-#ifndef RCG_CTAS_PER_SM
-#define RCG_CTAS_PER_SM 1
-#endif
-constexpr int kCtasPerSm = RCG_CTAS_PER_SM;
-constexpr int kConsumerWarps = RCG_CONSUMER_WARPS;
-constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kThreads = kConsumers + 32;
-constexpr int kItems = RCG_ITEMS;
-constexpr int kMaxItems = kItems * kConsumers;  // items per tile (2048 by default)
-constexpr uint32_t kMaxTileBytes = 2048;        // a TMA box row is at most 256 8-byte elements
+// A CTA of the tile engine is one producer warp (issues the tensor copies)
+// and CW consumer warps.  A consumer thread owns up to IT "items": one 16-byte
+// column vector of one row, for P and for the lifted Q accumulator (rows
+// 0..p-1, row p-1 being the imaginary row of the lift to F2[x]/(x^p - 1)).
+// A tile of W bytes of a p-row stripe has p * W/16 items.
+//
+// Two shapes are built:
+//   wide: 1 CTA per SM, 15 consumer warps x 4 items, 227 KB of shared memory
+//         (deep ring: the best choice when slots are large, e.g. p = 59);
+//   pair: 2 CTAs per SM, 6 consumer warps x 6 items, 113 KB each (one CTA's
+//         epilogue overlaps the other's streaming).
+constexpr uint32_t kMaxTileBytes = 2048;  // a TMA box row is at most 256 8-byte elements
 constexpr int kMaxSlots = 32;
 constexpr int kMaxP = 61;
 constexpr uint32_t kMaxSlotBytes = 32 * 1024;
+constexpr uint32_t kCtlBytes = 2048;            // barriers + slot headers
+constexpr uint32_t kFoldBytes = kMaxTileBytes;  // one row of W bytes (two are kept)
 
-// Dynamic shared memory: control block, exchange buffers, then the ring.
-constexpr uint32_t kCtlBytes = 2048;                       // barriers + slot headers
-constexpr uint32_t kXBytes = kMaxItems * 16;               // the p x W exchange buffer
-constexpr uint32_t kFoldBytes = kMaxTileBytes;             // one row of W bytes
-constexpr uint32_t kFixedSmem = kCtlBytes + kXBytes + 2 * kFoldBytes;  // two fold rows
-// 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
-constexpr uint32_t kSmemLimit = (228 / kCtasPerSm - 1) * 1024;
-constexpr uint32_t kRingBytes = kSmemLimit - kFixedSmem;
+template <int CW, int IT, int CT, int MINSLOTS>
+struct EngineShape {
+    static constexpr int kConsumerWarps = CW;
+    static constexpr int kConsumers = CW * 32;
+    static constexpr int kThreads = kConsumers + 32;
+    static constexpr int kItems = IT;
+    static constexpr int kMaxItems = IT * CW * 32;
+    static constexpr int kCtasPerSm = CT;
+    static constexpr int kMinSlots = MINSLOTS;  // a plan keeps at least this ring depth
+    // 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
+    static constexpr uint32_t kSmemLimit = (228 / CT - 1) * 1024;
+    static constexpr uint32_t kXBytes = kMaxItems * 16;  // the p x W exchange buffer
+    static constexpr uint32_t kFixedSmem = kCtlBytes + kXBytes + 2 * kFoldBytes;
+    static constexpr uint32_t kRingBytes = kSmemLimit - kFixedSmem;
+};
+using ShapeWide = EngineShape<15, 4, 1, 2>;
+using ShapePair = EngineShape<6, 6, 2, 4>;
+enum Shape : uint32_t { SHAPE_WIDE = 0, SHAPE_PAIR = 1 };
+
+struct ShapeInfo {
+    uint32_t max_items, ring_bytes, fixed_smem, smem_limit, ctas_per_sm, min_slots;
+};
+template <class S>
+constexpr ShapeInfo shape_info_of() {
+    return {static_cast<uint32_t>(S::kMaxItems), S::kRingBytes, S::kFixedSmem, S::kSmemLimit,
+            static_cast<uint32_t>(S::kCtasPerSm), static_cast<uint32_t>(S::kMinSlots)};
+}
+inline ShapeInfo shape_info(uint32_t shape) {
+    return shape == SHAPE_PAIR ? shape_info_of<ShapePair>() : shape_info_of<ShapeWide>();
+}
 
 enum Op : uint8_t { OP_ENCODE = 0, OP_RECOVER = 1, OP_DEGRADED = 2, OP_UPDATE = 3 };
 
@@ -89,33 +104,36 @@ struct alignas(128) BatchHeader {
     uint32_t n_jobs;
     uint32_t slot_bytes;
     uint32_t n_slots;
-    uint32_t pad[27];
+    uint32_t shape;  // the engine shape the table was planned for
+    uint32_t pad[26];
 };
 static_assert(sizeof(BatchHeader) == 128, "the job table after the header stays 128-byte aligned");
 static_assert(sizeof(Job) % 128 == 0, "jobs keep their tensor maps 128-byte aligned");
 
 struct Plan {
-    uint32_t W, tiles_per_stripe, slot_bytes, n_slots;
+    uint32_t W, tiles_per_stripe, slot_bytes, n_slots, shape;
 };
 
-// Host: tiling for one (p, C).  Returns false when out of range.
-bool make_plan(uint32_t p, uint64_t C, Plan *out);
+// Host: tiling for one (p, C) on one engine shape.  Returns false when out of range.
+bool make_plan(uint32_t p, uint64_t C, uint32_t shape, Plan *out);
 
 // Host: upload the per-p inverse tables to the current device (once).
 cudaError_t upload_inverse_tables();
 
-// Host launchers (rcg_engine.cu).
-cudaError_t launch_engine(const LaunchParams &prm, int grid, cudaStream_t stream);
+// Host launchers (rcg_engine.cu).  grid = SMs x ctas_per_sm of the shape (or fewer).
+cudaError_t launch_engine(const LaunchParams &prm, uint32_t shape, int grid, cudaStream_t stream);
 cudaError_t launch_batch(const uint8_t *table_dev, uint32_t *status, unsigned long long *counter,
-                         uint64_t timeout_ns, int grid, cudaStream_t stream);
+                         uint64_t timeout_ns, uint32_t shape, int grid, cudaStream_t stream);
 cudaError_t engine_init_attributes();
 cudaError_t launch_fill(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte_offset,
                         cudaStream_t stream);
 
 void inverse_masks(uint32_t p, uint64_t *masks);
 
-// Host: validate one public job and build its device descriptor with the
-// default copy mode and two-data solve (used by rcg_batch_submit_noalloc).
-bool noalloc_build_job(const rcg_job &in, Job *out, Plan *pl);
+// Host: validate public jobs and build the batch descriptor table with the
+// default copy mode, two-data solve and engine shape (used by
+// rcg_batch_submit_noalloc); *shape receives the shape to launch.
+bool noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, BatchHeader *hdr, Job *table,
+                         uint32_t *shape);
 
 }  // namespace rcg

@@ -81,21 +81,9 @@ extern "C" rcg_status rcg_batch_submit_noalloc(const rcg_job *jobs, uint32_t n_j
     if (n_jobs == 0) return RCG_OK;
 
     BatchHeader hdr;
-    memset(&hdr, 0, sizeof(hdr));
     Job *table = reinterpret_cast<Job *>(g_host_table + sizeof(BatchHeader));
-    uint64_t total = 0;
-    uint32_t slot_bytes = 0;
-    for (uint32_t k = 0; k < n_jobs; ++k) {
-        Plan pl;
-        if (!noalloc_build_job(jobs[k], &table[k], &pl)) return RCG_EINVAL;
-        table[k].tile_begin = total;
-        total += static_cast<uint64_t>(table[k].n_stripes) * table[k].tiles_per_stripe;
-        if (pl.slot_bytes > slot_bytes) slot_bytes = pl.slot_bytes;
-    }
-    hdr.total_tiles = total;
-    hdr.n_jobs = n_jobs;
-    hdr.slot_bytes = slot_bytes;
-    hdr.n_slots = kRingBytes / slot_bytes < kMaxSlots ? kRingBytes / slot_bytes : kMaxSlots;
+    uint32_t shape = SHAPE_WIDE;
+    if (!noalloc_build_table(jobs, n_jobs, &hdr, table, &shape)) return RCG_EINVAL;
     memcpy(g_host_table, &hdr, sizeof(hdr));
 
     int dev = 0;
@@ -113,6 +101,7 @@ extern "C" rcg_status rcg_batch_submit_noalloc(const rcg_job *jobs, uint32_t n_j
     cudaError_t e = cudaMemcpyAsync(table_dev, g_host_table, bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
-        e = launch_batch(table_dev, status, counter, 2000000000ull, d->sm_count * kCtasPerSm, s);
+        e = launch_batch(table_dev, status, counter, 2000000000ull, shape,
+                         d->sm_count * static_cast<int>(shape_info(shape).ctas_per_sm), s);
     return e == cudaSuccess ? RCG_OK : RCG_ECUDA;
 }

@@ -20,6 +20,7 @@ RCG_OP_ENCODE, RCG_OP_RECOVER, RCG_OP_DEGRADED_READ, RCG_OP_UPDATE = range(4)
 RCG_COPY_AUTO, RCG_COPY_ROWS = 0, 1
 RCG_SOLVE_CHAIN, RCG_SOLVE_TABLE = 0, 1
 RCG_NOALLOC_MAX_JOBS = 256
+RCG_SHAPE_AUTO, RCG_SHAPE_WIDE, RCG_SHAPE_PAIR = 0, 1, 2
 
 _u32, _u64, _vp, _int = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
 
@@ -46,7 +47,7 @@ class rcg_job(ctypes.Structure):
 
 class rcg_plan_info(ctypes.Structure):
     _fields_ = [("tile_bytes", _u32), ("tiles_per_stripe", _u32), ("slot_bytes", _u32), ("n_slots", _u32),
-                ("max_items", _u32), ("smem_bytes", _u32)]
+                ("max_items", _u32), ("smem_bytes", _u32), ("ctas_per_sm", _u32), ("shape", _u32)]
 
 
 EXPORTS = {
@@ -55,6 +56,7 @@ EXPORTS = {
     "rcg_set_timeout": (_int, [_vp, _u64]),
     "rcg_set_copy_mode": (_int, [_vp, _int]),
     "rcg_set_dd_solve": (_int, [_vp, _int]),
+    "rcg_set_engine_shape": (_int, [_vp, _int]),
     "rcg_last_device_status": (_int, [_vp, ctypes.POINTER(_u32)]),
     "rcg_status_str": (ctypes.c_char_p, [_int]),
     "rcg_abi_version": (_u32, []),
@@ -159,6 +161,10 @@ def rcg_set_copy_mode(ctx: int, mode: int):
 
 def rcg_set_dd_solve(ctx: int, solve: int):
     _check(lib().rcg_set_dd_solve(ctx, solve), "rcg_set_dd_solve")
+
+
+def rcg_set_engine_shape(ctx: int, shape: int):
+    _check(lib().rcg_set_engine_shape(ctx, shape), "rcg_set_engine_shape")
 
 
 def rcg_last_device_status(ctx: int) -> int:
@@ -299,6 +305,9 @@ class Context:
 
     def set_dd_solve(self, solve):
         rcg_set_dd_solve(self.handle, solve)
+
+    def set_engine_shape(self, shape):
+        rcg_set_engine_shape(self.handle, shape)
 
     def last_device_status(self) -> int:
         return rcg_last_device_status(self.handle)
