@@ -48,14 +48,16 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--stripes", type=int, default=S,
+                    help="stripes per GPU (default 8192; smaller values are profiling cases, not bench lines)")
     return ap.parse_args()
 
 
-def user_bytes_per_op(stripes=S):
+def user_bytes_per_op(stripes):
     return N * (P - 1) * C * stripes
 
 
-def moved_bytes_per_op(stripes=S):
+def moved_bytes_per_op(stripes):
     return (N + 2) * (P - 1) * C * stripes
 
 
@@ -146,6 +148,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     ctx = rcg.Context(local)
+    S = args.stripes
     sb = inputs.stripe_bytes(P, N, C)
     buf = torch.empty((S, N + 2, P - 1, C), dtype=torch.uint8, device=dev)
     rcg.rcg_fill_random(buf, S * sb, SEED + 100 * rank)
@@ -204,44 +207,38 @@ def run_ours(args):
     all_launch = [x for row in per_launch for x in row]
     avg_launch_ms = sum(all_launch) / len(all_launch)
     peak, peak_kind = peak_hbm()
-    achieved = moved_bytes_per_op() / (avg_launch_ms * 1e-3) / 1e9
+    achieved = moved_bytes_per_op(S) / (avg_launch_ms * 1e-3) / 1e9
 
-    user_step = 5 * user_bytes_per_op()
+    user_step = 5 * user_bytes_per_op(S)
     value = user_step * args.steps * world / (ms * 1e-3) / 1e9
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (SplitMix64 bytes generated on the device, seed %d)" % SEED,
-        "config": {"workload": WORKLOAD, "p": P, "n_data": N, "row_bytes": C, "stripes_per_gpu": S,
+        "config": {"workload": WORKLOAD if S == 8192 else "profiling case: %d stripes" % S,
+                   "p": P, "n_data": N, "row_bytes": C, "stripes_per_gpu": S,
                    "ops_per_step": ["encode", "recover_dd", "recover_dp", "recover_dq", "recover_pq"],
                    "user_bytes_per_step_per_gpu": user_step,
-                   "hbm_bytes_per_op_per_gpu": moved_bytes_per_op(),
+                   "hbm_bytes_per_op_per_gpu": moved_bytes_per_op(S),
                    "l2": "inputs (5.25 GiB per op) far larger than the 129 MB L2; no flush",
                    "parallelism": "stripe-sharded x%d, no collective" % world},
         "roofline": {"bound": "hbm", "kernel": "rcg_tile_engine",
                      "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                      "avg_launch_ms": round(avg_launch_ms, 4),
-                     "bytes_per_launch": moved_bytes_per_op()},
+                     "bytes_per_launch": moved_bytes_per_op(S)},
         "per_op": {name: {"ms": round(sum(row) / len(row), 4),
-                          "user_gbs": round(user_bytes_per_op() / (sum(row) / len(row) * 1e-3) / 1e9, 1),
-                          "hbm_frac": round(moved_bytes_per_op() / (sum(row) / len(row) * 1e-3) / 1e9 / peak, 4)}
+                          "user_gbs": round(user_bytes_per_op(S) / (sum(row) / len(row) * 1e-3) / 1e9, 1),
+                          "hbm_frac": round(moved_bytes_per_op(S) / (sum(row) / len(row) * 1e-3) / 1e9 / peak, 4)}
                    for name, row in zip(["encode", "dd", "dp", "dq", "pq"], per_launch)},
         "gpu_launches": launches,
         "clocks": clk,
     }
-    traffic = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(traffic):
-        try:
-            tj = json.load(open(traffic))
-            if tj.get("kernel") == "rcg_tile_engine" and tj.get("source_hash") == kernel_hash():
-                out["roofline"]["traffic"] = tj["bytes_per_launch"]
-        except Exception:
-            pass
+    out["roofline"]["traffic"] = measured_traffic(S)
 
     if not args.no_e2e:
-        out["e2e"] = e2e_ours(ctx, rcg, torch, dev, stream, pairs, args, world)
+        out["e2e"] = e2e_ours(ctx, rcg, torch, dev, stream, pairs, args, world, S)
     del buf
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
@@ -253,6 +250,8 @@ def run_ours(args):
 
 
 def kernel_hash():
+    """Hash of the tile engine's sources: DRAM counters taken on another
+    version of the kernel are not reported."""
     import hashlib
     h = hashlib.sha256()
     for f in ("rcg_engine.cu", "rcg_internal.h"):
@@ -260,47 +259,49 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def e2e_ours(ctx, rcg, torch, dev, stream, pairs, args, world):
-    """Same step through the public API with the stripes in pinned HOST memory:
-    every op copies its inputs host->device and its results device->host inside
-    the timed region (encode: data in, P and Q out; recovery: the N surviving
-    strips' stripes in, the two rebuilt strips out)."""
+def measured_traffic(stripes):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the
+    committed ncu summary, scaled to `stripes` by the stripes it captured;
+    None when the summary is missing or was taken on other kernel sources."""
+    import re
+    path = os.path.join(ROOT, "profiles", "rcg_tile_engine_c2_traffic.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
+    n = re.search(r"captured_stripes:\s*([0-9]+)", text)
+    if not (h and b and n) or h.group(1) != kernel_hash():
+        return None
+    return int(int(b.group(1)) * stripes / int(n.group(1)))
+
+
+def e2e_ours(ctx, rcg, torch, dev, stream, pairs, args, world, S):
+    """The same step through the public API with the stripes in pinned HOST
+    memory (rcg_encode_host / rcg_recover_many_host): every step uploads what
+    each operation reads and brings its results back to the host stripes."""
     from paper_cs_0611109_gb300 import inputs
     host = torch.empty((S, N + 2, P - 1, C), dtype=torch.uint8).pin_memory()
     dbuf = torch.empty((S, N + 2, P - 1, C), dtype=torch.uint8, device=dev)
     rcg.rcg_fill_random(dbuf, S * inputs.stripe_bytes(P, N, C), SEED)
-    L = rcg.make_layout(dbuf, P, N, C)
-    ctx.encode(L, 0, S)
+    ctx.encode(rcg.make_layout(dbuf, P, N, C), 0, S)
     host.copy_(dbuf)
     torch.cuda.synchronize()
-    pairs_host = {k: pairs[k].cpu().pin_memory() for k in CLASSES}
-    pd = {k: torch.empty_like(pairs[k]) for k in CLASSES}
+    del dbuf
+    torch.cuda.empty_cache()
+    HL = rcg.make_layout(host, P, N, C)
+    pairs_host = {k: pairs[k].cpu().numpy() for k in CLASSES}
     strip = (P - 1) * C
-    h2d = d2h = 0
 
     def step():
-        nonlocal h2d, d2h
-        # encode: data strips in, P and Q out
-        dbuf[:, :N].copy_(host[:, :N], non_blocking=True)
-        h2d += S * N * strip
-        ctx.encode(L, 0, S)
-        host[:, N:].copy_(dbuf[:, N:], non_blocking=True)
-        d2h += S * 2 * strip
+        ctx.encode_host(HL, 0, S, stream)
         for k in CLASSES:
-            # the surviving strips of each stripe: copy the whole stripe array in
-            # (the erased strips' bytes are never read), the pairs, and the two
-            # rebuilt strips back
-            dbuf.copy_(host, non_blocking=True)
-            pd[k].copy_(pairs_host[k], non_blocking=True)
-            h2d += S * (N + 2) * strip + 2 * S
-            ctx.recover_many(L, 0, S, pd[k])
-            host.copy_(dbuf, non_blocking=True)
-            d2h += S * (N + 2) * strip
+            ctx.recover_many_host(HL, 0, S, pairs_host[k], stream)
 
     for _ in range(2):
         step()
     torch.cuda.synchronize()
-    h2d = d2h = 0
     steps = max(2, args.steps // 4)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -310,11 +311,16 @@ def e2e_ours(ctx, rcg, torch, dev, stream, pairs, args, world):
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
-    value = 5 * user_bytes_per_op() * steps * world / (ms * 1e-3) / 1e9
-    del host, dbuf
-    return {"value": round(value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d // steps,
-            "d2h_bytes_per_step": d2h // steps,
-            "note": "torch pinned-host copies around the C-ABI device calls"}
+    if ctx.last_device_status() != 0:
+        raise RuntimeError("device status word set in the end-to-end run")
+    value = 5 * user_bytes_per_op(S) * steps * world / (ms * 1e-3) / 1e9
+    del host
+    # encode: N strips in, P and Q out; recovery: the stripe and its pair in, two strips out
+    h2d = S * N * strip + len(CLASSES) * S * ((N + 2) * strip + 2)
+    d2h = S * 2 * strip * (1 + len(CLASSES))
+    return {"value": round(value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h,
+            "api": "rcg_encode_host + rcg_recover_many_host (pinned host stripes)"}
 
 
 # --------------------------------------------------------------- CPU oracle

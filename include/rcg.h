@@ -118,7 +118,7 @@ rcg_status rcg_set_dd_solve(rcg_ctx *ctx, int solve);
  * deepest shared-memory ring (best for large p such as 59).  RCG_SHAPE_PAIR:
  * two CTAs per SM, 6 consumer warps each, so one CTA's epilogue overlaps the
  * other's streaming (best for small and medium p).  RCG_SHAPE_AUTO (default)
- * picks pair unless its ring would force tiles narrower than 512 bytes.
+ * picks pair for launches under 256 MB of traffic and wide above.
  * Results are identical. */
 #define RCG_SHAPE_AUTO 0
 #define RCG_SHAPE_WIDE 1
@@ -173,6 +173,31 @@ rcg_status rcg_update(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32
  * apart; 0 = C).  The stripe is not modified. */
 rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32_t j,
                              void *out, uint64_t out_row_stride, void *stream);
+
+/* ------------------------------------------------- stripes in host memory */
+
+/* rcg_encode and rcg_recover_many for stripes in HOST memory: L->base is a
+ * host address of page-locked memory (cudaHostAlloc, cudaHostRegister, or a
+ * pinned PyTorch tensor); pageable memory is RCG_EINVAL.  The stripes are
+ * streamed through context-owned device staging (three 256 MB chunks,
+ * allocated on first use) on three internal streams, so the upload of one
+ * chunk, the engine on another and the download of a third overlap.
+ *   encode:   uploads the data strips, downloads P and Q;
+ *   recovery: uploads whole stripes (the erased strips' bytes are never
+ *             read), and writes only the two rebuilt strips of each stripe
+ *             back into the host stripes, in place, through their mapped
+ *             device addresses.  pairs is a HOST array of 2*n_stripes bytes.
+ * Results are identical to the device calls.  The calls are ordered on
+ * `stream`: the work starts after what is already queued there, and work
+ * queued there afterwards sees the results. */
+rcg_status rcg_encode_host(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe,
+                           uint64_t n_stripes, void *stream);
+
+/* Size of one staging chunk of the host-memory calls (default 256 MB, at
+ * least 4096 bytes; a chunk always holds at least one stripe). */
+rcg_status rcg_set_host_chunk(rcg_ctx *ctx, uint64_t bytes);
+rcg_status rcg_recover_many_host(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe,
+                                 uint64_t n_stripes, const uint8_t *pairs, void *stream);
 
 /* ------------------------------------------------------------ batches */
 
@@ -266,7 +291,7 @@ typedef struct rcg_plan_info {
     uint32_t max_items;        /* the engine's limit on p x W/16 per tile */
     uint32_t smem_bytes;       /* dynamic shared memory of one CTA for this plan */
     uint32_t ctas_per_sm;      /* resident CTAs per SM of the engine shape */
-    uint32_t shape;            /* 0 = wide, 1 = pair (the shape RCG_SHAPE_AUTO picks) */
+    uint32_t shape;            /* 0 = wide, 1 = pair (the shape RCG_SHAPE_AUTO picks for large launches) */
 } rcg_plan_info;
 rcg_status rcg_plan(uint32_t p, uint64_t row_bytes, rcg_plan_info *out);
 

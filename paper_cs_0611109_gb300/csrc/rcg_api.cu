@@ -41,6 +41,16 @@ struct BatchSlot {
 
 }  // namespace
 
+namespace rcg {
+struct HostStaging;
+HostStaging *host_staging_create();
+void host_staging_destroy(HostStaging *h);
+rcg_status host_path(HostStaging *h, const rcg_layout *L, uint64_t first, uint64_t n_stripes,
+                     const uint8_t *pairs_host, cudaStream_t caller, uint64_t chunk_bytes,
+                     rcg_status (*run)(void *, const rcg_layout *, uint64_t, const uint8_t *, cudaStream_t),
+                     void *run_arg);
+}  // namespace rcg
+
 struct rcg_ctx {
     int device = 0;
     int sm_count = 0;
@@ -51,6 +61,8 @@ struct rcg_ctx {
     int shape = RCG_SHAPE_AUTO;
     uint64_t next_ticket = 1;
     BatchSlot slots[kBatchRing];
+    rcg::HostStaging *host = nullptr;  // staging of the host-memory calls (lazy)
+    uint64_t host_chunk_bytes = 256ull << 20;
 };
 
 namespace {
@@ -238,16 +250,20 @@ bool rcg::make_plan(uint32_t p, uint64_t C, uint32_t shape, Plan *out) {
     }
 }
 
-// The engine shape for a geometry: an explicit choice of the context, else
-// the pair shape (two CTAs per SM, epilogues overlap streaming) unless its
-// ring would force tiles narrower than 512 bytes, where the wide shape's
-// deep ring wins.
-uint32_t choose_shape(const rcg_ctx *ctx, uint32_t p, uint64_t C) {
+// The engine shape for a launch: the context's explicit choice, else pair
+// (two CTAs per SM: more CTAs in flight, epilogues overlapping streaming)
+// for launches under 256 MB of traffic, and wide (one CTA per SM with the
+// deepest ring) above that, where streaming throughput decides.
+constexpr uint64_t kSmallLaunchBytes = 256ull << 20;
+
+uint32_t choose_shape(const rcg_ctx *ctx, uint64_t launch_bytes) {
     if (ctx->shape == RCG_SHAPE_WIDE) return SHAPE_WIDE;
     if (ctx->shape == RCG_SHAPE_PAIR) return SHAPE_PAIR;
-    Plan pl;
-    if (make_plan(p, C, SHAPE_PAIR, &pl) && (pl.W >= 512 || pl.W >= C)) return SHAPE_PAIR;
-    return SHAPE_WIDE;
+    return launch_bytes < kSmallLaunchBytes ? SHAPE_PAIR : SHAPE_WIDE;
+}
+
+uint64_t launch_bytes(const Geo &g, uint64_t n_stripes) {
+    return (g.N + 2ull) * (g.p - 1) * g.C * n_stripes;
 }
 
 // =================================================================== C ABI
@@ -282,7 +298,7 @@ rcg_status rcg_plan(uint32_t p, uint64_t row_bytes, rcg_plan_info *out) {
     Plan pl;
     static const rcg_ctx defaults;
     if (!out || !is_odd_prime(p) || p > static_cast<uint32_t>(kMaxP)) return RCG_EINVAL;
-    if (!make_plan(p, row_bytes, choose_shape(&defaults, p, row_bytes), &pl)) return RCG_EINVAL;
+    if (!make_plan(p, row_bytes, choose_shape(&defaults, ~0ull), &pl)) return RCG_EINVAL;
     const ShapeInfo si = shape_info(pl.shape);
     out->tile_bytes = pl.W;
     out->tiles_per_stripe = pl.tiles_per_stripe;
@@ -330,6 +346,7 @@ rcg_status rcg_destroy(rcg_ctx *ctx) {
         if (s.done) cudaEventSynchronize(s.done);
         free_slot(s);
     }
+    host_staging_destroy(ctx->host);
     if (ctx->status) cudaFree(ctx->status);
     delete ctx;
     return RCG_OK;
@@ -351,6 +368,12 @@ rcg_status rcg_set_engine_shape(rcg_ctx *ctx, int shape) {
     if (!ctx || (shape != RCG_SHAPE_AUTO && shape != RCG_SHAPE_WIDE && shape != RCG_SHAPE_PAIR))
         return RCG_EINVAL;
     ctx->shape = shape;
+    return RCG_OK;
+}
+
+rcg_status rcg_set_host_chunk(rcg_ctx *ctx, uint64_t bytes) {
+    if (!ctx || bytes < 4096) return RCG_EINVAL;
+    ctx->host_chunk_bytes = bytes;
     return RCG_OK;
 }
 
@@ -382,7 +405,7 @@ rcg_status rcg_encode(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe, 
     if (n_stripes == 0) return RCG_OK;
     if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
     Plan pl;
-    if (!make_plan(g.p, g.C, choose_shape(ctx, g.p, g.C), &pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, n_stripes)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, first_stripe, n_stripes, pl);
     J.op = OP_ENCODE;
     DeviceGuard guard(ctx->device);
@@ -397,7 +420,7 @@ rcg_status rcg_recover(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint3
     if (st) return st;
     if (!(i < j && j <= g.N + 1)) return RCG_EINVAL;
     Plan pl;
-    if (!make_plan(g.p, g.C, choose_shape(ctx, g.p, g.C), &pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, 1)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, stripe, 1, pl);
     J.op = OP_RECOVER;
     J.i = static_cast<uint8_t>(i);
@@ -415,7 +438,7 @@ rcg_status rcg_recover_many(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_st
     if (n_stripes == 0) return RCG_OK;
     if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
     Plan pl;
-    if (!make_plan(g.p, g.C, choose_shape(ctx, g.p, g.C), &pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, n_stripes)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, first_stripe, n_stripes, pl);
     J.op = OP_RECOVER;
     J.pairs = pairs;
@@ -433,7 +456,7 @@ rcg_status rcg_update(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32
     const uint64_t ars = new_row_stride ? new_row_stride : g.C;
     if (ars < g.C || (ars & 15)) return RCG_EINVAL;
     Plan pl;
-    if (!make_plan(g.p, g.C, choose_shape(ctx, g.p, g.C), &pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, 1)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, stripe, 1, pl);
     J.op = OP_UPDATE;
     J.i = static_cast<uint8_t>(i);
@@ -454,7 +477,7 @@ rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe,
     const uint64_t ors = out_row_stride ? out_row_stride : g.C;
     if (ors < g.C || (ors & 15)) return RCG_EINVAL;
     Plan pl;
-    if (!make_plan(g.p, g.C, choose_shape(ctx, g.p, g.C), &pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, 1)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, stripe, 1, pl);
     J.op = OP_DEGRADED;
     J.j = static_cast<uint8_t>(j);
@@ -576,9 +599,12 @@ static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t jobs, uint32_t
 // One engine shape for a whole batch: the context's explicit choice, else
 // pair when every job's geometry prefers it.
 static uint32_t batch_shape(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs) {
-    for (uint32_t k = 0; k < n_jobs; ++k)
-        if (choose_shape(ctx, jobs[k].layout.p, jobs[k].layout.row_bytes) != SHAPE_PAIR) return SHAPE_WIDE;
-    return SHAPE_PAIR;
+    uint64_t bytes = 0;
+    for (uint32_t k = 0; k < n_jobs; ++k) {
+        Geo g;
+        if (check_layout(&jobs[k].layout, &g) == RCG_OK) bytes += launch_bytes(g, jobs[k].n_stripes);
+    }
+    return choose_shape(ctx, bytes);
 }
 
 // The descriptor table of a batch (header + jobs) for one engine shape.
@@ -671,6 +697,35 @@ rcg_status rcg_batch_wait(rcg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns) {
     BatchSlot &s = ctx->slots[ticket % kBatchRing];
     if (!s.used || s.ticket != ticket) return RCG_OK;  // slot reused: that batch finished
     return wait_event(s.done, timeout_ns);
+}
+
+// ===================================================== host-memory stripes
+
+static rcg_status run_encode(void *c, const rcg_layout *L, uint64_t n, const uint8_t *, cudaStream_t s) {
+    return rcg_encode(static_cast<rcg_ctx *>(c), L, 0, n, s);
+}
+
+static rcg_status run_recover(void *c, const rcg_layout *L, uint64_t n, const uint8_t *pairs,
+                              cudaStream_t s) {
+    return rcg_recover_many(static_cast<rcg_ctx *>(c), L, 0, n, pairs, s);
+}
+
+rcg_status rcg_encode_host(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe, uint64_t n_stripes,
+                           void *stream) {
+    if (!ctx) return RCG_EINVAL;
+    DeviceGuard guard(ctx->device);
+    if (!ctx->host) ctx->host = host_staging_create();
+    return host_path(ctx->host, L, first_stripe, n_stripes, nullptr, static_cast<cudaStream_t>(stream),
+                     ctx->host_chunk_bytes, run_encode, ctx);
+}
+
+rcg_status rcg_recover_many_host(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe,
+                                 uint64_t n_stripes, const uint8_t *pairs, void *stream) {
+    if (!ctx || !pairs) return RCG_EINVAL;
+    DeviceGuard guard(ctx->device);
+    if (!ctx->host) ctx->host = host_staging_create();
+    return host_path(ctx->host, L, first_stripe, n_stripes, pairs, static_cast<cudaStream_t>(stream),
+                     ctx->host_chunk_bytes, run_recover, ctx);
 }
 
 // =============================================================== utilities

@@ -1,0 +1,233 @@
+// rcg_host.cu -- encode and recovery of stripes that live in (page-locked)
+// HOST memory: the data are streamed through context-owned device staging
+// buffers in chunks of stripes, on three internal streams, so the upload of
+// one chunk, the tile engine on another and the download of a third overlap.
+//
+//   encode:   data strips in  -> rcg_encode on the chunk -> P and Q strips out
+//   recovery: whole stripes in (the erased strips' bytes are never read) ->
+//             rcg_recover_many on the chunk -> a small kernel writes the two
+//             rebuilt strips of each stripe straight back into the host
+//             stripes through their device-visible (mapped) addresses.
+//
+// The caller's stream orders the call: the internal streams wait for it on
+// entry and it waits for them on exit.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "../../include/rcg.h"
+#include "rcg_internal.h"
+
+namespace {
+
+// Copy the rebuilt strips (i, j) of each stripe of a device chunk back to the
+// host stripes.  One 16-byte vector per thread-iteration; pairs that are not
+// a valid erasure pair (the engine skipped those stripes) are skipped here too.
+__global__ void writeback_kernel(const uint8_t *chunk, uint64_t chunk_stripe_bytes, uint64_t strip_bytes,
+                                 uint8_t *host_dev, uint64_t h_row, uint64_t h_strip, uint64_t h_stripe,
+                                 const uint8_t *pairs, uint32_t n_stripes, uint32_t rows, uint32_t nvec,
+                                 uint32_t n_total) {
+    const uint64_t per_stripe = 2ull * rows * nvec;
+    const uint64_t total = per_stripe * n_stripes;
+    for (uint64_t q = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; q < total;
+         q += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t s = static_cast<uint32_t>(q / per_stripe);
+        uint64_t rem = q - s * per_stripe;
+        const uint32_t which = static_cast<uint32_t>(rem / (static_cast<uint64_t>(rows) * nvec));
+        rem -= which * static_cast<uint64_t>(rows) * nvec;
+        const uint32_t r = static_cast<uint32_t>(rem / nvec);
+        const uint32_t v = static_cast<uint32_t>(rem - static_cast<uint64_t>(r) * nvec);
+        const uint32_t a = pairs[2ull * s], b = pairs[2ull * s + 1];
+        if (!(a < b && b <= n_total + 1)) continue;
+        const uint32_t k = which ? b : a;
+        const uint4 val = *reinterpret_cast<const uint4 *>(chunk + s * chunk_stripe_bytes + k * strip_bytes +
+                                                           static_cast<uint64_t>(r) * nvec * 16 + v * 16ull);
+        *reinterpret_cast<uint4 *>(host_dev + s * h_stripe + k * h_strip + r * h_row + v * 16ull) = val;
+    }
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+struct HostGeo {
+    uint32_t p, N;
+    uint64_t C, rs, ss, st;
+    uint64_t strip_bytes;   // packed strip in the staging chunk: (p-1) * C
+    uint64_t stripe_bytes;  // packed stripe in the staging chunk: (N+2) * strip_bytes
+};
+
+bool host_geo(const rcg_layout *L, HostGeo *g) {
+    if (!L || !L->base) return false;
+    g->p = L->p;
+    g->N = L->n_data;
+    g->C = L->row_bytes;
+    if (g->p < 3 || g->p > 61 || g->N < 1 || g->N > g->p || g->C == 0 || (g->C & 15)) return false;
+    g->rs = L->row_stride ? L->row_stride : g->C;
+    g->ss = L->strip_stride ? L->strip_stride : (g->p - 1) * g->rs;
+    g->st = L->stripe_stride ? L->stripe_stride : (g->N + 2) * g->ss;
+    if (g->rs < g->C || (g->rs & 15) || (g->ss & 15) || (g->st & 15) || !aligned16(L->base)) return false;
+    g->strip_bytes = (g->p - 1) * g->C;
+    g->stripe_bytes = (g->N + 2) * g->strip_bytes;
+    return true;
+}
+
+// Copy strips [k0, k1) of n stripes between a host layout and the packed
+// staging chunk, in as few 2-D copies as the host strides allow.
+cudaError_t copy_strips(bool to_device, uint8_t *chunk, const HostGeo &g, uint8_t *host_first,
+                        uint32_t k0, uint32_t k1, uint64_t n, cudaStream_t s) {
+    const cudaMemcpyKind kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    const bool rows_packed = g.rs == g.C;
+    const bool strips_packed = rows_packed && g.ss == g.strip_bytes;
+    if (strips_packed) {  // strips k0..k1 of a stripe are one contiguous block
+        uint8_t *h = host_first + k0 * g.ss;
+        uint8_t *d = chunk + k0 * g.strip_bytes;
+        const uint64_t w = (k1 - k0) * g.strip_bytes;
+        return to_device ? cudaMemcpy2DAsync(d, g.stripe_bytes, h, g.st, w, n, kind, s)
+                         : cudaMemcpy2DAsync(h, g.st, d, g.stripe_bytes, w, n, kind, s);
+    }
+    for (uint32_t k = k0; k < k1; ++k) {
+        if (rows_packed) {
+            uint8_t *h = host_first + k * g.ss;
+            uint8_t *d = chunk + k * g.strip_bytes;
+            cudaError_t e = to_device ? cudaMemcpy2DAsync(d, g.stripe_bytes, h, g.st, g.strip_bytes, n, kind, s)
+                                      : cudaMemcpy2DAsync(h, g.st, d, g.stripe_bytes, g.strip_bytes, n, kind, s);
+            if (e != cudaSuccess) return e;
+        } else {
+            for (uint32_t r = 0; r + 1 < g.p; ++r) {
+                uint8_t *h = host_first + k * g.ss + r * g.rs;
+                uint8_t *d = chunk + k * g.strip_bytes + r * g.C;
+                cudaError_t e = to_device ? cudaMemcpy2DAsync(d, g.stripe_bytes, h, g.st, g.C, n, kind, s)
+                                          : cudaMemcpy2DAsync(h, g.st, d, g.stripe_bytes, g.C, n, kind, s);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+namespace rcg {
+
+// Context-owned staging for the host path (see rcg_api.cu for the owner).
+struct HostStaging {
+    uint8_t *buf[3] = {nullptr, nullptr, nullptr};
+    uint8_t *pairs[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t stream[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_in = nullptr, ev_out[3] = {nullptr, nullptr, nullptr};
+    uint64_t bytes = 0;        // per chunk buffer
+    uint64_t pair_bytes = 0;   // per chunk pairs buffer
+};
+
+HostStaging *host_staging_create() { return new HostStaging(); }
+
+void host_staging_destroy(HostStaging *h) {
+    if (!h) return;
+    for (int k = 0; k < 3; ++k) {
+        if (h->stream[k]) cudaStreamSynchronize(h->stream[k]);
+        if (h->buf[k]) cudaFree(h->buf[k]);
+        if (h->pairs[k]) cudaFree(h->pairs[k]);
+        if (h->stream[k]) cudaStreamDestroy(h->stream[k]);
+        if (h->ev_out[k]) cudaEventDestroy(h->ev_out[k]);
+    }
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    delete h;
+}
+
+static cudaError_t staging_ready(HostStaging *h, uint64_t bytes, uint64_t pair_bytes) {
+    if (!h->stream[0]) {
+        for (int k = 0; k < 3; ++k) {
+            cudaError_t e = cudaStreamCreateWithFlags(&h->stream[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out[k], cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    if (h->bytes < bytes || h->pair_bytes < pair_bytes) {
+        for (int k = 0; k < 3; ++k) {
+            cudaStreamSynchronize(h->stream[k]);
+            if (h->buf[k]) cudaFree(h->buf[k]);
+            if (h->pairs[k]) cudaFree(h->pairs[k]);
+            h->buf[k] = h->pairs[k] = nullptr;
+        }
+        h->bytes = h->pair_bytes = 0;
+        for (int k = 0; k < 3; ++k) {
+            cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&h->buf[k]), bytes);
+            if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->pairs[k]), pair_bytes);
+            if (e != cudaSuccess) return e;
+        }
+        h->bytes = bytes;
+        h->pair_bytes = pair_bytes;
+    }
+    return cudaSuccess;
+}
+
+// Shared driver of the two host-path calls.  encode_fn / recover_fn run the
+// tile engine on a packed device chunk of n stripes.
+rcg_status host_path(HostStaging *h, const rcg_layout *L, uint64_t first, uint64_t n_stripes,
+                     const uint8_t *pairs_host, cudaStream_t caller, uint64_t chunk_bytes,
+                     rcg_status (*run)(void *, const rcg_layout *, uint64_t, const uint8_t *, cudaStream_t),
+                     void *run_arg) {
+    HostGeo g;
+    if (!h || !host_geo(L, &g)) return RCG_EINVAL;
+    if (n_stripes == 0) return RCG_OK;
+    // the host stripes must be page-locked and visible to the device
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, L->base) != cudaSuccess || attr.type != cudaMemoryTypeHost ||
+        !attr.devicePointer) {
+        cudaGetLastError();
+        return RCG_EINVAL;
+    }
+    uint8_t *host = static_cast<uint8_t *>(L->base);
+    uint8_t *host_dev = static_cast<uint8_t *>(attr.devicePointer);
+    const uint64_t per_chunk = std::max<uint64_t>(1, chunk_bytes / g.stripe_bytes);
+    cudaError_t e = staging_ready(h, per_chunk * g.stripe_bytes, 2 * per_chunk);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? RCG_ENOMEM : RCG_ECUDA;
+
+    e = cudaEventRecord(h->ev_in, caller);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(h->stream[k], h->ev_in, 0);
+    rcg_status st = RCG_OK;
+    uint64_t c = 0;
+    for (uint64_t s0 = 0; s0 < n_stripes && e == cudaSuccess && st == RCG_OK; s0 += per_chunk, ++c) {
+        const int k = static_cast<int>(c % 3);
+        cudaStream_t s = h->stream[k];
+        const uint64_t n = std::min(per_chunk, n_stripes - s0);
+        uint8_t *hfirst = host + (first + s0) * g.st;
+        rcg_layout dl;
+        memset(&dl, 0, sizeof(dl));
+        dl.base = h->buf[k];
+        dl.p = g.p;
+        dl.n_data = g.N;
+        dl.row_bytes = g.C;
+        if (!pairs_host) {  // encode: data strips in, parity strips out
+            e = copy_strips(true, h->buf[k], g, hfirst, 0, g.N, n, s);
+            if (e == cudaSuccess) st = run(run_arg, &dl, n, nullptr, s);
+            if (e == cudaSuccess && st == RCG_OK) e = copy_strips(false, h->buf[k], g, hfirst, g.N, g.N + 2, n, s);
+        } else {            // recovery: stripes in, the two rebuilt strips written back
+            e = copy_strips(true, h->buf[k], g, hfirst, 0, g.N + 2, n, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->pairs[k], pairs_host + 2 * s0, 2 * n, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) st = run(run_arg, &dl, n, h->pairs[k], s);
+            if (e == cudaSuccess && st == RCG_OK) {
+                const uint32_t rows = g.p - 1, nvec = static_cast<uint32_t>(g.C / 16);
+                const uint64_t work = 2ull * rows * nvec * n;
+                const unsigned blocks = static_cast<unsigned>(std::min<uint64_t>((work + 255) / 256, 152ull * 8));
+                writeback_kernel<<<blocks, 256, 0, s>>>(h->buf[k], g.stripe_bytes, g.strip_bytes,
+                                                        host_dev + (first + s0) * g.st, g.rs, g.ss, g.st,
+                                                        h->pairs[k], static_cast<uint32_t>(n), rows, nvec, g.N);
+                e = cudaGetLastError();
+            }
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        cudaError_t e2 = cudaEventRecord(h->ev_out[k], h->stream[k]);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(caller, h->ev_out[k], 0);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (st != RCG_OK) return st;
+    return e == cudaSuccess ? RCG_OK : RCG_ECUDA;
+}
+
+}  // namespace rcg

@@ -57,6 +57,7 @@ EXPORTS = {
     "rcg_set_copy_mode": (_int, [_vp, _int]),
     "rcg_set_dd_solve": (_int, [_vp, _int]),
     "rcg_set_engine_shape": (_int, [_vp, _int]),
+    "rcg_set_host_chunk": (_int, [_vp, _u64]),
     "rcg_last_device_status": (_int, [_vp, ctypes.POINTER(_u32)]),
     "rcg_status_str": (ctypes.c_char_p, [_int]),
     "rcg_abi_version": (_u32, []),
@@ -66,6 +67,8 @@ EXPORTS = {
     "rcg_recover_many": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u64, _vp, _vp]),
     "rcg_update": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u32, _vp, _u64, _vp]),
     "rcg_degraded_read": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u32, _vp, _u64, _vp]),
+    "rcg_encode_host": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u64, _vp]),
+    "rcg_recover_many_host": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u64, _vp, _vp]),
     "rcg_batch_submit": (_int, [_vp, ctypes.POINTER(rcg_job), _u32, _vp, ctypes.POINTER(_u64)]),
     "rcg_batch_wait": (_int, [_vp, _u64, _u64]),
     "rcg_batch_submit_noalloc": (_int, [ctypes.POINTER(rcg_job), _u32, _vp, _vp]),
@@ -167,6 +170,10 @@ def rcg_set_engine_shape(ctx: int, shape: int):
     _check(lib().rcg_set_engine_shape(ctx, shape), "rcg_set_engine_shape")
 
 
+def rcg_set_host_chunk(ctx: int, nbytes: int):
+    _check(lib().rcg_set_host_chunk(ctx, nbytes), "rcg_set_host_chunk")
+
+
 def rcg_last_device_status(ctx: int) -> int:
     """Synchronise, return and clear the device status word (RCG_DEV_* bits)."""
     code = _u32(0)
@@ -202,6 +209,24 @@ def rcg_degraded_read(ctx: int, layout: rcg_layout, stripe: int, j: int, out, ou
                       stream=None):
     _check(lib().rcg_degraded_read(ctx, ctypes.byref(layout), stripe, j, _ptr(out), out_row_stride,
                                    _stream(stream)), "rcg_degraded_read")
+
+
+def rcg_encode_host(ctx: int, layout: rcg_layout, first_stripe: int, n_stripes: int, stream=None):
+    """rcg_encode for stripes in page-locked host memory (layout.base = host address)."""
+    _check(lib().rcg_encode_host(ctx, ctypes.byref(layout), first_stripe, n_stripes, _stream(stream)),
+           "rcg_encode_host")
+
+
+def rcg_recover_many_host(ctx: int, layout: rcg_layout, first_stripe: int, n_stripes: int, pairs,
+                          stream=None):
+    """rcg_recover_many for stripes in page-locked host memory; pairs is a HOST
+    uint8 array (numpy or CPU tensor) of shape [n_stripes, 2]."""
+    if hasattr(pairs, "ctypes"):
+        ptr = pairs.ctypes.data
+    else:
+        ptr = _ptr(pairs)
+    _check(lib().rcg_recover_many_host(ctx, ctypes.byref(layout), first_stripe, n_stripes, ptr,
+                                       _stream(stream)), "rcg_recover_many_host")
 
 
 def make_job(layout: rcg_layout, first_stripe: int, n_stripes: int, op: int, i: int = 0, j: int = 0,
@@ -285,6 +310,12 @@ class Context:
     def recover_many(self, layout, first_stripe, n_stripes, pairs, stream=None):
         rcg_recover_many(self.handle, layout, first_stripe, n_stripes, pairs, stream)
 
+    def encode_host(self, layout, first_stripe, n_stripes, stream=None):
+        rcg_encode_host(self.handle, layout, first_stripe, n_stripes, stream)
+
+    def recover_many_host(self, layout, first_stripe, n_stripes, pairs, stream=None):
+        rcg_recover_many_host(self.handle, layout, first_stripe, n_stripes, pairs, stream)
+
     def update(self, layout, stripe, i, new_strip, new_row_stride=0, stream=None):
         rcg_update(self.handle, layout, stripe, i, new_strip, new_row_stride, stream)
 
@@ -308,6 +339,9 @@ class Context:
 
     def set_engine_shape(self, shape):
         rcg_set_engine_shape(self.handle, shape)
+
+    def set_host_chunk(self, nbytes):
+        rcg_set_host_chunk(self.handle, nbytes)
 
     def last_device_status(self) -> int:
         return rcg_last_device_status(self.handle)

@@ -261,6 +261,39 @@ def test_row_copy_path_matches_oracle(rcg, oracle, p, N, C, S):
         assert np.array_equal(buf.cpu().numpy(), want)
 
 
+# ------------------------------------------------------- host-memory stripes
+
+@pytest.mark.parametrize("p,N,C,S,chunk", [(13, 12, 4096, 70, 1 << 28), (13, 12, 4096, 70, 3 << 20),
+                                              (5, 4, 1024, 33, 50000), (59, 58, 528, 5, 4096)])
+def test_host_memory_calls_match_oracle(rcg, oracle, p, N, C, S, chunk):
+    # chunk sizes that give one chunk, several chunks over three streams, and one stripe per chunk
+    host = host_stripes(1100 + p, p, N, C, S)
+    want = host.copy()
+    oracle.encode(p, N, C, want, S)
+    pinned = torch.from_numpy(host.copy()).pin_memory()
+    L = rcg.make_layout(pinned, p, N, C)
+    ctx = rcg.Context(0)
+    ctx.set_host_chunk(chunk)
+    ctx.encode_host(L, 0, S)
+    torch.cuda.synchronize()
+    assert np.array_equal(pinned.numpy(), want)
+    pairs = inputs.random_pairs(9, N, S, "any")
+    for s, (i, j) in enumerate(pairs):
+        pinned[s, int(i)] = POISON_I
+        pinned[s, int(j)] = POISON_J
+    ctx.recover_many_host(L, 0, S, pairs)
+    torch.cuda.synchronize()
+    assert ctx.last_device_status() == 0
+    assert np.array_equal(pinned.numpy(), want)
+    ctx.close()
+
+
+def test_host_memory_calls_need_pinned_memory(rcg, ctx):
+    pageable = torch.zeros((2, 6, 4, 16), dtype=torch.uint8)
+    with pytest.raises(rcg.RcgError):
+        ctx.encode_host(rcg.make_layout(pageable, 5, 4, 16), 0, 2)
+
+
 # ------------------------------------------------------------------ batches
 
 def test_batch_mixed_jobs_alone_and_in_the_mix(rcg, ctx, oracle):
