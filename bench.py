@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--stripes", type=int, default=S,
                     help="stripes per GPU (default 8192; smaller values are profiling cases, not bench lines)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "batched"],
+                    help="c2: the bench line; batched: the uneven 50k-stripe batch vs per-stripe launches")
+    ap.add_argument("--batch-jobs", type=int, default=50000)
+    ap.add_argument("--arena-gb", type=float, default=100.0)
     return ap.parse_args()
 
 
@@ -380,8 +384,104 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+# ----------------------------------------------------------- batched form
+
+def run_batched(args):
+    """The uneven batched workload: 50k single-stripe descriptors (p over
+    {5,13,29,59}, N in [3,p-1], rows 512 B..64 KiB log-uniform, 60 % encode /
+    40 % two-erasure recovery), 390 GiB with parity, so it runs in waves that
+    fit the device arena.  Each wave is timed twice on the same bytes: as ONE
+    persistent batch launch (rcg_batch_submit, CUDA graph) and as one launch
+    per stripe (rcg_encode / rcg_recover).  Recovery stripes are encoded before
+    the timed region."""
+    import torch
+
+    from paper_cs_0611109_gb300 import build, inputs
+    build.build()
+    from paper_cs_0611109_gb300 import rcg
+
+    torch.cuda.set_device(0)
+    ctx = rcg.Context(0)
+    stream = torch.cuda.current_stream()
+    jobs = inputs.batched_jobs(3, args.batch_jobs)
+    free = torch.cuda.mem_get_info()[0]
+    arena_bytes = int(min(args.arena_gb * 1e9, 0.8 * free))
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
+    base = arena.data_ptr()
+    align = lambda x: (x + 255) // 256 * 256
+    waves, cur, used = [], [], 0
+    for j in jobs:
+        sz = align(inputs.stripe_bytes(j["p"], j["n"], j["c"]))
+        if used + sz > arena_bytes and cur:
+            waves.append(cur)
+            cur, used = [], 0
+        cur.append((j, used))
+        used += sz
+    if cur:
+        waves.append(cur)
+
+    tot = {"batched_ms": 0.0, "per_stripe_ms": 0.0, "user": 0, "moved": 0, "launches_per_stripe": 0}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for w in waves:
+        used = w[-1][1] + align(inputs.stripe_bytes(w[-1][0]["p"], w[-1][0]["n"], w[-1][0]["c"]))
+        rcg.rcg_fill_random(arena, used, 3)
+        lays = [rcg.make_layout(base + o, j["p"], j["n"], j["c"]) for j, o in w]
+        pre = [rcg.make_job(L, 0, 1, rcg.RCG_OP_ENCODE) for L, (j, _) in zip(lays, w) if j["op"] == "recover"]
+        if pre:
+            assert ctx.batch_wait(ctx.batch_submit(pre))
+        mix = [rcg.make_job(L, 0, 1, rcg.RCG_OP_ENCODE) if j["op"] == "encode" else
+               rcg.make_job(L, 0, 1, rcg.RCG_OP_RECOVER, j["i"], j["j"]) for L, (j, _) in zip(lays, w)]
+        for _ in range(2):  # warm-up (graph capture, tensor maps, caches)
+            ctx.batch_wait(ctx.batch_submit(mix))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        t = ctx.batch_submit(mix)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot["batched_ms"] += e0.elapsed_time(e1)
+        e0.record(stream)
+        for L, (j, _) in zip(lays, w):
+            if j["op"] == "encode":
+                ctx.encode(L, 0, 1)
+            else:
+                ctx.recover(L, 0, j["i"], j["j"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot["per_stripe_ms"] += e0.elapsed_time(e1)
+        tot["launches_per_stripe"] += len(w)
+        for j, _ in w:
+            tot["user"] += j["n"] * (j["p"] - 1) * j["c"]
+            tot["moved"] += (j["n"] + 2) * (j["p"] - 1) * j["c"]
+    status = ctx.last_device_status()
+    if status:
+        raise RuntimeError("device status word %#x" % status)
+    peak, kind = peak_hbm()
+    gbs = lambda nbytes, ms: nbytes / (ms * 1e-3) / 1e9
+    out = {"metric": "batched uneven stripes: user GB/s, one persistent launch per wave vs one launch per stripe",
+           "value": round(gbs(tot["user"], tot["batched_ms"]), 2), "unit": "GB/s", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "u8", "data": "synthetic (SplitMix64 bytes, seed 3)",
+           "config": {"workload": "batched uneven: %d single-stripe jobs, p in {5,13,29,59}, N in [3,p-1], "
+                                  "rows 512 B..64 KiB log-uniform, 60%% encode / 40%% recovery" % len(jobs),
+                      "waves": len(waves), "arena_bytes": arena_bytes, "user_bytes": tot["user"],
+                      "hbm_bytes": tot["moved"]},
+           "batched": {"ms": round(tot["batched_ms"], 3), "user_gbs": round(gbs(tot["user"], tot["batched_ms"]), 1),
+                       "hbm_gbs": round(gbs(tot["moved"], tot["batched_ms"]), 1),
+                       "hbm_frac": round(gbs(tot["moved"], tot["batched_ms"]) / peak, 4), "launches": len(waves)},
+           "per_stripe": {"ms": round(tot["per_stripe_ms"], 3),
+                          "user_gbs": round(gbs(tot["user"], tot["per_stripe_ms"]), 1),
+                          "hbm_gbs": round(gbs(tot["moved"], tot["per_stripe_ms"]), 1),
+                          "launches": tot["launches_per_stripe"]},
+           "speedup_batched_over_per_stripe": round(tot["per_stripe_ms"] / tot["batched_ms"], 2),
+           "peak": peak, "peak_kind": kind}
+    ctx.close()
+    return out
+
+
 def main():
     args = parse()
+    if args.workload == "batched" and args.impl == "ours":
+        print(json.dumps(run_batched(args)), flush=True)
+        return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out), flush=True)

@@ -27,7 +27,7 @@ struct BatchSlot {
     uint8_t *host = nullptr;  // pinned descriptor table (header + jobs)
     uint8_t *dev = nullptr;   // device copy read by the kernel
     unsigned long long *counter = nullptr;
-    size_t cap_jobs = 0;
+    size_t cap_bytes = 0;      // size of the host and device table buffers
     size_t bytes = 0;          // bytes the captured memcpy node copies
     cudaStream_t capture = nullptr;
     cudaGraph_t graph = nullptr;       // kept alive: exec updates name its nodes
@@ -535,7 +535,7 @@ static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
     s.exec = nullptr;
     s.graph = nullptr;
     s.copy_node = nullptr;
-    const size_t bytes = sizeof(BatchHeader) + s.cap_jobs * sizeof(Job);
+    const size_t bytes = s.cap_bytes;
     s.bytes = bytes;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s.capture, cudaStreamCaptureModeThreadLocal);
@@ -575,15 +575,14 @@ static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
     return RCG_OK;
 }
 
-// (Re)allocate a batch slot for `jobs` descriptors; recapture its graph when
+// (Re)allocate a batch slot for a table of `bytes`; recapture its graph when
 // the engine shape changes.
-static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t jobs, uint32_t shape) {
-    if (s.cap_jobs >= jobs && s.exec) return s.shape == shape ? RCG_OK : capture_slot(ctx, s, shape);
+static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t bytes, uint32_t shape) {
+    if (s.cap_bytes >= bytes && s.exec) return s.shape == shape ? RCG_OK : capture_slot(ctx, s, shape);
     free_slot(s);
-    const size_t cap = std::max<size_t>(jobs, 256);
-    const size_t bytes = sizeof(BatchHeader) + cap * sizeof(Job);
-    cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&s.host), bytes, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s.dev), bytes);
+    const size_t cap = std::max<size_t>(bytes, 64 * 1024);
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&s.host), cap, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s.dev), cap);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s.counter), sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.capture, cudaStreamNonBlocking);
@@ -591,13 +590,13 @@ static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t jobs, uint32_t
         free_slot(s);
         return from_cuda(e, "batch slot allocation");
     }
-    memset(s.host, 0, bytes);
-    s.cap_jobs = cap;
+    memset(s.host, 0, cap);
+    s.cap_bytes = cap;
     return capture_slot(ctx, s, shape);
 }
 
 // One engine shape for a whole batch: the context's explicit choice, else
-// pair when every job's geometry prefers it.
+// by the batch's total traffic.
 static uint32_t batch_shape(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs) {
     uint64_t bytes = 0;
     for (uint32_t k = 0; k < n_jobs; ++k) {
@@ -607,25 +606,59 @@ static uint32_t batch_shape(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_
     return choose_shape(ctx, bytes);
 }
 
-// The descriptor table of a batch (header + jobs) for one engine shape.
+// The descriptor table of a batch for one engine shape, built in `out`:
+// header, jobs, then work items.  Items hold up to tiles_per_item tiles of
+// one job (kTilesPerItem, raised when max_items caps the item count); the
+// items of larger jobs come first so the batch ends on small items.
 static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, uint32_t shape,
-                              BatchHeader *hdr, Job *table) {
+                              uint64_t max_items, std::vector<uint8_t> &out) {
+    std::vector<Job> table(n_jobs);
+    std::vector<uint64_t> tiles(n_jobs);
     uint64_t total = 0;
     uint32_t slot_bytes = 0;
     for (uint32_t k = 0; k < n_jobs; ++k) {
         Plan pl;
         rcg_status st = build_job(ctx, jobs[k], shape, &table[k], &pl);
         if (st) return st;
+        tiles[k] = static_cast<uint64_t>(table[k].n_stripes) * table[k].tiles_per_stripe;
         table[k].tile_begin = total;
-        total += static_cast<uint64_t>(table[k].n_stripes) * table[k].tiles_per_stripe;
+        total += tiles[k];
         slot_bytes = std::max(slot_bytes, pl.slot_bytes);
     }
-    memset(hdr, 0, sizeof(*hdr));
-    hdr->total_tiles = total;
-    hdr->n_jobs = n_jobs;
-    hdr->slot_bytes = slot_bytes;
-    hdr->n_slots = std::min<uint32_t>(kMaxSlots, shape_info(shape).ring_bytes / slot_bytes);
-    hdr->shape = shape;
+    uint64_t per = kTilesPerItem;
+    if (max_items && (total + per - 1) / per > max_items) per = (total + max_items - 1) / max_items;
+    std::vector<uint32_t> order(n_jobs);
+    for (uint32_t k = 0; k < n_jobs; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        return table[x].n_stripes * static_cast<uint64_t>(table[x].p - 1) * table[x].C * (table[x].n + 2u) >
+               table[y].n_stripes * static_cast<uint64_t>(table[y].p - 1) * table[y].C * (table[y].n + 2u);
+    });
+    std::vector<WorkItem> items;
+    for (uint32_t k : order)
+        for (uint64_t t = 0; t < tiles[k]; t += per) {
+            WorkItem w;
+            w.job = k;
+            w.tile0 = static_cast<uint32_t>(t);
+            w.ntiles = static_cast<uint32_t>(std::min<uint64_t>(per, tiles[k] - t));
+            w.pad = 0;
+            items.push_back(w);
+        }
+    for (uint32_t k = 0; k < n_jobs; ++k)
+        if (tiles[k] > 0xffffffffull) return RCG_EINVAL;
+    if (items.size() > 0xffffffffull) return RCG_EINVAL;
+    BatchHeader hdr;
+    memset(&hdr, 0, sizeof(hdr));
+    hdr.total_tiles = total;
+    hdr.n_jobs = n_jobs;
+    hdr.slot_bytes = slot_bytes;
+    hdr.n_slots = std::min<uint32_t>(kMaxSlots, shape_info(shape).ring_bytes / slot_bytes);
+    hdr.shape = shape;
+    hdr.n_items = static_cast<uint32_t>(items.size());
+    hdr.items_offset = sizeof(BatchHeader) + static_cast<uint64_t>(n_jobs) * sizeof(Job);
+    out.resize(hdr.items_offset + items.size() * sizeof(WorkItem));
+    memcpy(out.data(), &hdr, sizeof(hdr));
+    memcpy(out.data() + sizeof(hdr), table.data(), static_cast<size_t>(n_jobs) * sizeof(Job));
+    memcpy(out.data() + hdr.items_offset, items.data(), items.size() * sizeof(WorkItem));
     return RCG_OK;
 }
 
@@ -634,10 +667,9 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
     if (!ctx || !ticket || (n_jobs && !jobs)) return RCG_EINVAL;
     *ticket = 0;
     if (n_jobs == 0) return RCG_OK;
-    std::vector<Job> table(n_jobs);
-    BatchHeader hdr;
+    std::vector<uint8_t> image;
     const uint32_t shape = batch_shape(ctx, jobs, n_jobs);
-    rcg_status st0 = build_table(ctx, jobs, n_jobs, shape, &hdr, table.data());
+    rcg_status st0 = build_table(ctx, jobs, n_jobs, shape, 0, image);
     if (st0) return st0;
 
     DeviceGuard guard(ctx->device);
@@ -648,11 +680,10 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
         if (st == RCG_ETIMEOUT) return RCG_EBUSY;
         if (st) return st;
     }
-    rcg_status st = prepare_slot(ctx, s, n_jobs, shape);
+    const size_t bytes = image.size();
+    rcg_status st = prepare_slot(ctx, s, bytes, shape);
     if (st) return st;
-    const size_t bytes = sizeof(BatchHeader) + static_cast<size_t>(n_jobs) * sizeof(Job);
-    memcpy(s.host, &hdr, sizeof(hdr));
-    memcpy(s.host + sizeof(hdr), table.data(), static_cast<size_t>(n_jobs) * sizeof(Job));
+    memcpy(s.host, image.data(), bytes);
     cudaError_t e = cudaSuccess;
     const char *where = "graph copy-size update";
     if (bytes != s.bytes) {
@@ -740,10 +771,17 @@ rcg_status rcg_fill_random(void *dev, uint64_t nbytes, uint64_t seed, uint64_t b
 }  // extern "C"
 
 // Descriptor table for rcg_batch_submit_noalloc (default copy mode, solve and
-// shape; no context).  Returns the engine shape through *shape.
-bool rcg::noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, BatchHeader *hdr, Job *table,
-                              uint32_t *shape) {
+// shape; no context), written into `table` of `capacity` bytes with at most
+// kNoallocItems work items.  Returns the engine shape through *shape.
+bool rcg::noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, uint8_t *table, size_t capacity,
+                              size_t *bytes, uint32_t *shape) {
     static const rcg_ctx defaults;
     *shape = batch_shape(&defaults, jobs, n_jobs);
-    return build_table(&defaults, jobs, n_jobs, *shape, hdr, table) == RCG_OK;
+    const uint64_t max_items = (capacity - sizeof(BatchHeader) - n_jobs * sizeof(Job)) / sizeof(WorkItem) - n_jobs;
+    std::vector<uint8_t> image;
+    if (build_table(&defaults, jobs, n_jobs, *shape, max_items, image) != RCG_OK || image.size() > capacity)
+        return false;
+    memcpy(table, image.data(), image.size());
+    *bytes = image.size();
+    return true;
 }

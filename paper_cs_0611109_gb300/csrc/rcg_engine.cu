@@ -175,22 +175,27 @@ enum : uint8_t {
 };
 
 // Slot header.  The first 16 bytes are read (one 16-byte load) for every
-// slot; the second half only on a tile's first slot.
+// slot; the rest -- everything a tile's consumers need, so they never read a
+// job descriptor from global memory -- only on a tile's first slot.
 struct SlotHdr {
     uint8_t flags;    // F_* bits
     uint8_t rot;      // x^rot for F_Q
     uint16_t w;       // tile width, bytes
-    uint32_t job;
-    uint32_t stripe;
-    uint32_t c0;      // first column byte of the tile
+    uint32_t pad0;
+    uint64_t pad1;
     uint8_t cls;      // epilogue class
     uint8_t p;
-    uint8_t a, b;     // the erased pair (a < b), or i / j of the op
+    uint8_t a, b;     // the erased pair (a < b), or i / j of the op; b = N for E_ENC
     uint16_t pitch;   // bytes between rows in the slot (the job's tile width W)
     uint8_t zinv;     // two-data tiles: (b - a)^(-1) mod p
-    uint8_t pad[9];
+    uint8_t pad2;
+    uint64_t base;            // the tile's column c0 of strip 0 of its stripe
+    uint64_t strip_stride;
+    uint64_t row_stride;
+    uint64_t out;             // degraded read: the tile's column of the output
+    uint64_t out_row_stride;
 };
-static_assert(sizeof(SlotHdr) == 32, "slot header is 32 bytes");
+static_assert(sizeof(SlotHdr) == 64, "slot header is 64 bytes");
 
 struct Smem {
     uint64_t *full;   // [kMaxSlots] producer -> consumers (tx-counted)
@@ -283,138 +288,153 @@ struct RingPos {
 };
 
 template <class S>
-__device__ void producer(const LaunchParams &prm, const Smem &sm, uint32_t n_jobs,
-                         uint64_t total_tiles, uint32_t slot_bytes, uint32_t n_slots) {
+__device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHeader *bh,
+                         uint64_t total_units, uint32_t slot_bytes, uint32_t n_slots) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t policy = l2_evict_first();
     const uint64_t timeout = prm.timeout_ns;
     const uint32_t ring0 = smem_addr(sm.ring);
+    // batches: work items (a job and a run of its tiles) from a global counter;
+    // single launches: one tile per unit, strided over the grid
+    const WorkItem *items =
+        bh ? reinterpret_cast<const WorkItem *>(reinterpret_cast<const uint8_t *>(bh) + bh->items_offset)
+           : nullptr;
     RingPos pos;
     uint32_t issued = 0;  // slots handed to the consumers
     bool ok = true;
     uint64_t next_static = blockIdx.x;
 
     for (;;) {
-        uint64_t t;
-        if (prm.dynamic_sched) {
+        uint32_t ji;
+        uint64_t lt0;
+        uint32_t nt;
+        if (items) {
             unsigned long long v = 0;
             if (lane == 0) v = atomicAdd(prm.tile_counter, 1ull);
-            t = __shfl_sync(0xffffffffu, v, 0);
+            const uint64_t u = __shfl_sync(0xffffffffu, v, 0);
+            if (u >= total_units) break;
+            const WorkItem wi = items[u];
+            ji = wi.job;
+            lt0 = wi.tile0;
+            nt = wi.ntiles;
         } else {
-            t = next_static;
+            if (next_static >= total_units) break;
+            ji = 0;
+            lt0 = next_static;
+            nt = 1;
             next_static += gridDim.x;
         }
-        if (t >= total_tiles) break;
 
-        // job of this tile: last job with tile_begin <= t
-        uint32_t ji = 0;
-        if (prm.jobs && n_jobs > 1) {
-            uint32_t lo = 0, hi = n_jobs - 1;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if (prm.jobs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
-            }
-            ji = lo;
-        }
         const Job &J = job_ref(prm, ji);  // the tensor map is used in place
-        // the fields this tile needs, loaded once into registers
+        // the fields of this job, loaded once into registers
         const uint32_t p = J.p, N = J.n, rows = p - 1;
         const uint32_t tps = J.tiles_per_stripe, W = J.W, C = J.C, n_stripes = J.n_stripes;
-        const uint32_t op = J.op, use_tmap = J.use_tmap;
-        const uint64_t local = t - J.tile_begin;
-        const uint32_t stripe = static_cast<uint32_t>(local / tps);
-        const uint32_t c0 = static_cast<uint32_t>(local % tps) * W;
-        const uint32_t w = min(W, C - c0);
-        // device-side guard: a tile must fit its slot and the item budget
-        if (p < 3 || p > kMaxP || N < 1 || N > p || (w & 15) || w == 0 || W > kMaxTileBytes ||
-            (W & 15) || rows * W > slot_bytes || p * (w >> 4) > static_cast<uint32_t>(S::kMaxItems) ||
-            stripe >= n_stripes) {
-            if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
-            continue;
-        }
+        const uint32_t op = J.op, use_tmap = J.use_tmap, dd_solve = J.dd_solve;
+        const uint32_t ji_i = J.i, ji_j = J.j;
+        const uint8_t *pairs = J.pairs;
+        uint8_t *const base = J.base;
+        uint8_t *const aux = J.aux;
+        const uint64_t strip_stride = J.strip_stride, row_stride = J.row_stride;
+        const uint64_t stripe_stride = J.stripe_stride;
+        const uint64_t aux_rs = J.aux_row_stride, aux_ss = J.aux_stripe_stride;
 
-        uint8_t cls = E_ENC;
-        uint32_t a = J.i, b = J.j;
-        const bool update = op == OP_UPDATE;
-        if (op == OP_RECOVER) {
-            if (J.pairs) {
-                a = J.pairs[2ull * stripe];
-                b = J.pairs[2ull * stripe + 1];
-            }
-            if (!(a < b && b <= N + 1)) {
-                if (lane == 0) set_status(prm.status, RCG_DEV_BADPAIR);
-                continue;
-            }
-            cls = (b < N) ? (J.dd_solve ? E_DD : E_DDC) : (a == N) ? E_ENC : (b == N) ? E_DP : E_DQ;
-        } else if (op == OP_DEGRADED) {
-            cls = (b == N + 1) ? E_DEGQ : E_DEGP;
-        } else if (update) {
-            if (a >= N) {
+        for (uint32_t q = 0; q < nt && ok; ++q) {
+            const uint64_t local = lt0 + q;
+            const uint32_t stripe = static_cast<uint32_t>(local / tps);
+            const uint32_t c0 = static_cast<uint32_t>(local % tps) * W;
+            const uint32_t w = min(W, C - c0);
+            // device-side guard: a tile must fit its slot and the item budget
+            if (p < 3 || p > kMaxP || N < 1 || N > p || (w & 15) || w == 0 || W > kMaxTileBytes ||
+                (W & 15) || rows * W > slot_bytes || p * (w >> 4) > static_cast<uint32_t>(S::kMaxItems) ||
+                stripe >= n_stripes) {
                 if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
                 continue;
             }
-        }
 
-        uint32_t zinv = 0;
-        if (cls == E_DDC) {  // (b - a)^(p-2) mod p, the inverse in Z/p
-            zinv = 1;
-            for (uint32_t e = 0; e + 2 < p; ++e) zinv = zinv * (b - a) % p;
-        }
+            uint8_t cls = E_ENC;
+            uint32_t a = ji_i, b = ji_j;
+            const bool update = op == OP_UPDATE;
+            if (op == OP_RECOVER) {
+                if (pairs) {
+                    a = pairs[2ull * stripe];
+                    b = pairs[2ull * stripe + 1];
+                }
+                if (!(a < b && b <= N + 1)) {
+                    if (lane == 0) set_status(prm.status, RCG_DEV_BADPAIR);
+                    continue;
+                }
+                cls = (b < N) ? (dd_solve ? E_DD : E_DDC) : (a == N) ? E_ENC : (b == N) ? E_DP : E_DQ;
+            } else if (op == OP_DEGRADED) {
+                cls = (b == N + 1) ? E_DEGQ : E_DEGP;
+            } else if (update) {
+                if (a >= N) {
+                    if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
+                    continue;
+                }
+            }
+            if (cls == E_ENC) b = N;  // P and Q are strips N and N+1
 
-        uint32_t count = 0, rot;
-        for (uint32_t k = 0; k < N + 3; ++k)
-            if (strip_role(cls, update, k, N, a, b, p, &rot)) ++count;
+            uint32_t zinv = 0;
+            if (cls == E_DDC) {  // (b - a)^(p-2) mod p, the inverse in Z/p
+                zinv = 1;
+                for (uint32_t e = 0; e + 2 < p; ++e) zinv = zinv * (b - a) % p;
+            }
 
-        const uint8_t *stripe_base = J.base + stripe * J.stripe_stride + c0;
-        const uint8_t *aux_base = J.aux + stripe * J.aux_stripe_stride + c0;
-        const uint64_t strip_stride = J.strip_stride, row_stride = J.row_stride;
-        const uint64_t aux_rs = J.aux_row_stride;
-        // rows sit W bytes apart in a slot; a tensor copy always lands the full
-        // W-wide box (columns past C are zero-filled), row copies land w bytes
-        const uint32_t tx_tensor = rows * W, tx_rows = rows * w;
-        uint32_t emitted = 0;
-        for (uint32_t k = 0; k < N + 3; ++k) {
-            const uint8_t fl = strip_role(cls, update, k, N, a, b, p, &rot);
-            if (!fl) continue;
-            if (!mbar_wait(smem_addr(&sm.empty[pos.slot]), pos.phase ^ 1u, timeout)) {
-                ok = false;
-                break;
+            uint32_t count = 0, rot;
+            for (uint32_t k = 0; k < N + 3; ++k)
+                if (strip_role(cls, update, k, N, a, b, p, &rot)) ++count;
+
+            uint8_t *const stripe_base = base + stripe * stripe_stride + c0;
+            const uint8_t *aux_base = aux + stripe * aux_ss + c0;
+            // rows sit W bytes apart in a slot; a tensor copy always lands the full
+            // W-wide box (columns past C are zero-filled), row copies land w bytes
+            const uint32_t tx_tensor = rows * W, tx_rows = rows * w;
+            uint32_t emitted = 0;
+            for (uint32_t k = 0; k < N + 3; ++k) {
+                const uint8_t fl = strip_role(cls, update, k, N, a, b, p, &rot);
+                if (!fl) continue;
+                if (!mbar_wait(smem_addr(&sm.empty[pos.slot]), pos.phase ^ 1u, timeout)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t full = smem_addr(&sm.full[pos.slot]);
+                const bool tensor = use_tmap && k < N + 2;
+                if (lane == 0) {
+                    SlotHdr h;
+                    h.flags = fl | (emitted == 0 ? F_FIRST : 0) | (emitted + 1 == count ? F_LAST : 0);
+                    h.rot = static_cast<uint8_t>(rot);
+                    h.w = static_cast<uint16_t>(w);
+                    h.cls = cls;
+                    h.p = static_cast<uint8_t>(p);
+                    h.a = static_cast<uint8_t>(a);
+                    h.b = static_cast<uint8_t>(b);
+                    h.pitch = static_cast<uint16_t>(W);
+                    h.zinv = static_cast<uint8_t>(zinv);
+                    h.base = reinterpret_cast<uint64_t>(stripe_base);
+                    h.strip_stride = strip_stride;
+                    h.row_stride = row_stride;
+                    h.out = reinterpret_cast<uint64_t>(aux_base);
+                    h.out_row_stride = aux_rs;
+                    sm.hdr[pos.slot] = h;
+                    mbar_arrive_tx(full, tensor ? tx_tensor : tx_rows);
+                }
+                __syncwarp();
+                const uint32_t dst = ring0 + pos.slot * slot_bytes;
+                if (tensor) {
+                    // one tensor copy: box (W/8 x p-1) at column c0, strip k, stripe
+                    if (lane == 0)
+                        tensor_load_4d(dst, &J.tmap, static_cast<int>(c0 >> 3), 0, static_cast<int>(k),
+                                       static_cast<int>(stripe), full, policy);
+                } else {
+                    const uint8_t *src = (k == N + 2) ? aux_base : stripe_base + k * strip_stride;
+                    const uint64_t rs = (k == N + 2) ? aux_rs : row_stride;
+                    for (uint32_t r = lane; r < rows; r += 32)
+                        bulk_load(dst + r * W, src + r * rs, w, full, policy);
+                }
+                pos.next(n_slots);
+                ++issued;
+                ++emitted;
             }
-            const uint32_t full = smem_addr(&sm.full[pos.slot]);
-            const bool tensor = use_tmap && k < N + 2;
-            if (lane == 0) {
-                SlotHdr h;
-                h.flags = fl | (emitted == 0 ? F_FIRST : 0) | (emitted + 1 == count ? F_LAST : 0);
-                h.rot = static_cast<uint8_t>(rot);
-                h.w = static_cast<uint16_t>(w);
-                h.job = ji;
-                h.stripe = stripe;
-                h.c0 = c0;
-                h.cls = cls;
-                h.p = static_cast<uint8_t>(p);
-                h.a = static_cast<uint8_t>(a);
-                h.b = static_cast<uint8_t>(b);
-                h.pitch = static_cast<uint16_t>(W);
-                h.zinv = static_cast<uint8_t>(zinv);
-                sm.hdr[pos.slot] = h;
-                mbar_arrive_tx(full, tensor ? tx_tensor : tx_rows);
-            }
-            __syncwarp();
-            const uint32_t dst = ring0 + pos.slot * slot_bytes;
-            if (tensor) {
-                // one tensor copy: box (W/8 x p-1) at column c0, strip k, stripe
-                if (lane == 0)
-                    tensor_load_4d(dst, &J.tmap, static_cast<int>(c0 >> 3), 0, static_cast<int>(k),
-                                   static_cast<int>(stripe), full, policy);
-            } else {
-                const uint8_t *src = (k == N + 2) ? aux_base : stripe_base + k * strip_stride;
-                const uint64_t rs = (k == N + 2) ? aux_rs : row_stride;
-                for (uint32_t r = lane; r < rows; r += 32)
-                    bulk_load(dst + r * W, src + r * rs, w, full, policy);
-            }
-            pos.next(n_slots);
-            ++issued;
-            ++emitted;
         }
         if (!ok) break;
     }
@@ -654,22 +674,20 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
         const uint32_t flags = hv.x & 0xffu;
         if (flags & F_END) break;
         if (flags & F_FIRST) {
-            const uint4 tv = lds_a(hdr0 + pos.slot * static_cast<uint32_t>(sizeof(SlotHdr)) + 16);
-            const uint32_t job = hv.y, stripe = hv.z, c0 = hv.w;
-            const Job &J = job_ref(prm, job);
+            const uint32_t ha = hdr0 + pos.slot * static_cast<uint32_t>(sizeof(SlotHdr));
+            const uint4 tv = lds_a(ha + 16), bv = lds_a(ha + 32), ov = lds_a(ha + 48);
             T.w = hv.x >> 16;
             T.nvec = T.w >> 4;
             T.cls = static_cast<uint8_t>(tv.x);
             T.p = (tv.x >> 8) & 0xffu;
             T.a = static_cast<uint8_t>(tv.x >> 16);
             T.b = static_cast<uint8_t>(tv.x >> 24);
-            T.strip_stride = J.strip_stride;
-            T.row_stride = J.row_stride;
-            T.base = J.base + stripe * J.stripe_stride + c0;
-            T.out = J.aux + stripe * J.aux_stripe_stride + c0;
-            T.out_row_stride = J.aux_row_stride;
-            copy_dst = T.base + static_cast<uint64_t>(T.a) * J.strip_stride;
-            if (T.cls == E_ENC) T.b = J.n;  // P and Q are strips N and N+1
+            T.base = reinterpret_cast<uint8_t *>(static_cast<uint64_t>(tv.z) | (static_cast<uint64_t>(tv.w) << 32));
+            T.strip_stride = static_cast<uint64_t>(bv.x) | (static_cast<uint64_t>(bv.y) << 32);
+            T.row_stride = static_cast<uint64_t>(bv.z) | (static_cast<uint64_t>(bv.w) << 32);
+            T.out = reinterpret_cast<uint8_t *>(static_cast<uint64_t>(ov.x) | (static_cast<uint64_t>(ov.y) << 32));
+            T.out_row_stride = static_cast<uint64_t>(ov.z) | (static_cast<uint64_t>(ov.w) << 32);
+            copy_dst = T.base + static_cast<uint64_t>(T.a) * T.strip_stride;
             p = static_cast<int>(T.p);
             pitch = tv.y & 0xffffu;
             T.zinv = static_cast<uint8_t>(tv.y >> 16);
@@ -731,13 +749,12 @@ __global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const Smem sm = carve<S>(smem_raw);
 
-    uint32_t n_jobs = prm.n_jobs, slot_bytes = prm.slot_bytes, n_slots = prm.n_slots;
-    uint64_t total = prm.total_tiles;
+    uint32_t slot_bytes = prm.slot_bytes, n_slots = prm.n_slots;
+    uint64_t total = prm.total_tiles;  // units: tiles of a single launch, or batch work items
     if (bh) {
-        n_jobs = bh->n_jobs;
         slot_bytes = bh->slot_bytes;
         n_slots = bh->n_slots;
-        total = bh->total_tiles;
+        total = bh->n_items;
     }
     const uint32_t my_shape = S::kCtasPerSm == 2 ? SHAPE_PAIR : SHAPE_WIDE;
     if ((bh && bh->shape != my_shape) || n_slots == 0 || n_slots > kMaxSlots || slot_bytes == 0 ||
@@ -757,7 +774,7 @@ __global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
     __syncthreads();
 
     if (threadIdx.x < 32)
-        producer<S>(prm, sm, n_jobs, total, slot_bytes, n_slots);
+        producer<S>(prm, sm, bh, total, slot_bytes, n_slots);
     else
         consumer<S>(prm, sm, slot_bytes, n_slots);
 }

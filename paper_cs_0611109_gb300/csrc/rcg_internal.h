@@ -26,7 +26,7 @@ constexpr uint32_t kMaxTileBytes = 2048;  // a TMA box row is at most 256 8-byte
 constexpr int kMaxSlots = 32;
 constexpr int kMaxP = 61;
 constexpr uint32_t kMaxSlotBytes = 32 * 1024;
-constexpr uint32_t kCtlBytes = 2048;            // barriers + slot headers
+constexpr uint32_t kCtlBytes = 3072;            // barriers (1 KB) + 32 slot headers of 64 B
 constexpr uint32_t kFoldBytes = kMaxTileBytes;  // one row of W bytes (two are kept)
 
 template <int CW, int IT, int CT, int MINSLOTS>
@@ -99,13 +99,26 @@ struct LaunchParams {
 
 // Header of a batch descriptor table: the graph-replayed batch kernel reads
 // its sizes from here so the captured kernel node never changes.
+// A unit of dynamic scheduling in a batch: up to a few tiles of one job,
+// taken from a global counter (large jobs are split into many items, listed
+// first, so the tail of the batch is made of small items).
+struct WorkItem {
+    uint32_t job;
+    uint32_t tile0;   // first tile of the job (local index: stripe * tiles_per_stripe + column tile)
+    uint32_t ntiles;
+    uint32_t pad;
+};
+
 struct alignas(128) BatchHeader {
     uint64_t total_tiles;
     uint32_t n_jobs;
     uint32_t slot_bytes;
     uint32_t n_slots;
-    uint32_t shape;  // the engine shape the table was planned for
-    uint32_t pad[26];
+    uint32_t shape;         // the engine shape the table was planned for
+    uint32_t n_items;       // work items after the jobs
+    uint32_t pad0;
+    uint64_t items_offset;  // bytes from the header to the first WorkItem
+    uint32_t pad[22];
 };
 static_assert(sizeof(BatchHeader) == 128, "the job table after the header stays 128-byte aligned");
 static_assert(sizeof(Job) % 128 == 0, "jobs keep their tensor maps 128-byte aligned");
@@ -133,7 +146,10 @@ void inverse_masks(uint32_t p, uint64_t *masks);
 // Host: validate public jobs and build the batch descriptor table with the
 // default copy mode, two-data solve and engine shape (used by
 // rcg_batch_submit_noalloc); *shape receives the shape to launch.
-bool noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, BatchHeader *hdr, Job *table,
-                         uint32_t *shape);
+bool noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, uint8_t *table, size_t capacity,
+                         size_t *bytes, uint32_t *shape);
+
+// Tiles per work item of a batch.
+constexpr uint32_t kTilesPerItem = 8;
 
 }  // namespace rcg

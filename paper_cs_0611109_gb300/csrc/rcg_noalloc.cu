@@ -28,7 +28,9 @@ namespace {
 
 using namespace rcg;
 
-constexpr uint32_t kTableBytes = sizeof(BatchHeader) + RCG_NOALLOC_MAX_JOBS * sizeof(Job);
+// header, up to RCG_NOALLOC_MAX_JOBS jobs and 2 x RCG_NOALLOC_MAX_JOBS work items
+constexpr uint32_t kTableBytes =
+    sizeof(BatchHeader) + RCG_NOALLOC_MAX_JOBS * sizeof(Job) + 2 * RCG_NOALLOC_MAX_JOBS * sizeof(WorkItem);
 constexpr uint32_t kCounterOff = (kTableBytes + 255) / 256 * 256;
 constexpr uint32_t kStatusOff = kCounterOff + 256;
 constexpr uint32_t kScratchBytes = kStatusOff + 256;
@@ -80,11 +82,9 @@ extern "C" rcg_status rcg_batch_submit_noalloc(const rcg_job *jobs, uint32_t n_j
     if (n_jobs && !jobs) return RCG_EINVAL;
     if (n_jobs == 0) return RCG_OK;
 
-    BatchHeader hdr;
-    Job *table = reinterpret_cast<Job *>(g_host_table + sizeof(BatchHeader));
     uint32_t shape = SHAPE_WIDE;
-    if (!noalloc_build_table(jobs, n_jobs, &hdr, table, &shape)) return RCG_EINVAL;
-    memcpy(g_host_table, &hdr, sizeof(hdr));
+    size_t bytes = 0;
+    if (!noalloc_build_table(jobs, n_jobs, g_host_table, kTableBytes, &bytes, &shape)) return RCG_EINVAL;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RCG_ECUDA;
@@ -96,7 +96,6 @@ extern "C" rcg_status rcg_batch_submit_noalloc(const rcg_job *jobs, uint32_t n_j
     uint8_t *table_dev = d->scratch;
     auto *counter = reinterpret_cast<unsigned long long *>(d->scratch + kCounterOff);
     uint32_t *status = status_dev ? status_dev : reinterpret_cast<uint32_t *>(d->scratch + kStatusOff);
-    const size_t bytes = sizeof(BatchHeader) + static_cast<size_t>(n_jobs) * sizeof(Job);
     // The host table is pageable: the copy has left it by the time the call returns.
     cudaError_t e = cudaMemcpyAsync(table_dev, g_host_table, bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);

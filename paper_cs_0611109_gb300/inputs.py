@@ -96,3 +96,32 @@ def random_pairs(seed: int, n_data: int, n: int, kind: str = "any") -> np.ndarra
     else:
         raise ValueError(kind)
     return out
+
+
+BATCH_PRIMES = (5, 13, 29, 59)
+
+
+def batched_jobs(seed: int, n: int, c_min: int = 512, c_max: int = 65536, encode_share: float = 0.6):
+    """Stripe descriptors of the uneven batched workload: p uniform over
+    {5, 13, 29, 59}, N uniform in [3, p-1], row bytes log-uniform in
+    [c_min, c_max] rounded down to a multiple of 16, and an operation --
+    encode with probability encode_share, else the recovery of an erasure
+    pair i < j drawn uniformly among the N+2 strips.  One stripe per
+    descriptor; returns a list of dicts (p, n, c, op, i, j)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = rng.choice(BATCH_PRIMES, size=n)
+    out = []
+    logc = rng.uniform(np.log(c_min), np.log(c_max), size=n)
+    u = rng.uniform(size=n)
+    for k in range(n):
+        pk = int(p[k])
+        nk = int(rng.integers(3, pk))           # [3, p-1]
+        ck = max(16, (int(np.exp(logc[k])) // 16) * 16)
+        if u[k] < encode_share:
+            out.append(dict(p=pk, n=nk, c=ck, op="encode", i=0, j=0))
+        else:
+            a = int(rng.integers(0, nk + 2))
+            b = int(rng.integers(0, nk + 1))
+            b = b + 1 if b >= a else b
+            out.append(dict(p=pk, n=nk, c=ck, op="recover", i=min(a, b), j=max(a, b)))
+    return out

@@ -341,6 +341,51 @@ def test_batch_mixed_jobs_alone_and_in_the_mix(rcg, ctx, oracle):
             assert np.array_equal(out.cpu().numpy(), want)
 
 
+def test_batched_uneven_jobs_alone_and_in_the_mix(rcg, ctx, oracle):
+    # the uneven batched workload's distributions (row bytes capped so the test
+    # stays small): every stripe of the one-launch batch equals the same stripe
+    # run alone (one launch per stripe), and sampled stripes equal the oracle
+    jobs = inputs.batched_jobs(17, 400, c_min=512, c_max=4096)
+    sizes = [inputs.stripe_bytes(j["p"], j["n"], j["c"]) for j in jobs]
+    offs = np.cumsum([0] + [(b + 255) // 256 * 256 for b in sizes])
+    arena = torch.empty(int(offs[-1]), dtype=torch.uint8, device="cuda")
+    rcg.rcg_fill_random(arena, arena.numel(), 21)
+    lays = [rcg.make_layout(arena.data_ptr() + int(o), j["p"], j["n"], j["c"]) for o, j in zip(offs, jobs)]
+    # recover jobs run on encoded stripes
+    t = ctx.batch_submit([rcg.make_job(L, 0, 1, rcg.RCG_OP_ENCODE) for L, j in zip(lays, jobs) if j["op"] == "recover"])
+    assert ctx.batch_wait(t)
+    start = arena.clone()
+    mix = [rcg.make_job(L, 0, 1, rcg.RCG_OP_ENCODE) if j["op"] == "encode" else
+           rcg.make_job(L, 0, 1, rcg.RCG_OP_RECOVER, j["i"], j["j"]) for L, j in zip(lays, jobs)]
+    for L, j in zip(lays, jobs):   # poison the erased strips of the recover jobs
+        if j["op"] == "recover":
+            sb = (j["p"] - 1) * j["c"]
+            for k in (j["i"], j["j"]):
+                arena[L.base - arena.data_ptr() + k * sb: L.base - arena.data_ptr() + (k + 1) * sb] = POISON_I
+    poisoned = arena.clone()
+    t = ctx.batch_submit(mix)
+    assert ctx.batch_wait(t)
+    check_clean(ctx)
+    in_mix = arena.clone()
+    arena.copy_(poisoned)
+    for L, j in zip(lays, jobs):   # alone: one launch per stripe
+        if j["op"] == "encode":
+            ctx.encode(L, 0, 1)
+        else:
+            ctx.recover(L, 0, j["i"], j["j"])
+    check_clean(ctx)
+    assert torch.equal(arena, in_mix)
+    got = in_mix.cpu().numpy()
+    ref = start.cpu().numpy()
+    for k in list(range(0, len(jobs), 37)):
+        j, o, b = jobs[k], int(offs[k]), sizes[k]
+        want = ref[o:o + b].copy()
+        if j["op"] == "encode":
+            want = np.ascontiguousarray(poisoned[o:o + b].cpu().numpy())
+            oracle.encode(j["p"], j["n"], j["c"], want, 1)
+        assert np.array_equal(got[o:o + b], want), k
+
+
 def test_batch_many_small_jobs_replays_graph(rcg, ctx, oracle):
     p, N, C, S = 13, 5, 64, 40
     host = host_stripes(900, p, N, C, S)
