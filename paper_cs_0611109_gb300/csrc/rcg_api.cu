@@ -634,15 +634,36 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
                table[y].n_stripes * static_cast<uint64_t>(table[y].p - 1) * table[y].C * (table[y].n + 2u);
     });
     std::vector<WorkItem> items;
-    for (uint32_t k : order)
+    for (uint32_t k : order) {
+        const Job &J = table[k];
+        WorkItem w;
+        memset(&w, 0, sizeof(w));
+        w.base = reinterpret_cast<uint64_t>(J.base);
+        w.aux = reinterpret_cast<uint64_t>(J.aux);
+        w.pairs = reinterpret_cast<uint64_t>(J.pairs);
+        w.strip_stride = J.strip_stride;
+        w.row_stride = J.row_stride;
+        w.stripe_stride = J.stripe_stride;
+        w.aux_row_stride = J.aux_row_stride;
+        w.aux_stripe_stride = J.aux_stripe_stride;
+        w.tiles_per_stripe = J.tiles_per_stripe;
+        w.W = J.W;
+        w.C = J.C;
+        w.n_stripes = J.n_stripes;
+        w.job = k;
+        w.p = J.p;
+        w.n = J.n;
+        w.op = J.op;
+        w.i = J.i;
+        w.j = J.j;
+        w.use_tmap = J.use_tmap;
+        w.dd_solve = J.dd_solve;
         for (uint64_t t = 0; t < tiles[k]; t += per) {
-            WorkItem w;
-            w.job = k;
             w.tile0 = static_cast<uint32_t>(t);
             w.ntiles = static_cast<uint32_t>(std::min<uint64_t>(per, tiles[k] - t));
-            w.pad = 0;
             items.push_back(w);
         }
+    }
     for (uint32_t k = 0; k < n_jobs; ++k)
         if (tiles[k] > 0xffffffffull) return RCG_EINVAL;
     if (items.size() > 0xffffffffull) return RCG_EINVAL;
@@ -650,8 +671,9 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     memset(&hdr, 0, sizeof(hdr));
     hdr.total_tiles = total;
     hdr.n_jobs = n_jobs;
-    hdr.slot_bytes = slot_bytes;
-    hdr.n_slots = std::min<uint32_t>(kMaxSlots, shape_info(shape).ring_bytes / slot_bytes);
+    hdr.slot_bytes = slot_bytes;  // the largest stage
+    hdr.n_slots = kMaxSlots;      // stages in flight share the byte ring
+    hdr.ring_bytes = shape_info(shape).ring_bytes & ~127u;
     hdr.shape = shape;
     hdr.n_items = static_cast<uint32_t>(items.size());
     hdr.items_offset = sizeof(BatchHeader) + static_cast<uint64_t>(n_jobs) * sizeof(Job);

@@ -181,7 +181,7 @@ struct SlotHdr {
     uint8_t flags;    // F_* bits
     uint8_t rot;      // x^rot for F_Q
     uint16_t w;       // tile width, bytes
-    uint32_t pad0;
+    uint32_t off;     // byte offset of the stage in the ring
     uint64_t pad1;
     uint8_t cls;      // epilogue class
     uint8_t p;
@@ -204,7 +204,7 @@ struct Smem {
     SlotHdr *hdr;     // [kMaxSlots]
     uint8_t *xb;      // exchange buffer [p][nvec] x 16 B
     uint8_t *fold;    // two rows [2][nvec] x 16 B, used alternately by successive tiles
-    uint8_t *ring;    // n_slots x slot_bytes
+    uint8_t *ring;    // byte ring: stages of any size, up to n_slots in flight
 };
 
 template <class S>
@@ -289,54 +289,66 @@ struct RingPos {
 
 template <class S>
 __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHeader *bh,
-                         uint64_t total_units, uint32_t slot_bytes, uint32_t n_slots) {
+                         uint64_t total_units, uint32_t ring_bytes, uint32_t n_slots) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t policy = l2_evict_first();
     const uint64_t timeout = prm.timeout_ns;
     const uint32_t ring0 = smem_addr(sm.ring);
-    // batches: work items (a job and a run of its tiles) from a global counter;
-    // single launches: one tile per unit, strided over the grid
+    // batches: work items (a run of one job's tiles); single launches: one
+    // tile per unit; both strided over the grid
     const WorkItem *items =
         bh ? reinterpret_cast<const WorkItem *>(reinterpret_cast<const uint8_t *>(bh) + bh->items_offset)
            : nullptr;
     RingPos pos;
-    uint32_t issued = 0;  // slots handed to the consumers
+    uint32_t issued = 0;    // stages handed to the consumers
+    uint32_t released = 0;  // stages known to be released (all earlier ones are)
+    uint32_t head = 0;      // next free byte of the ring
     bool ok = true;
     uint64_t next_static = blockIdx.x;
 
+    // Batches: items u = blockIdx.x, blockIdx.x + grid, ...; the next item's
+    // 128 bytes are loaded while the current one streams.
+    uint64_t u = blockIdx.x;
+    WorkItem nxt;
+    if (items && u < total_units) nxt = items[u];
+
     for (;;) {
-        uint32_t ji;
-        uint64_t lt0;
-        uint32_t nt;
+        // the fields of this unit, in registers
+        uint32_t ji, nt, p, N, tps, W, C, n_stripes, op, use_tmap, dd_solve, ji_i, ji_j;
+        uint64_t lt0, strip_stride, row_stride, stripe_stride, aux_rs, aux_ss;
+        const uint8_t *pairs;
+        uint8_t *base, *aux;
         if (items) {
-            unsigned long long v = 0;
-            if (lane == 0) v = atomicAdd(prm.tile_counter, 1ull);
-            const uint64_t u = __shfl_sync(0xffffffffu, v, 0);
             if (u >= total_units) break;
-            const WorkItem wi = items[u];
-            ji = wi.job;
-            lt0 = wi.tile0;
-            nt = wi.ntiles;
+            const WorkItem cur = nxt;
+            u += gridDim.x;
+            if (u < total_units) nxt = items[u];  // prefetch
+            ji = cur.job;
+            lt0 = cur.tile0;
+            nt = cur.ntiles;
+            p = cur.p; N = cur.n; tps = cur.tiles_per_stripe; W = cur.W; C = cur.C;
+            n_stripes = cur.n_stripes; op = cur.op; use_tmap = cur.use_tmap; dd_solve = cur.dd_solve;
+            ji_i = cur.i; ji_j = cur.j;
+            pairs = reinterpret_cast<const uint8_t *>(cur.pairs);
+            base = reinterpret_cast<uint8_t *>(cur.base);
+            aux = reinterpret_cast<uint8_t *>(cur.aux);
+            strip_stride = cur.strip_stride; row_stride = cur.row_stride; stripe_stride = cur.stripe_stride;
+            aux_rs = cur.aux_row_stride; aux_ss = cur.aux_stripe_stride;
         } else {
             if (next_static >= total_units) break;
             ji = 0;
             lt0 = next_static;
             nt = 1;
             next_static += gridDim.x;
+            const Job &J0 = prm.job0;
+            p = J0.p; N = J0.n; tps = J0.tiles_per_stripe; W = J0.W; C = J0.C; n_stripes = J0.n_stripes;
+            op = J0.op; use_tmap = J0.use_tmap; dd_solve = J0.dd_solve; ji_i = J0.i; ji_j = J0.j;
+            pairs = J0.pairs; base = J0.base; aux = J0.aux;
+            strip_stride = J0.strip_stride; row_stride = J0.row_stride; stripe_stride = J0.stripe_stride;
+            aux_rs = J0.aux_row_stride; aux_ss = J0.aux_stripe_stride;
         }
-
-        const Job &J = job_ref(prm, ji);  // the tensor map is used in place
-        // the fields of this job, loaded once into registers
-        const uint32_t p = J.p, N = J.n, rows = p - 1;
-        const uint32_t tps = J.tiles_per_stripe, W = J.W, C = J.C, n_stripes = J.n_stripes;
-        const uint32_t op = J.op, use_tmap = J.use_tmap, dd_solve = J.dd_solve;
-        const uint32_t ji_i = J.i, ji_j = J.j;
-        const uint8_t *pairs = J.pairs;
-        uint8_t *const base = J.base;
-        uint8_t *const aux = J.aux;
-        const uint64_t strip_stride = J.strip_stride, row_stride = J.row_stride;
-        const uint64_t stripe_stride = J.stripe_stride;
-        const uint64_t aux_rs = J.aux_row_stride, aux_ss = J.aux_stripe_stride;
+        const Job &J = job_ref(prm, ji);  // only its tensor map is used, in place
+        const uint32_t rows = p - 1;
 
         for (uint32_t q = 0; q < nt && ok; ++q) {
             const uint64_t local = lt0 + q;
@@ -345,7 +357,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
             const uint32_t w = min(W, C - c0);
             // device-side guard: a tile must fit its slot and the item budget
             if (p < 3 || p > kMaxP || N < 1 || N > p || (w & 15) || w == 0 || W > kMaxTileBytes ||
-                (W & 15) || rows * W > slot_bytes || p * (w >> 4) > static_cast<uint32_t>(S::kMaxItems) ||
+                (W & 15) || rows * W > ring_bytes || p * (w >> 4) > static_cast<uint32_t>(S::kMaxItems) ||
                 stripe >= n_stripes) {
                 if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
                 continue;
@@ -393,10 +405,39 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
             for (uint32_t k = 0; k < N + 3; ++k) {
                 const uint8_t fl = strip_role(cls, update, k, N, a, b, p, &rot);
                 if (!fl) continue;
+                // a free descriptor (its previous stage released) ...
                 if (!mbar_wait(smem_addr(&sm.empty[pos.slot]), pos.phase ^ 1u, timeout)) {
                     ok = false;
                     break;
                 }
+                if (issued >= n_slots && released < issued - n_slots + 1) released = issued - n_slots + 1;
+                // ... and room for the stage: the oldest stages in flight are
+                // released, in order, until the stage fits after head (or at 0)
+                const uint32_t B = (rows * W + 127) & ~127u;
+                uint32_t start = 0;
+                for (;;) {
+                    if (released == issued) {  // nothing in flight
+                        start = head + B <= ring_bytes ? head : 0;
+                        break;
+                    }
+                    const uint32_t t_off = sm.hdr[released % n_slots].off;
+                    bool fits = false;
+                    if (t_off < head) {         // occupied [t_off, head)
+                        if (head + B <= ring_bytes) { start = head; fits = true; }
+                        else if (B <= t_off) { start = 0; fits = true; }
+                    } else if (t_off > head) {  // occupied [t_off, end) and [0, head)
+                        if (head + B <= t_off) { start = head; fits = true; }
+                    }                           // t_off == head: full
+                    if (fits) break;
+                    if (!mbar_wait(smem_addr(&sm.empty[released % n_slots]), (released / n_slots) & 1u,
+                                   timeout)) {
+                        ok = false;
+                        break;
+                    }
+                    ++released;
+                }
+                if (!ok) break;
+                head = start + B;
                 const uint32_t full = smem_addr(&sm.full[pos.slot]);
                 const bool tensor = use_tmap && k < N + 2;
                 if (lane == 0) {
@@ -404,6 +445,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                     h.flags = fl | (emitted == 0 ? F_FIRST : 0) | (emitted + 1 == count ? F_LAST : 0);
                     h.rot = static_cast<uint8_t>(rot);
                     h.w = static_cast<uint16_t>(w);
+                    h.off = start;
                     h.cls = cls;
                     h.p = static_cast<uint8_t>(p);
                     h.a = static_cast<uint8_t>(a);
@@ -419,7 +461,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                     mbar_arrive_tx(full, tensor ? tx_tensor : tx_rows);
                 }
                 __syncwarp();
-                const uint32_t dst = ring0 + pos.slot * slot_bytes;
+                const uint32_t dst = ring0 + start;
                 if (tensor) {
                     // one tensor copy: box (W/8 x p-1) at column c0, strip k, stripe
                     if (lane == 0)
@@ -648,8 +690,7 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[S::k
 }
 
 template <class S>
-__device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_bytes,
-                         uint32_t n_slots) {
+__device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slots) {
     const int ctid = static_cast<int>(threadIdx.x) - 32;
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t timeout = prm.timeout_ns;
@@ -701,7 +742,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t slot_
                 accQ[t] = make_uint4(0, 0, 0, 0);
             }
         }
-        const uint32_t stage = ring0 + pos.slot * slot_bytes;
+        const uint32_t stage = ring0 + hv.y;  // the stage's offset in the byte ring
         const int rot = (hv.x >> 8) & 0xff;
         // row r of x^rot * strip is row r - rot (mod p) of the strip; the item
         // row whose source is the imaginary row p-1 is vrow = (p-1+rot) mod p
@@ -749,16 +790,19 @@ __global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const Smem sm = carve<S>(smem_raw);
 
-    uint32_t slot_bytes = prm.slot_bytes, n_slots = prm.n_slots;
+    // single launches: n_slots stages of slot_bytes; batches: a byte ring of
+    // stages of any size, at most n_slots of them in flight
+    uint32_t n_slots = prm.n_slots;
+    uint64_t ring_bytes = static_cast<uint64_t>(prm.n_slots) * prm.slot_bytes;
     uint64_t total = prm.total_tiles;  // units: tiles of a single launch, or batch work items
     if (bh) {
-        slot_bytes = bh->slot_bytes;
         n_slots = bh->n_slots;
+        ring_bytes = bh->ring_bytes;
         total = bh->n_items;
     }
     const uint32_t my_shape = S::kCtasPerSm == 2 ? SHAPE_PAIR : SHAPE_WIDE;
-    if ((bh && bh->shape != my_shape) || n_slots == 0 || n_slots > kMaxSlots || slot_bytes == 0 ||
-        static_cast<uint64_t>(n_slots) * slot_bytes > S::kRingBytes || (slot_bytes & 127)) {
+    if ((bh && bh->shape != my_shape) || n_slots == 0 || n_slots > kMaxSlots || ring_bytes < 128 ||
+        ring_bytes > S::kRingBytes || (ring_bytes & 127)) {
         if (threadIdx.x == 0) set_status(prm.status, RCG_DEV_BADJOB);
         return;
     }
@@ -774,9 +818,9 @@ __global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
     __syncthreads();
 
     if (threadIdx.x < 32)
-        producer<S>(prm, sm, bh, total, slot_bytes, n_slots);
+        producer<S>(prm, sm, bh, total, static_cast<uint32_t>(ring_bytes), n_slots);
     else
-        consumer<S>(prm, sm, slot_bytes, n_slots);
+        consumer<S>(prm, sm, n_slots);
 }
 
 // ------------------------------------------------------ test-data generator

@@ -99,15 +99,21 @@ struct LaunchParams {
 
 // Header of a batch descriptor table: the graph-replayed batch kernel reads
 // its sizes from here so the captured kernel node never changes.
-// A unit of dynamic scheduling in a batch: up to a few tiles of one job,
-// taken from a global counter (large jobs are split into many items, listed
-// first, so the tail of the batch is made of small items).
-struct WorkItem {
-    uint32_t job;
+// A unit of work in a batch: up to a few tiles of one job, with every field
+// the producer needs copied in, so one 128-byte load (prefetched while the
+// previous item streams) starts it.  Items are dealt to CTAs round-robin;
+// larger jobs' items come first, so the tail of a batch is made of small items.
+struct alignas(128) WorkItem {
+    uint64_t base, aux, pairs;
+    uint64_t strip_stride, row_stride, stripe_stride, aux_row_stride, aux_stripe_stride;
     uint32_t tile0;   // first tile of the job (local index: stripe * tiles_per_stripe + column tile)
     uint32_t ntiles;
-    uint32_t pad;
+    uint32_t tiles_per_stripe, W, C, n_stripes;
+    uint32_t job;     // index of the job (for its tensor map)
+    uint8_t p, n, op, i, j, use_tmap, dd_solve, pad0;
+    uint8_t pad[20];
 };
+static_assert(sizeof(WorkItem) == 128, "work items are 128 bytes");
 
 struct alignas(128) BatchHeader {
     uint64_t total_tiles;
@@ -116,7 +122,7 @@ struct alignas(128) BatchHeader {
     uint32_t n_slots;
     uint32_t shape;         // the engine shape the table was planned for
     uint32_t n_items;       // work items after the jobs
-    uint32_t pad0;
+    uint32_t ring_bytes;    // shared-memory byte ring shared by up to n_slots stages in flight
     uint64_t items_offset;  // bytes from the header to the first WorkItem
     uint32_t pad[22];
 };

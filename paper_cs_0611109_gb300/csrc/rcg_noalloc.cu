@@ -28,7 +28,7 @@ namespace {
 
 using namespace rcg;
 
-// header, up to RCG_NOALLOC_MAX_JOBS jobs and 2 x RCG_NOALLOC_MAX_JOBS work items
+// header, up to RCG_NOALLOC_MAX_JOBS jobs and 2 x RCG_NOALLOC_MAX_JOBS work items (~130 KB)
 constexpr uint32_t kTableBytes =
     sizeof(BatchHeader) + RCG_NOALLOC_MAX_JOBS * sizeof(Job) + 2 * RCG_NOALLOC_MAX_JOBS * sizeof(WorkItem);
 constexpr uint32_t kCounterOff = (kTableBytes + 255) / 256 * 256;
