@@ -54,6 +54,7 @@ def parse():
                     help="c2: the bench line; batched: the uneven 50k-stripe batch vs per-stripe launches")
     ap.add_argument("--batch-jobs", type=int, default=50000)
     ap.add_argument("--arena-gb", type=float, default=100.0)
+    ap.add_argument("--schedule", default="static", choices=["static", "dynamic"])
     return ap.parse_args()
 
 
@@ -402,6 +403,7 @@ def run_batched(args):
 
     torch.cuda.set_device(0)
     ctx = rcg.Context(0)
+    ctx.set_batch_schedule(rcg.RCG_SCHED_DYNAMIC if args.schedule == "dynamic" else rcg.RCG_SCHED_STATIC)
     stream = torch.cuda.current_stream()
     jobs = inputs.batched_jobs(3, args.batch_jobs)
     free = torch.cuda.mem_get_info()[0]
@@ -463,6 +465,7 @@ def run_batched(args):
            "config": {"workload": "batched uneven: %d single-stripe jobs, p in {5,13,29,59}, N in [3,p-1], "
                                   "rows 512 B..64 KiB log-uniform, 60%% encode / 40%% recovery" % len(jobs),
                       "waves": len(waves), "arena_bytes": arena_bytes, "user_bytes": tot["user"],
+                      "schedule": args.schedule,
                       "hbm_bytes": tot["moved"]},
            "batched": {"ms": round(tot["batched_ms"], 3), "user_gbs": round(gbs(tot["user"], tot["batched_ms"]), 1),
                        "hbm_gbs": round(gbs(tot["moved"], tot["batched_ms"]), 1),

@@ -219,9 +219,10 @@ typedef struct rcg_job {
     uint64_t aux_stripe_stride; /* bytes between stripes of aux; 0 = (p-1)*aux_row_stride */
 } rcg_job;
 
-/* Run a list of jobs of mixed p, N, C and op in ONE persistent-kernel launch
- * with dynamic tile scheduling (a global tile counter), so CTAs that finish
- * small stripes take tiles of large ones.  The job list is validated on the
+/* Run a list of jobs of mixed p, N, C and op in ONE persistent-kernel launch:
+ * jobs are cut into work items of a few tiles, largest jobs first, and the
+ * stages of all of them share one shared-memory byte ring per CTA, so small
+ * and large stripes keep the same number of bytes in flight.  The job list is validated on the
  * host, copied into a context-owned device descriptor table and replayed
  * through a CUDA graph captured once per context.  Jobs must not overlap in
  * memory.  On return *ticket identifies the batch for rcg_batch_wait.  The
@@ -229,6 +230,15 @@ typedef struct rcg_job {
  * a fifth waits (bounded) for the oldest, or returns RCG_EBUSY. */
 rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, void *stream,
                             uint64_t *ticket);
+
+/* How a batch's work items (runs of at most 8 tiles of one job, largest
+ * jobs first) reach the CTAs.  RCG_SCHED_STATIC (default): dealt
+ * round-robin, each CTA prefetching its next item while the current one
+ * streams.  RCG_SCHED_DYNAMIC: taken from a global counter as CTAs free up.
+ * Results are identical. */
+#define RCG_SCHED_STATIC 0
+#define RCG_SCHED_DYNAMIC 1
+rcg_status rcg_set_batch_schedule(rcg_ctx *ctx, int schedule);
 
 /* Wait at most timeout_ns for batch `ticket`; RCG_ETIMEOUT if it has not
  * finished (the batch keeps running). */

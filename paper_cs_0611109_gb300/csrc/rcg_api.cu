@@ -59,6 +59,7 @@ struct rcg_ctx {
     int copy_mode = RCG_COPY_AUTO;
     int dd_solve = RCG_SOLVE_CHAIN;
     int shape = RCG_SHAPE_AUTO;
+    int batch_schedule = RCG_SCHED_STATIC;
     uint64_t next_ticket = 1;
     BatchSlot slots[kBatchRing];
     rcg::HostStaging *host = nullptr;  // staging of the host-memory calls (lazy)
@@ -371,6 +372,12 @@ rcg_status rcg_set_engine_shape(rcg_ctx *ctx, int shape) {
     return RCG_OK;
 }
 
+rcg_status rcg_set_batch_schedule(rcg_ctx *ctx, int schedule) {
+    if (!ctx || (schedule != RCG_SCHED_STATIC && schedule != RCG_SCHED_DYNAMIC)) return RCG_EINVAL;
+    ctx->batch_schedule = schedule;
+    return RCG_OK;
+}
+
 rcg_status rcg_set_host_chunk(rcg_ctx *ctx, uint64_t bytes) {
     if (!ctx || bytes < 4096) return RCG_EINVAL;
     ctx->host_chunk_bytes = bytes;
@@ -674,6 +681,7 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     hdr.slot_bytes = slot_bytes;  // the largest stage
     hdr.n_slots = kMaxSlots;      // stages in flight share the byte ring
     hdr.ring_bytes = shape_info(shape).ring_bytes & ~127u;
+    hdr.dynamic = ctx->batch_schedule == RCG_SCHED_DYNAMIC ? 1u : 0u;
     hdr.shape = shape;
     hdr.n_items = static_cast<uint32_t>(items.size());
     hdr.items_offset = sizeof(BatchHeader) + static_cast<uint64_t>(n_jobs) * sizeof(Job);

@@ -303,12 +303,21 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
     uint32_t issued = 0;    // stages handed to the consumers
     uint32_t released = 0;  // stages known to be released (all earlier ones are)
     uint32_t head = 0;      // next free byte of the ring
+    // single launches have one stage size: slot k sits at k * slot bytes
+    const uint32_t fixed_slot = bh ? 0u : ring_bytes / n_slots;
     bool ok = true;
     uint64_t next_static = blockIdx.x;
 
-    // Batches: items u = blockIdx.x, blockIdx.x + grid, ...; the next item's
-    // 128 bytes are loaded while the current one streams.
-    uint64_t u = blockIdx.x;
+    // Batches, static: items u = blockIdx.x, blockIdx.x + grid, ...; dynamic:
+    // the next item index comes from the global counter.  Either way the next
+    // item's 128 bytes are requested while the current one streams.
+    const bool dynamic = bh && bh->dynamic;
+    auto next_index = [&]() -> uint64_t {
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(prm.tile_counter, 1ull);
+        return __shfl_sync(0xffffffffu, v, 0);
+    };
+    uint64_t u = items ? (dynamic ? next_index() : blockIdx.x) : 0;
     WorkItem nxt;
     if (items && u < total_units) nxt = items[u];
 
@@ -321,7 +330,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
         if (items) {
             if (u >= total_units) break;
             const WorkItem cur = nxt;
-            u += gridDim.x;
+            u = dynamic ? next_index() : u + gridDim.x;
             if (u < total_units) nxt = items[u];  // prefetch
             ji = cur.job;
             lt0 = cur.tile0;
@@ -410,34 +419,40 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                     ok = false;
                     break;
                 }
-                if (issued >= n_slots && released < issued - n_slots + 1) released = issued - n_slots + 1;
-                // ... and room for the stage: the oldest stages in flight are
-                // released, in order, until the stage fits after head (or at 0)
-                const uint32_t B = (rows * W + 127) & ~127u;
-                uint32_t start = 0;
-                for (;;) {
-                    if (released == issued) {  // nothing in flight
-                        start = head + B <= ring_bytes ? head : 0;
-                        break;
+                uint32_t start = pos.slot * fixed_slot;  // single launches: fixed slots
+                if (!fixed_slot) {
+                    // batches: room for the stage in the byte ring -- the oldest
+                    // stages in flight are released, in order, until it fits
+                    // after head (or at 0)
+                    if (issued >= n_slots && released < issued - n_slots + 1) released = issued - n_slots + 1;
+                    const uint32_t B = (rows * W + 127) & ~127u;
+                    for (;;) {
+                        if (released == issued) {  // nothing in flight
+                            start = head + B <= ring_bytes ? head : 0;
+                            break;
+                        }
+                        uint32_t t_off;  // offset of the oldest stage in flight (its header)
+                        asm volatile("ld.shared.u32 %0, [%1];"
+                                     : "=r"(t_off)
+                                     : "r"(smem_addr(&sm.hdr[released % n_slots].off)));
+                        bool fits = false;
+                        if (t_off < head) {         // occupied [t_off, head)
+                            if (head + B <= ring_bytes) { start = head; fits = true; }
+                            else if (B <= t_off) { start = 0; fits = true; }
+                        } else if (t_off > head) {  // occupied [t_off, end) and [0, head)
+                            if (head + B <= t_off) { start = head; fits = true; }
+                        }                           // t_off == head: full
+                        if (fits) break;
+                        if (!mbar_wait(smem_addr(&sm.empty[released % n_slots]), (released / n_slots) & 1u,
+                                       timeout)) {
+                            ok = false;
+                            break;
+                        }
+                        ++released;
                     }
-                    const uint32_t t_off = sm.hdr[released % n_slots].off;
-                    bool fits = false;
-                    if (t_off < head) {         // occupied [t_off, head)
-                        if (head + B <= ring_bytes) { start = head; fits = true; }
-                        else if (B <= t_off) { start = 0; fits = true; }
-                    } else if (t_off > head) {  // occupied [t_off, end) and [0, head)
-                        if (head + B <= t_off) { start = head; fits = true; }
-                    }                           // t_off == head: full
-                    if (fits) break;
-                    if (!mbar_wait(smem_addr(&sm.empty[released % n_slots]), (released / n_slots) & 1u,
-                                   timeout)) {
-                        ok = false;
-                        break;
-                    }
-                    ++released;
+                    if (!ok) break;
+                    head = start + B;
                 }
-                if (!ok) break;
-                head = start + B;
                 const uint32_t full = smem_addr(&sm.full[pos.slot]);
                 const bool tensor = use_tmap && k < N + 2;
                 if (lane == 0) {

@@ -124,7 +124,8 @@ struct alignas(128) BatchHeader {
     uint32_t n_items;       // work items after the jobs
     uint32_t ring_bytes;    // shared-memory byte ring shared by up to n_slots stages in flight
     uint64_t items_offset;  // bytes from the header to the first WorkItem
-    uint32_t pad[22];
+    uint32_t dynamic;       // 0: items dealt round-robin; 1: taken from the global counter
+    uint32_t pad[21];
 };
 static_assert(sizeof(BatchHeader) == 128, "the job table after the header stays 128-byte aligned");
 static_assert(sizeof(Job) % 128 == 0, "jobs keep their tensor maps 128-byte aligned");

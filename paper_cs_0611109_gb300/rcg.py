@@ -21,6 +21,7 @@ RCG_COPY_AUTO, RCG_COPY_ROWS = 0, 1
 RCG_SOLVE_CHAIN, RCG_SOLVE_TABLE = 0, 1
 RCG_NOALLOC_MAX_JOBS = 256
 RCG_SHAPE_AUTO, RCG_SHAPE_WIDE, RCG_SHAPE_PAIR = 0, 1, 2
+RCG_SCHED_STATIC, RCG_SCHED_DYNAMIC = 0, 1
 
 _u32, _u64, _vp, _int = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
 
@@ -58,6 +59,7 @@ EXPORTS = {
     "rcg_set_dd_solve": (_int, [_vp, _int]),
     "rcg_set_engine_shape": (_int, [_vp, _int]),
     "rcg_set_host_chunk": (_int, [_vp, _u64]),
+    "rcg_set_batch_schedule": (_int, [_vp, _int]),
     "rcg_last_device_status": (_int, [_vp, ctypes.POINTER(_u32)]),
     "rcg_status_str": (ctypes.c_char_p, [_int]),
     "rcg_abi_version": (_u32, []),
@@ -172,6 +174,10 @@ def rcg_set_engine_shape(ctx: int, shape: int):
 
 def rcg_set_host_chunk(ctx: int, nbytes: int):
     _check(lib().rcg_set_host_chunk(ctx, nbytes), "rcg_set_host_chunk")
+
+
+def rcg_set_batch_schedule(ctx: int, schedule: int):
+    _check(lib().rcg_set_batch_schedule(ctx, schedule), "rcg_set_batch_schedule")
 
 
 def rcg_last_device_status(ctx: int) -> int:
@@ -342,6 +348,9 @@ class Context:
 
     def set_host_chunk(self, nbytes):
         rcg_set_host_chunk(self.handle, nbytes)
+
+    def set_batch_schedule(self, schedule):
+        rcg_set_batch_schedule(self.handle, schedule)
 
     def last_device_status(self) -> int:
         return rcg_last_device_status(self.handle)
