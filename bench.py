@@ -54,7 +54,7 @@ def parse():
                     help="c2: the bench line; batched: the uneven 50k-stripe batch vs per-stripe launches")
     ap.add_argument("--batch-jobs", type=int, default=50000)
     ap.add_argument("--arena-gb", type=float, default=100.0)
-    ap.add_argument("--schedule", default="static", choices=["static", "dynamic"])
+    ap.add_argument("--schedule", default="dynamic", choices=["static", "dynamic"])
     return ap.parse_args()
 
 

@@ -232,9 +232,9 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
                             uint64_t *ticket);
 
 /* How a batch's work items (runs of at most 8 tiles of one job, largest
- * jobs first) reach the CTAs.  RCG_SCHED_STATIC (default): dealt
- * round-robin, each CTA prefetching its next item while the current one
- * streams.  RCG_SCHED_DYNAMIC: taken from a global counter as CTAs free up.
+ * jobs first) reach the CTAs.  RCG_SCHED_DYNAMIC (default): taken from a
+ * global counter as CTAs free up.  RCG_SCHED_STATIC: dealt round-robin.
+ * Either way a CTA requests its next item while the current one streams.
  * Results are identical. */
 #define RCG_SCHED_STATIC 0
 #define RCG_SCHED_DYNAMIC 1

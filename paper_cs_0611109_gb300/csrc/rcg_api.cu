@@ -59,7 +59,7 @@ struct rcg_ctx {
     int copy_mode = RCG_COPY_AUTO;
     int dd_solve = RCG_SOLVE_CHAIN;
     int shape = RCG_SHAPE_AUTO;
-    int batch_schedule = RCG_SCHED_STATIC;
+    int batch_schedule = RCG_SCHED_DYNAMIC;
     uint64_t next_ticket = 1;
     BatchSlot slots[kBatchRing];
     rcg::HostStaging *host = nullptr;  // staging of the host-memory calls (lazy)

@@ -302,6 +302,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
     RingPos pos;
     uint32_t issued = 0;    // stages handed to the consumers
     uint32_t released = 0;  // stages known to be released (all earlier ones are)
+    RingPos rel;            // descriptor slot and phase of stage `released`
     uint32_t head = 0;      // next free byte of the ring
     // single launches have one stage size: slot k sits at k * slot bytes
     const uint32_t fixed_slot = bh ? 0u : ring_bytes / n_slots;
@@ -401,9 +402,10 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                 for (uint32_t e = 0; e + 2 < p; ++e) zinv = zinv * (b - a) % p;
             }
 
-            uint32_t count = 0, rot;
-            for (uint32_t k = 0; k < N + 3; ++k)
-                if (strip_role(cls, update, k, N, a, b, p, &rot)) ++count;
+            // strips streamed per tile: N for every class (the other N survivors,
+            // or the N inputs of a rebuild), 4 for the small write
+            const uint32_t count = update ? 4u : N;
+            uint32_t rot;
 
             uint8_t *const stripe_base = base + stripe * stripe_stride + c0;
             const uint8_t *aux_base = aux + stripe * aux_ss + c0;
@@ -424,7 +426,12 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                     // batches: room for the stage in the byte ring -- the oldest
                     // stages in flight are released, in order, until it fits
                     // after head (or at 0)
-                    if (issued >= n_slots && released < issued - n_slots + 1) released = issued - n_slots + 1;
+                    if (issued >= n_slots && released < issued - n_slots + 1) {  // the descriptor wait released these
+                        while (released < issued - n_slots + 1) {
+                            ++released;
+                            rel.next(n_slots);
+                        }
+                    }
                     const uint32_t B = (rows * W + 127) & ~127u;
                     for (;;) {
                         if (released == issued) {  // nothing in flight
@@ -432,9 +439,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                             break;
                         }
                         uint32_t t_off;  // offset of the oldest stage in flight (its header)
-                        asm volatile("ld.shared.u32 %0, [%1];"
-                                     : "=r"(t_off)
-                                     : "r"(smem_addr(&sm.hdr[released % n_slots].off)));
+                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t_off) : "r"(smem_addr(&sm.hdr[rel.slot].off)));
                         bool fits = false;
                         if (t_off < head) {         // occupied [t_off, head)
                             if (head + B <= ring_bytes) { start = head; fits = true; }
@@ -443,12 +448,12 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                             if (head + B <= t_off) { start = head; fits = true; }
                         }                           // t_off == head: full
                         if (fits) break;
-                        if (!mbar_wait(smem_addr(&sm.empty[released % n_slots]), (released / n_slots) & 1u,
-                                       timeout)) {
+                        if (!mbar_wait(smem_addr(&sm.empty[rel.slot]), rel.phase, timeout)) {
                             ok = false;
                             break;
                         }
                         ++released;
+                        rel.next(n_slots);
                     }
                     if (!ok) break;
                     head = start + B;
@@ -456,23 +461,25 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                 const uint32_t full = smem_addr(&sm.full[pos.slot]);
                 const bool tensor = use_tmap && k < N + 2;
                 if (lane == 0) {
-                    SlotHdr h;
-                    h.flags = fl | (emitted == 0 ? F_FIRST : 0) | (emitted + 1 == count ? F_LAST : 0);
-                    h.rot = static_cast<uint8_t>(rot);
-                    h.w = static_cast<uint16_t>(w);
-                    h.off = start;
-                    h.cls = cls;
-                    h.p = static_cast<uint8_t>(p);
-                    h.a = static_cast<uint8_t>(a);
-                    h.b = static_cast<uint8_t>(b);
-                    h.pitch = static_cast<uint16_t>(W);
-                    h.zinv = static_cast<uint8_t>(zinv);
-                    h.base = reinterpret_cast<uint64_t>(stripe_base);
-                    h.strip_stride = strip_stride;
-                    h.row_stride = row_stride;
-                    h.out = reinterpret_cast<uint64_t>(aux_base);
-                    h.out_row_stride = aux_rs;
-                    sm.hdr[pos.slot] = h;
+                    // hot 16 bytes every stage; the tile part only on its first
+                    SlotHdr &h = sm.hdr[pos.slot];
+                    const uint32_t first = emitted == 0;
+                    const uint32_t fl2 = fl | (first ? F_FIRST : 0) | (emitted + 1 == count ? F_LAST : 0);
+                    const uint4 hot = make_uint4(fl2 | (rot << 8) | (w << 16), start, 0u, 0u);
+                    *reinterpret_cast<uint4 *>(&h) = hot;
+                    if (first) {
+                        h.cls = cls;
+                        h.p = static_cast<uint8_t>(p);
+                        h.a = static_cast<uint8_t>(a);
+                        h.b = static_cast<uint8_t>(b);
+                        h.pitch = static_cast<uint16_t>(W);
+                        h.zinv = static_cast<uint8_t>(zinv);
+                        h.base = reinterpret_cast<uint64_t>(stripe_base);
+                        h.strip_stride = strip_stride;
+                        h.row_stride = row_stride;
+                        h.out = reinterpret_cast<uint64_t>(aux_base);
+                        h.out_row_stride = aux_rs;
+                    }
                     mbar_arrive_tx(full, tensor ? tx_tensor : tx_rows);
                 }
                 __syncwarp();
