@@ -127,6 +127,11 @@ __device__ __forceinline__ void tensor_load_4d(uint32_t dst, const CUtensorMap *
         : "memory");
 }
 
+// Bring a tensor map into the TMA unit's descriptor cache ahead of its first use.
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }
@@ -361,6 +366,8 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
         const uint32_t rows = p - 1;
 
         for (uint32_t q = 0; q < nt && ok; ++q) {
+            if (q == 0 && items && u < total_units && lane == 0 && nxt.use_tmap)
+                prefetch_tmap(&prm.jobs[nxt.job].tmap);  // the next item's descriptor
             const uint64_t local = lt0 + q;
             const uint32_t stripe = static_cast<uint32_t>(local / tps);
             const uint32_t c0 = static_cast<uint32_t>(local % tps) * W;
