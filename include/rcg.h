@@ -220,7 +220,7 @@ typedef struct rcg_job {
 } rcg_job;
 
 /* Run a list of jobs of mixed p, N, C and op in ONE persistent-kernel launch:
- * jobs are cut into work items of a few tiles, largest jobs first, and the
+ * jobs are cut into work items of roughly equal bytes, largest jobs first, and the
  * stages of all of them share one shared-memory byte ring per CTA, so small
  * and large stripes keep the same number of bytes in flight.  The job list is validated on the
  * host, copied into a context-owned device descriptor table and replayed
@@ -231,8 +231,8 @@ typedef struct rcg_job {
 rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, void *stream,
                             uint64_t *ticket);
 
-/* How a batch's work items (runs of at most 8 tiles of one job, largest
- * jobs first) reach the CTAs.  RCG_SCHED_DYNAMIC (default): taken from a
+/* How a batch's work items (runs of tiles of one job of roughly equal bytes,
+ * largest jobs first) reach the CTAs.  RCG_SCHED_DYNAMIC (default): taken from a
  * global counter as CTAs free up.  RCG_SCHED_STATIC: dealt round-robin.
  * Either way a CTA requests its next item while the current one streams.
  * Results are identical. */

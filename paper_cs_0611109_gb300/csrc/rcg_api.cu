@@ -614,9 +614,8 @@ static uint32_t batch_shape(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_
 }
 
 // The descriptor table of a batch for one engine shape, built in `out`:
-// header, jobs, then work items.  Items hold up to tiles_per_item tiles of
-// one job (kTilesPerItem, raised when max_items caps the item count); the
-// items of larger jobs come first so the batch ends on small items.
+// header, jobs, then work items (runs of tiles of one job of roughly equal
+// bytes); the items of larger jobs come first so the batch ends on small items.
 static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, uint32_t shape,
                               uint64_t max_items, std::vector<uint8_t> &out) {
     std::vector<Job> table(n_jobs);
@@ -632,8 +631,25 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
         total += tiles[k];
         slot_bytes = std::max(slot_bytes, pl.slot_bytes);
     }
-    uint64_t per = kTilesPerItem;
-    if (max_items && (total + per - 1) / per > max_items) per = (total + max_items - 1) / max_items;
+    // Item size by bytes: about 1/16 of a CTA's share of the batch, clamped to
+    // [256 KB, 2 MB], so the largest stripes do not leave one CTA working
+    // alone at the end; max_items (the no-allocation table) can only raise it.
+    uint64_t batch_bytes = 0;
+    for (uint32_t k = 0; k < n_jobs; ++k)
+        batch_bytes += static_cast<uint64_t>(table[k].n_stripes) * (table[k].n + 2u) * (table[k].p - 1u) * table[k].C;
+    const uint64_t ctas = static_cast<uint64_t>(ctx->sm_count ? ctx->sm_count : 152) * shape_info(shape).ctas_per_sm;
+    const uint64_t target = std::min<uint64_t>(2ull << 20, std::max<uint64_t>(256ull << 10, batch_bytes / (ctas * 16)));
+    std::vector<uint64_t> per(n_jobs);
+    uint64_t n_items_est = 0;
+    for (uint32_t k = 0; k < n_jobs; ++k) {
+        const uint64_t tile_bytes = (table[k].n + 2ull) * (table[k].p - 1u) * table[k].W;
+        per[k] = std::max<uint64_t>(1, target / tile_bytes);
+        n_items_est += (tiles[k] + per[k] - 1) / per[k];
+    }
+    if (max_items && n_items_est > max_items) {  // coarser items to fit the table
+        const uint64_t scale = (n_items_est + max_items - 1) / max_items + 1;
+        for (uint32_t k = 0; k < n_jobs; ++k) per[k] *= scale;
+    }
     std::vector<uint32_t> order(n_jobs);
     for (uint32_t k = 0; k < n_jobs; ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
@@ -665,9 +681,9 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
         w.j = J.j;
         w.use_tmap = J.use_tmap;
         w.dd_solve = J.dd_solve;
-        for (uint64_t t = 0; t < tiles[k]; t += per) {
+        for (uint64_t t = 0; t < tiles[k]; t += per[k]) {
             w.tile0 = static_cast<uint32_t>(t);
-            w.ntiles = static_cast<uint32_t>(std::min<uint64_t>(per, tiles[k] - t));
+            w.ntiles = static_cast<uint32_t>(std::min<uint64_t>(per[k], tiles[k] - t));
             items.push_back(w);
         }
     }

@@ -99,7 +99,7 @@ struct LaunchParams {
 
 // Header of a batch descriptor table: the graph-replayed batch kernel reads
 // its sizes from here so the captured kernel node never changes.
-// A unit of work in a batch: up to a few tiles of one job, with every field
+// A unit of work in a batch: a run of tiles of one job (sized by bytes), with every field
 // the producer needs copied in, so one 128-byte load (prefetched while the
 // previous item streams) starts it.  Items are dealt to CTAs round-robin;
 // larger jobs' items come first, so the tail of a batch is made of small items.
@@ -156,7 +156,6 @@ void inverse_masks(uint32_t p, uint64_t *masks);
 bool noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, uint8_t *table, size_t capacity,
                          size_t *bytes, uint32_t *shape);
 
-// Tiles per work item of a batch.
-constexpr uint32_t kTilesPerItem = 8;
+
 
 }  // namespace rcg
