@@ -231,6 +231,19 @@ typedef struct rcg_job {
 rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, void *stream,
                             uint64_t *ticket);
 
+/* The two halves of rcg_batch_submit, for callers that overlap host work
+ * with the GPU.  rcg_batch_prepare does all host work -- validation, tiling,
+ * one TMA tensor map per job, the work-item list -- into an opaque batch that
+ * holds no pointer into `jobs`; rcg_batch_launch copies it into a batch slot
+ * and replays the slot's CUDA graph (same ticket semantics as
+ * rcg_batch_submit).  A prepared batch may be launched any number of times
+ * (it names the same device buffers each time) and is released with
+ * rcg_batch_free.  The context that prepared a batch must launch it. */
+typedef struct rcg_batch rcg_batch;
+rcg_status rcg_batch_prepare(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, rcg_batch **out);
+rcg_status rcg_batch_launch(rcg_ctx *ctx, const rcg_batch *batch, void *stream, uint64_t *ticket);
+rcg_status rcg_batch_free(rcg_batch *batch);
+
 /* How a batch's work items (runs of tiles of one job of roughly equal bytes,
  * largest jobs first) reach the CTAs.  RCG_SCHED_DYNAMIC (default): taken from a
  * global counter as CTAs free up.  RCG_SCHED_STATIC: dealt round-robin.

@@ -51,6 +51,13 @@ rcg_status host_path(HostStaging *h, const rcg_layout *L, uint64_t first, uint64
                      void *run_arg);
 }  // namespace rcg
 
+// A prepared batch: the descriptor-table image and the engine shape.
+struct rcg_batch {
+    std::vector<uint8_t> image;
+    uint32_t shape = 0;
+    uint32_t n_jobs = 0;
+};
+
 struct rcg_ctx {
     int device = 0;
     int sm_count = 0;
@@ -708,16 +715,35 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     return RCG_OK;
 }
 
-rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, void *stream,
-                            uint64_t *ticket) {
-    if (!ctx || !ticket || (n_jobs && !jobs)) return RCG_EINVAL;
-    *ticket = 0;
-    if (n_jobs == 0) return RCG_OK;
-    std::vector<uint8_t> image;
-    const uint32_t shape = batch_shape(ctx, jobs, n_jobs);
-    rcg_status st0 = build_table(ctx, jobs, n_jobs, shape, 0, image);
-    if (st0) return st0;
+rcg_status rcg_batch_prepare(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, rcg_batch **out) {
+    if (!ctx || !out || (n_jobs && !jobs)) return RCG_EINVAL;
+    *out = nullptr;
+    rcg_batch *b = new (std::nothrow) rcg_batch();
+    if (!b) return RCG_ENOMEM;
+    b->n_jobs = n_jobs;
+    if (n_jobs) {
+        DeviceGuard guard(ctx->device);
+        b->shape = batch_shape(ctx, jobs, n_jobs);
+        rcg_status st = build_table(ctx, jobs, n_jobs, b->shape, 0, b->image);
+        if (st) {
+            delete b;
+            return st;
+        }
+    }
+    *out = b;
+    return RCG_OK;
+}
 
+rcg_status rcg_batch_free(rcg_batch *b) {
+    if (!b) return RCG_EINVAL;
+    delete b;
+    return RCG_OK;
+}
+
+rcg_status rcg_batch_launch(rcg_ctx *ctx, const rcg_batch *b, void *stream, uint64_t *ticket) {
+    if (!ctx || !b || !ticket) return RCG_EINVAL;
+    *ticket = 0;
+    if (b->n_jobs == 0) return RCG_OK;
     DeviceGuard guard(ctx->device);
     const uint64_t tk = ctx->next_ticket;
     BatchSlot &s = ctx->slots[tk % kBatchRing];
@@ -726,10 +752,10 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
         if (st == RCG_ETIMEOUT) return RCG_EBUSY;
         if (st) return st;
     }
-    const size_t bytes = image.size();
-    rcg_status st = prepare_slot(ctx, s, bytes, shape);
+    const size_t bytes = b->image.size();
+    rcg_status st = prepare_slot(ctx, s, bytes, b->shape);
     if (st) return st;
-    memcpy(s.host, image.data(), bytes);
+    memcpy(s.host, b->image.data(), bytes);
     cudaError_t e = cudaSuccess;
     const char *where = "graph copy-size update";
     if (bytes != s.bytes) {
@@ -766,6 +792,19 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
     ctx->next_ticket = tk + 1;
     *ticket = tk;
     return RCG_OK;
+}
+
+rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, void *stream,
+                            uint64_t *ticket) {
+    if (!ctx || !ticket || (n_jobs && !jobs)) return RCG_EINVAL;
+    *ticket = 0;
+    if (n_jobs == 0) return RCG_OK;
+    rcg_batch *b = nullptr;
+    rcg_status st = rcg_batch_prepare(ctx, jobs, n_jobs, &b);
+    if (st) return st;
+    st = rcg_batch_launch(ctx, b, stream, ticket);
+    rcg_batch_free(b);
+    return st;
 }
 
 rcg_status rcg_batch_wait(rcg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns) {

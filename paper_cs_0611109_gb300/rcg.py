@@ -73,6 +73,9 @@ EXPORTS = {
     "rcg_recover_many_host": (_int, [_vp, ctypes.POINTER(rcg_layout), _u64, _u64, _vp, _vp]),
     "rcg_batch_submit": (_int, [_vp, ctypes.POINTER(rcg_job), _u32, _vp, ctypes.POINTER(_u64)]),
     "rcg_batch_wait": (_int, [_vp, _u64, _u64]),
+    "rcg_batch_prepare": (_int, [_vp, ctypes.POINTER(rcg_job), _u32, ctypes.POINTER(_vp)]),
+    "rcg_batch_launch": (_int, [_vp, _vp, _vp, ctypes.POINTER(_u64)]),
+    "rcg_batch_free": (_int, [_vp]),
     "rcg_batch_submit_noalloc": (_int, [ctypes.POINTER(rcg_job), _u32, _vp, _vp]),
     "rcg_fill_random": (_int, [_vp, _u64, _u64, _u64, _vp]),
     "rcg_inverse_table": (_int, [_u32, ctypes.POINTER(_u64)]),
@@ -249,6 +252,24 @@ def rcg_batch_submit(ctx: int, jobs, stream=None) -> int:
     return int(ticket.value)
 
 
+def rcg_batch_prepare(ctx: int, jobs) -> int:
+    """Host half of rcg_batch_submit: returns an opaque prepared-batch handle."""
+    arr = (rcg_job * max(1, len(jobs)))(*jobs)
+    h = _vp()
+    _check(lib().rcg_batch_prepare(ctx, arr, len(jobs), ctypes.byref(h)), "rcg_batch_prepare")
+    return h.value
+
+
+def rcg_batch_launch(ctx: int, batch: int, stream=None) -> int:
+    ticket = _u64(0)
+    _check(lib().rcg_batch_launch(ctx, batch, _stream(stream), ctypes.byref(ticket)), "rcg_batch_launch")
+    return int(ticket.value)
+
+
+def rcg_batch_free(batch: int):
+    _check(lib().rcg_batch_free(batch), "rcg_batch_free")
+
+
 def rcg_batch_submit_noalloc(jobs, status_dev=None, stream=None):
     """rcg_batch_submit without a context and without allocating device memory
     (scratch in a fixed device array; at most RCG_NOALLOC_MAX_JOBS jobs).
@@ -333,6 +354,12 @@ class Context:
 
     def batch_wait(self, ticket, timeout_ns=10 ** 10) -> bool:
         return rcg_batch_wait(self.handle, ticket, timeout_ns)
+
+    def batch_prepare(self, jobs) -> int:
+        return rcg_batch_prepare(self.handle, jobs)
+
+    def batch_launch(self, batch, stream=None) -> int:
+        return rcg_batch_launch(self.handle, batch, stream)
 
     def set_timeout(self, timeout_ns):
         rcg_set_timeout(self.handle, timeout_ns)

@@ -386,6 +386,22 @@ def test_batched_uneven_jobs_alone_and_in_the_mix(rcg, ctx, oracle):
         assert np.array_equal(got[o:o + b], want), k
 
 
+def test_prepared_batch_launches_repeatedly(rcg, ctx, oracle):
+    p, N, C, S = 13, 12, 1024, 6
+    host = host_stripes(950, p, N, C, S)
+    want = host.copy()
+    oracle.encode(p, N, C, want, S)
+    buf = dev(host)
+    L = rcg.make_layout(buf, p, N, C)
+    b = ctx.batch_prepare([rcg.make_job(L, s, 1, rcg.RCG_OP_ENCODE) for s in range(S)])
+    for _ in range(3):
+        buf.copy_(dev(host))
+        assert ctx.batch_wait(ctx.batch_launch(b))
+        assert np.array_equal(buf.cpu().numpy(), want)
+    rcg.rcg_batch_free(b)
+    check_clean(ctx)
+
+
 def test_batch_many_small_jobs_replays_graph(rcg, ctx, oracle):
     p, N, C, S = 13, 5, 64, 40
     host = host_stripes(900, p, N, C, S)
