@@ -257,6 +257,56 @@ rcg_status rcg_set_batch_schedule(rcg_ctx *ctx, int schedule);
  * finished (the batch keeps running). */
 rcg_status rcg_batch_wait(rcg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A request loop with continuous batching (not in the paper).  Requests are
+ * rcg_jobs on caller-owned device stripes (the stripe and parity state stay
+ * in device memory), each with an arrival time and an HBM footprint.  A
+ * scheduler thread, started by rcg_serve_start, owns the context until
+ * rcg_serve_destroy (do not use the context from other threads meanwhile) and
+ * repeats: retire launches whose completion event fired; admit requests
+ * whose arrival time has passed, in arrival order, while the in-flight
+ * request count and the HBM budget allow (a request on a stripe an admitted
+ * request still uses waits, so two jobs on one stripe never share a launch);
+ * launch everything admitted as ONE batch of the persistent engine while
+ * fewer than two launches are in flight -- requests arriving meanwhile join
+ * the next batch, which is prepared on the host while the GPU runs.  With
+ * per_job_launches = 1 each request is launched on its own with the single-
+ * operation call instead (the comparison). */
+typedef struct rcg_server rcg_server;
+
+typedef struct rcg_serve_config {
+    uint64_t hbm_budget_bytes;   /* sum of footprints admitted at once; 0 = min(120 GB, free HBM) */
+    uint32_t max_inflight_jobs;  /* admitted but not completed; 0 = 4096 */
+    uint32_t max_batch_jobs;     /* requests per launch; 0 = 4096 */
+    uint32_t per_job_launches;   /* 1: one single-operation launch per request */
+    uint32_t reserved;
+} rcg_serve_config;
+
+typedef struct rcg_serve_request {
+    rcg_job job;                /* one stripe (n_stripes = 1) unless op = encode */
+    uint64_t arrival_ns;        /* visible to the scheduler this long after rcg_serve_start */
+    uint64_t footprint_bytes;   /* HBM working set while in flight; 0 = the job's stripes (+ output) */
+} rcg_serve_request;
+
+typedef struct rcg_serve_result {
+    uint64_t id;                /* submission index */
+    uint64_t arrival_ns, admit_ns, launch_ns, complete_ns;  /* since rcg_serve_start */
+    uint32_t status;            /* RCG_OK, or RCG_EBUSY while not completed */
+    uint32_t batch;             /* launch number that carried the request */
+} rcg_serve_result;
+
+rcg_status rcg_serve_create(rcg_ctx *ctx, const rcg_serve_config *cfg, rcg_server **out);
+/* Queue n requests (before or after rcg_serve_start); *first_id = id of the first. */
+rcg_status rcg_serve_submit(rcg_server *s, const rcg_serve_request *reqs, uint32_t n, uint64_t *first_id);
+rcg_status rcg_serve_start(rcg_server *s);
+/* Wait (at most timeout_ns) until every submitted request has completed. */
+rcg_status rcg_serve_drain(rcg_server *s, uint64_t timeout_ns);
+/* Timings of requests [0, min(max, submitted)). */
+rcg_status rcg_serve_results(rcg_server *s, rcg_serve_result *out, uint64_t max, uint64_t *n);
+/* Stop the scheduler (after the launches in flight finish) and free the server. */
+rcg_status rcg_serve_destroy(rcg_server *s);
+
 /* ------------------------------------------------ no-allocation batches */
 
 /* The paper has no counterpart to this call: it exists for callers that may

@@ -870,3 +870,5 @@ bool rcg::noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, uint8_t *tab
     *bytes = image.size();
     return true;
 }
+
+int rcg::ctx_device(const rcg_ctx *ctx) { return ctx ? ctx->device : 0; }

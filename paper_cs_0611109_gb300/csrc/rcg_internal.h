@@ -150,6 +150,9 @@ cudaError_t launch_fill(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte
 
 void inverse_masks(uint32_t p, uint64_t *masks);
 
+// Host: the CUDA device of a context.
+int ctx_device(const rcg_ctx *ctx);
+
 // Host: validate public jobs and build the batch descriptor table with the
 // default copy mode, two-data solve and engine shape (used by
 // rcg_batch_submit_noalloc); *shape receives the shape to launch.

@@ -46,6 +46,20 @@ class rcg_job(ctypes.Structure):
                 ("aux_stripe_stride", _u64)]
 
 
+class rcg_serve_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", _u64), ("max_inflight_jobs", _u32), ("max_batch_jobs", _u32),
+                ("per_job_launches", _u32), ("reserved", _u32)]
+
+
+class rcg_serve_request(ctypes.Structure):
+    _fields_ = [("job", rcg_job), ("arrival_ns", _u64), ("footprint_bytes", _u64)]
+
+
+class rcg_serve_result(ctypes.Structure):
+    _fields_ = [("id", _u64), ("arrival_ns", _u64), ("admit_ns", _u64), ("launch_ns", _u64),
+                ("complete_ns", _u64), ("status", _u32), ("batch", _u32)]
+
+
 class rcg_plan_info(ctypes.Structure):
     _fields_ = [("tile_bytes", _u32), ("tiles_per_stripe", _u32), ("slot_bytes", _u32), ("n_slots", _u32),
                 ("max_items", _u32), ("smem_bytes", _u32), ("ctas_per_sm", _u32), ("shape", _u32)]
@@ -76,6 +90,12 @@ EXPORTS = {
     "rcg_batch_prepare": (_int, [_vp, ctypes.POINTER(rcg_job), _u32, ctypes.POINTER(_vp)]),
     "rcg_batch_launch": (_int, [_vp, _vp, _vp, ctypes.POINTER(_u64)]),
     "rcg_batch_free": (_int, [_vp]),
+    "rcg_serve_create": (_int, [_vp, ctypes.POINTER(rcg_serve_config), ctypes.POINTER(_vp)]),
+    "rcg_serve_submit": (_int, [_vp, ctypes.POINTER(rcg_serve_request), _u32, ctypes.POINTER(_u64)]),
+    "rcg_serve_start": (_int, [_vp]),
+    "rcg_serve_drain": (_int, [_vp, _u64]),
+    "rcg_serve_results": (_int, [_vp, ctypes.POINTER(rcg_serve_result), _u64, ctypes.POINTER(_u64)]),
+    "rcg_serve_destroy": (_int, [_vp]),
     "rcg_batch_submit_noalloc": (_int, [ctypes.POINTER(rcg_job), _u32, _vp, _vp]),
     "rcg_fill_random": (_int, [_vp, _u64, _u64, _u64, _vp]),
     "rcg_inverse_table": (_int, [_u32, ctypes.POINTER(_u64)]),
@@ -268,6 +288,44 @@ def rcg_batch_launch(ctx: int, batch: int, stream=None) -> int:
 
 def rcg_batch_free(batch: int):
     _check(lib().rcg_batch_free(batch), "rcg_batch_free")
+
+
+def rcg_serve_create(ctx: int, hbm_budget_bytes=0, max_inflight_jobs=0, max_batch_jobs=0,
+                     per_job_launches=False) -> int:
+    cfg = rcg_serve_config(hbm_budget_bytes, max_inflight_jobs, max_batch_jobs, 1 if per_job_launches else 0, 0)
+    h = _vp()
+    _check(lib().rcg_serve_create(ctx, ctypes.byref(cfg), ctypes.byref(h)), "rcg_serve_create")
+    return h.value
+
+
+def rcg_serve_submit(server: int, jobs, arrivals_ns, footprints=None) -> int:
+    n = len(jobs)
+    arr = (rcg_serve_request * max(1, n))()
+    for k in range(n):
+        arr[k] = rcg_serve_request(jobs[k], int(arrivals_ns[k]), int(footprints[k]) if footprints is not None else 0)
+    first = _u64(0)
+    _check(lib().rcg_serve_submit(server, arr, n, ctypes.byref(first)), "rcg_serve_submit")
+    return int(first.value)
+
+
+def rcg_serve_start(server: int):
+    _check(lib().rcg_serve_start(server), "rcg_serve_start")
+
+
+def rcg_serve_drain(server: int, timeout_ns: int = 60 * 10 ** 9):
+    _check(lib().rcg_serve_drain(server, timeout_ns), "rcg_serve_drain")
+
+
+def rcg_serve_results(server: int, n: int):
+    """Timings of the first n requests as a list of dicts."""
+    arr = (rcg_serve_result * max(1, n))()
+    got = _u64(0)
+    _check(lib().rcg_serve_results(server, arr, n, ctypes.byref(got)), "rcg_serve_results")
+    return [{f: int(getattr(arr[k], f)) for f, _ in rcg_serve_result._fields_} for k in range(int(got.value))]
+
+
+def rcg_serve_destroy(server: int):
+    _check(lib().rcg_serve_destroy(server), "rcg_serve_destroy")
 
 
 def rcg_batch_submit_noalloc(jobs, status_dev=None, stream=None):
