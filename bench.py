@@ -50,8 +50,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--stripes", type=int, default=S,
                     help="stripes per GPU (default 8192; smaller values are profiling cases, not bench lines)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "batched"],
-                    help="c2: the bench line; batched: the uneven 50k-stripe batch vs per-stripe launches")
+    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "serve"],
+                    help="c2: the bench line; batched: the uneven 50k-stripe batch vs per-stripe launches; "
+                         "serve: Poisson request stream, continuous batching vs per-job launches")
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--pool-gb", type=float, default=40.0)
     ap.add_argument("--batch-jobs", type=int, default=50000)
     ap.add_argument("--arena-gb", type=float, default=100.0)
     ap.add_argument("--schedule", default="dynamic", choices=["static", "dynamic"])
@@ -488,10 +491,107 @@ def run_batched(args):
     return out
 
 
+# ---------------------------------------------------------------- serving
+
+def run_serve(args):
+    """Serving: a pool of device-resident stripes with the batched workload's
+    geometry (encoded before the run), and a Poisson stream of requests on
+    uniformly drawn stripes -- 70 % encode, 20 % degraded read of one strip,
+    10 % double-erasure rebuild.  The arrival rate is swept from 10 % to 200 %
+    of the measured saturation rate; at each rate the same stream is served by
+    the continuous-batching server and by one launch per request.  Latency is
+    arrival to completion (as the host sees it)."""
+    import numpy as np
+    import torch
+
+    from paper_cs_0611109_gb300 import build, inputs
+    build.build()
+    from paper_cs_0611109_gb300 import rcg
+
+    torch.cuda.set_device(0)
+    ctx = rcg.Context(0)
+    geo = inputs.batched_jobs(4, 10 ** 6)
+    align = lambda x: (x + 255) // 256 * 256
+    pool_bytes = int(args.pool_gb * 1e9)
+    stripes, used = [], 0
+    for g in geo:
+        sz = align(inputs.stripe_bytes(g["p"], g["n"], g["c"]))
+        if used + sz > pool_bytes:
+            break
+        stripes.append((g, used))
+        used += sz
+    pool = torch.empty(used, dtype=torch.uint8, device="cuda")
+    rcg.rcg_fill_random(pool, used, 4)
+    lays = [rcg.make_layout(pool.data_ptr() + o, g["p"], g["n"], g["c"]) for g, o in stripes]
+    b = ctx.batch_prepare([rcg.make_job(L, 0, 1, rcg.RCG_OP_ENCODE) for L in lays])
+    assert ctx.batch_wait(ctx.batch_launch(b))
+    rcg.rcg_batch_free(b)
+
+    rng = np.random.Generator(np.random.PCG64(5))
+    n = args.serve_requests
+    pick = rng.integers(0, len(stripes), size=n)
+    kinds = rng.choice(3, size=n, p=[0.7, 0.2, 0.1])  # encode, degraded read, rebuild
+    out_sizes = [(stripes[s][0]["p"] - 1) * stripes[s][0]["c"] if k == 1 else 0 for s, k in zip(pick, kinds)]
+    out_offs = np.cumsum([0] + [align(x) for x in out_sizes])
+    outs = torch.empty(max(256, int(out_offs[-1])), dtype=torch.uint8, device="cuda")
+    jobs, user = [], 0
+    for r in range(n):
+        g, _ = stripes[pick[r]]
+        L = lays[pick[r]]
+        if kinds[r] == 0:
+            jobs.append(rcg.make_job(L, 0, 1, rcg.RCG_OP_ENCODE))
+        elif kinds[r] == 1:
+            jobs.append(rcg.make_job(L, 0, 1, rcg.RCG_OP_DEGRADED_READ, 0, int(rng.integers(0, g["n"] + 2)),
+                                     outs.data_ptr() + int(out_offs[r])))
+        else:
+            a, c = sorted(rng.choice(g["n"] + 2, size=2, replace=False).tolist())
+            jobs.append(rcg.make_job(L, 0, 1, rcg.RCG_OP_RECOVER, a, c))
+        user += g["n"] * (g["p"] - 1) * g["c"]
+    gaps = rng.exponential(1.0, size=n)
+
+    def serve(rate, per_job):
+        arrivals = (np.cumsum(gaps) * (1e9 / rate)).astype(np.int64) if rate else np.zeros(n, np.int64)
+        srv = rcg.rcg_serve_create(ctx.handle, per_job_launches=per_job)
+        rcg.rcg_serve_submit(srv, jobs, arrivals)
+        rcg.rcg_serve_start(srv)
+        rcg.rcg_serve_drain(srv, 600 * 10 ** 9)
+        res = rcg.rcg_serve_results(srv, n)
+        rcg.rcg_serve_destroy(srv)
+        lat = np.array([r["complete_ns"] - r["arrival_ns"] for r in res], dtype=np.float64) / 1e6
+        span = (max(r["complete_ns"] for r in res) - min(r["arrival_ns"] for r in res)) / 1e9
+        return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "user_gbs": round(user / span / 1e9, 1), "launches": max(r["batch"] for r in res)}
+
+    serve(0, False)  # warm-up: graph capture, caches
+    sat = serve(0, False)  # everything at t = 0: the saturation throughput
+    sat_rate = sat["user_gbs"] * 1e9 / (user / n)
+    points = []
+    for f in (0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.25, 1.5, 2.0):
+        rate = f * sat_rate
+        points.append({"load": f, "rate_req_per_s": round(rate), "batched": serve(rate, False),
+                       "per_job": serve(rate, True)})
+    status = ctx.last_device_status()
+    if status:
+        raise RuntimeError("device status word %#x" % status)
+    ctx.close()
+    return {"metric": "serving: p50/p99 latency and user GB/s vs arrival rate, continuous batching vs per-job launches",
+            "value": sat["user_gbs"], "unit": "GB/s (saturation, batched)", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "u8", "data": "synthetic (SplitMix64 bytes, seed 4)",
+            "config": {"workload": "serving: Poisson stream of %d requests on %d resident stripes (%.1f GB), "
+                                   "batched-workload geometry, 70%% encode / 20%% degraded read / 10%% rebuild"
+                                   % (n, len(stripes), used / 1e9),
+                       "requests": n, "resident_stripes": len(stripes), "pool_bytes": used,
+                       "mean_user_bytes_per_request": user // n},
+            "saturation": sat, "sweep": points}
+
+
 def main():
     args = parse()
     if args.workload == "batched" and args.impl == "ours":
         print(json.dumps(run_batched(args)), flush=True)
+        return
+    if args.workload == "serve" and args.impl == "ours":
+        print(json.dumps(run_serve(args)), flush=True)
         return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
