@@ -277,8 +277,8 @@ typedef struct rcg_server rcg_server;
 
 typedef struct rcg_serve_config {
     uint64_t hbm_budget_bytes;   /* sum of footprints admitted at once; 0 = min(120 GB, free HBM) */
-    uint32_t max_inflight_jobs;  /* admitted but not completed; 0 = 4096 */
-    uint32_t max_batch_jobs;     /* requests per launch; 0 = 4096 */
+    uint32_t max_inflight_jobs;  /* admitted but not completed; 0 = 4 x max_batch_jobs */
+    uint32_t max_batch_jobs;     /* requests per launch; 0 = 2048 */
     uint32_t per_job_launches;   /* 1: one single-operation launch per request */
     uint32_t reserved;
 } rcg_serve_config;

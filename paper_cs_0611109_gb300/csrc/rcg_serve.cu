@@ -255,8 +255,9 @@ rcg_status rcg_serve_create(rcg_ctx *ctx, const rcg_serve_config *cfg, rcg_serve
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     if (s->cfg.hbm_budget_bytes == 0) s->cfg.hbm_budget_bytes = std::min<uint64_t>(120000000000ull, free_b);
-    if (s->cfg.max_inflight_jobs == 0) s->cfg.max_inflight_jobs = 4096;
-    if (s->cfg.max_batch_jobs == 0) s->cfg.max_batch_jobs = 4096;
+    if (s->cfg.max_batch_jobs == 0) s->cfg.max_batch_jobs = 2048;
+    // room for two full batches in flight, so the next one is prepared while one runs
+    if (s->cfg.max_inflight_jobs == 0) s->cfg.max_inflight_jobs = 4 * s->cfg.max_batch_jobs;
     const cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess) {
