@@ -69,6 +69,23 @@ def moved_bytes_per_op(stripes):
     return (N + 2) * (P - 1) * C * stripes
 
 
+def max_over_ranks(ms, device=None):
+    """The timed region's duration as the slowest rank saw it (all ranks get it)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(user_bytes_per_rank_step, steps, world, ms):
+    """Whole-job throughput: the user bytes every rank processed over the slowest
+    rank's time (weak scaling: each rank encodes and recovers its own stripes)."""
+    return user_bytes_per_rank_step * steps * world / (ms * 1e-3) / 1e9
+
+
 def peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -201,11 +218,7 @@ def run_ours(args):
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t0.elapsed_time(t1), dev)
     status = ctx.last_device_status()
     if status != 0:
         raise RuntimeError("device status word %#x after the timed region" % status)
@@ -218,7 +231,7 @@ def run_ours(args):
     achieved = moved_bytes_per_op(S) / (avg_launch_ms * 1e-3) / 1e9
 
     user_step = 5 * user_bytes_per_op(S)
-    value = user_step * args.steps * world / (ms * 1e-3) / 1e9
+    value = whole_job_gbs(user_step, args.steps, world, ms)
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),

@@ -349,6 +349,14 @@ rcg_status rcg_batch_submit_noalloc(const rcg_job *jobs, uint32_t n_jobs, uint32
 rcg_status rcg_fill_random(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte_offset,
                            void *stream);
 
+/* Failure detection without a fault (not in the paper): launch one thread
+ * that waits, with the same bounded mbarrier wait every engine kernel uses,
+ * on a barrier nothing completes.  The wait runs out after timeout_ns (at
+ * most 10 s), the kernel sets RCG_DEV_TIMEOUT in the context's status word
+ * and returns; the context stays usable.  Read the bit with
+ * rcg_last_device_status. */
+rcg_status rcg_selftest_wait_timeout(rcg_ctx *ctx, uint64_t timeout_ns, void *stream);
+
 /* Host: the per-p table of Section 4.6, (1 + x^z)^(-1) = sum_{j=0}^{(p-1)/2}
  * x^(2jz), for z = 1..p-1, as exponent sets modulo x^p - 1: bit m of masks[z]
  * set means the term x^m (0 <= m < p; x^(p-1) stands for its residue mod f).

@@ -846,6 +846,13 @@ rcg_status rcg_recover_many_host(rcg_ctx *ctx, const rcg_layout *L, uint64_t fir
 
 // =============================================================== utilities
 
+rcg_status rcg_selftest_wait_timeout(rcg_ctx *ctx, uint64_t timeout_ns, void *stream) {
+    if (!ctx || timeout_ns == 0 || timeout_ns > 10000000000ull) return RCG_EINVAL;
+    DeviceGuard guard(ctx->device);
+    return from_cuda(launch_wait_probe(ctx->status, timeout_ns, static_cast<cudaStream_t>(stream)),
+                     "wait probe");
+}
+
 rcg_status rcg_fill_random(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte_offset,
                            void *stream) {
     if ((!dev && nbytes) || !aligned16(dev) || (byte_offset & 7))

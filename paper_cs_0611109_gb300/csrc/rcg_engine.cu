@@ -852,6 +852,20 @@ __global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
         consumer<S>(prm, sm, n_slots);
 }
 
+// --------------------------------------------------- bounded-wait self test
+
+// One thread waits, with the engine's own bounded wait, on an mbarrier that
+// nothing will complete: the wait runs out after timeout_ns, the kernel
+// records RCG_DEV_TIMEOUT and returns -- no trap, no hang.
+__global__ void rcg_wait_probe_kernel(uint32_t *status, uint64_t timeout_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_addr(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(b, 0, timeout_ns)) set_status(status, RCG_DEV_TIMEOUT);
+}
+
 // ------------------------------------------------------ test-data generator
 
 __device__ __forceinline__ uint64_t splitmix_word(uint64_t seed, uint64_t w) {
@@ -947,6 +961,11 @@ cudaError_t launch_batch(const uint8_t *table_dev, uint32_t *status, unsigned lo
     const ShapeInfo si = shape_info(shape);
     return shape == SHAPE_PAIR ? launch_shape<ShapePair>(prm, bh, si.smem_limit, grid, stream)
                                : launch_shape<ShapeWide>(prm, bh, si.smem_limit, grid, stream);
+}
+
+cudaError_t launch_wait_probe(uint32_t *status, uint64_t timeout_ns, cudaStream_t stream) {
+    rcg_wait_probe_kernel<<<1, 32, 0, stream>>>(status, timeout_ns);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fill(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte_offset,

@@ -147,6 +147,7 @@ cudaError_t launch_batch(const uint8_t *table_dev, uint32_t *status, unsigned lo
 cudaError_t engine_init_attributes();
 cudaError_t launch_fill(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte_offset,
                         cudaStream_t stream);
+cudaError_t launch_wait_probe(uint32_t *status, uint64_t timeout_ns, cudaStream_t stream);
 
 void inverse_masks(uint32_t p, uint64_t *masks);
 

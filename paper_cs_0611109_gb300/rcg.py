@@ -98,6 +98,7 @@ EXPORTS = {
     "rcg_serve_destroy": (_int, [_vp]),
     "rcg_batch_submit_noalloc": (_int, [ctypes.POINTER(rcg_job), _u32, _vp, _vp]),
     "rcg_fill_random": (_int, [_vp, _u64, _u64, _u64, _vp]),
+    "rcg_selftest_wait_timeout": (_int, [_vp, _u64, _vp]),
     "rcg_inverse_table": (_int, [_u32, ctypes.POINTER(_u64)]),
     "rcg_plan": (_int, [_u32, _u64, ctypes.POINTER(rcg_plan_info)]),
 }
@@ -349,6 +350,10 @@ def rcg_batch_wait(ctx: int, ticket: int, timeout_ns: int = 10 ** 10) -> bool:
 def rcg_fill_random(dev, nbytes: int, seed: int, byte_offset: int = 0, stream=None):
     _check(lib().rcg_fill_random(_ptr(dev), nbytes, seed, byte_offset, _stream(stream)),
            "rcg_fill_random")
+
+
+def rcg_selftest_wait_timeout(ctx: int, timeout_ns: int, stream=None):
+    _check(lib().rcg_selftest_wait_timeout(ctx, timeout_ns, _stream(stream)), "rcg_selftest_wait_timeout")
 
 
 def rcg_inverse_table(p: int) -> list[int]:

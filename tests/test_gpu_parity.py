@@ -294,6 +294,43 @@ def test_host_memory_calls_need_pinned_memory(rcg, ctx):
         ctx.encode_host(rcg.make_layout(pageable, 5, 4, 16), 0, 2)
 
 
+# ------------------------------------------------------- failure detection
+
+def test_bounded_wait_runs_out_and_reports(rcg, oracle):
+    # a wait that nothing completes: the kernel gives up after 20 ms, records
+    # RCG_DEV_TIMEOUT and returns; the context keeps working afterwards
+    import time
+    with rcg.Context(0) as c:
+        t0 = time.perf_counter()
+        rcg.rcg_selftest_wait_timeout(c.handle, 20 * 10 ** 6)
+        torch.cuda.synchronize()
+        elapsed = time.perf_counter() - t0
+        assert c.last_device_status() == rcg.RCG_DEV_TIMEOUT
+        assert 0.015 < elapsed < 5.0
+        assert c.last_device_status() == 0  # reading cleared it
+        host = host_stripes(77, 5, 4, 64, 2)
+        want = host.copy()
+        oracle.encode(5, 4, 64, want, 2)
+        buf = dev(host)
+        c.encode(rcg.make_layout(buf, 5, 4, 64), 0, 2)
+        assert c.last_device_status() == 0
+        assert np.array_equal(buf.cpu().numpy(), want)
+
+
+def test_batch_wait_times_out_on_the_host(rcg):
+    # the host-side wait is bounded too: a zero-ish limit on a running batch
+    # returns RCG_ETIMEOUT (False) while the batch keeps going
+    p, N, C, S = 59, 58, 2048, 64
+    buf = torch.empty((S, N + 2, p - 1, C), dtype=torch.uint8, device="cuda")
+    with rcg.Context(0) as c:
+        L = rcg.make_layout(buf, p, N, C)
+        rcg.rcg_selftest_wait_timeout(c.handle, 50 * 10 ** 6)  # keeps the stream busy ~50 ms
+        t = c.batch_submit([rcg.make_job(L, 0, S, rcg.RCG_OP_ENCODE)])
+        assert c.batch_wait(t, 1000) is False
+        assert c.batch_wait(t, 10 ** 10) is True
+        assert c.last_device_status() == rcg.RCG_DEV_TIMEOUT  # from the probe only
+
+
 # ------------------------------------------------------------------ batches
 
 def test_batch_mixed_jobs_alone_and_in_the_mix(rcg, ctx, oracle):
