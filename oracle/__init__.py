@@ -7,8 +7,9 @@ module and this module never imports the product package.
 This file is a thin ctypes binding over ``rcg_oracle.c`` (compiled with gcc into
 ``oracle/_build/``).  All arithmetic lives in the C file: bit-level polynomial
 arithmetic in R = F2[x]/(1 + x + ... + x^(p-1)), one codeword per bit position,
-following Corollary 3.2.4 (encode) and Lemma 3.1.2 (the four erasure-pair
-cases).  Buffers are numpy uint8 arrays in the stripe layout
+following Corollary 3.2.4 (encode, extended to 2p - 1 data strips by equation
+qext of Section 3.3 when Theorem 3.3.3 allows it) and Lemma 3.1.2 (the four
+erasure-pair cases).  Buffers are numpy uint8 arrays in the stripe layout
 ``[stripe][strip 0..N+1][row 0..p-2][C bytes]`` (strip N = P, strip N+1 = Q),
 with optional explicit byte strides.
 
@@ -50,6 +51,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.oracle_ring_xpow.argtypes = [_uint, _uint]
     lib.oracle_ring_inv.restype = _u64
     lib.oracle_ring_inv.argtypes = [_uint, _u64]
+    lib.oracle_weight.restype = _u64
+    lib.oracle_weight.argtypes = [_uint, _uint]
+    lib.oracle_ord2.restype = _uint
+    lib.oracle_ord2.argtypes = [_uint]
+    lib.oracle_cone_extends.restype = ctypes.c_int
+    lib.oracle_cone_extends.argtypes = [_uint]
     lib.oracle_mul_xpow_array.restype = None
     lib.oracle_mul_xpow_array.argtypes = [_uint, _uint, _vp, _vp, ctypes.c_size_t]
     lib.oracle_encode.restype = ctypes.c_int
@@ -106,6 +113,23 @@ def ring_xpow(p: int, k: int) -> int:
 def ring_inv(p: int, a: int) -> int:
     """Inverse in R by extended Euclid; 0 if a is not invertible."""
     return int(lib().oracle_ring_inv(p, a))
+
+
+def weight(p: int, k: int) -> int:
+    """Q weight of data strip k: x^k for k < p, 1 + x^(k-p+1) for p <= k <= 2p-2
+    (equation qext of Section 3.3)."""
+    return int(lib().oracle_weight(p, k))
+
+
+def ord2(p: int) -> int:
+    """Order of 2 modulo the prime p (Lemma 3.3.1)."""
+    return int(lib().oracle_ord2(p))
+
+
+def cone_extends(p: int) -> bool:
+    """Condition (3) of Theorem 3.3.3 for the prime p (3 <= p <= 127): the
+    code extends to 2p - 1 data strips."""
+    return bool(lib().oracle_cone_extends(p))
 
 
 def mul_xpow_array(p: int, k: int, a: np.ndarray) -> np.ndarray:

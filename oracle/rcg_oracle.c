@@ -16,6 +16,11 @@
  * g = S_p and 0-based data indices as in Section 4.1 (data strip k is weighted
  * by g^k):
  *     P = sum_k d_k,            Q = sum_k x^k d_k   (mod f).
+ * For p < N <= 2p-1 data strips the Q weights continue with the extension
+ * (qext) of Section 3.3: strip k >= p is weighted by 1 + x^(k-p+1).  That
+ * code is MDS exactly when p satisfies the conditions of Theorem 3.3.3; this
+ * file checks condition (3) of that theorem (oracle_cone_extends) and accepts
+ * N > p only for such p.
  *
  * Storage (bit slicing).  A strip is p-1 rows of C bytes.  Bit b of the row
  * region (byte b/8, bit b%8) of row r holds the coefficient of x^r of the b-th
@@ -133,6 +138,54 @@ u64 oracle_ring_inv(unsigned p, u64 a)
     return (u64)r1;
 }
 
+/* Weight of data strip k in Q.  k < p: g^k (Corollary 3.2.4, with g = x);
+ * p <= k <= 2p-2: Id + g^(k-p+1), equation (qext) of Section 3.3. */
+u64 oracle_weight(unsigned p, unsigned k)
+{
+    if (k < p)
+        return oracle_ring_xpow(p, k);
+    return 1u ^ oracle_ring_xpow(p, k - p + 1);
+}
+
+/* Lemma 3.3.1: the order d of 2 modulo the prime p (R is a field exactly
+ * when d = p - 1). */
+unsigned oracle_ord2(unsigned p)
+{
+    unsigned d = 1, v = 2 % p;
+    while (v != 1) {
+        v = (2 * v) % p;
+        d++;
+    }
+    return d;
+}
+
+/* Greatest common divisor in F2[x] by Euclid's algorithm. */
+static u128 poly_gcd(u128 a, u128 b)
+{
+    while (b != 0) {
+        u128 r;
+        poly_divmod(a, b, NULL, &r);
+        a = b;
+        b = r;
+    }
+    return a;
+}
+
+/* Condition (3) of Theorem 3.3.3 for the prime p (3 <= p <= 127): for every
+ * 0 < m < p the polynomials X^p + 1 and X^m + X + 1 are coprime.  Returns 1
+ * when it holds, i.e. when the cone {g^k} + {Id + g^m} extends the code to
+ * 2p - 1 data strips. */
+int oracle_cone_extends(unsigned p)
+{
+    u128 xp1 = (((u128)1) << p) | 1u;
+    for (unsigned m = 1; m < p; m++) {
+        u128 t = (((u128)1) << m) ^ 2u ^ 1u;
+        if (poly_gcd(xp1, t) != 1)
+            return 0;
+    }
+    return 1;
+}
+
 /* out[t] = x^k * in[t] in R, for n elements. */
 void oracle_mul_xpow_array(unsigned p, unsigned k, const u64 *in, u64 *out, size_t n)
 {
@@ -184,24 +237,27 @@ static int check_args(unsigned p, unsigned N)
     for (unsigned t = 3; t * t <= p; t += 2)
         if (p % t == 0)
             return -1;
-    if (N < 1 || N > p)
+    if (N < 1 || N > 2 * p - 1)
+        return -1;
+    if (N > p && !oracle_cone_extends(p))
         return -1;
     return 0;
 }
 
 /* ------------------------------------------------------------- encode */
 
-/* Equation (znparity) of Corollary 3.2.4 with g = S_p and g_k = g^k:
- * P = sum_k d_k, Q = sum_k g^k d_k.  Writes strips N and N+1. */
+/* Equation (znparity) of Corollary 3.2.4 with g = S_p and g_k = g^k, extended
+ * by (qext) for k >= p: P = sum_k d_k, Q = sum_k g_k d_k.  Writes strips N
+ * and N+1. */
 int oracle_encode(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
                   u64 row_stride, u64 strip_stride, u64 stripe_stride)
 {
     if (check_args(p, N))
         return -1;
     layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1};
-    u64 g[64];
+    u64 g[128];
     for (unsigned k = 0; k < N; k++)
-        g[k] = oracle_ring_xpow(p, k);
+        g[k] = oracle_weight(p, k);
     for (u64 s = 0; s < n_stripes; s++) {
         for (u64 b = 0; b < 8 * C; b++) {
             u64 P = 0, Q = 0;
@@ -229,10 +285,10 @@ int oracle_encode(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
  *                    then d_i = P + sum_{k != i} d_k.
  * Inverses come from the extended Euclidean algorithm.  The erased strips'
  * contents are never read. */
-static void recover_one(const layout_t *L, unsigned p, unsigned N, u64 s, u64 b,
-                        unsigned i, unsigned j, const u64 *g)
+static int recover_one(const layout_t *L, unsigned p, unsigned N, u64 s, u64 b,
+                       unsigned i, unsigned j, const u64 *g)
 {
-    u64 d[64];
+    u64 d[128];
     if (i == N && j == N + 1) {
         u64 P = 0, Q = 0;
         for (unsigned k = 0; k < N; k++) {
@@ -242,7 +298,7 @@ static void recover_one(const layout_t *L, unsigned p, unsigned N, u64 s, u64 b,
         }
         scatter(L, s, N, b, P);
         scatter(L, s, N + 1, b, Q);
-        return;
+        return 0;
     }
     if (j == N) { /* d_i and P lost */
         u64 Q = gather(L, s, N + 1, b);
@@ -253,13 +309,16 @@ static void recover_one(const layout_t *L, unsigned p, unsigned N, u64 s, u64 b,
             d[k] = gather(L, s, k, b);
             acc ^= oracle_ring_mul(p, g[k], d[k]);
         }
-        d[i] = oracle_ring_mul(p, oracle_ring_inv(p, g[i]), acc);
+        u64 gi_inv = oracle_ring_inv(p, g[i]);
+        if (gi_inv == 0)
+            return -3;
+        d[i] = oracle_ring_mul(p, gi_inv, acc);
         u64 P = 0;
         for (unsigned k = 0; k < N; k++)
             P ^= d[k];
         scatter(L, s, i, b, d[i]);
         scatter(L, s, N, b, P);
-        return;
+        return 0;
     }
     if (j == N + 1) { /* d_i and Q lost */
         u64 P = gather(L, s, N, b);
@@ -276,7 +335,7 @@ static void recover_one(const layout_t *L, unsigned p, unsigned N, u64 s, u64 b,
             Q ^= oracle_ring_mul(p, g[k], d[k]);
         scatter(L, s, i, b, d[i]);
         scatter(L, s, N + 1, b, Q);
-        return;
+        return 0;
     }
     /* two data strips lost */
     u64 P = gather(L, s, N, b);
@@ -288,13 +347,17 @@ static void recover_one(const layout_t *L, unsigned p, unsigned N, u64 s, u64 b,
         d[k] = gather(L, s, k, b);
         rhs ^= oracle_ring_mul(p, g[k] ^ g[i], d[k]);
     }
-    d[j] = oracle_ring_mul(p, oracle_ring_inv(p, g[i] ^ g[j]), rhs);
+    u64 sum_inv = oracle_ring_inv(p, g[i] ^ g[j]);
+    if (sum_inv == 0) /* the pair is not in a cone: Theorem 3.3.3 fails for p */
+        return -3;
+    d[j] = oracle_ring_mul(p, sum_inv, rhs);
     u64 di = P ^ d[j];
     for (unsigned k = 0; k < N; k++)
         if (k != i && k != j)
             di ^= d[k];
     scatter(L, s, i, b, di);
     scatter(L, s, j, b, d[j]);
+    return 0;
 }
 
 /* Recover strips i < j of stripes [0, n_stripes) in place.  pairs, when not
@@ -306,16 +369,17 @@ int oracle_recover(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
     if (check_args(p, N))
         return -1;
     layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1};
-    u64 g[64];
+    u64 g[128];
     for (unsigned k = 0; k < N; k++)
-        g[k] = oracle_ring_xpow(p, k);
+        g[k] = oracle_weight(p, k);
     for (u64 s = 0; s < n_stripes; s++) {
         unsigned a = pairs ? pairs[2 * s] : i;
         unsigned c = pairs ? pairs[2 * s + 1] : j;
         if (!(a < c && c < N + 2))
             return -2;
         for (u64 b = 0; b < 8 * C; b++)
-            recover_one(&L, p, N, s, b, a, c, g);
+            if (recover_one(&L, p, N, s, b, a, c, g))
+                return -3;
     }
     return 0;
 }
@@ -359,7 +423,7 @@ int oracle_degraded_read(unsigned p, unsigned N, u64 C, const uint8_t *buf, u64 
         u64 v = 0;
         if (j == N + 1) {
             for (unsigned k = 0; k < N; k++)
-                v ^= oracle_ring_mul(p, oracle_ring_xpow(p, k), gather(&L, stripe, k, b));
+                v ^= oracle_ring_mul(p, oracle_weight(p, k), gather(&L, stripe, k, b));
         } else {
             for (unsigned k = 0; k <= N; k++)
                 if (k != j)

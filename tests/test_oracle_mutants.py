@@ -22,10 +22,16 @@ MUTANTS = {
     "dd_wrong_weight": ("rhs ^= oracle_ring_mul(p, g[k] ^ g[i], d[k]);", "rhs ^= oracle_ring_mul(p, g[k] ^ g[j], d[k]);"),
     "dd_transposed_solve": ("rhs = oracle_ring_mul(p, g[i], P) ^ Q;", "rhs = oracle_ring_mul(p, g[j], P) ^ Q;"),
     "dd_back_substitution_dropped": ("u64 di = P ^ d[j];", "u64 di = P;"),
-    "dp_missing_inverse": ("d[i] = oracle_ring_mul(p, oracle_ring_inv(p, g[i]), acc);", "d[i] = oracle_ring_mul(p, g[i], acc);"),
+    "dp_missing_inverse": ("d[i] = oracle_ring_mul(p, gi_inv, acc);", "d[i] = oracle_ring_mul(p, g[i], acc);"),
     "dq_drops_survivors": ("            acc ^= d[k];\n", "            acc ^= 0;\n"),
     "euclid_swapped_cofactors": ("u128 r0 = f, r1, s0 = 0, s1 = 1;", "u128 r0 = f, r1, s0 = 1, s1 = 0;"),
     "degraded_read_drops_p": ("for (unsigned k = 0; k <= N; k++)", "for (unsigned k = 0; k < N; k++)"),
+    "qext_weight_exponent_off_by_one": ("return 1u ^ oracle_ring_xpow(p, k - p + 1);",
+                                        "return 1u ^ oracle_ring_xpow(p, k - p);"),
+    "qext_weight_drops_identity": ("return 1u ^ oracle_ring_xpow(p, k - p + 1);", "return oracle_ring_xpow(p, k - p + 1);"),
+    "cone_check_ignores_common_factor": ("if (poly_gcd(xp1, t) != 1)", "if (poly_gcd(xp1, t) == 0)"),
+    "ord2_counts_from_zero": ("unsigned d = 1, v = 2 % p;", "unsigned d = 0, v = 2 % p;"),
+    "extension_allowed_for_every_prime": ("if (N > p && !oracle_cone_extends(p))", "if (N > p && 0)"),
     "update_wrong_stripe": ("return oracle_encode(p, N, C, buf + stripe * stripe_stride, 1,",
                             "return oracle_encode(p, N, C, buf, 1,"),
 }
@@ -44,6 +50,7 @@ def test_pins_catch_planted_mistake(name):
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", so, mutant])
         env = dict(os.environ, RCG_ORACLE_LIB=so)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                            os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_qext_pins.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, "planted mistake %r passed every pin:\n%s" % (name, r.stdout[-2000:])

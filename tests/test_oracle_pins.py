@@ -493,7 +493,7 @@ def test_update_and_degraded_read(oracle):
 
 def test_invalid_arguments_rejected(oracle):
     buf = np.zeros((1, 6, 4, 16), dtype=np.uint8)
-    for p, N in ((9, 4), (2, 1), (63, 4), (5, 0), (5, 6), (15, 4)):
+    for p, N in ((9, 4), (2, 1), (63, 4), (5, 0), (5, 10), (7, 8), (15, 4)):
         with pytest.raises(ValueError):
             oracle.encode(p, N, 16, buf, 1)
     with pytest.raises(ValueError):
