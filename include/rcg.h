@@ -14,6 +14,15 @@
  * precomputed inverses (1 + x^z)^(-1).  Everything is XOR over GF(2): results
  * are exact and the solution of every erasure pair is unique (Lemma 3.1.2).
  *
+ * Extended Q-parity (Section 3.3, equation (qext)).  For a prime p that
+ * satisfies Theorem 3.3.3 (every 1 + x^u + x^v, 0 < u < v < p, is a unit of
+ * R -- true for 5, 11, 13, 17, 19, 23, 29, ..., 59, 61 and false for 3, 7, 31)
+ * a stripe may hold up to 2p - 1 data strips: data strip k >= p is weighted
+ * in Q by 1 + x^(k-p+1), so
+ *     Q = sum_{k<p} x^k d_k + sum_{k=p}^{N-1} (1 + x^(k-p+1)) d_k,
+ * and P stays the plain XOR.  For N <= p this is the code above; every call
+ * below accepts the extended range (rcg_prime_info gives the limit).
+ *
  * Storage (bit-sliced).  A strip is p-1 rows of C bytes; row r holds the
  * coefficient of x^r of 8*C independent codewords, one per bit position.
  * Byte order, word width and bit order inside a row are irrelevant: every
@@ -74,7 +83,8 @@ typedef struct rcg_ctx rcg_ctx;
 typedef struct rcg_layout {
     void *base;             /* device address of stripe 0 */
     uint32_t p;             /* odd prime, 3 <= p <= 61; strips have p-1 rows */
-    uint32_t n_data;        /* N, 1 <= N <= p (Corollary 3.2.4); strip N = P, N+1 = Q */
+    uint32_t n_data;        /* N, 1 <= N <= p (Corollary 3.2.4), or N <= 2p - 1 where
+                               Theorem 3.3.3 holds (equation qext); strip N = P, N+1 = Q */
     uint64_t row_bytes;     /* C, bytes per row, a positive multiple of 16 */
     uint64_t row_stride;    /* bytes between rows of a strip; 0 = row_bytes */
     uint64_t strip_stride;  /* bytes between strips; 0 = (p-1)*row_stride */
@@ -148,7 +158,13 @@ rcg_status rcg_encode(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe,
 /* Recover strips i < j (0 <= i < j <= N+1) of one stripe in place from the
  * other N strips (Lemma 3.1.2): two data strips by Section 4.6's solve,
  * data + P through x^(-i) = x^(p-i), data + Q as in RAID-5, P + Q by
- * re-encoding.  The contents of strips i and j are not read. */
+ * re-encoding.  The contents of strips i and j are not read.
+ * With extended strips (i or j >= p, equation qext) the same four cases
+ * hold with the weights w_k of Q: data i + P solves (1 + x^(i-p+1)) D_i = dQ;
+ * two data strips solve (w_i + w_j) D_j = w_i dP + dQ, which the engine
+ * brings to (1 + x^z) D_j = T when both are extended, and multiplies by the
+ * inverse of a trinomial 1 + x^u + x^v (a unit by Theorem 3.3.3) when only
+ * j is. */
 rcg_status rcg_recover(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32_t i,
                        uint32_t j, void *stream);
 
@@ -362,6 +378,25 @@ rcg_status rcg_selftest_wait_timeout(rcg_ctx *ctx, uint64_t timeout_ns, void *st
  * set means the term x^m (0 <= m < p; x^(p-1) stands for its residue mod f).
  * masks[0] is set to 0.  masks must hold p entries. */
 rcg_status rcg_inverse_table(uint32_t p, uint64_t *masks);
+
+/* Host: facts about a prime p (3 <= p <= 61) that decide the code.
+ * ord2: the order of 2 modulo p (Lemma 3.3.1: R is a product of
+ * (p-1)/ord2 copies of GF(2^ord2)); is_field: ord2 == p - 1 (R is a field);
+ * extends: Theorem 3.3.3 holds, checked as "every 1 + x^u + x^v with
+ * 0 < u < v < p is a unit of R"; max_data: the largest N a layout may have,
+ * 2p - 1 when extends, else p.  RCG_EINVAL for p not an odd prime <= 61. */
+typedef struct rcg_prime_info_t {
+    uint32_t ord2;
+    uint32_t is_field;
+    uint32_t extends;
+    uint32_t max_data;
+} rcg_prime_info_t;
+rcg_status rcg_prime_info(uint32_t p, rcg_prime_info_t *out);
+
+/* Host: the inverse in R = F2[x]/(1 + ... + x^(p-1)) of a (bit m = coefficient
+ * of x^m, 0 <= m < p-1), computed as a^(2^d - 2), d = ord2 (Lemma 3.3.1), and
+ * checked.  RCG_EINVAL when a is not a unit or not a residue (bit p-1 set). */
+rcg_status rcg_ring_inverse(uint32_t p, uint64_t a, uint64_t *inv);
 
 /* Host: the tiling the library uses for one stripe geometry. */
 typedef struct rcg_plan_info {

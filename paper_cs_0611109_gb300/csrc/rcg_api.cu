@@ -116,7 +116,7 @@ struct Geo {
 rcg_status check_layout(const rcg_layout *L, Geo *g) {
     if (!L || !L->base || !aligned16(L->base)) return RCG_EINVAL;
     if (!is_odd_prime(L->p) || L->p > static_cast<uint32_t>(kMaxP)) return RCG_EINVAL;
-    if (L->n_data < 1 || L->n_data > L->p) return RCG_EINVAL;
+    if (L->n_data < 1 || L->n_data > max_data_strips(L->p)) return RCG_EINVAL;
     const uint64_t C = L->row_bytes;
     if (C == 0 || (C & 15) || C > 0xffffffffull) return RCG_EINVAL;
     g->p = L->p;
@@ -300,6 +300,22 @@ rcg_status rcg_inverse_table(uint32_t p, uint64_t *masks) {
     if (!masks || !is_odd_prime(p) || p > static_cast<uint32_t>(kMaxP)) return RCG_EINVAL;
     inverse_masks(p, masks);
     return RCG_OK;
+}
+
+rcg_status rcg_prime_info(uint32_t p, rcg_prime_info_t *out) {
+    if (!out || !is_odd_prime(p) || p > static_cast<uint32_t>(kMaxP)) return RCG_EINVAL;
+    out->ord2 = order_of_two(p);
+    out->is_field = out->ord2 == p - 1 ? 1u : 0u;
+    out->extends = cone_extends(p) ? 1u : 0u;
+    out->max_data = max_data_strips(p);
+    return RCG_OK;
+}
+
+rcg_status rcg_ring_inverse(uint32_t p, uint64_t a, uint64_t *inv) {
+    if (!inv || !is_odd_prime(p) || p > static_cast<uint32_t>(kMaxP)) return RCG_EINVAL;
+    if (a >> (p - 1)) return RCG_EINVAL;  // not a residue modulo f
+    *inv = ring_inverse(p, a);
+    return *inv ? RCG_OK : RCG_EINVAL;
 }
 
 rcg_status rcg_plan(uint32_t p, uint64_t row_bytes, rcg_plan_info *out) {

@@ -22,11 +22,22 @@
 // where (1 + x^z)^(-1) = sum_{t=0}^{(p-1)/2} x^(2tz) is read from a per-p
 // table precomputed on the host and kept in constant memory.
 //
+// Extended Q-parity (Section 3.3, equation qext).  For primes that satisfy
+// Theorem 3.3.3 a stripe may hold up to 2p - 1 data strips; strip k >= p is
+// weighted in Q by 1 + x^m, m = k - p + 1.  Such a strip feeds the lifted Q
+// accumulator twice (rotations m and 0) -- a second index remap of the same
+// slot.  Recovery multiplies the system of Lemma 3.1.2 by a monomial so that
+// it keeps the shape (1 + x^z) D = T wherever it can; the one case that
+// cannot (one regular and one extended data strip) multiplies T by the
+// inverse of a trinomial 1 + x^u + x^v, read from a host-computed table.
+//
 // Every wait is bounded (mbarrier try_wait against %globaltimer); an expired
 // wait sets RCG_DEV_TIMEOUT in the status word and the thread returns after
 // the copies it issued have landed.  No trap, no unbounded spin.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "../../include/rcg.h"
 #include "rcg_internal.h"
@@ -34,6 +45,24 @@
 namespace rcg {
 
 __constant__ uint64_t c_inv[kMaxP + 1][kMaxP + 1];
+
+// (1 + x^u + x^v)^(-1) for the primes that allow the extension: entry
+// c_tri_off[p] + u * p + v of g_tri; c_tri_off[p] = ~0u for the other primes.
+constexpr bool odd_prime_c(uint32_t p) {
+    if (p < 3 || (p & 1) == 0) return false;
+    for (uint32_t d = 3; d * d <= p; d += 2)
+        if (p % d == 0) return false;
+    return true;
+}
+constexpr uint32_t tri_entries() {
+    uint32_t n = 0;
+    for (uint32_t p = 3; p <= static_cast<uint32_t>(kMaxP); ++p)
+        if (odd_prime_c(p)) n += p * p;
+    return n;
+}
+constexpr uint32_t kTriEntries = tri_entries();
+__constant__ uint32_t c_tri_off[kMaxP + 1];
+__device__ uint64_t g_tri[kTriEntries];
 
 namespace {
 
@@ -165,6 +194,7 @@ enum : uint8_t {
     F_COPY = 4,   // also store the slot to the job's data strip i (small write)
     F_FIRST = 8,  // first slot of a tile
     F_LAST = 16,  // last slot of a tile: run the epilogue after it
+    F_Q2 = 32,    // also XOR the slot, rotated by `rot2`, into the lifted Q accumulators
     F_END = 128   // no more tiles for this CTA
 };
 
@@ -176,7 +206,10 @@ enum : uint8_t {
     E_DQ = 3,    // data strip i and Q
     E_DEGP = 4,  // degraded read of a data strip or P: out = accP
     E_DEGQ = 5,  // degraded read of Q: out = fold(accQ)
-    E_DDC = 6    // two data strips, solved by the chain along x^z (same result as E_DD)
+    E_DDC = 6,   // two data strips, solved by the chain along x^z (same result as E_DD)
+    E_DQX = 7,   // extended data strip i and Q: Q = fold(accQ + (1 + x^z) D_i)
+    E_DPXC = 8,  // extended data strip i and P: (1 + x^z) D_i = dQ by the chain
+    E_DPX = 9    // the same by the table, (1 + x^z)^(-1) dQ
 };
 
 // Slot header.  The first 16 bytes are read (one 16-byte load) for every
@@ -187,17 +220,19 @@ struct SlotHdr {
     uint8_t rot;      // x^rot for F_Q
     uint16_t w;       // tile width, bytes
     uint32_t off;     // byte offset of the stage in the ring
-    uint64_t pad1;
+    uint32_t rot2;    // x^rot2 for F_Q2
+    uint32_t pad1;
     uint8_t cls;      // epilogue class
     uint8_t p;
-    uint8_t a, b;     // the erased pair (a < b), or i / j of the op; b = N for E_ENC
+    uint8_t a, b;     // strips the epilogue writes (the erased pair, or i / j of the op)
     uint16_t pitch;   // bytes between rows in the slot (the job's tile width W)
-    uint8_t zinv;     // two-data tiles: (b - a)^(-1) mod p
-    uint8_t pad2;
+    uint8_t zinv;     // chain solves: z^(-1) mod p
+    uint8_t z;        // chain solves: the z of (1 + x^z); data + Q: the rotation of D_i's weight
     uint64_t base;            // the tile's column c0 of strip 0 of its stripe
     uint64_t strip_stride;
     uint64_t row_stride;
-    uint64_t out;             // degraded read: the tile's column of the output
+    uint64_t out;             // degraded read: the tile's column of the output;
+                              // table solves: the exponent mask of the inverse
     uint64_t out_row_stride;
 };
 static_assert(sizeof(SlotHdr) == 64, "slot header is 64 bytes");
@@ -230,47 +265,59 @@ __device__ __forceinline__ void set_status(uint32_t *status, uint32_t bits) {
 }
 
 // Role of strip k (0..N-1 data, N = P, N+1 = Q, N+2 = the small write's new
-// strip) in a tile of class `cls` with pair (a, b): returns flags (0 = not
-// read) and the rotation for Q.  For the two classes whose result involves
-// x^(-a) dQ (two data strips, data + P) the rotation is applied while
-// accumulating: strip k is weighted by x^(k-a) and Q by x^(-a) = x^(p-a), so
-// the lifted accumulator holds x^(-a) dQ directly.
-__device__ __forceinline__ uint8_t strip_role(uint8_t cls, bool update, uint32_t k, uint32_t N,
-                                              uint32_t a, uint32_t b, uint32_t p, uint32_t *rot) {
+// strip) in a tile of class `cls` with erased (or replaced) strips a < b:
+// returns flags (0 = not read) and the rotations for Q.  Data strip k is
+// weighted in Q by x^k (k < p) or 1 + x^(k-p+1) (k >= p, equation qext): one
+// or two rotations.  The tile's pre-rotation x^(-s) multiplies every Q weight
+// (so the lifted accumulator holds x^(-s) times the sum); with `pone` the data
+// weights become 1 + w_k and P feeds Q as well (the accumulator then holds
+// x^(-s) (dP + dQ)).
+__device__ __forceinline__ uint32_t strip_role(uint8_t cls, bool update, uint32_t k, uint32_t N,
+                                               uint32_t a, uint32_t b, uint32_t p, uint32_t s, bool pone,
+                                               uint32_t *rot, uint32_t *rot2) {
     *rot = 0;
-    const bool data = k < N;
+    *rot2 = 0;
     if (update) {  // old d_a, P, Q, new d_a (last, so d_a is read before it is overwritten)
-        if (k == a) { *rot = a; return F_P | F_Q; }
+        if (k == a || k == N + 2) {
+            const uint32_t cp = k == N + 2 ? F_COPY : 0u;
+            if (a < p) { *rot = a; return F_P | F_Q | cp; }
+            *rot = a - p + 1;
+            return F_P | F_Q | F_Q2 | cp;  // rot2 = 0
+        }
         if (k == N) return F_P;
         if (k == N + 1) return F_Q;
-        if (k == N + 2) { *rot = a; return F_P | F_Q | F_COPY; }
         return 0;
     }
-    const uint32_t back = (k + p - a) % p;  // k - a (mod p)
+    bool skip_a = true, skip_b = false, read_p = false, read_q = false;
+    uint32_t dflags = F_P | F_Q;
     switch (cls) {
-        case E_ENC:
-            if (data) { *rot = k; return F_P | F_Q; }
-            return 0;
-        case E_DD:
-        case E_DDC:
-            if (data && k != a && k != b) { *rot = back; return F_P | F_Q; }
-            if (k == N) return F_P;
-            if (k == N + 1) { *rot = (p - a) % p; return F_Q; }
-            return 0;
-        case E_DP:
-            if (data && k != a) { *rot = back; return F_P | F_Q; }
-            if (k == N + 1) { *rot = (p - a) % p; return F_Q; }
-            return 0;
-        case E_DQ:
-            if (data && k != a) { *rot = k; return F_P | F_Q; }
-            if (k == N) return F_P;
-            return 0;
-        case E_DEGP:  // strip b (data or P) from the first equation
-            if (k <= N && k != b) return F_P;
-            return 0;
-        case E_DEGQ:
-            if (data) { *rot = k; return F_Q; }
-            return 0;
+        case E_ENC: skip_a = false; break;
+        case E_DEGQ: skip_a = false; dflags = F_Q; break;
+        case E_DEGP: return (k <= N && k != b) ? F_P : 0u;  // data or P from the first equation
+        case E_DQ: case E_DQX: read_p = true; break;
+        case E_DP: case E_DPX: case E_DPXC: read_q = true; break;
+        default: skip_b = true; read_p = true; read_q = true; break;  // two data strips
+    }
+    const uint32_t back = s ? p - s : 0u;  // x^(-s), in [0, p)
+    if (k < N) {
+        if ((skip_a && k == a) || (skip_b && k == b)) return 0;
+        // the weight's one or two exponents (1 + w_k when pone)
+        const bool ext = k >= p;
+        const uint32_t e1 = (ext ? k - p + 1 : k) + back;
+        const bool two = ext != pone;  // x^k + 1, or 1 + x^m
+        *rot = e1 >= p ? e1 - p : e1;
+        if (!two) return dflags;
+        *rot2 = back;
+        return dflags | F_Q2;
+    }
+    if (k == N && read_p) {
+        if (!pone) return F_P;
+        *rot = back;
+        return F_P | F_Q;
+    }
+    if (k == N + 1 && read_q) {
+        *rot = back;
+        return F_Q;
     }
     return 0;
 }
@@ -323,9 +370,14 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
         if (lane == 0) v = atomicAdd(prm.tile_counter, 1ull);
         return __shfl_sync(0xffffffffu, v, 0);
     };
+    // The next item is held spread over the warp, word `lane` of its 128
+    // bytes in each lane (one coalesced load); fields come out by shuffles.
+    auto fetch = [&](uint64_t idx) -> uint32_t {
+        return reinterpret_cast<const uint32_t *>(items + idx)[lane];
+    };
     uint64_t u = items ? (dynamic ? next_index() : blockIdx.x) : 0;
-    WorkItem nxt;
-    if (items && u < total_units) nxt = items[u];
+    uint32_t nxt = 0;
+    if (items && u < total_units) nxt = fetch(u);
 
     for (;;) {
         // the fields of this unit, in registers
@@ -335,20 +387,22 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
         uint8_t *base, *aux;
         if (items) {
             if (u >= total_units) break;
-            const WorkItem cur = nxt;
+            const uint32_t cur = nxt;
             u = dynamic ? next_index() : u + gridDim.x;
-            if (u < total_units) nxt = items[u];  // prefetch
-            ji = cur.job;
-            lt0 = cur.tile0;
-            nt = cur.ntiles;
-            p = cur.p; N = cur.n; tps = cur.tiles_per_stripe; W = cur.W; C = cur.C;
-            n_stripes = cur.n_stripes; op = cur.op; use_tmap = cur.use_tmap; dd_solve = cur.dd_solve;
-            ji_i = cur.i; ji_j = cur.j;
-            pairs = reinterpret_cast<const uint8_t *>(cur.pairs);
-            base = reinterpret_cast<uint8_t *>(cur.base);
-            aux = reinterpret_cast<uint8_t *>(cur.aux);
-            strip_stride = cur.strip_stride; row_stride = cur.row_stride; stripe_stride = cur.stripe_stride;
-            aux_rs = cur.aux_row_stride; aux_ss = cur.aux_stripe_stride;
+            if (u < total_units) nxt = fetch(u);  // prefetch
+            // word offsets of the WorkItem fields
+            auto w32 = [&](int i) { return __shfl_sync(0xffffffffu, cur, i); };
+            auto w64 = [&](int i) { return static_cast<uint64_t>(w32(i)) | (static_cast<uint64_t>(w32(i + 1)) << 32); };
+            base = reinterpret_cast<uint8_t *>(w64(0));
+            aux = reinterpret_cast<uint8_t *>(w64(2));
+            pairs = reinterpret_cast<const uint8_t *>(w64(4));
+            strip_stride = w64(6); row_stride = w64(8); stripe_stride = w64(10);
+            aux_rs = w64(12); aux_ss = w64(14);
+            lt0 = w32(16); nt = w32(17); tps = w32(18); W = w32(19); C = w32(20); n_stripes = w32(21);
+            ji = w32(22);
+            const uint32_t b0 = w32(23), b1 = w32(24);
+            p = b0 & 0xffu; N = (b0 >> 8) & 0xffu; op = (b0 >> 16) & 0xffu; ji_i = b0 >> 24;
+            ji_j = b1 & 0xffu; use_tmap = (b1 >> 8) & 0xffu; dd_solve = (b1 >> 16) & 0xffu;
         } else {
             if (next_static >= total_units) break;
             ji = 0;
@@ -366,14 +420,17 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
         const uint32_t rows = p - 1;
 
         for (uint32_t q = 0; q < nt && ok; ++q) {
-            if (q == 0 && items && u < total_units && lane == 0 && nxt.use_tmap)
-                prefetch_tmap(&prm.jobs[nxt.job].tmap);  // the next item's descriptor
+            if (q == 0 && items && u < total_units) {  // the next item's descriptor
+                const uint32_t njob = __shfl_sync(0xffffffffu, nxt, 22);
+                const uint32_t ntm = (__shfl_sync(0xffffffffu, nxt, 24) >> 8) & 0xffu;
+                if (lane == 0 && ntm) prefetch_tmap(&prm.jobs[njob].tmap);
+            }
             const uint64_t local = lt0 + q;
             const uint32_t stripe = static_cast<uint32_t>(local / tps);
             const uint32_t c0 = static_cast<uint32_t>(local % tps) * W;
             const uint32_t w = min(W, C - c0);
             // device-side guard: a tile must fit its slot and the item budget
-            if (p < 3 || p > kMaxP || N < 1 || N > p || (w & 15) || w == 0 || W > kMaxTileBytes ||
+            if (p < 3 || p > kMaxP || N < 1 || N > 2 * p - 1 || (w & 15) || w == 0 || W > kMaxTileBytes ||
                 (W & 15) || rows * W > ring_bytes || p * (w >> 4) > static_cast<uint32_t>(S::kMaxItems) ||
                 stripe >= n_stripes) {
                 if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
@@ -382,6 +439,11 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
 
             uint8_t cls = E_ENC;
             uint32_t a = ji_i, b = ji_j;
+            uint32_t s = 0;         // pre-rotation x^(-s) of the Q weights
+            bool pone = false;      // Q weights 1 + w_k, P feeds Q
+            uint32_t z = 0;         // chain: (1 + x^z); data + Q: rotation of D_a's weight
+            uint64_t mask = 0;      // table solves: exponents of the inverse
+            uint32_t oa, ob;        // strips the epilogue writes
             const bool update = op == OP_UPDATE;
             if (op == OP_RECOVER) {
                 if (pairs) {
@@ -392,27 +454,78 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                     if (lane == 0) set_status(prm.status, RCG_DEV_BADPAIR);
                     continue;
                 }
-                cls = (b < N) ? (dd_solve ? E_DD : E_DDC) : (a == N) ? E_ENC : (b == N) ? E_DP : E_DQ;
+                if (b < N) {  // two data strips: (w_a + w_b) D_b = w_a dP + dQ
+                    if (b < p) {           // x^(-a): (1 + x^(b-a)) D_b = dP + x^(-a) dQ
+                        s = a;
+                        z = b - a;
+                        cls = dd_solve ? E_DD : E_DDC;
+                    } else if (a >= p) {   // x^(-m_a): (1 + x^(b-a)) D_b = dP + x^(-m_a)(dP + dQ)
+                        s = a - p + 1;
+                        pone = true;
+                        z = b - a;
+                        cls = dd_solve ? E_DD : E_DDC;
+                    } else {               // x^(-a): (1 + x^(-a) + x^(m_b-a)) D_b = dP + x^(-a) dQ
+                        s = a;
+                        cls = E_DD;
+                        const uint32_t off = c_tri_off[p];
+                        const uint32_t u = p - a == p ? 0u : p - a, v = (b - p + 1 + p - a) % p;
+                        mask = off == ~0u ? 0ull : g_tri[off + u * p + v];
+                        if (mask == 0) {  // p does not allow the extension
+                            if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
+                            continue;
+                        }
+                    }
+                    if (cls == E_DD && z) mask = c_inv[p][z];
+                    oa = a;
+                    ob = b;
+                } else if (a == N) {      // P and Q: encode
+                    cls = E_ENC;
+                    oa = N;
+                    ob = N;
+                } else if (b == N) {      // data a and P
+                    if (a < p) {
+                        cls = E_DP;
+                        s = a;
+                        oa = a;
+                        ob = N;
+                    } else {              // (1 + x^m_a) D_a = dQ, P = dP + D_a
+                        z = a - p + 1;
+                        cls = dd_solve ? E_DPX : E_DPXC;
+                        if (dd_solve) mask = c_inv[p][z];
+                        oa = N;           // receives D + accP
+                        ob = a;           // receives D
+                    }
+                } else {                  // data a and Q
+                    cls = a < p ? E_DQ : E_DQX;
+                    z = a < p ? a : a - p + 1;
+                    oa = a;
+                    ob = N + 1;
+                }
             } else if (op == OP_DEGRADED) {
                 cls = (b == N + 1) ? E_DEGQ : E_DEGP;
-            } else if (update) {
-                if (a >= N) {
+                oa = a;
+                ob = b;
+            } else {
+                if (update && a >= N) {
                     if (lane == 0) set_status(prm.status, RCG_DEV_BADJOB);
                     continue;
                 }
+                oa = a;
+                ob = N;  // P and Q are strips N and N+1
             }
-            if (cls == E_ENC) b = N;  // P and Q are strips N and N+1
+            if (cls == E_ENC) ob = N;
 
             uint32_t zinv = 0;
-            if (cls == E_DDC) {  // (b - a)^(p-2) mod p, the inverse in Z/p
+            if (cls == E_DDC || cls == E_DPXC) {  // z^(p-2) mod p, the inverse in Z/p
+                const uint32_t zz = z % p;
                 zinv = 1;
-                for (uint32_t e = 0; e + 2 < p; ++e) zinv = zinv * (b - a) % p;
+                for (uint32_t e = 0; e + 2 < p; ++e) zinv = zinv * zz % p;
             }
 
             // strips streamed per tile: N for every class (the other N survivors,
             // or the N inputs of a rebuild), 4 for the small write
             const uint32_t count = update ? 4u : N;
-            uint32_t rot;
+            uint32_t rot, rot2;
 
             uint8_t *const stripe_base = base + stripe * stripe_stride + c0;
             const uint8_t *aux_base = aux + stripe * aux_ss + c0;
@@ -421,7 +534,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
             const uint32_t tx_tensor = rows * W, tx_rows = rows * w;
             uint32_t emitted = 0;
             for (uint32_t k = 0; k < N + 3; ++k) {
-                const uint8_t fl = strip_role(cls, update, k, N, a, b, p, &rot);
+                const uint32_t fl = strip_role(cls, update, k, N, a, b, p, s, pone, &rot, &rot2);
                 if (!fl) continue;
                 // a free descriptor (its previous stage released) ...
                 if (!mbar_wait(smem_addr(&sm.empty[pos.slot]), pos.phase ^ 1u, timeout)) {
@@ -472,19 +585,20 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                     SlotHdr &h = sm.hdr[pos.slot];
                     const uint32_t first = emitted == 0;
                     const uint32_t fl2 = fl | (first ? F_FIRST : 0) | (emitted + 1 == count ? F_LAST : 0);
-                    const uint4 hot = make_uint4(fl2 | (rot << 8) | (w << 16), start, 0u, 0u);
+                    const uint4 hot = make_uint4(fl2 | (rot << 8) | (w << 16), start, rot2, 0u);
                     *reinterpret_cast<uint4 *>(&h) = hot;
                     if (first) {
                         h.cls = cls;
                         h.p = static_cast<uint8_t>(p);
-                        h.a = static_cast<uint8_t>(a);
-                        h.b = static_cast<uint8_t>(b);
+                        h.a = static_cast<uint8_t>(oa);
+                        h.b = static_cast<uint8_t>(ob);
                         h.pitch = static_cast<uint16_t>(W);
                         h.zinv = static_cast<uint8_t>(zinv);
+                        h.z = static_cast<uint8_t>(z);
                         h.base = reinterpret_cast<uint64_t>(stripe_base);
                         h.strip_stride = strip_stride;
                         h.row_stride = row_stride;
-                        h.out = reinterpret_cast<uint64_t>(aux_base);
+                        h.out = (cls == E_DD || cls == E_DPX) ? mask : reinterpret_cast<uint64_t>(aux_base);
                         h.out_row_stride = aux_rs;
                     }
                     mbar_arrive_tx(full, tensor ? tx_tensor : tx_rows);
@@ -539,10 +653,10 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
 
 struct Tile {
     uint8_t *base;      // stripe base + c0
-    uint8_t *out;       // degraded read output + c0 (stripe applied)
+    uint8_t *out;       // degraded read output + c0 (stripe applied); table solves: the mask
     uint64_t strip_stride, row_stride, out_row_stride;
     uint32_t p, nvec, w;
-    uint8_t cls, a, b, zinv;
+    uint8_t cls, a, b, zinv, z;
 };
 
 // Epilogue barrier among the consumer warps (bounded).
@@ -617,19 +731,22 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[S::k
             }
             break;
         }
-        case E_DQ: {  // D_a = accP; Q = fold(accQ + x^a D_a)
+        case E_DQ:      // D_a = accP; Q = fold(accQ + x^z D_a), z = a
+        case E_DQX: {   // extended a: Q = fold(accQ + (1 + x^z) D_a), z = a - p + 1
             const uint4 zero = make_uint4(0, 0, 0, 0);
             #pragma unroll
             for (int t = 0; t < S::kItems; ++t)
                 if (row[t] < p) sts(X(sm.xb, row[t], col[t]), row[t] < p - 1 ? accP[t] : zero);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
-            const int a = T.a;
+            const int z = T.z;
+            const bool ext = T.cls == E_DQX;
             #pragma unroll
             for (int t = 0; t < S::kItems; ++t) {
                 if (row[t] >= p) continue;
-                int s = row[t] - a;
+                int s = row[t] - z;
                 if (s < 0) s += p;
                 accQ[t] = xor4(accQ[t], lds(X(sm.xb, s, col[t])));
+                if (ext && row[t] < p - 1) accQ[t] = xor4(accQ[t], accP[t]);
                 if (row[t] == p - 1) sts(fold + col[t] * 16, accQ[t]);
             }
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
@@ -641,18 +758,23 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[S::k
             }
             break;
         }
-        case E_DDC: {
-            // (1 + x^z) D = T in R, z = b - a.  Lifted to F2[x]/(x^p - 1) the
+        case E_DDC:
+        case E_DPXC: {
+            // (1 + x^z) D = T in R, T = accP + accQ (two data strips) or accQ
+            // (extended data strip + P).  Lifted to F2[x]/(x^p - 1) the
             // solution with D[p-1] = 0 satisfies D[r] + D[r-z] = T[r] + c, where
             // c (the XOR of all p rows of T) makes T + c*f vanish at x = 1.
             // One thread per column walks r_t = p-1 + t z (t = 1..p-1), turning
             // T into its prefix XOR E_t in place; then D[r_t] = E_t + (t odd) c.
+            // D goes to strip b, D + accP to strip a.
             const uint4 zero = make_uint4(0, 0, 0, 0);
+            const bool tp = T.cls == E_DDC;
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t)
-                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), row[t] < p - 1 ? xor4(accP[t], accQ[t]) : accQ[t]);
+                if (row[t] < p)
+                    sts(X(sm.xb, row[t], col[t]), (tp && row[t] < p - 1) ? xor4(accP[t], accQ[t]) : accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
-            const int z = T.b - T.a;
+            const int z = T.z;
             if (ctid < static_cast<int>(nv)) {
                 uint4 e = zero;
                 int r = p - 1;
@@ -679,16 +801,22 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[S::k
             }
             break;
         }
-        case E_DD: {
-            // accQ = x^(-a) dQ (lifted), so T = dP + x^(-a) dQ is formed in place
-            // (row p-1 of dP is zero); D_b = (1 + x^z)^(-1) T needs every row of T.
+        case E_DD:
+        case E_DPX: {
+            // accQ = x^(-s) dQ (lifted), so T = dP + x^(-s) dQ is formed in place
+            // (row p-1 of dP is zero), or T = accQ (extended data strip + P);
+            // D_b = c^(-1) T needs every row of T.  The exponent mask of c^(-1)
+            // -- (1 + x^z)^(-1) of Section 4.6, or a trinomial's inverse --
+            // comes in the tile header.
             const uint4 zero = make_uint4(0, 0, 0, 0);
+            const bool tp = T.cls == E_DD;
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t)
-                if (row[t] < p) sts(X(sm.xb, row[t], col[t]), row[t] < p - 1 ? xor4(accP[t], accQ[t]) : accQ[t]);
+                if (row[t] < p)
+                    sts(X(sm.xb, row[t], col[t]), (tp && row[t] < p - 1) ? xor4(accP[t], accQ[t]) : accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
-            // D_b (lifted) = sum over the table's exponent set of x^m T
-            const uint64_t mask = c_inv[p][T.b - T.a];
+            // D_b (lifted) = sum over the mask's exponent set of x^m T
+            const uint64_t mask = reinterpret_cast<uint64_t>(T.out) & ((1ull << p) - 1);  // exponents < p
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t) {
                 if (row[t] >= p) continue;
@@ -761,6 +889,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
             p = static_cast<int>(T.p);
             pitch = tv.y & 0xffffu;
             T.zinv = static_cast<uint8_t>(tv.y >> 16);
+            T.z = static_cast<uint8_t>(tv.y >> 24);
             pw = p * pitch;
             for (int t = 0; t < S::kItems; ++t) {
                 const int item = ctid + t * S::kConsumers;
@@ -777,7 +906,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
         // row whose source is the imaginary row p-1 is vrow = (p-1+rot) mod p
         const uint32_t qbase = stage - rot * pitch;  // + p*pitch for rows r < rot
         const int vrow = rot == 0 ? p - 1 : rot - 1;
-        if ((flags & (F_P | F_Q | F_COPY)) == (F_P | F_Q)) {
+        if ((flags & (F_P | F_Q | F_Q2 | F_COPY)) == (F_P | F_Q)) {
             // a data strip feeding both accumulators: the common case
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t) {
@@ -785,8 +914,23 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
                 if (r < p - 1) accP[t] = xor4(accP[t], lds_a(stage + off[t]));
                 if (r < p && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
             }
+        } else if ((flags & (F_P | F_Q | F_Q2 | F_COPY)) == (F_P | F_Q | F_Q2) && hv.z == 0) {
+            // an extended data strip (weight 1 + x^rot) feeding both accumulators
+#pragma unroll
+            for (int t = 0; t < S::kItems; ++t) {
+                const int r = row[t];
+                if (r < p - 1) {
+                    const uint4 v = lds_a(stage + off[t]);
+                    accP[t] = xor4(accP[t], v);
+                    accQ[t] = xor4(accQ[t], v);
+                }
+                if (r < p && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
+            }
         } else {
-            const bool fp = flags & F_P, fq = flags & F_Q, fc = flags & F_COPY;
+            const bool fp = flags & F_P, fq = flags & F_Q, fq2 = flags & F_Q2, fc = flags & F_COPY;
+            const int rot2 = static_cast<int>(hv.z);
+            const uint32_t qbase2 = stage - rot2 * pitch;
+            const int vrow2 = rot2 == 0 ? p - 1 : rot2 - 1;
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t) {
                 const int r = row[t];
@@ -797,6 +941,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
                     if (fc) stg(copy_dst + static_cast<uint64_t>(r) * T.row_stride + (off[t] - r * pitch), v);
                 }
                 if (fq && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
+                if (fq2 && r != vrow2) accQ[t] = xor4(accQ[t], lds_a(qbase2 + off[t] + (r < rot2 ? pw : 0u)));
             }
         }
         __syncwarp();
@@ -917,12 +1062,29 @@ static bool is_odd_prime(uint32_t p) {
 }
 
 cudaError_t upload_inverse_tables() {
+    // built once per process, uploaded to every device that asks
     static uint64_t table[kMaxP + 1][kMaxP + 1];
-    for (uint32_t p = 0; p <= static_cast<uint32_t>(kMaxP); ++p) {
-        for (uint32_t z = 0; z <= static_cast<uint32_t>(kMaxP); ++z) table[p][z] = 0;
-        if (is_odd_prime(p)) inverse_masks(p, table[p]);
-    }
-    return cudaMemcpyToSymbol(c_inv, table, sizeof(table));
+    static uint64_t tri[kTriEntries];
+    static uint32_t tri_off[kMaxP + 1];
+    static std::once_flag built;
+    std::call_once(built, [] {
+        uint32_t n = 0;
+        for (uint32_t p = 0; p <= static_cast<uint32_t>(kMaxP); ++p) {
+            for (uint32_t z = 0; z <= static_cast<uint32_t>(kMaxP); ++z) table[p][z] = 0;
+            tri_off[p] = ~0u;
+            if (!is_odd_prime(p)) continue;
+            inverse_masks(p, table[p]);
+            if (cone_extends(p)) {
+                tri_off[p] = n;
+                trinomial_inverses(p, tri + n);
+            }
+            n += p * p;
+        }
+    });
+    cudaError_t e = cudaMemcpyToSymbol(c_inv, table, sizeof(table));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tri_off, tri_off, sizeof(tri_off));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tri, tri, sizeof(tri));
+    return e;
 }
 
 cudaError_t engine_init_attributes() {

@@ -4,6 +4,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/rcg.h"
@@ -114,6 +115,18 @@ struct alignas(128) WorkItem {
     uint8_t pad[20];
 };
 static_assert(sizeof(WorkItem) == 128, "work items are 128 bytes");
+// the producer reads a work item as 32 words spread over a warp
+static_assert(offsetof(WorkItem, aux) == 8 && offsetof(WorkItem, pairs) == 16 &&
+                  offsetof(WorkItem, strip_stride) == 24 && offsetof(WorkItem, row_stride) == 32 &&
+                  offsetof(WorkItem, stripe_stride) == 40 && offsetof(WorkItem, aux_row_stride) == 48 &&
+                  offsetof(WorkItem, aux_stripe_stride) == 56 && offsetof(WorkItem, tile0) == 64 &&
+                  offsetof(WorkItem, ntiles) == 68 && offsetof(WorkItem, tiles_per_stripe) == 72 &&
+                  offsetof(WorkItem, W) == 76 && offsetof(WorkItem, C) == 80 &&
+                  offsetof(WorkItem, n_stripes) == 84 && offsetof(WorkItem, job) == 88 &&
+                  offsetof(WorkItem, p) == 92 && offsetof(WorkItem, n) == 93 && offsetof(WorkItem, op) == 94 &&
+                  offsetof(WorkItem, i) == 95 && offsetof(WorkItem, j) == 96 && offsetof(WorkItem, use_tmap) == 97 &&
+                  offsetof(WorkItem, dd_solve) == 98,
+              "WorkItem word layout");
 
 struct alignas(128) BatchHeader {
     uint64_t total_tiles;
@@ -150,6 +163,16 @@ cudaError_t launch_fill(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte
 cudaError_t launch_wait_probe(uint32_t *status, uint64_t timeout_ns, cudaStream_t stream);
 
 void inverse_masks(uint32_t p, uint64_t *masks);
+
+// Host ring arithmetic in R = F2[x]/(1 + ... + x^(p-1)) (rcg_ring.cu).
+uint64_t ring_reduce(uint32_t p, uint64_t a);
+uint32_t order_of_two(uint32_t p);
+uint64_t ring_inverse(uint32_t p, uint64_t u);       // 0 when u is not a unit
+void trinomial_inverses(uint32_t p, uint64_t *masks);  // [u * p + v] = (1 + x^u + x^v)^(-1)
+bool cone_extends(uint32_t p);                        // Theorem 3.3.3 holds for p
+// Largest number of data strips for p: 2p - 1 where the extended Q-parity of
+// Section 3.3 applies (Theorem 3.3.3), else p (Corollary 3.2.4).
+inline uint32_t max_data_strips(uint32_t p) { return cone_extends(p) ? 2 * p - 1 : p; }
 
 // Host: the CUDA device of a context.
 int ctx_device(const rcg_ctx *ctx);

@@ -65,6 +65,10 @@ class rcg_plan_info(ctypes.Structure):
                 ("max_items", _u32), ("smem_bytes", _u32), ("ctas_per_sm", _u32), ("shape", _u32)]
 
 
+class rcg_prime_info_t(ctypes.Structure):
+    _fields_ = [("ord2", _u32), ("is_field", _u32), ("extends", _u32), ("max_data", _u32)]
+
+
 EXPORTS = {
     "rcg_create": (_int, [_int, ctypes.POINTER(_vp)]),
     "rcg_destroy": (_int, [_vp]),
@@ -101,6 +105,8 @@ EXPORTS = {
     "rcg_selftest_wait_timeout": (_int, [_vp, _u64, _vp]),
     "rcg_inverse_table": (_int, [_u32, ctypes.POINTER(_u64)]),
     "rcg_plan": (_int, [_u32, _u64, ctypes.POINTER(rcg_plan_info)]),
+    "rcg_prime_info": (_int, [_u32, ctypes.POINTER(rcg_prime_info_t)]),
+    "rcg_ring_inverse": (_int, [_u32, _u64, ctypes.POINTER(_u64)]),
 }
 
 _lib: ctypes.CDLL | None = None
@@ -360,6 +366,20 @@ def rcg_inverse_table(p: int) -> list[int]:
     masks = (_u64 * p)()
     _check(lib().rcg_inverse_table(p, masks), "rcg_inverse_table")
     return [int(m) for m in masks]
+
+
+def rcg_prime_info(p: int) -> dict:
+    """ord2 (Lemma 3.3.1), is_field, extends (Theorem 3.3.3) and max_data for p."""
+    info = rcg_prime_info_t()
+    _check(lib().rcg_prime_info(p, ctypes.byref(info)), "rcg_prime_info")
+    return {f: int(getattr(info, f)) for f, _ in rcg_prime_info_t._fields_}
+
+
+def rcg_ring_inverse(p: int, a: int) -> int:
+    """Inverse of a (bit m = coefficient of x^m) in F2[x]/(1 + ... + x^(p-1))."""
+    inv = _u64()
+    _check(lib().rcg_ring_inverse(p, a, ctypes.byref(inv)), "rcg_ring_inverse")
+    return int(inv.value)
 
 
 def rcg_plan(p: int, row_bytes: int) -> dict:

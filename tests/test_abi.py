@@ -105,3 +105,55 @@ def test_create_without_a_gpu_is_an_error_not_a_crash(rcg):
     st = rcg.lib().rcg_create(0, ctypes.byref(h))
     assert st in (rcg.RCG_EUNSUPPORTED, rcg.RCG_ECUDA)
     assert not h.value
+
+
+# ------------------------------------------- extended Q-parity (Section 3.3)
+
+# Section 3.3: primes below 100 for which 2 is a primitive root modulo p (so R
+# is a field), as the paper lists them; those up to the library's 61.
+PAPER_FIELD_PRIMES = [3, 5, 11, 13, 19, 29, 37, 53, 59, 61]
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_prime_info_matches_oracle_and_paper(rcg, oracle, p):
+    info = rcg.rcg_prime_info(p)
+    assert info["ord2"] == oracle.ord2(p)
+    assert info["is_field"] == (p in PAPER_FIELD_PRIMES)
+    # Corollary 3.3.4 and the remark after it: below 500 only Mersenne primes
+    # and 73 fail Theorem 3.3.3; of the library's primes that is 3, 7 and 31.
+    assert info["extends"] == (p not in (3, 7, 31))
+    assert info["extends"] == oracle.cone_extends(p)
+    assert info["max_data"] == (2 * p - 1 if info["extends"] else p)
+
+
+def test_prime_info_rejects_non_primes(rcg):
+    for p in (1, 2, 9, 15, 63, 67):
+        with pytest.raises(rcg.RcgError):
+            rcg.rcg_prime_info(p)
+
+
+@pytest.mark.parametrize("p", [5, 7, 13, 17, 29, 31, 59, 61])
+def test_ring_inverse_matches_oracle(rcg, oracle, p):
+    # The library inverts by Frobenius exponentiation (a^(2^d - 2)), the
+    # oracle by the extended Euclidean algorithm.
+    import numpy as np
+    rng = np.random.default_rng(p)
+    elems = [int(rng.integers(1, 1 << (p - 1))) for _ in range(40)]
+    # the trinomials the extension needs, and the binomials of Section 4.6
+    elems += [1 ^ (1 << 1) ^ (1 << (p - 2)), 1 ^ (1 << (p - 2)), 1 << (p - 2), 1]
+    for a in elems:
+        want = oracle.ring_inv(p, a)
+        if want == 0:
+            with pytest.raises(rcg.RcgError):
+                rcg.rcg_ring_inverse(p, a)
+        else:
+            assert rcg.rcg_ring_inverse(p, a) == want, (p, a)
+
+
+def test_ring_inverse_rejects_non_units(rcg):
+    with pytest.raises(rcg.RcgError):
+        rcg.rcg_ring_inverse(5, 0)
+    with pytest.raises(rcg.RcgError):
+        rcg.rcg_ring_inverse(5, 1 << 4)  # not a residue mod f (bit p-1)
+    # 1 + x + x^2 + x^3 = x^4 modulo f (p = 5), whose inverse is x
+    assert rcg.rcg_ring_inverse(5, 0b1111) == 0b0010

@@ -189,7 +189,7 @@ def test_host_validation(rcg, ctx):
     with pytest.raises(rcg.RcgError):
         ctx.encode(rcg.make_layout(buf, 9, 4, 16), 0, 1)  # 9 is not prime
     with pytest.raises(rcg.RcgError):
-        ctx.encode(rcg.make_layout(buf, 5, 6, 16), 0, 1)  # N > p
+        ctx.encode(rcg.make_layout(buf, 7, 8, 16), 0, 1)  # N > p, and 7 fails Theorem 3.3.3
     with pytest.raises(rcg.RcgError):
         ctx.encode(rcg.make_layout(buf, 5, 4, 24), 0, 1)  # C not a multiple of 16
     with pytest.raises(rcg.RcgError):
