@@ -199,10 +199,11 @@ rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe,
  * allocated on first use) on three internal streams, so the upload of one
  * chunk, the engine on another and the download of a third overlap.
  *   encode:   uploads the data strips, downloads P and Q;
- *   recovery: uploads whole stripes (the erased strips' bytes are never
- *             read), and writes only the two rebuilt strips of each stripe
- *             back into the host stripes, in place, through their mapped
- *             device addresses.  pairs is a HOST array of 2*n_stripes bytes.
+ *   recovery: uploads only the N surviving strips of each stripe (a gather
+ *             kernel reads them through the stripes' mapped device
+ *             addresses; the erased strips never cross the link), and writes
+ *             only the two rebuilt strips of each stripe back into the host
+ *             stripes, in place.  pairs is a HOST array of 2*n_stripes bytes.
  * Results are identical to the device calls.  The calls are ordered on
  * `stream`: the work starts after what is already queued there, and work
  * queued there afterwards sees the results. */

@@ -4,10 +4,14 @@
 // one chunk, the tile engine on another and the download of a third overlap.
 //
 //   encode:   data strips in  -> rcg_encode on the chunk -> P and Q strips out
-//   recovery: whole stripes in (the erased strips' bytes are never read) ->
+//   recovery: the N surviving strips of each stripe in (a gather kernel reads
+//             them from the host stripes through their device-visible
+//             (mapped) addresses; the erased strips are never moved) ->
 //             rcg_recover_many on the chunk -> a small kernel writes the two
-//             rebuilt strips of each stripe straight back into the host
-//             stripes through their device-visible (mapped) addresses.
+//             rebuilt strips of each stripe straight back into the host stripes.
+// The host link, not HBM, bounds this path (about 211 GB/s host to device on
+// GB300, the same for copy engines and for kernel loads), so what counts is
+// the bytes that cross it: N strips in and 2 out per stripe.
 //
 // The caller's stream orders the call: the internal streams wait for it on
 // entry and it waits for them on exit.
@@ -23,28 +27,82 @@
 namespace {
 
 // Copy the rebuilt strips (i, j) of each stripe of a device chunk back to the
-// host stripes.  One 16-byte vector per thread-iteration; pairs that are not
-// a valid erasure pair (the engine skipped those stripes) are skipped here too.
+// host stripes (mapped device addresses).  Same shape as the gather below: a
+// CTA takes whole units (stripe, one of its two strips), so a few CTAs keep
+// the link busy and leave the SMs to the gather and the tile engine of the
+// neighbouring chunks.  Pairs that are not a valid erasure pair (the engine
+// skipped those stripes) are skipped here too.
 __global__ void writeback_kernel(const uint8_t *chunk, uint64_t chunk_stripe_bytes, uint64_t strip_bytes,
                                  uint8_t *host_dev, uint64_t h_row, uint64_t h_strip, uint64_t h_stripe,
                                  const uint8_t *pairs, uint32_t n_stripes, uint32_t rows, uint32_t nvec,
                                  uint32_t n_total) {
-    const uint64_t per_stripe = 2ull * rows * nvec;
-    const uint64_t total = per_stripe * n_stripes;
-    for (uint64_t q = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; q < total;
-         q += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        const uint32_t s = static_cast<uint32_t>(q / per_stripe);
-        uint64_t rem = q - s * per_stripe;
-        const uint32_t which = static_cast<uint32_t>(rem / (static_cast<uint64_t>(rows) * nvec));
-        rem -= which * static_cast<uint64_t>(rows) * nvec;
-        const uint32_t r = static_cast<uint32_t>(rem / nvec);
-        const uint32_t v = static_cast<uint32_t>(rem - static_cast<uint64_t>(r) * nvec);
+    const uint64_t units = 2ull * n_stripes;
+    const uint32_t row_bytes = nvec * 16;
+    for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const uint32_t s = static_cast<uint32_t>(u >> 1);
         const uint32_t a = pairs[2ull * s], b = pairs[2ull * s + 1];
         if (!(a < b && b <= n_total + 1)) continue;
-        const uint32_t k = which ? b : a;
-        const uint4 val = *reinterpret_cast<const uint4 *>(chunk + s * chunk_stripe_bytes + k * strip_bytes +
-                                                           static_cast<uint64_t>(r) * nvec * 16 + v * 16ull);
-        *reinterpret_cast<uint4 *>(host_dev + s * h_stripe + k * h_strip + r * h_row + v * 16ull) = val;
+        const uint32_t k = (u & 1) ? b : a;
+        const uint8_t *src = chunk + s * chunk_stripe_bytes + k * strip_bytes;
+        uint8_t *dst = host_dev + s * h_stripe + k * h_strip;
+        if (h_row == row_bytes) {  // one contiguous run
+            const uint4 *sv = reinterpret_cast<const uint4 *>(src);
+            uint4 *dv = reinterpret_cast<uint4 *>(dst);
+            const uint32_t n = rows * nvec;
+            for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) dv[t] = sv[t];
+        } else {
+            for (uint32_t r = 0; r < rows; ++r)
+                for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x)
+                    reinterpret_cast<uint4 *>(dst + r * h_row)[v] =
+                        reinterpret_cast<const uint4 *>(src + static_cast<uint64_t>(r) * row_bytes)[v];
+        }
+    }
+}
+
+// Copy the surviving strips (all but the pair's two) of each stripe from the
+// host stripes (mapped device addresses) into the packed chunk.  Reads over
+// the host link have a long latency under load: keeping the link busy takes
+// several MB of loads in flight, from every SM.  A CTA takes whole units
+// (stripe, surviving strip); a strip whose rows are packed is one contiguous
+// run, copied with GATHER_UNROLL independent 16-byte loads in flight per
+// thread.  Stripes whose pair is invalid move nothing (the engine skips them
+// and records the error).
+constexpr int GATHER_UNROLL = 8;
+
+__global__ void gather_kernel(const uint8_t *host_dev, uint64_t h_row, uint64_t h_strip, uint64_t h_stripe,
+                              uint8_t *chunk, uint64_t chunk_stripe_bytes, uint64_t strip_bytes,
+                              const uint8_t *pairs, uint32_t n_stripes, uint32_t rows, uint32_t nvec,
+                              uint32_t n_total) {
+    const uint64_t units = static_cast<uint64_t>(n_stripes) * n_total;
+    const uint32_t row_bytes = nvec * 16;
+    for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const uint32_t s = static_cast<uint32_t>(u / n_total);
+        uint32_t k = static_cast<uint32_t>(u - static_cast<uint64_t>(s) * n_total);
+        const uint32_t a = pairs[2ull * s], b = pairs[2ull * s + 1];
+        if (!(a < b && b <= n_total + 1)) continue;
+        if (k >= a) ++k;  // the k-th surviving strip
+        if (k >= b) ++k;
+        const uint8_t *src = host_dev + s * h_stripe + k * h_strip;
+        uint8_t *dst = chunk + s * chunk_stripe_bytes + k * strip_bytes;
+        if (h_row == row_bytes) {  // one contiguous run of rows * nvec vectors
+            const uint4 *sv = reinterpret_cast<const uint4 *>(src);
+            uint4 *dv = reinterpret_cast<uint4 *>(dst);
+            const uint32_t n = rows * nvec, step = blockDim.x;
+            uint32_t t = threadIdx.x;
+            for (; t + (GATHER_UNROLL - 1) * step < n; t += GATHER_UNROLL * step) {
+                uint4 v[GATHER_UNROLL];
+#pragma unroll
+                for (int q = 0; q < GATHER_UNROLL; ++q) v[q] = sv[t + q * step];
+#pragma unroll
+                for (int q = 0; q < GATHER_UNROLL; ++q) dv[t + q * step] = v[q];
+            }
+            for (; t < n; t += step) dv[t] = sv[t];
+        } else {
+            for (uint32_t r = 0; r < rows; ++r)
+                for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x)
+                    reinterpret_cast<uint4 *>(dst + static_cast<uint64_t>(r) * row_bytes)[v] =
+                        reinterpret_cast<const uint4 *>(src + r * h_row)[v];
+        }
     }
 }
 
@@ -62,7 +120,8 @@ bool host_geo(const rcg_layout *L, HostGeo *g) {
     g->p = L->p;
     g->N = L->n_data;
     g->C = L->row_bytes;
-    if (g->p < 3 || g->p > 61 || g->N < 1 || g->N > g->p || g->C == 0 || (g->C & 15)) return false;
+    if (g->p < 3 || g->p > 61 || g->N < 1 || g->N > rcg::max_data_strips(g->p) || g->C == 0 || (g->C & 15))
+        return false;
     g->rs = L->row_stride ? L->row_stride : g->C;
     g->ss = L->strip_stride ? L->strip_stride : (g->p - 1) * g->rs;
     g->st = L->stripe_stride ? L->stripe_stride : (g->N + 2) * g->ss;
@@ -109,6 +168,12 @@ cudaError_t copy_strips(bool to_device, uint8_t *chunk, const HostGeo &g, uint8_
 }  // namespace
 
 namespace rcg {
+
+// CTAs of the gather kernel (512 threads each): the host link needs loads in
+// flight from every SM.  The write-back's stores are posted, so a few CTAs
+// keep its direction busy and leave the SMs to the gather and the engine.
+constexpr unsigned kGatherCtas = 152;
+constexpr unsigned kWritebackCtas = 32;
 
 // Context-owned staging for the host path (see rcg_api.cu for the owner).
 struct HostStaging {
@@ -182,6 +247,8 @@ rcg_status host_path(HostStaging *h, const rcg_layout *L, uint64_t first, uint64
     }
     uint8_t *host = static_cast<uint8_t *>(L->base);
     uint8_t *host_dev = static_cast<uint8_t *>(attr.devicePointer);
+    // the gather and write-back kernels index a strip's vectors with 32 bits
+    if (g.strip_bytes / 16 > 0xffffffffull) return RCG_EINVAL;
     const uint64_t per_chunk = std::max<uint64_t>(1, chunk_bytes / g.stripe_bytes);
     cudaError_t e = staging_ready(h, per_chunk * g.stripe_bytes, 2 * per_chunk);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? RCG_ENOMEM : RCG_ECUDA;
@@ -205,16 +272,18 @@ rcg_status host_path(HostStaging *h, const rcg_layout *L, uint64_t first, uint64
             e = copy_strips(true, h->buf[k], g, hfirst, 0, g.N, n, s);
             if (e == cudaSuccess) st = run(run_arg, &dl, n, nullptr, s);
             if (e == cudaSuccess && st == RCG_OK) e = copy_strips(false, h->buf[k], g, hfirst, g.N, g.N + 2, n, s);
-        } else {            // recovery: stripes in, the two rebuilt strips written back
-            e = copy_strips(true, h->buf[k], g, hfirst, 0, g.N + 2, n, s);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(h->pairs[k], pairs_host + 2 * s0, 2 * n, cudaMemcpyHostToDevice, s);
+        } else {            // recovery: surviving strips in, the two rebuilt strips written back
+            const uint32_t rows = g.p - 1, nvec = static_cast<uint32_t>(g.C / 16);
+            e = cudaMemcpyAsync(h->pairs[k], pairs_host + 2 * s0, 2 * n, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) {
+                gather_kernel<<<kGatherCtas, 512, 0, s>>>(host_dev + (first + s0) * g.st, g.rs, g.ss, g.st,
+                                                         h->buf[k], g.stripe_bytes, g.strip_bytes, h->pairs[k],
+                                                         static_cast<uint32_t>(n), rows, nvec, g.N);
+                e = cudaGetLastError();
+            }
             if (e == cudaSuccess) st = run(run_arg, &dl, n, h->pairs[k], s);
             if (e == cudaSuccess && st == RCG_OK) {
-                const uint32_t rows = g.p - 1, nvec = static_cast<uint32_t>(g.C / 16);
-                const uint64_t work = 2ull * rows * nvec * n;
-                const unsigned blocks = static_cast<unsigned>(std::min<uint64_t>((work + 255) / 256, 152ull * 8));
-                writeback_kernel<<<blocks, 256, 0, s>>>(h->buf[k], g.stripe_bytes, g.strip_bytes,
+                writeback_kernel<<<kWritebackCtas, 512, 0, s>>>(h->buf[k], g.stripe_bytes, g.strip_bytes,
                                                         host_dev + (first + s0) * g.st, g.rs, g.ss, g.st,
                                                         h->pairs[k], static_cast<uint32_t>(n), rows, nvec, g.N);
                 e = cudaGetLastError();
