@@ -48,10 +48,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--stripes", type=int, default=S,
-                    help="stripes per GPU (default 8192; smaller values are profiling cases, not bench lines)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "serve"],
-                    help="c2: the bench line; batched: the uneven 50k-stripe batch vs per-stripe launches; "
+    ap.add_argument("--stripes", type=int, default=None,
+                    help="stripes per GPU (default: the workload's own, 8192 for c2; other values are "
+                         "profiling cases, not bench lines)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "qext", "batched", "serve"],
+                    help="c2: the bench line; c1 / c3: the p=5 and p=59 plain configurations; "
+                         "qext: extended Q-parity, p=59 with 117 data strips; "
+                         "batched: the uneven 50k-stripe batch vs per-stripe launches; "
                          "serve: Poisson request stream, continuous batching vs per-job launches")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--pool-gb", type=float, default=40.0)
@@ -173,7 +176,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     ctx = rcg.Context(local)
-    S = args.stripes
+    S = args.stripes or globals()["S"]
     sb = inputs.stripe_bytes(P, N, C)
     buf = torch.empty((S, N + 2, P - 1, C), dtype=torch.uint8, device=dev)
     rcg.rcg_fill_random(buf, S * sb, SEED + 100 * rank)
@@ -315,10 +318,20 @@ def e2e_ours(ctx, rcg, torch, dev, stream, pairs, args, world, S):
     pairs_host = {k: pairs[k].cpu().numpy() for k in CLASSES}
     strip = (P - 1) * C
 
-    def step():
+    marks = []
+
+    def step(record=False):
+        def mark():
+            if record:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                marks.append(e)
+        mark()
         ctx.encode_host(HL, 0, S, stream)
+        mark()
         for k in CLASSES:
             ctx.recover_many_host(HL, 0, S, pairs_host[k], stream)
+        mark()
 
     for _ in range(2):
         step()
@@ -328,20 +341,53 @@ def e2e_ours(ctx, rcg, torch, dev, stream, pairs, args, world, S):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(steps):
-        step()
+        step(record=True)
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
+    enc_each = [marks[3 * i].elapsed_time(marks[3 * i + 1]) for i in range(steps)]
+    rec_each = [marks[3 * i + 1].elapsed_time(marks[3 * i + 2]) / len(CLASSES) for i in range(steps)]
+    enc_ms, rec_ms = statistics.median(enc_each), statistics.median(rec_each)
     if ctx.last_device_status() != 0:
         raise RuntimeError("device status word set in the end-to-end run")
     value = 5 * user_bytes_per_op(S) * steps * world / (ms * 1e-3) / 1e9
+    link = pinned_link_gbs(torch, dev, stream)
     del host
-    # encode: N strips in, P and Q out; recovery: the stripe and its pair in, two strips out
-    h2d = S * N * strip + len(CLASSES) * S * ((N + 2) * strip + 2)
+    # encode: N strips in, P and Q out; recovery: the N surviving strips and the pair in,
+    # the two rebuilt strips out
+    h2d = S * N * strip + len(CLASSES) * S * (N * strip + 2)
     d2h = S * 2 * strip * (1 + len(CLASSES))
     return {"value": round(value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h,
-            "api": "rcg_encode_host + rcg_recover_many_host (pinned host stripes)"}
+            "api": "rcg_encode_host + rcg_recover_many_host (pinned host stripes)",
+            "link_gbs": link,
+            "per_op_ms": {"encode_host": round(enc_ms, 3), "recover_many_host": round(rec_ms, 3),
+                          "encode_host_each": [round(x, 2) for x in enc_each],
+                          "recover_many_host_each": [round(x, 2) for x in rec_each]},
+            # the copies of one direction cannot beat the link: an upper bound
+            "ceiling_gbs": round(5 * user_bytes_per_op(S) / max(h2d / link["h2d"], d2h / link["d2h"]) * world, 1)
+            if link["h2d"] and link["d2h"] else None}
+
+
+def pinned_link_gbs(torch, dev, stream, nbytes=1 << 30):
+    """Plain pinned host<->device copy speed on this machine (one 1 GiB copy each
+    way, best of 3): the ceiling of the end-to-end number."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, fn in (("h2d", lambda: d.copy_(h, non_blocking=True)), ("d2h", lambda: h.copy_(d, non_blocking=True))):
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        out[name] = round(nbytes / (best * 1e-3) / 1e9, 1)
+    del h, d
+    return out
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -399,6 +445,137 @@ def run_reference(args):
                              "sample": "%d stripes per step of the 8192, full 5-op step" % stripes},
             "e2e": {"value": round(value, 6), "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+
+
+# ------------------------------------------------------ other geometries
+
+GEOMETRIES = {
+    # name: (p, N, C, stripes, seed, description)
+    "c1": (5, 4, 1024, 1024, 0, "p=5, N=4 data strips + P + Q, 4 rows x 1 KiB per strip, 1024 stripes; "
+                                "encode, then each of the 15 erasure pairs over all stripes, one launch per op"),
+    "c3": (59, 58, 2048, 1024, 2, "p=59, N=58 data strips + P + Q, 58 rows x 2 KiB per strip, 1024 stripes; "
+                                  "two-data recovery with a uniformly drawn pair per stripe, one launch per op"),
+    "qext": (59, 117, 2048, 512, 6, "extended Q-parity (Section 3.3, equation qext): p=59, N=117 data strips "
+                                    "+ P + Q, 58 rows x 2 KiB per strip, 512 stripes; encode and each recovery "
+                                    "class, one launch per op"),
+}
+
+
+def geometry_ops(name, N, S, dev, torch):
+    """(op name, per-stripe pair tensor or None for encode) of one step."""
+    import numpy as np
+
+    from paper_cs_0611109_gb300 import inputs
+    P_ = GEOMETRIES[name][0]
+    if name == "c1":
+        return [("encode", None)] + [("pair_%d_%d" % (i, j), torch.from_numpy(
+            np.tile(np.array([[i, j]], dtype=np.uint8), (S, 1))).to(dev))
+            for i in range(N + 2) for j in range(i + 1, N + 2)]
+    if name == "c3":
+        return [("dd", torch.from_numpy(inputs.random_pairs(22, N, S, "dd")).to(dev))]
+    # qext: encode, and one launch per recovery class; pairs drawn uniformly within the class
+    rng = np.random.Generator(np.random.PCG64(61))
+
+    def draw(lo_i, hi_i, lo_j, hi_j):
+        out = np.empty((S, 2), dtype=np.uint8)
+        for s in range(S):
+            while True:
+                i, j = int(rng.integers(lo_i, hi_i)), int(rng.integers(lo_j, hi_j))
+                if i < j:
+                    break
+            out[s] = (i, j)
+        return torch.from_numpy(out).to(dev)
+
+    return [("encode", None),
+            ("dd_regular", draw(0, P_, 0, P_)),          # (1 + x^z)
+            ("dd_mixed", draw(0, P_, P_, N)),            # trinomial inverse
+            ("dd_extended", draw(P_, N, P_, N)),         # (1 + x^z) after x^(-m_i)
+            ("dp_extended", draw(P_, N, N, N + 1)),      # (1 + x^m) D = dQ
+            ("dq_extended", draw(P_, N, N + 1, N + 2)),
+            ("dd_any", torch.from_numpy(inputs.random_pairs(23, N, S, "dd")).to(dev)),
+            ("any", torch.from_numpy(inputs.random_pairs(24, N, S, "any")).to(dev))]
+
+
+def run_geometry(args):
+    """One plain (one launch per op over all stripes) geometry: every op timed
+    with CUDA events on the launching stream; HBM fraction per op against the
+    measured copy peak."""
+    import torch
+
+    from paper_cs_0611109_gb300 import build, inputs
+    build.build()
+    from paper_cs_0611109_gb300 import rcg
+
+    p, n, c, S, seed, desc = GEOMETRIES[args.workload]
+    if args.stripes and args.stripes != S:
+        S, desc = args.stripes, "profiling case: %d stripes of %s" % (args.stripes, desc)
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    ctx = rcg.Context(0)
+    buf = torch.empty((S, n + 2, p - 1, c), dtype=torch.uint8, device=dev)
+    rcg.rcg_fill_random(buf, S * inputs.stripe_bytes(p, n, c), seed)
+    L = rcg.make_layout(buf, p, n, c)
+    ctx.encode(L, 0, S)
+    ops = geometry_ops(args.workload, n, S, dev, torch)
+    # an L2 flush between launches when one op's traffic fits in L2: a READ of
+    # 256 MB, so L2 holds clean unrelated lines (a write would leave dirty
+    # lines that the timed kernel then pays to write back)
+    moved = (n + 2) * (p - 1) * c * S
+    flush = torch.ones(256 << 20 >> 3, dtype=torch.int64, device=dev) if moved < (512 << 20) else None
+
+    def run(name, pairs):
+        if pairs is None:
+            ctx.encode(L, 0, S)
+        else:
+            ctx.recover_many(L, 0, S, pairs)
+
+    for _ in range(args.warmup):
+        for name, pairs in ops:
+            run(name, pairs)
+    torch.cuda.synchronize()
+    if ctx.last_device_status() != 0:
+        raise RuntimeError("device status word set during warm-up")
+    evs = {name: [] for name, _ in ops}
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(args.steps):
+        for name, pairs in ops:
+            if flush is not None:
+                flush.sum()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run(name, pairs)
+            e1.record(stream)
+            evs[name].append((e0, e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    status = ctx.last_device_status()
+    if status:
+        raise RuntimeError("device status word %#x" % status)
+    peak, kind = peak_hbm()
+    user = n * (p - 1) * c * S
+    per_op, total_ms = {}, 0.0
+    for name, _ in ops:
+        ms = sum(a.elapsed_time(b) for a, b in evs[name]) / len(evs[name])
+        total_ms += ms
+        per_op[name] = {"ms": round(ms, 4), "user_gbs": round(user / (ms * 1e-3) / 1e9, 1),
+                        "hbm_gbs": round(moved / (ms * 1e-3) / 1e9, 1),
+                        "hbm_frac": round(moved / (ms * 1e-3) / 1e9 / peak, 4)}
+    achieved = moved * len(ops) / (total_ms * 1e-3) / 1e9
+    ctx.close()
+    return {"metric": METRIC, "value": round(user * len(ops) / (total_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms, 4),
+            "higher_is_better": True, "dtype": "u8",
+            "data": "synthetic (SplitMix64 bytes generated on the device, seed %d)" % seed,
+            "config": {"workload": desc, "p": p, "n_data": n, "row_bytes": c, "stripes": S,
+                       "hbm_bytes_per_op": moved,
+                       "l2": "256 MB buffer read between launches" if flush is not None else
+                             "inputs far larger than the 129 MB L2; no flush"},
+            "roofline": {"bound": "hbm", "kernel": "rcg_tile_engine", "achieved": round(achieved, 1),
+                         "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(achieved / peak, 4)},
+            "per_op": per_op, "gpu_launches": len(ops) * args.steps, "clocks": clk}
 
 
 # ----------------------------------------------------------- batched form
@@ -605,6 +782,9 @@ def main():
         return
     if args.workload == "serve" and args.impl == "ours":
         print(json.dumps(run_serve(args)), flush=True)
+        return
+    if args.workload in GEOMETRIES and args.impl == "ours":
+        print(json.dumps(run_geometry(args)), flush=True)
         return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

@@ -232,3 +232,81 @@ def test_qext_batch_mixed_with_regular_jobs(rcg, ctx, oracle):
     assert ctx.last_device_status() == 0
     for buf, want in zip(bufs, wants):
         assert np.array_equal(buf.cpu().numpy(), want)
+
+
+# ------------------------------------------------------- full-size workload
+
+def class_draw(rng, p, N, S, lo_i, hi_i, lo_j, hi_j):
+    out = np.empty((S, 2), dtype=np.uint8)
+    for s in range(S):
+        while True:
+            i, j = int(rng.integers(lo_i, hi_i)), int(rng.integers(lo_j, hi_j))
+            if i < j:
+                break
+        out[s] = (i, j)
+    return out
+
+
+@pytest.mark.slow
+def test_qext_full_size_every_class(rcg, ctx, oracle):
+    # the extended bench geometry: p=59, N=117, 2 KiB rows, 512 stripes
+    # (7.1 GB of user data), seed 6; one launch per class over all stripes
+    p, N, C, S, seed = 59, 117, 2048, 512, 6
+    sb = inputs.stripe_bytes(p, N, C)
+    buf = torch.empty((S, N + 2, p - 1, C), dtype=torch.uint8, device="cuda")
+    rcg.rcg_fill_random(buf, S * sb, seed)
+    L = rcg.make_layout(buf, p, N, C)
+    ctx.encode(L, 0, S)
+    torch.cuda.synchronize()
+    assert ctx.last_device_status() == 0
+    for s in (0, S - 1):
+        host = np.ascontiguousarray(inputs.random_stripes(seed, p, N, C, 1, first_stripe=s))
+        oracle.encode(p, N, C, host, 1)
+        assert np.array_equal(buf[s].cpu().numpy(), host[0]), s
+    x = buf[:, 0].clone()  # property at full size: P is the XOR of the data strips
+    for k in range(1, N):
+        x ^= buf[:, k]
+    assert torch.equal(x, buf[:, N])
+    del x
+    enc = buf.clone()
+    rng = np.random.Generator(np.random.PCG64(62))
+    classes = {"dd_regular": (0, p, 0, p), "dd_mixed": (0, p, p, N), "dd_extended": (p, N, p, N),
+               "dp_extended": (p, N, N, N + 1), "dq_extended": (p, N, N + 1, N + 2)}
+    idx = torch.arange(S, device="cuda")
+    for n, (kind, box) in enumerate(classes.items()):
+        pairs = class_draw(rng, p, N, S, *box)
+        pd = dev(pairs)
+        buf[idx, pd[:, 0].long()] = POISON_I
+        buf[idx, pd[:, 1].long()] = POISON_J
+        ctx.recover_many(L, 0, S, pd)
+        torch.cuda.synchronize()
+        assert ctx.last_device_status() == 0
+        assert torch.equal(buf, enc), kind
+        s = (97 * n + 13) % S
+        lost = enc[s:s + 1].cpu().numpy()
+        lost[0, pairs[s, 0]] = POISON_I
+        lost[0, pairs[s, 1]] = POISON_J
+        oracle.recover(p, N, C, lost, 1, int(pairs[s, 0]), int(pairs[s, 1]))
+        assert np.array_equal(lost[0], buf[s].cpu().numpy()), (kind, s)
+
+
+def test_qext_host_memory_calls(rcg, oracle):
+    # stripes in pinned host memory, streamed through device staging
+    p, N, C, S = 13, 25, 2048, 9
+    want = encoded(oracle, 2800, p, N, C, S)
+    host = np.ascontiguousarray(inputs.random_stripes(2800, p, N, C, S))
+    pinned = torch.from_numpy(host).pin_memory()
+    L = rcg.make_layout(pinned, p, N, C)
+    with rcg.Context(0) as c:
+        c.set_host_chunk(3 * inputs.stripe_bytes(p, N, C))
+        c.encode_host(L, 0, S)
+        torch.cuda.synchronize()
+        assert np.array_equal(pinned.numpy(), want)
+        pairs = class_pairs(p, N)[:S]
+        for s, (i, j) in enumerate(pairs):
+            pinned[s, int(i)] = POISON_I
+            pinned[s, int(j)] = POISON_J
+        c.recover_many_host(L, 0, S, pairs)
+        torch.cuda.synchronize()
+        assert c.last_device_status() == 0
+        assert np.array_equal(pinned.numpy(), want)
