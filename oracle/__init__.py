@@ -67,6 +67,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.oracle_update.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _u64, _uint, _vp, _u64]
     lib.oracle_degraded_read.restype = ctypes.c_int
     lib.oracle_degraded_read.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _u64, _uint, _vp, _u64]
+    lib.oracle_h_encode.restype = ctypes.c_int
+    lib.oracle_h_encode.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64]
+    lib.oracle_h_recover.restype = ctypes.c_int
+    lib.oracle_h_recover.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _uint, _uint, _vp]
     return lib
 
 
@@ -189,3 +193,37 @@ def degraded_read(p, N, C, buf, stripe, j, row_stride=None, strip_stride=None,
     if rc:
         raise ValueError("oracle_degraded_read: invalid arguments")
     return out
+
+
+# --------------------------------------------------------- horizontal strips
+
+def _h_strides(N, strip_bytes, strip_stride, stripe_stride):
+    strip_stride = strip_bytes if strip_stride is None else strip_stride
+    stripe_stride = (N + 2) * strip_stride if stripe_stride is None else stripe_stride
+    return strip_stride, stripe_stride
+
+
+def h_encode(p, N, strip_bytes, buf, n_stripes, strip_stride=None, stripe_stride=None):
+    """Encode stripes in the horizontal representation of Section 4.5: element
+    e of a strip is bits [e(p-1), (e+1)(p-1)) of the strip, little-endian (for
+    p = 17 the 16-bit word e)."""
+    _check_buf(buf)
+    ss, st = _h_strides(N, strip_bytes, strip_stride, stripe_stride)
+    rc = lib().oracle_h_encode(p, N, strip_bytes, _ptr(buf), n_stripes, ss, st)
+    if rc:
+        raise ValueError("oracle_h_encode: invalid arguments")
+
+
+def h_recover(p, N, strip_bytes, buf, n_stripes, i=0, j=1, pairs=None, strip_stride=None,
+              stripe_stride=None):
+    """Rebuild strips i < j (or per-stripe pairs) of horizontal stripes in place
+    (Lemma 3.1.2)."""
+    _check_buf(buf)
+    ss, st = _h_strides(N, strip_bytes, strip_stride, stripe_stride)
+    pp = None
+    if pairs is not None:
+        pairs = np.ascontiguousarray(pairs, dtype=np.uint8)
+        pp = _ptr(pairs)
+    rc = lib().oracle_h_recover(p, N, strip_bytes, _ptr(buf), n_stripes, ss, st, i, j, pp)
+    if rc:
+        raise ValueError("oracle_h_recover: invalid arguments (rc=%d)" % rc)

@@ -38,6 +38,14 @@
  * Stripe layout: stripe s starts at buf + s*stripe_stride; strip k (data
  * 0..N-1, then P = strip N and Q = strip N+1) at + k*strip_stride; row r at
  * + r*row_stride; the row is C bytes.
+ *
+ * Horizontal storage (the oracle_h_* functions).  Section 4.5 keeps one ring
+ * element per machine word instead: for p = 17 a 16-bit word holds y_0..y_15,
+ * the coefficients of x^0..x^15.  In general element e of a strip is the
+ * little-endian bit string at bits [e(p-1), (e+1)(p-1)) of the strip (bit t is
+ * bit t%8 of byte t/8), bit r of it the coefficient of x^r; for p = 17 that is
+ * the 16-bit little-endian word e.  The arithmetic is the same; only gather
+ * and scatter differ.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -199,7 +207,8 @@ void oracle_mul_xpow_array(unsigned p, unsigned k, const u64 *in, u64 *out, size
 typedef struct {
     uint8_t *base;
     u64 row_stride, strip_stride, stripe_stride;
-    unsigned rows; /* p - 1 */
+    unsigned rows;       /* p - 1 */
+    int horizontal;      /* 1: element e is bits [e*rows, (e+1)*rows) of the strip */
 } layout_t;
 
 static uint8_t *row_ptr(const layout_t *L, u64 s, unsigned k, unsigned r)
@@ -207,10 +216,19 @@ static uint8_t *row_ptr(const layout_t *L, u64 s, unsigned k, unsigned r)
     return L->base + s * L->stripe_stride + (u64)k * L->strip_stride + (u64)r * L->row_stride;
 }
 
-/* Polynomial of codeword (bit position) b of strip k of stripe s. */
+/* Polynomial of codeword b (a bit position, or an element of a horizontal
+ * strip) of strip k of stripe s. */
 static u64 gather(const layout_t *L, u64 s, unsigned k, u64 b)
 {
     u64 a = 0;
+    if (L->horizontal) {
+        const uint8_t *strip = L->base + s * L->stripe_stride + (u64)k * L->strip_stride;
+        for (unsigned r = 0; r < L->rows; r++) {
+            u64 t = b * L->rows + r;
+            a |= (u64)((strip[t >> 3] >> (t & 7)) & 1u) << r;
+        }
+        return a;
+    }
     for (unsigned r = 0; r < L->rows; r++) {
         const uint8_t *row = row_ptr(L, s, k, r);
         a |= (u64)((row[b >> 3] >> (b & 7)) & 1u) << r;
@@ -220,6 +238,18 @@ static u64 gather(const layout_t *L, u64 s, unsigned k, u64 b)
 
 static void scatter(const layout_t *L, u64 s, unsigned k, u64 b, u64 a)
 {
+    if (L->horizontal) {
+        uint8_t *strip = L->base + s * L->stripe_stride + (u64)k * L->strip_stride;
+        for (unsigned r = 0; r < L->rows; r++) {
+            u64 t = b * L->rows + r;
+            uint8_t m = (uint8_t)(1u << (t & 7));
+            if ((a >> r) & 1u)
+                strip[t >> 3] |= m;
+            else
+                strip[t >> 3] &= (uint8_t)~m;
+        }
+        return;
+    }
     for (unsigned r = 0; r < L->rows; r++) {
         uint8_t *row = row_ptr(L, s, k, r);
         uint8_t m = (uint8_t)(1u << (b & 7));
@@ -249,17 +279,14 @@ static int check_args(unsigned p, unsigned N)
 /* Equation (znparity) of Corollary 3.2.4 with g = S_p and g_k = g^k, extended
  * by (qext) for k >= p: P = sum_k d_k, Q = sum_k g_k d_k.  Writes strips N
  * and N+1. */
-int oracle_encode(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
-                  u64 row_stride, u64 strip_stride, u64 stripe_stride)
+static void encode_layout(const layout_t *Lp, unsigned p, unsigned N, u64 n_codewords, u64 n_stripes)
 {
-    if (check_args(p, N))
-        return -1;
-    layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1};
+    const layout_t L = *Lp;
     u64 g[128];
     for (unsigned k = 0; k < N; k++)
         g[k] = oracle_weight(p, k);
     for (u64 s = 0; s < n_stripes; s++) {
-        for (u64 b = 0; b < 8 * C; b++) {
+        for (u64 b = 0; b < n_codewords; b++) {
             u64 P = 0, Q = 0;
             for (unsigned k = 0; k < N; k++) {
                 u64 d = gather(&L, s, k, b);
@@ -270,6 +297,15 @@ int oracle_encode(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
             scatter(&L, s, N + 1, b, Q);
         }
     }
+}
+
+int oracle_encode(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
+                  u64 row_stride, u64 strip_stride, u64 stripe_stride)
+{
+    if (check_args(p, N))
+        return -1;
+    layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1, 0};
+    encode_layout(&L, p, N, 8 * C, n_stripes);
     return 0;
 }
 
@@ -362,13 +398,9 @@ static int recover_one(const layout_t *L, unsigned p, unsigned N, u64 s, u64 b,
 
 /* Recover strips i < j of stripes [0, n_stripes) in place.  pairs, when not
  * NULL, gives a per-stripe (i, j) as two bytes per stripe and overrides i, j. */
-int oracle_recover(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
-                   u64 row_stride, u64 strip_stride, u64 stripe_stride,
-                   unsigned i, unsigned j, const uint8_t *pairs)
+static int recover_layout(const layout_t *L, unsigned p, unsigned N, u64 n_codewords, u64 n_stripes,
+                          unsigned i, unsigned j, const uint8_t *pairs)
 {
-    if (check_args(p, N))
-        return -1;
-    layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1};
     u64 g[128];
     for (unsigned k = 0; k < N; k++)
         g[k] = oracle_weight(p, k);
@@ -377,11 +409,47 @@ int oracle_recover(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
         unsigned c = pairs ? pairs[2 * s + 1] : j;
         if (!(a < c && c < N + 2))
             return -2;
-        for (u64 b = 0; b < 8 * C; b++)
-            if (recover_one(&L, p, N, s, b, a, c, g))
+        for (u64 b = 0; b < n_codewords; b++)
+            if (recover_one(L, p, N, s, b, a, c, g))
                 return -3;
     }
     return 0;
+}
+
+int oracle_recover(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes,
+                   u64 row_stride, u64 strip_stride, u64 stripe_stride,
+                   unsigned i, unsigned j, const uint8_t *pairs)
+{
+    if (check_args(p, N))
+        return -1;
+    layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1, 0};
+    return recover_layout(&L, p, N, 8 * C, n_stripes, i, j, pairs);
+}
+
+/* ---------------------------------------------------- horizontal strips */
+
+/* Encode and recovery of stripes in the horizontal representation of Section
+ * 4.5 (see the header): strips of strip_bytes bytes, strip_bytes*8 a multiple
+ * of p-1, so a strip holds strip_bytes*8/(p-1) ring elements; strip k of
+ * stripe s at buf + s*stripe_stride + k*strip_stride.  Same code, same
+ * Lemma 3.1.2 case analysis as the bit-sliced functions. */
+int oracle_h_encode(unsigned p, unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes,
+                    u64 strip_stride, u64 stripe_stride)
+{
+    if (check_args(p, N) || (strip_bytes * 8) % (p - 1))
+        return -1;
+    layout_t L = {buf, 0, strip_stride, stripe_stride, p - 1, 1};
+    encode_layout(&L, p, N, strip_bytes * 8 / (p - 1), n_stripes);
+    return 0;
+}
+
+int oracle_h_recover(unsigned p, unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes,
+                     u64 strip_stride, u64 stripe_stride, unsigned i, unsigned j, const uint8_t *pairs)
+{
+    if (check_args(p, N) || (strip_bytes * 8) % (p - 1))
+        return -1;
+    layout_t L = {buf, 0, strip_stride, stripe_stride, p - 1, 1};
+    return recover_layout(&L, p, N, strip_bytes * 8 / (p - 1), n_stripes, i, j, pairs);
 }
 
 /* ------------------------------------------------------------- update */
@@ -397,7 +465,7 @@ int oracle_update(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 stripe,
 {
     if (check_args(p, N) || i >= N)
         return -1;
-    layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1};
+    layout_t L = {buf, row_stride, strip_stride, stripe_stride, p - 1, 0};
     for (unsigned r = 0; r < p - 1; r++)
         memmove(row_ptr(&L, stripe, i, r), new_strip + (u64)r * new_row_stride, C);
     return oracle_encode(p, N, C, buf + stripe * stripe_stride, 1, row_stride, strip_stride,
@@ -417,8 +485,8 @@ int oracle_degraded_read(unsigned p, unsigned N, u64 C, const uint8_t *buf, u64 
 {
     if (check_args(p, N) || j >= N + 2)
         return -1;
-    layout_t L = {(uint8_t *)buf, row_stride, strip_stride, stripe_stride, p - 1};
-    layout_t O = {out, out_row_stride, 0, 0, p - 1};
+    layout_t L = {(uint8_t *)buf, row_stride, strip_stride, stripe_stride, p - 1, 0};
+    layout_t O = {out, out_row_stride, 0, 0, p - 1, 0};
     for (u64 b = 0; b < 8 * C; b++) {
         u64 v = 0;
         if (j == N + 1) {

@@ -34,6 +34,13 @@ MUTANTS = {
     "extension_allowed_for_every_prime": ("if (N > p && !oracle_cone_extends(p))", "if (N > p && 0)"),
     "update_wrong_stripe": ("return oracle_encode(p, N, C, buf + stripe * stripe_stride, 1,",
                             "return oracle_encode(p, N, C, buf, 1,"),
+    "h_bits_reversed": ("a |= (u64)((strip[t >> 3] >> (t & 7)) & 1u) << r;",
+                        "a |= (u64)((strip[t >> 3] >> (t & 7)) & 1u) << (L->rows - 1 - r);"),
+    "h_scatter_toggles": ("strip[t >> 3] |= m;", "strip[t >> 3] ^= m;"),
+    "h_element_stride": ("const uint8_t *strip = L->base + s * L->stripe_stride + (u64)k * L->strip_stride;\n"
+                         "        for (unsigned r = 0; r < L->rows; r++) {\n            u64 t = b * L->rows + r;",
+                         "const uint8_t *strip = L->base + s * L->stripe_stride + (u64)k * L->strip_stride;\n"
+                         "        for (unsigned r = 0; r < L->rows; r++) {\n            u64 t = b * (L->rows + 1) + r;"),
 }
 
 
@@ -51,6 +58,7 @@ def test_pins_catch_planted_mistake(name):
         env = dict(os.environ, RCG_ORACLE_LIB=so)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                            os.path.join(ROOT, "tests", "test_oracle_qext_pins.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_qext_pins.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_horizontal_pins.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, "planted mistake %r passed every pin:\n%s" % (name, r.stdout[-2000:])
