@@ -51,9 +51,10 @@ def parse():
     ap.add_argument("--stripes", type=int, default=None,
                     help="stripes per GPU (default: the workload's own, 8192 for c2; other values are "
                          "profiling cases, not bench lines)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "qext", "batched", "serve"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "qext", "h17", "batched", "serve"],
                     help="c2: the bench line; c1 / c3: the p=5 and p=59 plain configurations; "
                          "qext: extended Q-parity, p=59 with 117 data strips; "
+                         "h17: the horizontal Z_17 representation (one element per 16-bit word); "
                          "batched: the uneven 50k-stripe batch vs per-stripe launches; "
                          "serve: Poisson request stream, continuous batching vs per-job launches")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -578,6 +579,91 @@ def run_geometry(args):
             "per_op": per_op, "gpu_launches": len(ops) * args.steps, "clocks": clk}
 
 
+# ------------------------------------------------ horizontal representation
+
+H17 = (17, 16, 65536, 4096, 5)  # p, N, strip bytes, stripes, seed
+
+
+def run_h17(args):
+    """The horizontal representation of Section 4.5 (one Z_17 element per
+    16-bit word): p = 17, N = 16 data strips + P + Q of 64 KiB, 4096 stripes
+    (4.3 GB of user data, 4.8 GB moved per op); encode and one launch per
+    recovery class with a uniformly drawn pair per stripe."""
+    import torch
+
+    from paper_cs_0611109_gb300 import build, inputs
+    build.build()
+    from paper_cs_0611109_gb300 import rcg
+
+    p, n, B, S, seed = H17
+    desc = ("horizontal Z_17 (Section 4.5): p=17, N=16 data strips + P + Q of 64 KiB "
+            "(32768 16-bit elements), %d stripes; encode + DD/DP/DQ/PQ, one launch per op")
+    if args.stripes and args.stripes != S:
+        S = args.stripes
+        desc = "profiling case: " + desc
+    desc = desc % S
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    ctx = rcg.Context(0)
+    buf = torch.empty((S, n + 2, B), dtype=torch.uint8, device=dev)
+    rcg.rcg_fill_random(buf, buf.numel(), seed)
+    L = rcg.make_hlayout(buf, p, n, B)
+    ctx.h_encode(L, 0, S)
+    ops = [("encode", None)] + [(k, torch.from_numpy(inputs.random_pairs(3500 + m, n, S, k)).to(dev))
+                                for m, k in enumerate(CLASSES)]
+    moved = (n + 2) * B * S
+    user = n * B * S
+
+    def run(pairs):
+        if pairs is None:
+            ctx.h_encode(L, 0, S)
+        else:
+            ctx.h_recover_many(L, 0, S, pairs)
+
+    for _ in range(args.warmup):
+        for _, pr in ops:
+            run(pr)
+    torch.cuda.synchronize()
+    if ctx.last_device_status() != 0:
+        raise RuntimeError("device status word set during warm-up")
+    evs = {name: [] for name, _ in ops}
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(args.steps):
+        for name, pr in ops:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run(pr)
+            e1.record(stream)
+            evs[name].append((e0, e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    status = ctx.last_device_status()
+    if status:
+        raise RuntimeError("device status word %#x" % status)
+    peak, kind = peak_hbm()
+    per_op, total_ms = {}, 0.0
+    for name, _ in ops:
+        ms = sum(a.elapsed_time(b) for a, b in evs[name]) / len(evs[name])
+        total_ms += ms
+        per_op[name] = {"ms": round(ms, 4), "user_gbs": round(user / (ms * 1e-3) / 1e9, 1),
+                        "hbm_gbs": round(moved / (ms * 1e-3) / 1e9, 1),
+                        "hbm_frac": round(moved / (ms * 1e-3) / 1e9 / peak, 4)}
+    achieved = moved * len(ops) / (total_ms * 1e-3) / 1e9
+    ctx.close()
+    return {"metric": METRIC, "value": round(user * len(ops) / (total_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms, 4),
+            "higher_is_better": True, "dtype": "u16 lanes",
+            "data": "synthetic (SplitMix64 bytes generated on the device, seed %d)" % seed,
+            "config": {"workload": desc, "p": p, "n_data": n, "strip_bytes": B, "stripes": S,
+                       "hbm_bytes_per_op": moved, "l2": "inputs far larger than the 129 MB L2; no flush"},
+            "roofline": {"bound": "hbm", "kernel": "rcg_h_kernel<16>", "achieved": round(achieved, 1),
+                         "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(achieved / peak, 4)},
+            "per_op": per_op, "gpu_launches": len(ops) * args.steps, "clocks": clk}
+
+
 # ----------------------------------------------------------- batched form
 
 def run_batched(args):
@@ -782,6 +868,9 @@ def main():
         return
     if args.workload == "serve" and args.impl == "ours":
         print(json.dumps(run_serve(args)), flush=True)
+        return
+    if args.workload == "h17" and args.impl == "ours":
+        print(json.dumps(run_h17(args)), flush=True)
         return
     if args.workload in GEOMETRIES and args.impl == "ours":
         print(json.dumps(run_geometry(args)), flush=True)

@@ -190,6 +190,50 @@ rcg_status rcg_update(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32
 rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32_t j,
                              void *out, uint64_t out_row_stride, void *stream);
 
+/* ------------------------------------------- horizontal representation */
+
+/* Section 4.5 keeps one ring element per machine word instead of bit-slicing
+ * it over rows: for p = 17 a 16-bit word holds y_0..y_15, the coefficients of
+ * x^0..x^15.  In this representation a strip is an array of elements, element
+ * e being the little-endian bit field [e(p-1), (e+1)(p-1)) of the strip: for
+ * p = 17 the 16-bit little-endian word e, for p = 5 a nibble, for p = 3 two
+ * bits (bit r of the field = coefficient of x^r).  Multiplication by x^k is
+ * the word formula of Section 4.6 applied lane by lane.  The code, the
+ * erasure pairs (data 0..N-1, P = strip N, Q = strip N+1) and the extension
+ * to 2p - 1 data strips (p = 5 and 17, equation qext) are those of the
+ * bit-sliced calls; results are identical to encoding the transposed stripe.
+ * Layout: stripe s at base + s*stripe_stride, strip k at + k*strip_stride,
+ * strip_bytes bytes per strip.  base, strides and strip_bytes are multiples of
+ * 16; zero strides mean packed. */
+typedef struct rcg_hlayout {
+    void *base;             /* device address of stripe 0 */
+    uint32_t p;             /* 3, 5 or 17 */
+    uint32_t n_data;        /* N, 1 <= N <= p (or 2p - 1 for p = 5, 17) */
+    uint64_t strip_bytes;   /* bytes per strip, a positive multiple of 16 */
+    uint64_t strip_stride;  /* bytes between strips; 0 = strip_bytes */
+    uint64_t stripe_stride; /* bytes between stripes; 0 = (N+2)*strip_stride */
+} rcg_hlayout;
+
+/* Encode P and Q of stripes [first_stripe, first_stripe + n_stripes)
+ * (Corollary 3.2.4; Q by Horner's rule Q = d + xQ over the data strips from
+ * the last to the first, Section 4.2).  One launch. */
+rcg_status rcg_h_encode(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t first_stripe, uint64_t n_stripes,
+                        void *stream);
+
+/* Recover strips i < j of one stripe in place (Lemma 3.1.2): two data strips
+ * by (w_i + w_j) D_j = w_i dP + dQ with the inverse precomputed per pair (for
+ * regular strips it is x^(-i) (1 + x^(j-i))^(-1), Section 4.6), data + P by
+ * w_i^(-1) dQ, data + Q as RAID-5, P + Q by re-encoding.  Strips i and j are
+ * not read. */
+rcg_status rcg_h_recover(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t stripe, uint32_t i, uint32_t j,
+                         void *stream);
+
+/* rcg_h_recover for a per-stripe pair: pairs is a DEVICE array of
+ * 2*n_stripes bytes, as in rcg_recover_many; an invalid pair leaves its
+ * stripe untouched and sets RCG_DEV_BADPAIR. */
+rcg_status rcg_h_recover_many(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t first_stripe, uint64_t n_stripes,
+                              const uint8_t *pairs, void *stream);
+
 /* ------------------------------------------------- stripes in host memory */
 
 /* rcg_encode and rcg_recover_many for stripes in HOST memory: L->base is a

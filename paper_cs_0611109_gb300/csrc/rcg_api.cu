@@ -350,6 +350,7 @@ rcg_status rcg_create(int device, rcg_ctx **out) {
     ctx->device = device;
     ctx->sm_count = prop.multiProcessorCount;
     rcg_status st = from_cuda(upload_inverse_tables());
+    if (st == RCG_OK) st = from_cuda(upload_h_tables(), "horizontal tables");
     if (st == RCG_OK) st = from_cuda(engine_init_attributes());
     if (st == RCG_OK) st = from_cuda(cudaMalloc(&ctx->status, 256));
     if (st == RCG_OK) st = from_cuda(cudaMemset(ctx->status, 0, 256));
@@ -516,6 +517,50 @@ rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe,
     J.aux_stripe_stride = (g.p - 1) * ors;
     DeviceGuard guard(ctx->device);
     return launch_single(ctx, J, pl, static_cast<cudaStream_t>(stream));
+}
+
+// ================================================== horizontal representation
+
+static rcg_status check_hlayout(const rcg_hlayout *L, uint64_t *ss, uint64_t *st) {
+    if (!L || !L->base || !aligned16(L->base)) return RCG_EINVAL;
+    if (L->p != 3 && L->p != 5 && L->p != 17) return RCG_EINVAL;
+    if (L->n_data < 1 || L->n_data > max_data_strips(L->p)) return RCG_EINVAL;
+    if (L->strip_bytes == 0 || (L->strip_bytes & 15) || L->strip_bytes / 16 > 0xffffffffull) return RCG_EINVAL;
+    *ss = L->strip_stride ? L->strip_stride : L->strip_bytes;
+    *st = L->stripe_stride ? L->stripe_stride : (L->n_data + 2ull) * *ss;
+    if (*ss < L->strip_bytes || (*ss & 15) || (*st & 15)) return RCG_EINVAL;
+    return RCG_OK;
+}
+
+static rcg_status h_launch(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t first, uint64_t n, uint32_t i, uint32_t j,
+                           const uint8_t *pairs, void *stream) {
+    uint64_t ss, st;
+    if (!ctx) return RCG_EINVAL;
+    rcg_status s = check_hlayout(L, &ss, &st);
+    if (s) return s;
+    if (n == 0) return RCG_OK;
+    DeviceGuard guard(ctx->device);
+    return from_cuda(launch_h(static_cast<uint8_t *>(L->base) + first * st, L->p, L->n_data, L->strip_bytes, ss, st,
+                              n, i, j, pairs, ctx->status, ctx->sm_count, static_cast<cudaStream_t>(stream)),
+                     "horizontal kernel launch");
+}
+
+rcg_status rcg_h_encode(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t first_stripe, uint64_t n_stripes,
+                        void *stream) {
+    if (!L) return RCG_EINVAL;
+    return h_launch(ctx, L, first_stripe, n_stripes, L->n_data, L->n_data + 1, nullptr, stream);
+}
+
+rcg_status rcg_h_recover(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t stripe, uint32_t i, uint32_t j,
+                         void *stream) {
+    if (!L || !(i < j && j <= L->n_data + 1)) return RCG_EINVAL;
+    return h_launch(ctx, L, stripe, 1, i, j, nullptr, stream);
+}
+
+rcg_status rcg_h_recover_many(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t first_stripe, uint64_t n_stripes,
+                              const uint8_t *pairs, void *stream) {
+    if (!L || !pairs) return RCG_EINVAL;
+    return h_launch(ctx, L, first_stripe, n_stripes, 0, 0, pairs, stream);
 }
 
 // ================================================================= batches

@@ -174,6 +174,14 @@ bool cone_extends(uint32_t p);                        // Theorem 3.3.3 holds for
 // Section 3.3 applies (Theorem 3.3.3), else p (Corollary 3.2.4).
 inline uint32_t max_data_strips(uint32_t p) { return cone_extends(p) ? 2 * p - 1 : p; }
 
+// Horizontal representation (rcg_horizontal.cu): the per-prime inverse masks
+// (uploaded to the current device), and one launch over n_stripes stripes of
+// recovery pair (i, j) or per-stripe pairs; i = N, j = N+1 encodes.
+cudaError_t upload_h_tables();
+cudaError_t launch_h(uint8_t *base, uint32_t p, uint32_t N, uint64_t strip_bytes, uint64_t strip_stride,
+                     uint64_t stripe_stride, uint64_t n_stripes, uint32_t i, uint32_t j, const uint8_t *pairs,
+                     uint32_t *status, int sm_count, cudaStream_t stream);
+
 // Host: the CUDA device of a context.
 int ctx_device(const rcg_ctx *ctx);
 

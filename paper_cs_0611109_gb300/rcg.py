@@ -65,6 +65,11 @@ class rcg_plan_info(ctypes.Structure):
                 ("max_items", _u32), ("smem_bytes", _u32), ("ctas_per_sm", _u32), ("shape", _u32)]
 
 
+class rcg_hlayout(ctypes.Structure):
+    _fields_ = [("base", _vp), ("p", _u32), ("n_data", _u32), ("strip_bytes", _u64),
+                ("strip_stride", _u64), ("stripe_stride", _u64)]
+
+
 class rcg_prime_info_t(ctypes.Structure):
     _fields_ = [("ord2", _u32), ("is_field", _u32), ("extends", _u32), ("max_data", _u32)]
 
@@ -106,6 +111,9 @@ EXPORTS = {
     "rcg_inverse_table": (_int, [_u32, ctypes.POINTER(_u64)]),
     "rcg_plan": (_int, [_u32, _u64, ctypes.POINTER(rcg_plan_info)]),
     "rcg_prime_info": (_int, [_u32, ctypes.POINTER(rcg_prime_info_t)]),
+    "rcg_h_encode": (_int, [_vp, ctypes.POINTER(rcg_hlayout), _u64, _u64, _vp]),
+    "rcg_h_recover": (_int, [_vp, ctypes.POINTER(rcg_hlayout), _u64, _u32, _u32, _vp]),
+    "rcg_h_recover_many": (_int, [_vp, ctypes.POINTER(rcg_hlayout), _u64, _u64, _vp, _vp]),
     "rcg_ring_inverse": (_int, [_u32, _u64, ctypes.POINTER(_u64)]),
 }
 
@@ -154,6 +162,13 @@ def make_layout(base, p: int, n_data: int, row_bytes: int, row_stride: int = 0,
                 strip_stride: int = 0, stripe_stride: int = 0) -> rcg_layout:
     """Describe stripes at device address `base` (tensor or int); zero strides = packed."""
     return rcg_layout(_ptr(base), p, n_data, row_bytes, row_stride, strip_stride, stripe_stride)
+
+
+def make_hlayout(base, p: int, n_data: int, strip_bytes: int, strip_stride: int = 0,
+                 stripe_stride: int = 0) -> rcg_hlayout:
+    """Describe stripes in the horizontal representation (one ring element per
+    (p-1)-bit field) at device address `base`; zero strides = packed."""
+    return rcg_hlayout(_ptr(base), p, n_data, strip_bytes, strip_stride, stripe_stride)
 
 
 # ------------------------------------------------------------- the C calls
@@ -368,6 +383,19 @@ def rcg_inverse_table(p: int) -> list[int]:
     return [int(m) for m in masks]
 
 
+def rcg_h_encode(ctx: int, layout: rcg_hlayout, first_stripe: int, n_stripes: int, stream=None):
+    _check(lib().rcg_h_encode(ctx, ctypes.byref(layout), first_stripe, n_stripes, _stream(stream)), "rcg_h_encode")
+
+
+def rcg_h_recover(ctx: int, layout: rcg_hlayout, stripe: int, i: int, j: int, stream=None):
+    _check(lib().rcg_h_recover(ctx, ctypes.byref(layout), stripe, i, j, _stream(stream)), "rcg_h_recover")
+
+
+def rcg_h_recover_many(ctx: int, layout: rcg_hlayout, first_stripe: int, n_stripes: int, pairs, stream=None):
+    _check(lib().rcg_h_recover_many(ctx, ctypes.byref(layout), first_stripe, n_stripes, _ptr(pairs),
+                                    _stream(stream)), "rcg_h_recover_many")
+
+
 def rcg_prime_info(p: int) -> dict:
     """ord2 (Lemma 3.3.1), is_field, extends (Theorem 3.3.3) and max_data for p."""
     info = rcg_prime_info_t()
@@ -428,6 +456,15 @@ class Context:
 
     def update(self, layout, stripe, i, new_strip, new_row_stride=0, stream=None):
         rcg_update(self.handle, layout, stripe, i, new_strip, new_row_stride, stream)
+
+    def h_encode(self, layout, first_stripe, n_stripes, stream=None):
+        rcg_h_encode(self.handle, layout, first_stripe, n_stripes, stream)
+
+    def h_recover(self, layout, stripe, i, j, stream=None):
+        rcg_h_recover(self.handle, layout, stripe, i, j, stream)
+
+    def h_recover_many(self, layout, first_stripe, n_stripes, pairs, stream=None):
+        rcg_h_recover_many(self.handle, layout, first_stripe, n_stripes, pairs, stream)
 
     def degraded_read(self, layout, stripe, j, out, out_row_stride=0, stream=None):
         rcg_degraded_read(self.handle, layout, stripe, j, out, out_row_stride, stream)
