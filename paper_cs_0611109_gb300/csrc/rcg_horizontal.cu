@@ -13,8 +13,9 @@
 //
 // Kernel.  No shared memory: a thread owns one 16-byte column of a stripe
 // (8 elements at p = 17) and streams it through every strip with coalesced
-// 16-byte loads, eight strips in flight.  Q is accumulated by Horner's rule
-// over the data strips from the last to the first (Section 4.2, Q = d + g Q),
+// 16-byte loads, four strips in flight, four 256-thread CTAs per SM.  Q is
+// accumulated by Horner's rule over the data strips from the last to the
+// first (Section 4.2, Q = d + g Q),
 // a second Horner sum covering the extended strips k >= p of equation (qext)
 // (weights 1 + x^(k-p+1)).  Lemma 3.1.2's four cases then need, per erasure
 // pair, at most one multiplication by an inverse -- of w_i (data + P) or of
@@ -76,6 +77,29 @@ struct Lanes {
     }
 };
 
+// 16-bit lanes: the sign of each lane spreads over the lane with one byte
+// permute (prmt's sign-replicating selectors: bytes 0-1 take the sign of
+// byte 1, bytes 2-3 the sign of byte 3), so x y is three instructions.
+__device__ __forceinline__ uint32_t lane_signs16(uint32_t y) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(r) : "r"(y));
+    return r;
+}
+
+template <>
+__device__ __forceinline__ uint32_t Lanes<16>::mulx(uint32_t y) {
+    return ((y << 1) & 0xFFFEFFFEu) ^ lane_signs16(y);
+}
+
+template <>
+__device__ __forceinline__ uint32_t Lanes<16>::mulxk(uint32_t y, uint32_t k) {
+    if (k == 0) return y;
+    const uint32_t below_k = ((1u << k) - 1) * LSB;
+    const uint32_t below_k1 = ((1u << (k - 1)) - 1) * LSB;
+    // the bit p-1-k = 16-k of each lane is the top bit of that lane of y << (k-1)
+    return ((y << k) & ~below_k) ^ ((y >> (17 - k)) & below_k1) ^ lane_signs16(y << (k - 1));
+}
+
 __device__ __forceinline__ uint4 x4(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }
@@ -125,10 +149,12 @@ __device__ __forceinline__ void stg4(uint8_t *p, uint4 v) {
                  : "memory");
 }
 
-constexpr int kBatch = 8;  // strips whose loads are in flight together
+constexpr int kBatch = 4;  // strips whose loads are in flight together (measured best with 4 CTAs per SM)
 
-template <int E>
-__global__ void __launch_bounds__(256) rcg_h_kernel(const HParams prm) {
+// EXT: the layout has extended strips (N > p); without them the second
+// Horner sum and its registers drop out.
+template <int E, bool EXT>
+__global__ void __launch_bounds__(256, 4) rcg_h_kernel(const HParams prm) {
     constexpr uint32_t P = E + 1;
     constexpr int slot = E == 2 ? 0 : E == 4 ? 1 : 2;
     const uint32_t N = prm.N;
@@ -172,7 +198,7 @@ __global__ void __launch_bounds__(256) rcg_h_kernel(const HParams prm) {
                 const int k = k0 - 1 - q;
                 if (k < 0) break;
                 dp = x4(dp, d[q]);
-                if (static_cast<uint32_t>(k) >= P) {
+                if (EXT && static_cast<uint32_t>(k) >= P) {
                     hx = x4(mulx4<E>(hx), d[q]);
                     ex = x4(ex, d[q]);
                 } else {
@@ -180,7 +206,8 @@ __global__ void __launch_bounds__(256) rcg_h_kernel(const HParams prm) {
                 }
             }
         }
-        uint4 dq = x4(x4(hl, ex), mulx4<E>(hx));  // sum of w_k d_k over the survivors
+        uint4 dq = hl;  // sum of w_k d_k over the survivors
+        if (EXT) dq = x4(x4(dq, ex), mulx4<E>(hx));
         dp = x4(dp, pv);
         dq = x4(dq, qv);
 
@@ -249,15 +276,23 @@ cudaError_t launch_h(uint8_t *base, uint32_t p, uint32_t N, uint64_t strip_bytes
     prm.status = status;
     const uint64_t total = n_stripes * prm.vps;
     if (total == 0) return cudaSuccess;
-    const uint64_t blocks = std::min<uint64_t>((total + 255) / 256, static_cast<uint64_t>(sm_count) * 8);
-    const unsigned g = static_cast<unsigned>(blocks);
+    // a resident grid (every block of the grid-stride loop runs from the start)
+    auto go = [&](auto kernel) -> cudaError_t {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
+        if (e != cudaSuccess) return e;
+        const uint64_t resident = static_cast<uint64_t>(sm_count) * static_cast<uint64_t>(std::max(per_sm, 1));
+        const unsigned g = static_cast<unsigned>(std::min<uint64_t>((total + 255) / 256, resident));
+        kernel<<<g, 256, 0, stream>>>(prm);
+        return cudaGetLastError();
+    };
+    const bool ext = N > p;
     switch (p) {
-        case 3: rcg_h_kernel<2><<<g, 256, 0, stream>>>(prm); break;
-        case 5: rcg_h_kernel<4><<<g, 256, 0, stream>>>(prm); break;
-        case 17: rcg_h_kernel<16><<<g, 256, 0, stream>>>(prm); break;
+        case 3: return go(rcg_h_kernel<2, false>);  // 3 has no extension
+        case 5: return ext ? go(rcg_h_kernel<4, true>) : go(rcg_h_kernel<4, false>);
+        case 17: return ext ? go(rcg_h_kernel<16, true>) : go(rcg_h_kernel<16, false>);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace rcg
