@@ -565,6 +565,30 @@ def run_geometry(args):
                         "hbm_gbs": round(moved / (ms * 1e-3) / 1e9, 1),
                         "hbm_frac": round(moved / (ms * 1e-3) / 1e9 / peak, 4)}
     achieved = moved * len(ops) / (total_ms * 1e-3) / 1e9
+    ref = None
+    if flush is not None:
+        # what any single launch of this traffic achieves here: a plain
+        # elementwise kernel that reads as many bytes as an op reads and writes
+        # the 2 strips it writes, timed the same way (after the same L2 flush)
+        wr = torch.empty(2 * (p - 1) * c * S, dtype=torch.uint8, device=dev)
+        rd = torch.empty(max(n, 2) * (p - 1) * c * S, dtype=torch.uint8, device=dev)
+        a_in, b_in = rd[:wr.numel()], rd[wr.numel():2 * wr.numel()]
+        tot = 0.0
+        for it in range(args.warmup + args.steps):
+            flush.sum()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.bitwise_xor(a_in, b_in, out=wr)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                tot += e0.elapsed_time(e1)
+        ms_ref = tot / args.steps
+        ref = {"what": "torch.bitwise_xor reading %d B and writing %d B, after the same L2 flush"
+                       % (2 * wr.numel(), wr.numel()),
+               "ms": round(ms_ref, 4), "hbm_frac": round(3 * wr.numel() / (ms_ref * 1e-3) / 1e9 / peak, 4),
+               "note": "a launch this small is bound by launch and DRAM latency, not by bandwidth"}
+        del rd, wr
     ctx.close()
     return {"metric": METRIC, "value": round(user * len(ops) / (total_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms, 4),
@@ -576,7 +600,8 @@ def run_geometry(args):
                              "inputs far larger than the 129 MB L2; no flush"},
             "roofline": {"bound": "hbm", "kernel": "rcg_tile_engine", "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(achieved / peak, 4)},
-            "per_op": per_op, "gpu_launches": len(ops) * args.steps, "clocks": clk}
+            "per_op": per_op, "gpu_launches": len(ops) * args.steps, "clocks": clk,
+            "small_launch_reference": ref}
 
 
 # ------------------------------------------------ horizontal representation

@@ -135,6 +135,18 @@ rcg_status rcg_set_dd_solve(rcg_ctx *ctx, int solve);
 #define RCG_SHAPE_PAIR 2
 rcg_status rcg_set_engine_shape(rcg_ctx *ctx, int shape);
 
+/* Kernel for single-operation encode and recovery calls (rcg_encode,
+ * rcg_recover, rcg_recover_many and the host-memory calls built on them) of
+ * small primes.  RCG_COLUMN_AUTO (default): for p <= 7 a column kernel -- a
+ * thread owns a 16-byte column of all p-1 rows of a stripe in registers, Q by
+ * Horner's rule, no shared memory -- whose launches cost one DRAM round trip,
+ * where the tile engine's stages would be tiny (p = 5, 1 KiB rows: 4 KB).
+ * RCG_COLUMN_OFF: always the tile engine.  Results are identical; batches,
+ * the small write and the degraded read always use the tile engine. */
+#define RCG_COLUMN_AUTO 0
+#define RCG_COLUMN_OFF 1
+rcg_status rcg_set_column_kernel(rcg_ctx *ctx, int mode);
+
 /* Synchronise the device and read, then clear, the device status word.
  * Returns RCG_EDEVICE when any bit was set (then *code holds the bits). */
 rcg_status rcg_last_device_status(rcg_ctx *ctx, uint32_t *code);

@@ -67,6 +67,7 @@ struct rcg_ctx {
     int dd_solve = RCG_SOLVE_CHAIN;
     int shape = RCG_SHAPE_AUTO;
     int batch_schedule = RCG_SCHED_DYNAMIC;
+    int column = RCG_COLUMN_AUTO;
     uint64_t next_ticket = 1;
     BatchSlot slots[kBatchRing];
     rcg::HostStaging *host = nullptr;  // staging of the host-memory calls (lazy)
@@ -195,6 +196,18 @@ rcg_status launch_single(rcg_ctx *ctx, const Job &J, const Plan &pl, cudaStream_
     const uint64_t grid = std::min<uint64_t>(
         prm.total_tiles, static_cast<uint64_t>(ctx->sm_count) * shape_info(pl.shape).ctas_per_sm);
     return from_cuda(launch_engine(prm, pl.shape, static_cast<int>(grid), stream));
+}
+
+// The column kernel serves single-operation encode and recovery launches of
+// p <= 7 unless the context asks for the tile engine.
+bool use_column(const rcg_ctx *ctx, const Geo &g) { return ctx->column == RCG_COLUMN_AUTO && g.p <= 7; }
+
+rcg_status launch_column_op(rcg_ctx *ctx, const rcg_layout *L, const Geo &g, uint64_t first, uint64_t n,
+                            uint32_t i, uint32_t j, const uint8_t *pairs, cudaStream_t stream) {
+    DeviceGuard guard(ctx->device);
+    return from_cuda(launch_column(static_cast<uint8_t *>(L->base) + first * g.st, g.p, g.N, g.C, g.rs, g.ss, g.st, n,
+                                   i, j, pairs, ctx->status, ctx->sm_count, stream),
+                     "column kernel launch");
 }
 
 uint64_t now_ns() {
@@ -351,6 +364,7 @@ rcg_status rcg_create(int device, rcg_ctx **out) {
     ctx->sm_count = prop.multiProcessorCount;
     rcg_status st = from_cuda(upload_inverse_tables());
     if (st == RCG_OK) st = from_cuda(upload_h_tables(), "horizontal tables");
+    if (st == RCG_OK) st = from_cuda(upload_column_tables(), "column kernel tables");
     if (st == RCG_OK) st = from_cuda(engine_init_attributes());
     if (st == RCG_OK) st = from_cuda(cudaMalloc(&ctx->status, 256));
     if (st == RCG_OK) st = from_cuda(cudaMemset(ctx->status, 0, 256));
@@ -396,6 +410,12 @@ rcg_status rcg_set_engine_shape(rcg_ctx *ctx, int shape) {
     return RCG_OK;
 }
 
+rcg_status rcg_set_column_kernel(rcg_ctx *ctx, int mode) {
+    if (!ctx || (mode != RCG_COLUMN_AUTO && mode != RCG_COLUMN_OFF)) return RCG_EINVAL;
+    ctx->column = mode;
+    return RCG_OK;
+}
+
 rcg_status rcg_set_batch_schedule(rcg_ctx *ctx, int schedule) {
     if (!ctx || (schedule != RCG_SCHED_STATIC && schedule != RCG_SCHED_DYNAMIC)) return RCG_EINVAL;
     ctx->batch_schedule = schedule;
@@ -435,6 +455,9 @@ rcg_status rcg_encode(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe, 
     if (st) return st;
     if (n_stripes == 0) return RCG_OK;
     if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
+    if (use_column(ctx, g))
+        return launch_column_op(ctx, L, g, first_stripe, n_stripes, g.N, g.N + 1, nullptr,
+                                static_cast<cudaStream_t>(stream));
     Plan pl;
     if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, n_stripes)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, first_stripe, n_stripes, pl);
@@ -450,6 +473,8 @@ rcg_status rcg_recover(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint3
     rcg_status st = check_layout(L, &g);
     if (st) return st;
     if (!(i < j && j <= g.N + 1)) return RCG_EINVAL;
+    if (use_column(ctx, g))
+        return launch_column_op(ctx, L, g, stripe, 1, i, j, nullptr, static_cast<cudaStream_t>(stream));
     Plan pl;
     if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, 1)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, stripe, 1, pl);
@@ -468,6 +493,8 @@ rcg_status rcg_recover_many(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_st
     if (st) return st;
     if (n_stripes == 0) return RCG_OK;
     if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
+    if (use_column(ctx, g))
+        return launch_column_op(ctx, L, g, first_stripe, n_stripes, 0, 0, pairs, static_cast<cudaStream_t>(stream));
     Plan pl;
     if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, n_stripes)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, first_stripe, n_stripes, pl);

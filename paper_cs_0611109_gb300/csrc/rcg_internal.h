@@ -182,6 +182,13 @@ cudaError_t launch_h(uint8_t *base, uint32_t p, uint32_t N, uint64_t strip_bytes
                      uint64_t stripe_stride, uint64_t n_stripes, uint32_t i, uint32_t j, const uint8_t *pairs,
                      uint32_t *status, int sm_count, cudaStream_t stream);
 
+// Column kernel (rcg_column.cu): bit-sliced stripes of p <= 7 without shared
+// memory; same pair convention as launch_h.
+cudaError_t upload_column_tables();
+cudaError_t launch_column(uint8_t *base, uint32_t p, uint32_t N, uint64_t C, uint64_t row_stride,
+                          uint64_t strip_stride, uint64_t stripe_stride, uint64_t n_stripes, uint32_t i, uint32_t j,
+                          const uint8_t *pairs, uint32_t *status, int sm_count, cudaStream_t stream);
+
 // Host: the CUDA device of a context.
 int ctx_device(const rcg_ctx *ctx);
 

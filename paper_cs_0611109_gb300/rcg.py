@@ -22,6 +22,7 @@ RCG_SOLVE_CHAIN, RCG_SOLVE_TABLE = 0, 1
 RCG_NOALLOC_MAX_JOBS = 256
 RCG_SHAPE_AUTO, RCG_SHAPE_WIDE, RCG_SHAPE_PAIR = 0, 1, 2
 RCG_SCHED_STATIC, RCG_SCHED_DYNAMIC = 0, 1
+RCG_COLUMN_AUTO, RCG_COLUMN_OFF = 0, 1
 
 _u32, _u64, _vp, _int = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
 
@@ -111,6 +112,7 @@ EXPORTS = {
     "rcg_inverse_table": (_int, [_u32, ctypes.POINTER(_u64)]),
     "rcg_plan": (_int, [_u32, _u64, ctypes.POINTER(rcg_plan_info)]),
     "rcg_prime_info": (_int, [_u32, ctypes.POINTER(rcg_prime_info_t)]),
+    "rcg_set_column_kernel": (_int, [_vp, _int]),
     "rcg_h_encode": (_int, [_vp, ctypes.POINTER(rcg_hlayout), _u64, _u64, _vp]),
     "rcg_h_recover": (_int, [_vp, ctypes.POINTER(rcg_hlayout), _u64, _u32, _u32, _vp]),
     "rcg_h_recover_many": (_int, [_vp, ctypes.POINTER(rcg_hlayout), _u64, _u64, _vp, _vp]),
@@ -215,6 +217,10 @@ def rcg_set_dd_solve(ctx: int, solve: int):
 
 def rcg_set_engine_shape(ctx: int, shape: int):
     _check(lib().rcg_set_engine_shape(ctx, shape), "rcg_set_engine_shape")
+
+
+def rcg_set_column_kernel(ctx: int, mode: int):
+    _check(lib().rcg_set_column_kernel(ctx, mode), "rcg_set_column_kernel")
 
 
 def rcg_set_host_chunk(ctx: int, nbytes: int):
@@ -495,6 +501,9 @@ class Context:
 
     def set_host_chunk(self, nbytes):
         rcg_set_host_chunk(self.handle, nbytes)
+
+    def set_column_kernel(self, mode):
+        rcg_set_column_kernel(self.handle, mode)
 
     def set_batch_schedule(self, schedule):
         rcg_set_batch_schedule(self.handle, schedule)
