@@ -726,7 +726,9 @@ def run_batched(args):
     if cur:
         waves.append(cur)
 
-    tot = {"batched_ms": 0.0, "per_stripe_ms": 0.0, "user": 0, "moved": 0, "launches_per_stripe": 0}
+    tot = {"batched_ms": 0.0, "default_ms": 0.0, "per_stripe_ms": 0.0, "user": 0, "moved": 0,
+           "launches_per_stripe": 0}
+    tuning = None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for w in waves:
         used = w[-1][1] + align(inputs.stripe_bytes(w[-1][0]["p"], w[-1][0]["n"], w[-1][0]["c"]))
@@ -737,20 +739,31 @@ def run_batched(args):
             assert ctx.batch_wait(ctx.batch_submit(pre))
         mix = [rcg.make_job(L, 0, 1, rcg.RCG_OP_ENCODE) if j["op"] == "encode" else
                rcg.make_job(L, 0, 1, rcg.RCG_OP_RECOVER, j["i"], j["j"]) for L, (j, _) in zip(lays, w)]
-        # host half (validation, tiling, tensor maps, work items): can overlap
-        # the previous batch on the GPU, reported separately
-        h0 = time.perf_counter()
-        prepared = ctx.batch_prepare(mix)
-        tot["prepare_host_ms"] = tot.get("prepare_host_ms", 0.0) + (time.perf_counter() - h0) * 1e3
-        for _ in range(2):  # warm-up (graph capture, descriptor caches)
-            ctx.batch_wait(ctx.batch_launch(prepared))
-        torch.cuda.synchronize()
-        e0.record(stream)
-        t = ctx.batch_launch(prepared)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        rcg.rcg_batch_free(prepared)
-        tot["batched_ms"] += e0.elapsed_time(e1)
+        if tuning is None:
+            # autotune the layout once, on the first wave (the batch itself runs
+            # repeatedly: every op is idempotent on non-overlapping jobs)
+            h0 = time.perf_counter()
+            tuning = ctx.batch_autotune(mix)
+            tot["autotune_s"] = round(time.perf_counter() - h0, 2)
+        for mode in ("default", "tuned"):
+            ctx.set_batch_tuning(None if mode == "default" else tuning)
+            if mode == "default" and args.schedule == "static":
+                ctx.set_batch_schedule(rcg.RCG_SCHED_STATIC)
+            # host half (validation, tiling, tensor maps, work items): can overlap
+            # the previous batch on the GPU, reported separately
+            h0 = time.perf_counter()
+            prepared = ctx.batch_prepare(mix)
+            if mode == "tuned":
+                tot["prepare_host_ms"] = tot.get("prepare_host_ms", 0.0) + (time.perf_counter() - h0) * 1e3
+            for _ in range(2):  # warm-up (graph capture, descriptor caches)
+                ctx.batch_wait(ctx.batch_launch(prepared))
+            torch.cuda.synchronize()
+            e0.record(stream)
+            t = ctx.batch_launch(prepared)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rcg.rcg_batch_free(prepared)
+            tot["batched_ms" if mode == "tuned" else "default_ms"] += e0.elapsed_time(e1)
         e0.record(stream)
         for L, (j, _) in zip(lays, w):
             if j["op"] == "encode":
@@ -769,7 +782,8 @@ def run_batched(args):
         raise RuntimeError("device status word %#x" % status)
     peak, kind = peak_hbm()
     gbs = lambda nbytes, ms: nbytes / (ms * 1e-3) / 1e9
-    out = {"metric": "batched uneven stripes: user GB/s, one persistent launch per wave vs one launch per stripe",
+    out = {"metric": "batched uneven stripes: user GB/s, one persistent launch per wave (autotuned layout) "
+                     "vs the default layout vs one launch per stripe",
            "value": round(gbs(tot["user"], tot["batched_ms"]), 2), "unit": "GB/s", "n_gpus": 1,
            "higher_is_better": True, "dtype": "u8", "data": "synthetic (SplitMix64 bytes, seed 3)",
            "config": {"workload": "batched uneven: %d single-stripe jobs, p in {5,13,29,59}, N in [3,p-1], "
@@ -777,6 +791,10 @@ def run_batched(args):
                       "waves": len(waves), "arena_bytes": arena_bytes, "user_bytes": tot["user"],
                       "schedule": args.schedule,
                       "hbm_bytes": tot["moved"]},
+           "autotune": {"tuning": tuning, "seconds": tot.get("autotune_s"),
+                        "default_layout_ms": round(tot["default_ms"], 3),
+                        "default_layout_user_gbs": round(gbs(tot["user"], tot["default_ms"]), 1),
+                        "default_layout_hbm_frac": round(gbs(tot["moved"], tot["default_ms"]) / peak, 4)},
            "batched": {"ms": round(tot["batched_ms"], 3), "user_gbs": round(gbs(tot["user"], tot["batched_ms"]), 1),
                        "hbm_gbs": round(gbs(tot["moved"], tot["batched_ms"]), 1),
                        "hbm_frac": round(gbs(tot["moved"], tot["batched_ms"]) / peak, 4), "launches": len(waves),

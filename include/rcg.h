@@ -326,6 +326,37 @@ rcg_status rcg_batch_free(rcg_batch *batch);
 #define RCG_SCHED_DYNAMIC 1
 rcg_status rcg_set_batch_schedule(rcg_ctx *ctx, int schedule);
 
+/* Batch tuning (not in the paper).  How rcg_batch_prepare lays a batch out:
+ * the engine shape of the launch, how work items reach the CTAs, the bytes per
+ * work item, and a narrowing of every job's tile (tile_div = 2 or 4 gives
+ * tiles of 1/2 or 1/4 of the widest width the engine allows, so more stages
+ * fit the ring).  Results never depend on the tuning. */
+typedef struct rcg_batch_tuning {
+    uint32_t shape;       /* RCG_SHAPE_AUTO (by the batch's bytes), _WIDE or _PAIR */
+    uint32_t schedule;    /* RCG_SCHED_DYNAMIC or RCG_SCHED_STATIC */
+    uint64_t item_bytes;  /* bytes per work item, >= 64 KB; 0 = 1/16 of a CTA's share, 256 KB..2 MB */
+    uint32_t tile_div;    /* 1 (widest tiles), 2 or 4 */
+    float ms;             /* rcg_batch_autotune: the chosen layout's time for the batch */
+} rcg_batch_tuning;
+
+/* Autotune the batch layout on a real job list: runs the batch under the
+ * current tuning and under candidate values of each knob in turn (engine
+ * shape; schedule; item bytes 256 KB / 1 MB / 4 MB / default; tile_div
+ * 1 / 2 / 4), each once untimed and twice timed with CUDA events on `stream`,
+ * keeps the fastest value of each knob, applies the result to the context
+ * (later batches use it) and returns it.  The jobs run for real, about 30
+ * times: every batch operation is idempotent on jobs that do not overlap in
+ * memory (encode rewrites P and Q from the data, a recovery rewrites the same
+ * bytes into the strips it never reads, a small write's second run changes
+ * nothing, a degraded read rewrites its output), so the results are those of
+ * one run.  Synchronous: returns when the timing is done. */
+rcg_status rcg_batch_autotune(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, void *stream,
+                              rcg_batch_tuning *out);
+
+/* Apply a tuning (e.g. one saved from an earlier rcg_batch_autotune on the
+ * same GPU model); NULL restores the defaults. */
+rcg_status rcg_set_batch_tuning(rcg_ctx *ctx, const rcg_batch_tuning *tuning);
+
 /* Wait at most timeout_ns for batch `ticket`; RCG_ETIMEOUT if it has not
  * finished (the batch keeps running). */
 rcg_status rcg_batch_wait(rcg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns);

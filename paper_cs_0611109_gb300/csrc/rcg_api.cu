@@ -68,6 +68,10 @@ struct rcg_ctx {
     int shape = RCG_SHAPE_AUTO;
     int batch_schedule = RCG_SCHED_DYNAMIC;
     int column = RCG_COLUMN_AUTO;
+    // batch tuning (rcg_batch_autotune / rcg_set_batch_tuning)
+    int tune_shape = RCG_SHAPE_AUTO;  // engine shape of batches; AUTO = the size rule
+    uint64_t tune_item_bytes = 0;     // work-item size; 0 = the rule in build_table
+    uint32_t tune_tile_div = 1;       // narrower tiles than the widest allowed
     uint64_t next_ticket = 1;
     BatchSlot slots[kBatchRing];
     rcg::HostStaging *host = nullptr;  // staging of the host-memory calls (lazy)
@@ -248,8 +252,8 @@ void free_slot(BatchSlot &s) {
 
 // ====================================================================== plan
 
-bool rcg::make_plan(uint32_t p, uint64_t C, uint32_t shape, Plan *out) {
-    if (!is_odd_prime(p) || p > static_cast<uint32_t>(kMaxP) || C == 0 || (C & 15)) return false;
+bool rcg::make_plan(uint32_t p, uint64_t C, uint32_t shape, Plan *out, uint32_t tile_div) {
+    if (!is_odd_prime(p) || p > static_cast<uint32_t>(kMaxP) || C == 0 || (C & 15) || tile_div == 0) return false;
     const ShapeInfo si = shape_info(shape);
     const uint64_t nvec_total = C / 16;
     uint64_t nvec_max = si.max_items / p;                                  // items per tile
@@ -257,6 +261,7 @@ bool rcg::make_plan(uint32_t p, uint64_t C, uint32_t shape, Plan *out) {
     nvec_max = std::min<uint64_t>(nvec_max, kMaxTileBytes / 16);           // TMA box row
     nvec_max = std::min<uint64_t>(nvec_max, si.ring_bytes / si.min_slots / ((p - 1) * 16ull));
     if (nvec_max == 0) return false;
+    nvec_max = std::max<uint64_t>(1, nvec_max / tile_div);
     for (;;) {
         const uint64_t tiles = (nvec_total + nvec_max - 1) / nvec_max;
         if (tiles > 0xffffffffull) return false;
@@ -597,7 +602,7 @@ static rcg_status build_job(const rcg_ctx *ctx, const rcg_job &in, uint32_t shap
     rcg_status st = check_layout(&in.layout, &g);
     if (st) return st;
     if (in.n_stripes == 0 || in.n_stripes > 0x7fffffffull) return RCG_EINVAL;
-    if (!make_plan(g.p, g.C, shape, pl)) return RCG_EINVAL;
+    if (!make_plan(g.p, g.C, shape, pl, ctx->tune_tile_div)) return RCG_EINVAL;
     Job J = base_job(ctx, &in.layout, g, in.first_stripe, in.n_stripes, *pl);
     const uint64_t ars = in.aux_row_stride ? in.aux_row_stride : g.C;
     const uint64_t ass = in.aux_stripe_stride ? in.aux_stripe_stride : (g.p - 1) * ars;
@@ -700,6 +705,8 @@ static rcg_status prepare_slot(rcg_ctx *ctx, BatchSlot &s, size_t bytes, uint32_
 // One engine shape for a whole batch: the context's explicit choice, else
 // by the batch's total traffic.
 static uint32_t batch_shape(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs) {
+    if (ctx->tune_shape == RCG_SHAPE_WIDE) return SHAPE_WIDE;
+    if (ctx->tune_shape == RCG_SHAPE_PAIR) return SHAPE_PAIR;
     uint64_t bytes = 0;
     for (uint32_t k = 0; k < n_jobs; ++k) {
         Geo g;
@@ -733,7 +740,9 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     for (uint32_t k = 0; k < n_jobs; ++k)
         batch_bytes += static_cast<uint64_t>(table[k].n_stripes) * (table[k].n + 2u) * (table[k].p - 1u) * table[k].C;
     const uint64_t ctas = static_cast<uint64_t>(ctx->sm_count ? ctx->sm_count : 152) * shape_info(shape).ctas_per_sm;
-    const uint64_t target = std::min<uint64_t>(2ull << 20, std::max<uint64_t>(256ull << 10, batch_bytes / (ctas * 16)));
+    const uint64_t target = ctx->tune_item_bytes
+                                ? ctx->tune_item_bytes
+                                : std::min<uint64_t>(2ull << 20, std::max<uint64_t>(256ull << 10, batch_bytes / (ctas * 16)));
     std::vector<uint64_t> per(n_jobs);
     uint64_t n_items_est = 0;
     for (uint32_t k = 0; k < n_jobs; ++k) {
@@ -893,6 +902,109 @@ rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, 
     st = rcg_batch_launch(ctx, b, stream, ticket);
     rcg_batch_free(b);
     return st;
+}
+
+rcg_status rcg_set_batch_tuning(rcg_ctx *ctx, const rcg_batch_tuning *t) {
+    if (!ctx) return RCG_EINVAL;
+    if (!t) {
+        ctx->tune_shape = RCG_SHAPE_AUTO;
+        ctx->batch_schedule = RCG_SCHED_DYNAMIC;
+        ctx->tune_item_bytes = 0;
+        ctx->tune_tile_div = 1;
+        return RCG_OK;
+    }
+    if ((t->shape != RCG_SHAPE_AUTO && t->shape != RCG_SHAPE_WIDE && t->shape != RCG_SHAPE_PAIR) ||
+        (t->schedule != RCG_SCHED_STATIC && t->schedule != RCG_SCHED_DYNAMIC) ||
+        (t->item_bytes != 0 && t->item_bytes < (64u << 10)) || t->tile_div < 1 || t->tile_div > 8)
+        return RCG_EINVAL;
+    ctx->tune_shape = static_cast<int>(t->shape);
+    ctx->batch_schedule = static_cast<int>(t->schedule);
+    ctx->tune_item_bytes = t->item_bytes;
+    ctx->tune_tile_div = t->tile_div;
+    return RCG_OK;
+}
+
+// Time one configuration: prepare under the context's current tuning, then
+// one untimed and `reps` timed launches (CUDA events on `stream`); the best.
+static rcg_status time_batch(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, cudaStream_t stream, int reps,
+                             cudaEvent_t e0, cudaEvent_t e1, float *best_ms) {
+    rcg_batch *b = nullptr;
+    rcg_status st = rcg_batch_prepare(ctx, jobs, n_jobs, &b);
+    if (st) return st;
+    float best = -1.0f;
+    for (int r = 0; r <= reps && st == RCG_OK; ++r) {
+        uint64_t ticket = 0;
+        cudaError_t e = cudaEventRecord(e0, stream);
+        if (e == cudaSuccess) st = rcg_batch_launch(ctx, b, stream, &ticket);
+        if (st == RCG_OK && e == cudaSuccess) e = cudaEventRecord(e1, stream);
+        if (st == RCG_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (st == RCG_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) st = from_cuda(e, "autotune timing");
+        if (st == RCG_OK && r > 0 && (best < 0.0f || ms < best)) best = ms;
+    }
+    rcg_batch_free(b);
+    *best_ms = best;
+    return st;
+}
+
+rcg_status rcg_batch_autotune(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, void *stream,
+                              rcg_batch_tuning *out) {
+    if (!ctx || !jobs || n_jobs == 0 || !out) return RCG_EINVAL;
+    for (uint32_t k = 0; k < n_jobs; ++k) {  // timing relaunches the batch: only idempotent ops
+        Geo g;
+        if (check_layout(&jobs[k].layout, &g) != RCG_OK) return RCG_EINVAL;
+    }
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return RCG_ECUDA;
+    }
+    rcg_batch_tuning cur;
+    cur.shape = static_cast<uint32_t>(ctx->tune_shape);
+    cur.schedule = static_cast<uint32_t>(ctx->batch_schedule);
+    cur.item_bytes = ctx->tune_item_bytes;
+    cur.tile_div = ctx->tune_tile_div;
+    cur.ms = 0.0f;
+    rcg_status st = rcg_set_batch_tuning(ctx, &cur);
+    float best_ms = -1.0f;
+    if (st == RCG_OK) st = time_batch(ctx, jobs, n_jobs, s, 2, e0, e1, &best_ms);
+    // coordinate descent: one knob at a time, keeping the best value of each
+    const uint32_t shapes[] = {RCG_SHAPE_WIDE, RCG_SHAPE_PAIR};
+    const uint32_t schedules[] = {RCG_SCHED_DYNAMIC, RCG_SCHED_STATIC};
+    const uint64_t items[] = {0, 256ull << 10, 1ull << 20, 4ull << 20};
+    const uint32_t divs[] = {1, 2, 4};
+    for (int knob = 0; knob < 4 && st == RCG_OK; ++knob) {
+        const int n_vals = knob == 0 ? 2 : knob == 1 ? 2 : knob == 2 ? 4 : 3;
+        for (int v = 0; v < n_vals && st == RCG_OK; ++v) {
+            rcg_batch_tuning cand = cur;
+            if (knob == 0) cand.shape = shapes[v];
+            if (knob == 1) cand.schedule = schedules[v];
+            if (knob == 2) cand.item_bytes = items[v];
+            if (knob == 3) cand.tile_div = divs[v];
+            if (memcmp(&cand, &cur, sizeof(cand)) == 0) continue;
+            st = rcg_set_batch_tuning(ctx, &cand);
+            float ms = -1.0f;
+            if (st == RCG_OK) st = time_batch(ctx, jobs, n_jobs, s, 2, e0, e1, &ms);
+            if (st == RCG_EINVAL) {  // a plan that does not fit this shape: skip it
+                st = RCG_OK;
+                continue;
+            }
+            if (st == RCG_OK && ms >= 0.0f && (best_ms < 0.0f || ms < best_ms)) {
+                best_ms = ms;
+                cur = cand;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cur.ms = best_ms;
+    const rcg_status st2 = rcg_set_batch_tuning(ctx, &cur);  // apply the best
+    if (st) return st;
+    *out = cur;
+    return st2;
 }
 
 rcg_status rcg_batch_wait(rcg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns) {

@@ -148,7 +148,9 @@ struct Plan {
 };
 
 // Host: tiling for one (p, C) on one engine shape.  Returns false when out of range.
-bool make_plan(uint32_t p, uint64_t C, uint32_t shape, Plan *out);
+// tile_div > 1 narrows the widest tile the constraints allow by that factor
+// (a batch autotuning knob).
+bool make_plan(uint32_t p, uint64_t C, uint32_t shape, Plan *out, uint32_t tile_div = 1);
 
 // Host: upload the per-p inverse tables to the current device (once).
 cudaError_t upload_inverse_tables();

@@ -71,6 +71,11 @@ class rcg_hlayout(ctypes.Structure):
                 ("strip_stride", _u64), ("stripe_stride", _u64)]
 
 
+class rcg_batch_tuning(ctypes.Structure):
+    _fields_ = [("shape", _u32), ("schedule", _u32), ("item_bytes", _u64), ("tile_div", _u32),
+                ("ms", ctypes.c_float)]
+
+
 class rcg_prime_info_t(ctypes.Structure):
     _fields_ = [("ord2", _u32), ("is_field", _u32), ("extends", _u32), ("max_data", _u32)]
 
@@ -113,6 +118,8 @@ EXPORTS = {
     "rcg_plan": (_int, [_u32, _u64, ctypes.POINTER(rcg_plan_info)]),
     "rcg_prime_info": (_int, [_u32, ctypes.POINTER(rcg_prime_info_t)]),
     "rcg_set_column_kernel": (_int, [_vp, _int]),
+    "rcg_batch_autotune": (_int, [_vp, _vp, _u32, _vp, ctypes.POINTER(rcg_batch_tuning)]),
+    "rcg_set_batch_tuning": (_int, [_vp, ctypes.POINTER(rcg_batch_tuning)]),
     "rcg_h_encode": (_int, [_vp, ctypes.POINTER(rcg_hlayout), _u64, _u64, _vp]),
     "rcg_h_recover": (_int, [_vp, ctypes.POINTER(rcg_hlayout), _u64, _u32, _u32, _vp]),
     "rcg_h_recover_many": (_int, [_vp, ctypes.POINTER(rcg_hlayout), _u64, _u64, _vp, _vp]),
@@ -217,6 +224,53 @@ def rcg_set_dd_solve(ctx: int, solve: int):
 
 def rcg_set_engine_shape(ctx: int, shape: int):
     _check(lib().rcg_set_engine_shape(ctx, shape), "rcg_set_engine_shape")
+
+
+def rcg_batch_autotune(ctx: int, jobs, stream=None) -> dict:
+    """Tune the batch layout on a real job list (see include/rcg.h) and apply it."""
+    arr = (rcg_job * len(jobs))(*jobs)
+    t = rcg_batch_tuning()
+    _check(lib().rcg_batch_autotune(ctx, arr, len(jobs), _stream(stream), ctypes.byref(t)), "rcg_batch_autotune")
+    return {f: (float(getattr(t, f)) if f == "ms" else int(getattr(t, f))) for f, _ in rcg_batch_tuning._fields_}
+
+
+def rcg_set_batch_tuning(ctx: int, tuning: dict | None):
+    if tuning is None:
+        _check(lib().rcg_set_batch_tuning(ctx, None), "rcg_set_batch_tuning")
+        return
+    t = rcg_batch_tuning(tuning["shape"], tuning["schedule"], tuning["item_bytes"], tuning["tile_div"],
+                         tuning.get("ms", 0.0))
+    _check(lib().rcg_set_batch_tuning(ctx, ctypes.byref(t)), "rcg_set_batch_tuning")
+
+
+def tuning_key(device: int = 0) -> str:
+    """Cache key of a tuning: the GPU model and its SM count."""
+    import torch
+    prop = torch.cuda.get_device_properties(device)
+    return "%s/%d" % (prop.name, prop.multi_processor_count)
+
+
+def save_tuning(path: str, tuning: dict, device: int = 0):
+    """Store a tuning in a JSON file under this GPU's key (other keys kept)."""
+    import json
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    cache[tuning_key(device)] = tuning
+    with open(path, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+
+
+def load_tuning(path: str, device: int = 0) -> dict | None:
+    """The tuning stored for this GPU's key, or None."""
+    import json
+    try:
+        with open(path) as f:
+            return json.load(f).get(tuning_key(device))
+    except (OSError, ValueError):
+        return None
 
 
 def rcg_set_column_kernel(ctx: int, mode: int):
@@ -501,6 +555,12 @@ class Context:
 
     def set_host_chunk(self, nbytes):
         rcg_set_host_chunk(self.handle, nbytes)
+
+    def batch_autotune(self, jobs, stream=None) -> dict:
+        return rcg_batch_autotune(self.handle, jobs, stream)
+
+    def set_batch_tuning(self, tuning):
+        rcg_set_batch_tuning(self.handle, tuning)
 
     def set_column_kernel(self, mode):
         rcg_set_column_kernel(self.handle, mode)
