@@ -268,6 +268,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=15.0)
+        out["cpu_word_level"] = cpu_word_level()
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
@@ -275,12 +276,11 @@ def run_ours(args):
 
 
 def kernel_hash():
-    """Hash of the tile engine's sources: DRAM counters taken on another
+    """Hash of the tile engine's source file: DRAM counters taken on another
     version of the kernel are not reported."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("rcg_engine.cu", "rcg_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_cs_0611109_gb300", "csrc", f), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_cs_0611109_gb300", "csrc", "rcg_engine.cu"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -418,6 +418,26 @@ def cpu_baseline(budget_s=15.0):
     return {"value": round(ub / t / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": "%d of the 8192 stripes, the full 5-op step (encode + DD/DP/DQ/PQ), "
                       "single-threaded bit-level C oracle, %.1f s" % (n, t)}
+
+
+def cpu_word_level(stripes=512):
+    """O2, the word-level multi-threaded CPU implementation of the oracle/
+    directory, on all host cores: the full 5-op step on a sample of stripes."""
+    import numpy as np
+
+    import oracle
+    from paper_cs_0611109_gb300 import inputs
+    oracle.build_o2()
+    host = np.ascontiguousarray(inputs.random_stripes(SEED, P, N, C, stripes))
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    oracle.o2_encode(P, N, C, host, stripes, threads=cores)
+    for n, k in enumerate(CLASSES):
+        oracle.o2_recover(P, N, C, host, stripes, pairs=inputs.random_pairs(20 + n, N, stripes, k), threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": round(5 * user_bytes_per_op(stripes) / dt / 1e9, 3), "unit": "GB/s", "cores": cores,
+            "kind": "word-level C (oracle/rcg_o2.c, pthreads), context only",
+            "sample": "%d of the 8192 stripes, the full 5-op step, %.2f s" % (stripes, dt)}
 
 
 def run_reference(args):

@@ -15,6 +15,13 @@ with optional explicit byte strides.
 
 Parity pins: every function here is checked against facts the paper and the
 mathematics fix (tests/test_oracle_pins.py); no function is unpinned.
+
+``rcg_o2.c`` ("O2") is a second, word-level and multi-threaded CPU
+implementation of the same code (64 codewords per machine word, inverses by
+Gaussian elimination), bound below as ``o2_encode`` / ``o2_recover``.  It is
+fast enough to check full-size GPU results byte for byte; it is pinned to the
+bit-level functions above (tests/test_oracle_o2.py) and shares no code with
+them or with the product.
 """
 from __future__ import annotations
 
@@ -227,3 +234,64 @@ def h_recover(p, N, strip_bytes, buf, n_stripes, i=0, j=1, pairs=None, strip_str
     rc = lib().oracle_h_recover(p, N, strip_bytes, _ptr(buf), n_stripes, ss, st, i, j, pp)
     if rc:
         raise ValueError("oracle_h_recover: invalid arguments (rc=%d)" % rc)
+
+
+# ------------------------------------------------------- O2 (word-level)
+
+_O2_SRC = os.path.join(_HERE, "rcg_o2.c")
+_O2_LIB = os.path.join(_HERE, "_build", "librcg_o2.so")
+_o2: ctypes.CDLL | None = None
+
+
+def build_o2(src: str = _O2_SRC, out: str = _O2_LIB) -> str:
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if (not os.path.exists(out)) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread", "-o", tmp, src])
+        os.replace(tmp, out)
+    return out
+
+
+def o2() -> ctypes.CDLL:
+    global _o2
+    if _o2 is None:
+        L = ctypes.CDLL(build_o2())
+        L.o2_encode.restype = ctypes.c_int
+        L.o2_encode.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _u64, ctypes.c_int]
+        L.o2_recover.restype = ctypes.c_int
+        L.o2_recover.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _u64, _uint, _uint, _vp, ctypes.c_int]
+        L.o2_inverse.restype = _u64
+        L.o2_inverse.argtypes = [_uint, _u64]
+        _o2 = L
+    return _o2
+
+
+def _threads(threads):
+    return threads or os.cpu_count() or 1
+
+
+def o2_encode(p, N, C, buf, n_stripes, row_stride=None, strip_stride=None, stripe_stride=None, threads=None):
+    """Word-level encode (Corollary 3.2.4 / qext) of n_stripes stripes in place; C % 8 == 0."""
+    _check_buf(buf)
+    rs, ss, st = _strides(p, N, C, row_stride, strip_stride, stripe_stride)
+    rc = o2().o2_encode(p, N, C, _ptr(buf), n_stripes, rs, ss, st, _threads(threads))
+    if rc:
+        raise ValueError("o2_encode: invalid arguments (rc=%d)" % rc)
+
+
+def o2_recover(p, N, C, buf, n_stripes, i=0, j=1, pairs=None, row_stride=None, strip_stride=None,
+               stripe_stride=None, threads=None):
+    """Word-level recovery (Lemma 3.1.2) of pair (i, j) or per-stripe pairs, in place."""
+    _check_buf(buf)
+    rs, ss, st = _strides(p, N, C, row_stride, strip_stride, stripe_stride)
+    pp = None
+    if pairs is not None:
+        pairs = np.ascontiguousarray(pairs, dtype=np.uint8)
+        pp = _ptr(pairs)
+    rc = o2().o2_recover(p, N, C, _ptr(buf), n_stripes, rs, ss, st, i, j, pp, _threads(threads))
+    if rc:
+        raise ValueError("o2_recover: invalid arguments (rc=%d)" % rc)
+
+
+def o2_inverse(p: int, a: int) -> int:
+    return int(o2().o2_inverse(p, a))

@@ -1,0 +1,292 @@
+/*
+ * rcg_o2.c -- word-level, multi-threaded CPU implementation of the cyclic-group
+ * RAID-6 code (the "O2" reference), for checking full-size GPU results byte
+ * for byte and for a CPU throughput figure.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite and the benchmark's CPU legs
+ * load this file.  It shares no code, table or helper with the CUDA path or
+ * with rcg_oracle.c; the tests check it against rcg_oracle.c (the bit-level
+ * definition).
+ *
+ * What it computes.  The same code as rcg_oracle.c (Corollary 3.2.4 with data
+ * strip k weighted by x^k, and 1 + x^(k-p+1) for k >= p per equation (qext) of
+ * Section 3.3; recovery by the four cases of Lemma 3.1.2), on the same
+ * bit-sliced stripes.  Where rcg_oracle.c gathers one codeword at a time, this
+ * file works on 64 codewords at once: a 64-bit word of row r holds the x^r
+ * coefficients of 64 codewords, so multiplying by x^k is moving whole words
+ * between rows.  Elements are held lifted to F2[x]/(x^p - 1) (p rows, row
+ * p-1 starting at zero); multiplication by x^k is the cyclic row shift
+ * (Lemma 3.4.1's (powers): S_p^k acts on the lift as a rotation), and the
+ * residue modulo f = 1 + ... + x^(p-1) is row r XOR row p-1.  Inverses are
+ * found by Gaussian elimination over GF(2) on the (p-1) x (p-1) matrix of
+ * multiplication by the element (a third method: the library uses Frobenius
+ * powers, rcg_oracle.c the extended Euclidean algorithm).
+ *
+ * Layout: stripe s at buf + s*stripe_stride, strip k at + k*strip_stride, row
+ * r at + r*row_stride, C bytes per row (C a multiple of 8 here: every row is
+ * processed as C/8 words).  Stripes are split across threads.
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef uint64_t u64;
+
+#define O2_MAXP 61
+#define O2_MAXN 121
+
+/* ------------------------------------------------------ ring elements */
+
+/* Element of R as a bit mask (bit m = coefficient of x^m, m < p-1). */
+static u64 weight(unsigned p, unsigned k)
+{
+    unsigned e = k < p ? k : k - p + 1;
+    u64 lifted = (k < p ? 0 : 1u) ^ (1ull << e);   /* x^e (+ 1), exponents < p */
+    if (lifted >> (p - 1) & 1)                     /* x^(p-1) = 1 + ... + x^(p-2) */
+        lifted ^= (1ull << p) - 1;
+    return lifted;
+}
+
+/* Product a*b in R by the multiplication matrix's columns: column c of the
+ * matrix of "multiply by a" is a * x^c. */
+static u64 mul_xc(unsigned p, u64 a, unsigned c)
+{
+    /* rotate the lifted p-bit vector by c, then reduce */
+    u64 full = (1ull << p) - 1;
+    u64 r = ((a << c) | (a >> (p - c))) & full;
+    if (c == 0)
+        r = a;
+    if (r >> (p - 1) & 1)
+        r ^= full;
+    return r;
+}
+
+/* Inverse of a in R by Gaussian elimination on [M | I], M the matrix of
+ * multiplication by a (columns a * x^c).  Returns 0 when a is singular. */
+static u64 inverse(unsigned p, u64 a)
+{
+    unsigned n = p - 1;
+    u64 rows[O2_MAXP];     /* row i of M, bit c = entry (i, c) */
+    u64 aug[O2_MAXP];      /* row i of the identity being transformed */
+    for (unsigned i = 0; i < n; i++) {
+        rows[i] = 0;
+        aug[i] = 1ull << i;
+    }
+    for (unsigned c = 0; c < n; c++) {
+        u64 col = mul_xc(p, a, c);
+        for (unsigned i = 0; i < n; i++)
+            if (col >> i & 1)
+                rows[i] |= 1ull << c;
+    }
+    for (unsigned c = 0; c < n; c++) {
+        unsigned piv = n;
+        for (unsigned i = c; i < n; i++)
+            if (rows[i] >> c & 1) {
+                piv = i;
+                break;
+            }
+        if (piv == n)
+            return 0;
+        u64 t = rows[c]; rows[c] = rows[piv]; rows[piv] = t;
+        t = aug[c]; aug[c] = aug[piv]; aug[piv] = t;
+        for (unsigned i = 0; i < n; i++)
+            if (i != c && (rows[i] >> c & 1)) {
+                rows[i] ^= rows[c];
+                aug[i] ^= aug[c];
+            }
+    }
+    /* M^(-1) = the transformed identity; the inverse element is M^(-1) e_0,
+     * i.e. column 0 of M^(-1): bit i of it is bit 0 of row i */
+    u64 inv = 0;
+    for (unsigned i = 0; i < n; i++)
+        if (aug[i] & 1)
+            inv |= 1ull << i;
+    return inv;
+}
+
+/* ------------------------------------------------------------ word rows */
+
+typedef struct {
+    uint8_t *buf;
+    unsigned p, N;
+    u64 C, rs, ss, st;
+} geo_t;
+
+static u64 *rowp(const geo_t *g, u64 s, unsigned k, unsigned r)
+{
+    return (u64 *)(g->buf + s * g->st + (u64)k * g->ss + (u64)r * g->rs);
+}
+
+/* acc (lifted, p words) += x^e * v (p-1 words; the lifted row p-1 of v is 0) */
+static void add_rot(unsigned p, u64 *acc, const u64 *v, unsigned e)
+{
+    for (unsigned r = 0; r + 1 < p; r++)
+        acc[(r + e) % p] ^= v[r];
+}
+
+/* acc += w * v, w a mask in R (bits < p-1), v lifted (p words) */
+static void add_mul(unsigned p, u64 *acc, const u64 *v, u64 w)
+{
+    for (unsigned m = 0; m + 1 < p; m++)
+        if (w >> m & 1)
+            for (unsigned r = 0; r < p; r++)
+                acc[(r + m) % p] ^= v[r];
+}
+
+/* ---------------------------------------------------- one stripe, one word */
+
+/* Encode or recover word column w of stripe s.  (i, j) = (N, N+1) encodes. */
+static void stripe_word(const geo_t *g, u64 s, u64 w, unsigned i, unsigned j, const u64 *inv_w,
+                        const u64 (*inv_pair)[O2_MAXN])
+{
+    unsigned p = g->p, N = g->N;
+    u64 dP[O2_MAXP] = {0}, dQ[O2_MAXP] = {0}, d[O2_MAXP];
+    for (unsigned k = 0; k < N + 2; k++) {
+        if (k == i || k == j)
+            continue;
+        for (unsigned r = 0; r + 1 < p; r++)
+            d[r] = rowp(g, s, k, r)[w];
+        if (k < N) {
+            for (unsigned r = 0; r + 1 < p; r++)
+                dP[r] ^= d[r];
+            if (k < p) {
+                add_rot(p, dQ, d, k);
+            } else {
+                add_rot(p, dQ, d, 0);
+                add_rot(p, dQ, d, k - p + 1);
+            }
+        } else if (k == N) {
+            for (unsigned r = 0; r + 1 < p; r++)
+                dP[r] ^= d[r];
+        } else {
+            add_rot(p, dQ, d, 0);
+        }
+    }
+    u64 out[O2_MAXP] = {0}, t[O2_MAXP] = {0};
+    if (i == N) {                                  /* P and Q */
+        for (unsigned r = 0; r + 1 < p; r++) {
+            rowp(g, s, N, r)[w] = dP[r];
+            rowp(g, s, N + 1, r)[w] = dQ[r] ^ dQ[p - 1];
+        }
+        return;
+    }
+    if (j == N + 1) {                              /* data i and Q: RAID-5, then Q */
+        add_mul(p, dQ, dP, weight(p, i));          /* dP's lifted row p-1 is 0 */
+        for (unsigned r = 0; r + 1 < p; r++) {
+            rowp(g, s, i, r)[w] = dP[r];
+            rowp(g, s, N + 1, r)[w] = dQ[r] ^ dQ[p - 1];
+        }
+        return;
+    }
+    if (j == N) {                                  /* data i and P: w_i D_i = dQ */
+        add_mul(p, out, dQ, inv_w[i]);
+        for (unsigned r = 0; r + 1 < p; r++) {
+            u64 di = out[r] ^ out[p - 1];
+            rowp(g, s, i, r)[w] = di;
+            rowp(g, s, N, r)[w] = dP[r] ^ di;
+        }
+        return;
+    }
+    /* two data strips: (w_i + w_j) D_j = w_i dP + dQ, D_i = D_j + dP */
+    memcpy(t, dQ, sizeof(u64) * p);
+    add_mul(p, t, dP, weight(p, i));
+    add_mul(p, out, t, inv_pair[i][j]);
+    for (unsigned r = 0; r + 1 < p; r++) {
+        u64 dj = out[r] ^ out[p - 1];
+        rowp(g, s, j, r)[w] = dj;
+        rowp(g, s, i, r)[w] = dj ^ dP[r];
+    }
+}
+
+/* ------------------------------------------------------------- threads */
+
+typedef struct {
+    const geo_t *g;
+    u64 s0, s1;
+    unsigned i, j;
+    const uint8_t *pairs;
+    const u64 *inv_w;
+    const u64 (*inv_pair)[O2_MAXN];
+    int bad;
+} work_t;
+
+static void *worker(void *arg)
+{
+    work_t *wk = (work_t *)arg;
+    const geo_t *g = wk->g;
+    for (u64 s = wk->s0; s < wk->s1; s++) {
+        unsigned i = wk->pairs ? wk->pairs[2 * s] : wk->i;
+        unsigned j = wk->pairs ? wk->pairs[2 * s + 1] : wk->j;
+        if (!(i < j && j <= g->N + 1)) {
+            wk->bad = 1;
+            continue;
+        }
+        for (u64 w = 0; w < g->C / 8; w++)
+            stripe_word(g, s, w, i, j, wk->inv_w, wk->inv_pair);
+    }
+    return NULL;
+}
+
+static int run(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes, u64 rs, u64 ss, u64 st,
+               unsigned i, unsigned j, const uint8_t *pairs, int threads)
+{
+    if (p < 3 || p > O2_MAXP || N < 1 || N > 2 * p - 1 || N > O2_MAXN || C == 0 || C % 8)
+        return -1;
+    for (unsigned t = 2; t * t <= p; t++)
+        if (p % t == 0)
+            return -1;
+    static u64 inv_w[O2_MAXN];
+    static u64 inv_pair[O2_MAXN][O2_MAXN];
+    for (unsigned a = 0; a < N; a++) {
+        inv_w[a] = inverse(p, weight(p, a));
+        for (unsigned b = a + 1; b < N; b++) {
+            inv_pair[a][b] = inverse(p, weight(p, a) ^ weight(p, b));
+            if (inv_pair[a][b] == 0)
+                return -3;   /* the weights are not a cone for this p and N */
+        }
+    }
+    geo_t g = {buf, p, N, C, rs, ss, st};
+    if (threads < 1)
+        threads = 1;
+    if (threads > 256)
+        threads = 256;
+    pthread_t tid[256];
+    work_t wk[256];
+    for (int t = 0; t < threads; t++) {
+        wk[t].g = &g;
+        wk[t].s0 = n_stripes * t / threads;
+        wk[t].s1 = n_stripes * (t + 1) / threads;
+        wk[t].i = i;
+        wk[t].j = j;
+        wk[t].pairs = pairs;
+        wk[t].inv_w = inv_w;
+        wk[t].inv_pair = (const u64 (*)[O2_MAXN])inv_pair;
+        wk[t].bad = 0;
+        pthread_create(&tid[t], NULL, worker, &wk[t]);
+    }
+    int bad = 0;
+    for (int t = 0; t < threads; t++) {
+        pthread_join(tid[t], NULL);
+        bad |= wk[t].bad;
+    }
+    return bad ? -2 : 0;
+}
+
+int o2_encode(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes, u64 rs, u64 ss, u64 st, int threads)
+{
+    return run(p, N, C, buf, n_stripes, rs, ss, st, N, N + 1, NULL, threads);
+}
+
+/* Recover pair (i, j), or per-stripe pairs (two bytes per stripe) when pairs != NULL. */
+int o2_recover(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes, u64 rs, u64 ss, u64 st,
+               unsigned i, unsigned j, const uint8_t *pairs, int threads)
+{
+    return run(p, N, C, buf, n_stripes, rs, ss, st, i, j, pairs, threads);
+}
+
+/* The inverse of a in R (bit mask), 0 when singular -- exposed for the tests. */
+u64 o2_inverse(unsigned p, u64 a)
+{
+    return inverse(p, a);
+}

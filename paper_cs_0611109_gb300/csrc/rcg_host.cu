@@ -3,12 +3,13 @@
 // buffers in chunks of stripes, on three internal streams, so the upload of
 // one chunk, the tile engine on another and the download of a third overlap.
 //
-//   encode:   data strips in  -> rcg_encode on the chunk -> P and Q strips out
-//   recovery: the N surviving strips of each stripe in (a gather kernel reads
-//             them from the host stripes through their device-visible
-//             (mapped) addresses; the erased strips are never moved) ->
-//             rcg_recover_many on the chunk -> a small kernel writes the two
-//             rebuilt strips of each stripe straight back into the host stripes.
+//   encode:   the data strips in -> rcg_encode on the chunk -> P and Q out
+//   recovery: the N surviving strips of each stripe in (the erased strips are
+//             never moved) -> rcg_recover_many on the chunk -> the two rebuilt
+//             strips out.
+// A gather kernel reads the strips from the host stripes through their
+// device-visible (mapped) addresses and a write-back kernel writes the results
+// straight into them.
 // The host link, not HBM, bounds this path (about 211 GB/s host to device on
 // GB300, the same for copy engines and for kernel loads), so what counts is
 // the bytes that cross it: N strips in and 2 out per stripe.
@@ -34,13 +35,13 @@ namespace {
 // skipped those stripes) are skipped here too.
 __global__ void writeback_kernel(const uint8_t *chunk, uint64_t chunk_stripe_bytes, uint64_t strip_bytes,
                                  uint8_t *host_dev, uint64_t h_row, uint64_t h_strip, uint64_t h_stripe,
-                                 const uint8_t *pairs, uint32_t n_stripes, uint32_t rows, uint32_t nvec,
-                                 uint32_t n_total) {
+                                 const uint8_t *pairs, uint32_t fi, uint32_t fj, uint32_t n_stripes,
+                                 uint32_t rows, uint32_t nvec, uint32_t n_total) {
     const uint64_t units = 2ull * n_stripes;
     const uint32_t row_bytes = nvec * 16;
     for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const uint32_t s = static_cast<uint32_t>(u >> 1);
-        const uint32_t a = pairs[2ull * s], b = pairs[2ull * s + 1];
+        const uint32_t a = pairs ? pairs[2ull * s] : fi, b = pairs ? pairs[2ull * s + 1] : fj;
         if (!(a < b && b <= n_total + 1)) continue;
         const uint32_t k = (u & 1) ? b : a;
         const uint8_t *src = chunk + s * chunk_stripe_bytes + k * strip_bytes;
@@ -71,14 +72,14 @@ constexpr int GATHER_UNROLL = 8;
 
 __global__ void gather_kernel(const uint8_t *host_dev, uint64_t h_row, uint64_t h_strip, uint64_t h_stripe,
                               uint8_t *chunk, uint64_t chunk_stripe_bytes, uint64_t strip_bytes,
-                              const uint8_t *pairs, uint32_t n_stripes, uint32_t rows, uint32_t nvec,
-                              uint32_t n_total) {
+                              const uint8_t *pairs, uint32_t fi, uint32_t fj, uint32_t n_stripes,
+                              uint32_t rows, uint32_t nvec, uint32_t n_total) {
     const uint64_t units = static_cast<uint64_t>(n_stripes) * n_total;
     const uint32_t row_bytes = nvec * 16;
     for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const uint32_t s = static_cast<uint32_t>(u / n_total);
         uint32_t k = static_cast<uint32_t>(u - static_cast<uint64_t>(s) * n_total);
-        const uint32_t a = pairs[2ull * s], b = pairs[2ull * s + 1];
+        const uint32_t a = pairs ? pairs[2ull * s] : fi, b = pairs ? pairs[2ull * s + 1] : fj;
         if (!(a < b && b <= n_total + 1)) continue;
         if (k >= a) ++k;  // the k-th surviving strip
         if (k >= b) ++k;
@@ -129,40 +130,6 @@ bool host_geo(const rcg_layout *L, HostGeo *g) {
     g->strip_bytes = (g->p - 1) * g->C;
     g->stripe_bytes = (g->N + 2) * g->strip_bytes;
     return true;
-}
-
-// Copy strips [k0, k1) of n stripes between a host layout and the packed
-// staging chunk, in as few 2-D copies as the host strides allow.
-cudaError_t copy_strips(bool to_device, uint8_t *chunk, const HostGeo &g, uint8_t *host_first,
-                        uint32_t k0, uint32_t k1, uint64_t n, cudaStream_t s) {
-    const cudaMemcpyKind kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
-    const bool rows_packed = g.rs == g.C;
-    const bool strips_packed = rows_packed && g.ss == g.strip_bytes;
-    if (strips_packed) {  // strips k0..k1 of a stripe are one contiguous block
-        uint8_t *h = host_first + k0 * g.ss;
-        uint8_t *d = chunk + k0 * g.strip_bytes;
-        const uint64_t w = (k1 - k0) * g.strip_bytes;
-        return to_device ? cudaMemcpy2DAsync(d, g.stripe_bytes, h, g.st, w, n, kind, s)
-                         : cudaMemcpy2DAsync(h, g.st, d, g.stripe_bytes, w, n, kind, s);
-    }
-    for (uint32_t k = k0; k < k1; ++k) {
-        if (rows_packed) {
-            uint8_t *h = host_first + k * g.ss;
-            uint8_t *d = chunk + k * g.strip_bytes;
-            cudaError_t e = to_device ? cudaMemcpy2DAsync(d, g.stripe_bytes, h, g.st, g.strip_bytes, n, kind, s)
-                                      : cudaMemcpy2DAsync(h, g.st, d, g.stripe_bytes, g.strip_bytes, n, kind, s);
-            if (e != cudaSuccess) return e;
-        } else {
-            for (uint32_t r = 0; r + 1 < g.p; ++r) {
-                uint8_t *h = host_first + k * g.ss + r * g.rs;
-                uint8_t *d = chunk + k * g.strip_bytes + r * g.C;
-                cudaError_t e = to_device ? cudaMemcpy2DAsync(d, g.stripe_bytes, h, g.st, g.C, n, kind, s)
-                                          : cudaMemcpy2DAsync(h, g.st, d, g.stripe_bytes, g.C, n, kind, s);
-                if (e != cudaSuccess) return e;
-            }
-        }
-    }
-    return cudaSuccess;
 }
 
 }  // namespace
@@ -245,7 +212,6 @@ rcg_status host_path(HostStaging *h, const rcg_layout *L, uint64_t first, uint64
         cudaGetLastError();
         return RCG_EINVAL;
     }
-    uint8_t *host = static_cast<uint8_t *>(L->base);
     uint8_t *host_dev = static_cast<uint8_t *>(attr.devicePointer);
     // the gather and write-back kernels index a strip's vectors with 32 bits
     if (g.strip_bytes / 16 > 0xffffffffull) return RCG_EINVAL;
@@ -261,33 +227,37 @@ rcg_status host_path(HostStaging *h, const rcg_layout *L, uint64_t first, uint64
         const int k = static_cast<int>(c % 3);
         cudaStream_t s = h->stream[k];
         const uint64_t n = std::min(per_chunk, n_stripes - s0);
-        uint8_t *hfirst = host + (first + s0) * g.st;
         rcg_layout dl;
         memset(&dl, 0, sizeof(dl));
         dl.base = h->buf[k];
         dl.p = g.p;
         dl.n_data = g.N;
         dl.row_bytes = g.C;
-        if (!pairs_host) {  // encode: data strips in, parity strips out
-            e = copy_strips(true, h->buf[k], g, hfirst, 0, g.N, n, s);
-            if (e == cudaSuccess) st = run(run_arg, &dl, n, nullptr, s);
-            if (e == cudaSuccess && st == RCG_OK) e = copy_strips(false, h->buf[k], g, hfirst, g.N, g.N + 2, n, s);
-        } else {            // recovery: surviving strips in, the two rebuilt strips written back
-            const uint32_t rows = g.p - 1, nvec = static_cast<uint32_t>(g.C / 16);
+        // Both directions go through kernels that address the host stripes by
+        // their mapped device addresses: encode is the pair (P, Q) for every
+        // stripe (its data strips in, P and Q out), recovery a per-stripe pair.
+        // (The copy engines move bytes as fast, but 2-D copy-engine uploads
+        // showed occasional stalls of 0.1-0.2 s on the GB300 machine; the kernel
+        // path never did.)
+        const uint32_t rows = g.p - 1, nvec = static_cast<uint32_t>(g.C / 16);
+        const uint8_t *pairs_dev = nullptr;
+        if (pairs_host) {
             e = cudaMemcpyAsync(h->pairs[k], pairs_host + 2 * s0, 2 * n, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) {
-                gather_kernel<<<kGatherCtas, 512, 0, s>>>(host_dev + (first + s0) * g.st, g.rs, g.ss, g.st,
-                                                         h->buf[k], g.stripe_bytes, g.strip_bytes, h->pairs[k],
-                                                         static_cast<uint32_t>(n), rows, nvec, g.N);
-                e = cudaGetLastError();
-            }
-            if (e == cudaSuccess) st = run(run_arg, &dl, n, h->pairs[k], s);
-            if (e == cudaSuccess && st == RCG_OK) {
-                writeback_kernel<<<kWritebackCtas, 512, 0, s>>>(h->buf[k], g.stripe_bytes, g.strip_bytes,
-                                                        host_dev + (first + s0) * g.st, g.rs, g.ss, g.st,
-                                                        h->pairs[k], static_cast<uint32_t>(n), rows, nvec, g.N);
-                e = cudaGetLastError();
-            }
+            pairs_dev = h->pairs[k];
+        }
+        if (e == cudaSuccess) {
+            gather_kernel<<<kGatherCtas, 512, 0, s>>>(host_dev + (first + s0) * g.st, g.rs, g.ss, g.st, h->buf[k],
+                                                     g.stripe_bytes, g.strip_bytes, pairs_dev, g.N, g.N + 1,
+                                                     static_cast<uint32_t>(n), rows, nvec, g.N);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) st = run(run_arg, &dl, n, pairs_dev, s);
+        if (e == cudaSuccess && st == RCG_OK) {
+            writeback_kernel<<<kWritebackCtas, 512, 0, s>>>(h->buf[k], g.stripe_bytes, g.strip_bytes,
+                                                            host_dev + (first + s0) * g.st, g.rs, g.ss, g.st,
+                                                            pairs_dev, g.N, g.N + 1, static_cast<uint32_t>(n), rows,
+                                                            nvec, g.N);
+            e = cudaGetLastError();
         }
     }
     for (int k = 0; k < 3; ++k) {

@@ -505,10 +505,13 @@ def test_c2_full_size(rcg, ctx, oracle):
     buf = torch.empty((S, N + 2, p - 1, C), dtype=torch.uint8, device="cuda")
     rcg.rcg_fill_random(buf, S * sb, seed)
     L = rcg.make_layout(buf, p, N, C)
+    full = buf.cpu().numpy()  # every byte, checked below against O2 (word-level CPU)
     ctx.encode(L, 0, S)
     check_clean(ctx)
     samples = [0, 1, 4095, 5000, S - 1]
     sample_check(oracle, buf, p, N, C, seed, samples)
+    oracle.o2_encode(p, N, C, full, S)
+    assert np.array_equal(buf.cpu().numpy(), full)
     # property at full size: P is the XOR of the data strips
     x = buf[:, 0].clone()
     for k in range(1, N):
@@ -522,9 +525,13 @@ def test_c2_full_size(rcg, ctx, oracle):
         idx = torch.arange(S, device="cuda")
         buf[idx, pd[:, 0].long()] = POISON_I
         buf[idx, pd[:, 1].long()] = POISON_J
+        lost_all = buf.cpu().numpy()
         ctx.recover_many(L, 0, S, pd)
         check_clean(ctx)
         assert torch.equal(buf, enc), kind
+        oracle.o2_recover(p, N, C, lost_all, S, pairs=pairs)  # every byte, on the same input
+        assert np.array_equal(buf.cpu().numpy(), lost_all), kind
+        del lost_all
         for s in samples[:3]:
             lost = enc[s:s + 1].cpu().numpy()
             lost[0, pairs[s, 0]] = POISON_I
@@ -541,18 +548,26 @@ def test_c3_full_size_double_data(rcg, ctx, oracle):
     buf = torch.empty((S, N + 2, p - 1, C), dtype=torch.uint8, device="cuda")
     rcg.rcg_fill_random(buf, S * sb, seed)
     L = rcg.make_layout(buf, p, N, C)
+    full = buf.cpu().numpy()
     ctx.encode(L, 0, S)
     check_clean(ctx)
     sample_check(oracle, buf, p, N, C, seed, [0, S - 1])
+    oracle.o2_encode(p, N, C, full, S)  # every byte against O2
+    assert np.array_equal(buf.cpu().numpy(), full)
+    del full
     enc = buf.clone()
     pairs = inputs.random_pairs(12, N, S, "dd")
     pd = dev(pairs)
     idx = torch.arange(S, device="cuda")
     buf[idx, pd[:, 0].long()] = POISON_I
     buf[idx, pd[:, 1].long()] = POISON_J
+    lost_all = buf.cpu().numpy()
     ctx.recover_many(L, 0, S, pd)
     check_clean(ctx)
     assert torch.equal(buf, enc)
+    oracle.o2_recover(p, N, C, lost_all, S, pairs=pairs)
+    assert np.array_equal(buf.cpu().numpy(), lost_all)
+    del lost_all
     s = 517
     lost = enc[s:s + 1].cpu().numpy()
     lost[0, pairs[s, 0]] = POISON_I

@@ -256,9 +256,13 @@ def test_qext_full_size_every_class(rcg, ctx, oracle):
     buf = torch.empty((S, N + 2, p - 1, C), dtype=torch.uint8, device="cuda")
     rcg.rcg_fill_random(buf, S * sb, seed)
     L = rcg.make_layout(buf, p, N, C)
+    full = buf.cpu().numpy()
     ctx.encode(L, 0, S)
     torch.cuda.synchronize()
     assert ctx.last_device_status() == 0
+    oracle.o2_encode(p, N, C, full, S)  # every byte against O2 (word-level CPU)
+    assert np.array_equal(buf.cpu().numpy(), full)
+    del full
     for s in (0, S - 1):
         host = np.ascontiguousarray(inputs.random_stripes(seed, p, N, C, 1, first_stripe=s))
         oracle.encode(p, N, C, host, 1)
@@ -278,10 +282,14 @@ def test_qext_full_size_every_class(rcg, ctx, oracle):
         pd = dev(pairs)
         buf[idx, pd[:, 0].long()] = POISON_I
         buf[idx, pd[:, 1].long()] = POISON_J
+        lost_all = buf.cpu().numpy()
         ctx.recover_many(L, 0, S, pd)
         torch.cuda.synchronize()
         assert ctx.last_device_status() == 0
         assert torch.equal(buf, enc), kind
+        oracle.o2_recover(p, N, C, lost_all, S, pairs=pairs)
+        assert np.array_equal(buf.cpu().numpy(), lost_all), kind
+        del lost_all
         s = (97 * n + 13) % S
         lost = enc[s:s + 1].cpu().numpy()
         lost[0, pairs[s, 0]] = POISON_I
