@@ -328,21 +328,27 @@ rcg_status rcg_set_batch_schedule(rcg_ctx *ctx, int schedule);
 
 /* Batch tuning (not in the paper).  How rcg_batch_prepare lays a batch out:
  * the engine shape of the launch, how work items reach the CTAs, the bytes per
- * work item, and a narrowing of every job's tile (tile_div = 2 or 4 gives
- * tiles of 1/2 or 1/4 of the widest width the engine allows, so more stages
- * fit the ring).  Results never depend on the tuning. */
+ * work item, a narrowing of every job's tile (tile_div = 2 or 4 gives tiles
+ * of 1/2 or 1/4 of the widest width the engine allows, so more stages fit the
+ * ring), and how stages share each CTA's shared memory.  Results never depend
+ * on the tuning. */
+#define RCG_RING_FIXED 0  /* equal shared-memory slots sized for the batch's largest stage (default) */
+#define RCG_RING_BYTES 1  /* a byte ring: stages of any size, up to 32 in flight */
 typedef struct rcg_batch_tuning {
     uint32_t shape;       /* RCG_SHAPE_AUTO (by the batch's bytes), _WIDE or _PAIR */
     uint32_t schedule;    /* RCG_SCHED_DYNAMIC or RCG_SCHED_STATIC */
     uint64_t item_bytes;  /* bytes per work item, >= 64 KB; 0 = 1/16 of a CTA's share, 256 KB..2 MB */
     uint32_t tile_div;    /* 1 (widest tiles), 2 or 4 */
+    uint32_t ring;        /* RCG_RING_FIXED or RCG_RING_BYTES */
     float ms;             /* rcg_batch_autotune: the chosen layout's time for the batch */
+    uint32_t reserved;
 } rcg_batch_tuning;
 
 /* Autotune the batch layout on a real job list: runs the batch under the
  * current tuning and under candidate values of each knob in turn (engine
  * shape; schedule; item bytes 256 KB / 1 MB / 4 MB / default; tile_div
- * 1 / 2 / 4), each once untimed and twice timed with CUDA events on `stream`,
+ * 1 / 2 / 4; ring discipline), each once untimed and twice timed with CUDA
+ * events on `stream`,
  * keeps the fastest value of each knob, applies the result to the context
  * (later batches use it) and returns it.  The jobs run for real, about 30
  * times: every batch operation is idempotent on jobs that do not overlap in

@@ -72,6 +72,7 @@ struct rcg_ctx {
     int tune_shape = RCG_SHAPE_AUTO;  // engine shape of batches; AUTO = the size rule
     uint64_t tune_item_bytes = 0;     // work-item size; 0 = the rule in build_table
     uint32_t tune_tile_div = 1;       // narrower tiles than the widest allowed
+    int tune_ring = RCG_RING_FIXED;   // shared-memory stage discipline of batches
     uint64_t next_ticket = 1;
     BatchSlot slots[kBatchRing];
     rcg::HostStaging *host = nullptr;  // staging of the host-memory calls (lazy)
@@ -799,8 +800,18 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     hdr.total_tiles = total;
     hdr.n_jobs = n_jobs;
     hdr.slot_bytes = slot_bytes;  // the largest stage
-    hdr.n_slots = kMaxSlots;      // stages in flight share the byte ring
-    hdr.ring_bytes = shape_info(shape).ring_bytes & ~127u;
+    if (ctx->tune_ring == RCG_RING_FIXED) {
+        // equal slots of the largest stage, as many as the ring holds (the
+        // single-launch discipline: one wait per slot reuse)
+        const uint32_t slot = (slot_bytes + 127) & ~127u;
+        hdr.n_slots = std::min<uint32_t>(kMaxSlots, (shape_info(shape).ring_bytes & ~127u) / slot);
+        hdr.ring_bytes = hdr.n_slots * slot;
+        hdr.fixed_slots = 1;
+    } else {
+        hdr.n_slots = kMaxSlots;  // stages of any size, up to 32 in flight, share the byte ring
+        hdr.ring_bytes = shape_info(shape).ring_bytes & ~127u;
+        hdr.fixed_slots = 0;
+    }
     hdr.dynamic = ctx->batch_schedule == RCG_SCHED_DYNAMIC ? 1u : 0u;
     hdr.shape = shape;
     hdr.n_items = static_cast<uint32_t>(items.size());
@@ -911,16 +922,19 @@ rcg_status rcg_set_batch_tuning(rcg_ctx *ctx, const rcg_batch_tuning *t) {
         ctx->batch_schedule = RCG_SCHED_DYNAMIC;
         ctx->tune_item_bytes = 0;
         ctx->tune_tile_div = 1;
+        ctx->tune_ring = RCG_RING_FIXED;
         return RCG_OK;
     }
     if ((t->shape != RCG_SHAPE_AUTO && t->shape != RCG_SHAPE_WIDE && t->shape != RCG_SHAPE_PAIR) ||
         (t->schedule != RCG_SCHED_STATIC && t->schedule != RCG_SCHED_DYNAMIC) ||
-        (t->item_bytes != 0 && t->item_bytes < (64u << 10)) || t->tile_div < 1 || t->tile_div > 8)
+        (t->item_bytes != 0 && t->item_bytes < (64u << 10)) || t->tile_div < 1 || t->tile_div > 8 ||
+        (t->ring != RCG_RING_FIXED && t->ring != RCG_RING_BYTES))
         return RCG_EINVAL;
     ctx->tune_shape = static_cast<int>(t->shape);
     ctx->batch_schedule = static_cast<int>(t->schedule);
     ctx->tune_item_bytes = t->item_bytes;
     ctx->tune_tile_div = t->tile_div;
+    ctx->tune_ring = static_cast<int>(t->ring);
     return RCG_OK;
 }
 
@@ -967,6 +981,7 @@ rcg_status rcg_batch_autotune(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs
     cur.schedule = static_cast<uint32_t>(ctx->batch_schedule);
     cur.item_bytes = ctx->tune_item_bytes;
     cur.tile_div = ctx->tune_tile_div;
+    cur.ring = static_cast<uint32_t>(ctx->tune_ring);
     cur.ms = 0.0f;
     rcg_status st = rcg_set_batch_tuning(ctx, &cur);
     float best_ms = -1.0f;
@@ -976,14 +991,16 @@ rcg_status rcg_batch_autotune(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs
     const uint32_t schedules[] = {RCG_SCHED_DYNAMIC, RCG_SCHED_STATIC};
     const uint64_t items[] = {0, 256ull << 10, 1ull << 20, 4ull << 20};
     const uint32_t divs[] = {1, 2, 4};
-    for (int knob = 0; knob < 4 && st == RCG_OK; ++knob) {
-        const int n_vals = knob == 0 ? 2 : knob == 1 ? 2 : knob == 2 ? 4 : 3;
+    const uint32_t rings[] = {RCG_RING_FIXED, RCG_RING_BYTES};
+    for (int knob = 0; knob < 5 && st == RCG_OK; ++knob) {
+        const int n_vals = knob == 0 ? 2 : knob == 1 ? 2 : knob == 2 ? 4 : knob == 3 ? 3 : 2;
         for (int v = 0; v < n_vals && st == RCG_OK; ++v) {
             rcg_batch_tuning cand = cur;
             if (knob == 0) cand.shape = shapes[v];
             if (knob == 1) cand.schedule = schedules[v];
             if (knob == 2) cand.item_bytes = items[v];
             if (knob == 3) cand.tile_div = divs[v];
+            if (knob == 4) cand.ring = rings[v];
             if (memcmp(&cand, &cur, sizeof(cand)) == 0) continue;
             st = rcg_set_batch_tuning(ctx, &cand);
             float ms = -1.0f;

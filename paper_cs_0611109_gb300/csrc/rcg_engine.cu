@@ -357,7 +357,9 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
     RingPos rel;            // descriptor slot and phase of stage `released`
     uint32_t head = 0;      // next free byte of the ring
     // single launches have one stage size: slot k sits at k * slot bytes
-    const uint32_t fixed_slot = bh ? 0u : ring_bytes / n_slots;
+    // fixed slots: single launches, and batches laid out with equal slots;
+    // otherwise a byte ring of stages of any size
+    const uint32_t fixed_slot = (bh && !bh->fixed_slots) ? 0u : ring_bytes / n_slots;
     bool ok = true;
     uint64_t next_static = blockIdx.x;
 

@@ -138,7 +138,8 @@ struct alignas(128) BatchHeader {
     uint32_t ring_bytes;    // shared-memory byte ring shared by up to n_slots stages in flight
     uint64_t items_offset;  // bytes from the header to the first WorkItem
     uint32_t dynamic;       // 0: items dealt round-robin; 1: taken from the global counter
-    uint32_t pad[21];
+    uint32_t fixed_slots;   // 1: n_slots equal slots of slot_bytes (as single launches); 0: byte ring
+    uint32_t pad[20];
 };
 static_assert(sizeof(BatchHeader) == 128, "the job table after the header stays 128-byte aligned");
 static_assert(sizeof(Job) % 128 == 0, "jobs keep their tensor maps 128-byte aligned");

@@ -23,6 +23,7 @@ RCG_NOALLOC_MAX_JOBS = 256
 RCG_SHAPE_AUTO, RCG_SHAPE_WIDE, RCG_SHAPE_PAIR = 0, 1, 2
 RCG_SCHED_STATIC, RCG_SCHED_DYNAMIC = 0, 1
 RCG_COLUMN_AUTO, RCG_COLUMN_OFF = 0, 1
+RCG_RING_FIXED, RCG_RING_BYTES = 0, 1
 
 _u32, _u64, _vp, _int = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
 
@@ -73,7 +74,7 @@ class rcg_hlayout(ctypes.Structure):
 
 class rcg_batch_tuning(ctypes.Structure):
     _fields_ = [("shape", _u32), ("schedule", _u32), ("item_bytes", _u64), ("tile_div", _u32),
-                ("ms", ctypes.c_float)]
+                ("ring", _u32), ("ms", ctypes.c_float), ("reserved", _u32)]
 
 
 class rcg_prime_info_t(ctypes.Structure):
@@ -231,7 +232,8 @@ def rcg_batch_autotune(ctx: int, jobs, stream=None) -> dict:
     arr = (rcg_job * len(jobs))(*jobs)
     t = rcg_batch_tuning()
     _check(lib().rcg_batch_autotune(ctx, arr, len(jobs), _stream(stream), ctypes.byref(t)), "rcg_batch_autotune")
-    return {f: (float(getattr(t, f)) if f == "ms" else int(getattr(t, f))) for f, _ in rcg_batch_tuning._fields_}
+    return {f: (float(getattr(t, f)) if f == "ms" else int(getattr(t, f))) for f, _ in rcg_batch_tuning._fields_
+            if f != "reserved"}
 
 
 def rcg_set_batch_tuning(ctx: int, tuning: dict | None):
@@ -239,7 +241,7 @@ def rcg_set_batch_tuning(ctx: int, tuning: dict | None):
         _check(lib().rcg_set_batch_tuning(ctx, None), "rcg_set_batch_tuning")
         return
     t = rcg_batch_tuning(tuning["shape"], tuning["schedule"], tuning["item_bytes"], tuning["tile_div"],
-                         tuning.get("ms", 0.0))
+                         tuning.get("ring", RCG_RING_FIXED), tuning.get("ms", 0.0), 0)
     _check(lib().rcg_set_batch_tuning(ctx, ctypes.byref(t)), "rcg_set_batch_tuning")
 
 

@@ -93,7 +93,8 @@ def test_autotune_leaves_one_runs_results(rcg, oracle):
         assert c.last_device_status() == 0
         assert t["shape"] in (rcg.RCG_SHAPE_AUTO, rcg.RCG_SHAPE_WIDE, rcg.RCG_SHAPE_PAIR)
         assert t["schedule"] in (rcg.RCG_SCHED_STATIC, rcg.RCG_SCHED_DYNAMIC)
-        assert t["tile_div"] in (1, 2, 4) and t["ms"] > 0
+        assert t["tile_div"] in (1, 2, 4) and t["ring"] in (rcg.RCG_RING_FIXED, rcg.RCG_RING_BYTES)
+        assert t["ms"] > 0
         assert_all(checks)
         # the tuning stays on the context: a fresh batch under it is exact too
         jobs2, checks2 = mixed_batch(rcg, oracle, 5100)
@@ -106,11 +107,13 @@ def test_autotune_leaves_one_runs_results(rcg, oracle):
 @pytest.mark.parametrize("tile_div", [1, 2, 4])
 @pytest.mark.parametrize("item_bytes", [0, 64 << 10, 4 << 20])
 @pytest.mark.parametrize("schedule", ["static", "dynamic"])
-def test_every_tuning_gives_identical_results(rcg, oracle, shape, tile_div, item_bytes, schedule):
+@pytest.mark.parametrize("ring", ["fixed", "bytes"])
+def test_every_tuning_gives_identical_results(rcg, oracle, shape, tile_div, item_bytes, schedule, ring):
     jobs, checks = mixed_batch(rcg, oracle, 5200)
     tuning = {"shape": rcg.RCG_SHAPE_WIDE if shape == "wide" else rcg.RCG_SHAPE_PAIR,
               "schedule": rcg.RCG_SCHED_STATIC if schedule == "static" else rcg.RCG_SCHED_DYNAMIC,
-              "item_bytes": item_bytes, "tile_div": tile_div}
+              "item_bytes": item_bytes, "tile_div": tile_div,
+              "ring": rcg.RCG_RING_FIXED if ring == "fixed" else rcg.RCG_RING_BYTES}
     with rcg.Context(0) as c:
         c.set_batch_tuning(tuning)
         assert c.batch_wait(c.batch_submit(jobs))
@@ -123,7 +126,7 @@ def test_tuning_validation_and_cache(rcg, tmp_path):
         good = {"shape": rcg.RCG_SHAPE_WIDE, "schedule": rcg.RCG_SCHED_DYNAMIC, "item_bytes": 0, "tile_div": 2}
         c.set_batch_tuning(good)
         for bad in ({**good, "shape": 9}, {**good, "schedule": 5}, {**good, "item_bytes": 1000},
-                    {**good, "tile_div": 0}, {**good, "tile_div": 9}):
+                    {**good, "tile_div": 0}, {**good, "tile_div": 9}, {**good, "ring": 4}):
             with pytest.raises(rcg.RcgError):
                 c.set_batch_tuning(bad)
         c.set_batch_tuning(None)
