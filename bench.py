@@ -51,10 +51,11 @@ def parse():
     ap.add_argument("--stripes", type=int, default=None,
                     help="stripes per GPU (default: the workload's own, 8192 for c2; other values are "
                          "profiling cases, not bench lines)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "qext", "h17", "batched", "serve"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "qext", "h17", "c2ops", "batched", "serve"],
                     help="c2: the bench line; c1 / c3: the p=5 and p=59 plain configurations; "
                          "qext: extended Q-parity, p=59 with 117 data strips; "
                          "h17: the horizontal Z_17 representation (one element per 16-bit word); "
+                         "c2ops: degraded read and small write on the c2 geometry; "
                          "batched: the uneven 50k-stripe batch vs per-stripe launches; "
                          "serve: Poisson request stream, continuous batching vs per-job launches")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -624,6 +625,83 @@ def run_geometry(args):
             "small_launch_reference": ref}
 
 
+# ---------------------------------------------- degraded read, small write
+
+def run_c2ops(args):
+    """The degraded read (rebuild one strip without touching the stripe) and
+    the small write (replace a data strip, update P and Q) over the c2
+    geometry: 8192 stripes, one launch per op (a batch of one job).
+    Algorithmic bytes per stripe: degraded read (N+1)(p-1)C -- N strips read,
+    one written; small write 7(p-1)C -- old strip, new strip, P, Q read; strip,
+    P, Q written."""
+    import torch
+
+    from paper_cs_0611109_gb300 import build, inputs
+    build.build()
+    from paper_cs_0611109_gb300 import rcg
+
+    S = args.stripes or globals()["S"]
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    ctx = rcg.Context(0)
+    buf = torch.empty((S, N + 2, P - 1, C), dtype=torch.uint8, device=dev)
+    rcg.rcg_fill_random(buf, buf.numel(), SEED)
+    L = rcg.make_layout(buf, P, N, C)
+    ctx.encode(L, 0, S)
+    aux = torch.empty((S, P - 1, C), dtype=torch.uint8, device=dev)
+    rcg.rcg_fill_random(aux, aux.numel(), SEED + 7)
+    strip = (P - 1) * C
+    ops = [("degraded_read_data", rcg.make_job(L, 0, S, rcg.RCG_OP_DEGRADED_READ, 0, 3, aux), (N + 1) * strip, N * strip),
+           ("degraded_read_q", rcg.make_job(L, 0, S, rcg.RCG_OP_DEGRADED_READ, 0, N + 1, aux), (N + 1) * strip, N * strip),
+           ("small_write", rcg.make_job(L, 0, S, rcg.RCG_OP_UPDATE, 5, 0, aux), 7 * strip, strip)]
+    prepared = {name: ctx.batch_prepare([job]) for name, job, _, _ in ops}
+    for _ in range(args.warmup):
+        for name, _, _, _ in ops:
+            ctx.batch_launch(prepared[name])
+    torch.cuda.synchronize()
+    evs = {name: [] for name, _, _, _ in ops}
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(args.steps):
+        for name, _, _, _ in ops:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.batch_launch(prepared[name])
+            e1.record(stream)
+            evs[name].append((e0, e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    status = ctx.last_device_status()
+    if status:
+        raise RuntimeError("device status word %#x" % status)
+    peak, kind = peak_hbm()
+    per_op, tot_ms, tot_user, tot_moved = {}, 0.0, 0, 0
+    for name, _, moved1, user1 in ops:
+        ms = sum(a.elapsed_time(b) for a, b in evs[name]) / len(evs[name])
+        moved, user = moved1 * S, user1 * S
+        tot_ms += ms
+        tot_user += user
+        tot_moved += moved
+        per_op[name] = {"ms": round(ms, 4), "hbm_gbs": round(moved / (ms * 1e-3) / 1e9, 1),
+                        "hbm_frac": round(moved / (ms * 1e-3) / 1e9 / peak, 4), "bytes": moved}
+    for b in prepared.values():
+        rcg.rcg_batch_free(b)
+    ctx.close()
+    achieved = tot_moved / (tot_ms * 1e-3) / 1e9
+    return {"metric": "degraded read and small write: HBM GB/s vs roofline", "value": round(achieved, 1),
+            "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot_ms, 4), "higher_is_better": True, "dtype": "u8",
+            "data": "synthetic (SplitMix64 bytes generated on the device, seed %d)" % SEED,
+            "config": {"workload": "p=13, N=12, 12 rows x 4 KiB per strip, %d stripes: degraded read of data "
+                                   "strip 3, degraded read of Q, small write of data strip 5; one launch each" % S,
+                       "l2": "inputs far larger than the 129 MB L2; no flush"},
+            "roofline": {"bound": "hbm", "kernel": "rcg_tile_engine", "achieved": round(achieved, 1),
+                         "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(achieved / peak, 4)},
+            "per_op": per_op, "gpu_launches": len(ops) * args.steps, "clocks": clk}
+
+
 # ------------------------------------------------ horizontal representation
 
 H17 = (17, 16, 65536, 4096, 5)  # p, N, strip bytes, stripes, seed
@@ -931,6 +1009,9 @@ def main():
         return
     if args.workload == "serve" and args.impl == "ours":
         print(json.dumps(run_serve(args)), flush=True)
+        return
+    if args.workload == "c2ops" and args.impl == "ours":
+        print(json.dumps(run_c2ops(args)), flush=True)
         return
     if args.workload == "h17" and args.impl == "ours":
         print(json.dumps(run_h17(args)), flush=True)

@@ -574,3 +574,34 @@ def test_c3_full_size_double_data(rcg, ctx, oracle):
     lost[0, pairs[s, 1]] = POISON_J
     oracle.recover(p, N, C, lost, 1, int(pairs[s, 0]), int(pairs[s, 1]))
     assert np.array_equal(lost[0], buf[s].cpu().numpy())
+
+
+@pytest.mark.slow
+def test_c2_geometry_degraded_read_and_small_write(rcg, ctx, oracle):
+    # the launches bench.py --workload c2ops times: one batch job over 8192
+    # stripes each; every rebuilt byte is checked, sampled stripes by the oracle
+    p, N, C, S, seed = 13, 12, 4096, 8192, 1
+    buf = torch.empty((S, N + 2, p - 1, C), dtype=torch.uint8, device="cuda")
+    rcg.rcg_fill_random(buf, buf.numel(), seed)
+    L = rcg.make_layout(buf, p, N, C)
+    ctx.encode(L, 0, S)
+    aux = torch.zeros((S, p - 1, C), dtype=torch.uint8, device="cuda")
+    for j in (3, N, N + 1):
+        assert ctx.batch_wait(ctx.batch_submit([rcg.make_job(L, 0, S, rcg.RCG_OP_DEGRADED_READ, 0, j, aux)]))
+        check_clean(ctx)
+        assert torch.equal(aux, buf[:, j]), j
+    new = torch.empty_like(aux)
+    rcg.rcg_fill_random(new, new.numel(), seed + 7)
+    before = buf[[0, S - 1]].cpu().numpy()
+    assert ctx.batch_wait(ctx.batch_submit([rcg.make_job(L, 0, S, rcg.RCG_OP_UPDATE, 5, 0, new)]))
+    check_clean(ctx)
+    assert torch.equal(buf[:, 5], new)
+    x = buf[:, 0].clone()
+    for k in range(1, N):
+        x ^= buf[:, k]
+    assert torch.equal(x, buf[:, N])  # P is the XOR of the (new) data everywhere
+    del x
+    for n, s in enumerate((0, S - 1)):
+        want = np.ascontiguousarray(before[n:n + 1])
+        oracle.update(p, N, C, want, 0, 5, new[s].cpu().numpy())
+        assert np.array_equal(buf[s].cpu().numpy(), want[0]), s
