@@ -555,13 +555,21 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                         }
                     }
                     const uint32_t B = (rows * W + 127) & ~127u;
+                    // The fewest oldest stages whose release makes room, found
+                    // from their offsets alone (where a stage goes does not
+                    // depend on when stages finish); then ONE wait, on the last
+                    // of them -- releases come in order -- and the copy issues
+                    // right after it, as with fixed slots.
+                    uint32_t need = released;  // stages [released, need) must be released
+                    RingPos scan = rel;        // descriptor slot and phase of stage `need`
+                    RingPos last = rel;        // ... of stage need - 1
                     for (;;) {
-                        if (released == issued) {  // nothing in flight
+                        if (need == issued) {  // the ring would be empty
                             start = head + B <= ring_bytes ? head : 0;
                             break;
                         }
-                        uint32_t t_off;  // offset of the oldest stage in flight (its header)
-                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t_off) : "r"(smem_addr(&sm.hdr[rel.slot].off)));
+                        uint32_t t_off;  // offset of the oldest stage still in flight then
+                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t_off) : "r"(smem_addr(&sm.hdr[scan.slot].off)));
                         bool fits = false;
                         if (t_off < head) {         // occupied [t_off, head)
                             if (head + B <= ring_bytes) { start = head; fits = true; }
@@ -570,14 +578,18 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                             if (head + B <= t_off) { start = head; fits = true; }
                         }                           // t_off == head: full
                         if (fits) break;
-                        if (!mbar_wait(smem_addr(&sm.empty[rel.slot]), rel.phase, timeout)) {
+                        last = scan;
+                        ++need;
+                        scan.next(n_slots);
+                    }
+                    if (need > released) {
+                        if (!mbar_wait(smem_addr(&sm.empty[last.slot]), last.phase, timeout)) {
                             ok = false;
                             break;
                         }
-                        ++released;
-                        rel.next(n_slots);
+                        released = need;
+                        rel = scan;
                     }
-                    if (!ok) break;
                     head = start + B;
                 }
                 const uint32_t full = smem_addr(&sm.full[pos.slot]);
