@@ -11,9 +11,10 @@
 // the sign bit is spread over its lane by a multiply.  x itself (k = 1) is
 // Section 4.5's doubling with the sign mask.
 //
-// Kernel.  No shared memory: a thread owns one 16-byte column of a stripe
-// (8 elements at p = 17) and streams it through every strip with coalesced
-// 16-byte loads, four strips in flight, four 256-thread CTAs per SM.  Q is
+// Kernel.  A thread owns one 16-byte column of a stripe (8 elements at
+// p = 17) and streams it through every strip with coalesced 16-byte loads,
+// four strips in flight, four 256-thread CTAs per SM; shared memory holds only
+// the product tables of a recovery's inverse (p = 17).  Q is
 // accumulated by Horner's rule over the data strips from the last to the
 // first (Section 4.2, Q = d + g Q),
 // a second Horner sum covering the extended strips k >= p of equation (qext)
@@ -52,6 +53,7 @@ struct HParams {
     uint32_t vps;              // 16-byte vectors per strip
     uint32_t N, i, j;
     uint32_t *status;
+    uint32_t contiguous;       // 1: each CTA walks a contiguous range of blocks; 0: blocks interleaved
 };
 
 template <int E>
@@ -151,27 +153,68 @@ __device__ __forceinline__ void stg4(uint8_t *p, uint4 v) {
 
 constexpr int kBatch = 4;  // strips whose loads are in flight together (measured best with 4 CTAs per SM)
 
+// Multiplication of 16-bit elements by a fixed ring element through two
+// 256-entry tables of its products (low byte, high byte): R is linear over
+// GF(2), so c*y = c*(y & 0xff) + c*(y & 0xff00).  Four table reads per 32-bit
+// word instead of about nine lane-wise x^m.
+__device__ __forceinline__ uint32_t tab_mul(const uint32_t (&tab)[2][256], uint32_t y) {
+    const uint32_t lo = tab[0][y & 0xffu] ^ tab[1][(y >> 8) & 0xffu];
+    const uint32_t hi = tab[0][(y >> 16) & 0xffu] ^ tab[1][y >> 24];
+    return lo | (hi << 16);
+}
+
+__device__ __forceinline__ uint4 tab_mul4(const uint32_t (&tab)[2][256], uint4 v) {
+    return make_uint4(tab_mul(tab, v.x), tab_mul(tab, v.y), tab_mul(tab, v.z), tab_mul(tab, v.w));
+}
+
 // EXT: the layout has extended strips (N > p); without them the second
 // Horner sum and its registers drop out.
+//
+// Work: 256-column blocks (a block lies in one stripe), a thread one 16-byte
+// column of a block.  At p = 17 the inverse a recovery multiplies by (per
+// stripe, uniform over a block) goes into the CTA's shared-memory product
+// tables, rebuilt only when it changes; for such launches a CTA takes a
+// contiguous range of blocks, so consecutive blocks mostly share a stripe.
 template <int E, bool EXT>
 __global__ void __launch_bounds__(256, 4) rcg_h_kernel(const HParams prm) {
     constexpr uint32_t P = E + 1;
     constexpr int slot = E == 2 ? 0 : E == 4 ? 1 : 2;
+    constexpr bool TABLES = E == 16;
+    __shared__ uint32_t tab[2][256];
+    uint32_t key = 0;  // the multiplier the tables hold (0: none); the same in every thread
     const uint32_t N = prm.N;
-    const uint64_t total = prm.n_stripes * prm.vps;
-    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-    for (uint64_t u = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; u < total; u += stride) {
-        const uint64_t s = u / prm.vps;
-        const uint32_t v = static_cast<uint32_t>(u - s * prm.vps);
+    const uint32_t bps = (prm.vps + 255) / 256;  // blocks per stripe
+    const uint64_t blocks = prm.n_stripes * bps;
+    // contiguous ranges keep a CTA on one stripe (and its tables) for several
+    // blocks; launches that need no tables interleave blocks over the CTAs,
+    // which streams a little better
+    const uint64_t per = (blocks + gridDim.x - 1) / gridDim.x;
+    const uint64_t first = prm.contiguous ? blockIdx.x * per : blockIdx.x;
+    const uint64_t last = prm.contiguous ? (first + per < blocks ? first + per : blocks) : blocks;
+    const uint64_t step = prm.contiguous ? 1 : gridDim.x;
+    for (uint64_t blk = first; blk < last; blk += step) {
+        const uint64_t s = blk / bps;
+        const uint32_t v = static_cast<uint32_t>(blk - s * bps) * 256 + threadIdx.x;
         uint32_t a = prm.i, b = prm.j;
         if (prm.pairs) {
             a = prm.pairs[2 * s];
             b = prm.pairs[2 * s + 1];
         }
-        if (!(a < b && b <= N + 1)) {
+        if (!(a < b && b <= N + 1)) {  // uniform over the block
             if (v == 0 && prm.status) atomicOr(prm.status, RCG_DEV_BADPAIR);
             continue;
         }
+        // the inverse this stripe needs: of w_a (data + P) or of w_a + w_b (two data)
+        const uint32_t mul = (b == N) ? c_h_inv_w[slot][a] : (b < N) ? c_h_inv_pair[slot][a][b] : 0u;
+        if (TABLES && mul != 0 && mul != key) {
+            __syncthreads();  // every read of the old tables is done
+            const uint32_t t = threadIdx.x;
+            tab[0][t] = mulmask4<E>(make_uint4(t, 0, 0, 0), mul).x;
+            tab[1][t] = mulmask4<E>(make_uint4(t << 8, 0, 0, 0), mul).x;
+            __syncthreads();
+            key = mul;
+        }
+        if (v >= prm.vps) continue;
         uint8_t *const col = prm.base + s * prm.stripe_stride + v * 16ull;
         const uint64_t ss = prm.strip_stride;
         // the surviving parities, in flight while the data strips stream
@@ -218,12 +261,12 @@ __global__ void __launch_bounds__(256, 4) rcg_h_kernel(const HParams prm) {
             stg4(col + a * ss, dp);
             stg4(col + (N + 1) * ss, x4(dq, mulw4<E>(dp, a)));
         } else if (b == N) {               // data a and P: w_a D_a = dQ
-            const uint4 da = mulmask4<E>(dq, c_h_inv_w[slot][a]);
+            const uint4 da = TABLES ? tab_mul4(tab, dq) : mulmask4<E>(dq, mul);
             stg4(col + a * ss, da);
             stg4(col + N * ss, x4(dp, da));
         } else {                           // two data: (w_a + w_b) D_b = w_a dP + dQ
             const uint4 t = x4(mulw4<E>(dp, a), dq);
-            const uint4 db = mulmask4<E>(t, c_h_inv_pair[slot][a][b]);
+            const uint4 db = TABLES ? tab_mul4(tab, t) : mulmask4<E>(t, mul);
             stg4(col + b * ss, db);
             stg4(col + a * ss, x4(db, dp));
         }
@@ -274,6 +317,8 @@ cudaError_t launch_h(uint8_t *base, uint32_t p, uint32_t N, uint64_t strip_bytes
     prm.i = i;
     prm.j = j;
     prm.status = status;
+    // product tables are used by per-stripe pairs and by fixed two-data or data + P pairs
+    prm.contiguous = (pairs != nullptr || (i < N && j <= N)) ? 1u : 0u;
     const uint64_t total = n_stripes * prm.vps;
     if (total == 0) return cudaSuccess;
     // a resident grid (every block of the grid-stride loop runs from the start)
@@ -282,7 +327,8 @@ cudaError_t launch_h(uint8_t *base, uint32_t p, uint32_t N, uint64_t strip_bytes
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
         if (e != cudaSuccess) return e;
         const uint64_t resident = static_cast<uint64_t>(sm_count) * static_cast<uint64_t>(std::max(per_sm, 1));
-        const unsigned g = static_cast<unsigned>(std::min<uint64_t>((total + 255) / 256, resident));
+        const uint64_t blocks = n_stripes * ((prm.vps + 255) / 256);
+        const unsigned g = static_cast<unsigned>(std::min<uint64_t>(blocks, resident));
         kernel<<<g, 256, 0, stream>>>(prm);
         return cudaGetLastError();
     };
