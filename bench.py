@@ -16,7 +16,7 @@ workload on its own stripes (weak scaling, no collective on the data path);
 the timing is the max over ranks.
 
 --impl reference times the CPU oracle on a bounded sample of the same
-workload (the reference arm of this build; the paper ships no code).
+workload (the reference arm: the paper ships no code to run).
 """
 from __future__ import annotations
 
@@ -49,13 +49,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--stripes", type=int, default=None,
-                    help="stripes per GPU (default: the workload's own, 8192 for c2; other values are "
+                    help="stripes per GPU (default: the workload's own, 8192 for p13n12; other values are "
                          "profiling cases, not bench lines)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "qext", "h17", "c2ops", "batched", "serve"],
-                    help="c2: the bench line; c1 / c3: the p=5 and p=59 plain configurations; "
+    ap.add_argument("--workload", default="p13n12",
+                    choices=["p13n12", "p5n4", "p59n58", "qext", "h17", "p13n12_ops", "batched", "serve"],
+                    help="p13n12: the bench line; p5n4 / p59n58: the p=5 and p=59 plain geometries; "
                          "qext: extended Q-parity, p=59 with 117 data strips; "
                          "h17: the horizontal Z_17 representation (one element per 16-bit word); "
-                         "c2ops: degraded read and small write on the c2 geometry; "
+                         "p13n12_ops: degraded read and small write on the bench line's geometry; "
                          "batched: the uneven 50k-stripe batch vs per-stripe launches; "
                          "serve: Poisson request stream, continuous batching vs per-job launches")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -290,7 +291,7 @@ def measured_traffic(stripes):
     committed ncu summary, scaled to `stripes` by the stripes it captured;
     None when the summary is missing or was taken on other kernel sources."""
     import re
-    path = os.path.join(ROOT, "profiles", "rcg_tile_engine_c2_traffic.md")
+    path = os.path.join(ROOT, "profiles", "rcg_tile_engine_p13n12_traffic.md")
     try:
         text = open(path).read()
     except OSError:
@@ -473,9 +474,9 @@ def run_reference(args):
 
 GEOMETRIES = {
     # name: (p, N, C, stripes, seed, description)
-    "c1": (5, 4, 1024, 1024, 0, "p=5, N=4 data strips + P + Q, 4 rows x 1 KiB per strip, 1024 stripes; "
+    "p5n4": (5, 4, 1024, 1024, 0, "p=5, N=4 data strips + P + Q, 4 rows x 1 KiB per strip, 1024 stripes; "
                                 "encode, then each of the 15 erasure pairs over all stripes, one launch per op"),
-    "c3": (59, 58, 2048, 1024, 2, "p=59, N=58 data strips + P + Q, 58 rows x 2 KiB per strip, 1024 stripes; "
+    "p59n58": (59, 58, 2048, 1024, 2, "p=59, N=58 data strips + P + Q, 58 rows x 2 KiB per strip, 1024 stripes; "
                                   "two-data recovery with a uniformly drawn pair per stripe, one launch per op"),
     "qext": (59, 117, 2048, 512, 6, "extended Q-parity (Section 3.3, equation qext): p=59, N=117 data strips "
                                     "+ P + Q, 58 rows x 2 KiB per strip, 512 stripes; encode and each recovery "
@@ -489,11 +490,11 @@ def geometry_ops(name, N, S, dev, torch):
 
     from paper_cs_0611109_gb300 import inputs
     P_ = GEOMETRIES[name][0]
-    if name == "c1":
+    if name == "p5n4":
         return [("encode", None)] + [("pair_%d_%d" % (i, j), torch.from_numpy(
             np.tile(np.array([[i, j]], dtype=np.uint8), (S, 1))).to(dev))
             for i in range(N + 2) for j in range(i + 1, N + 2)]
-    if name == "c3":
+    if name == "p59n58":
         return [("dd", torch.from_numpy(inputs.random_pairs(22, N, S, "dd")).to(dev))]
     # qext: encode, and one launch per recovery class; pairs drawn uniformly within the class
     rng = np.random.Generator(np.random.PCG64(61))
@@ -627,7 +628,7 @@ def run_geometry(args):
 
 # ---------------------------------------------- degraded read, small write
 
-def run_c2ops(args):
+def run_ops(args):
     """The degraded read (rebuild one strip without touching the stripe) and
     the small write (replace a data strip, update P and Q) over the c2
     geometry: 8192 stripes, one launch per op (a batch of one job).
@@ -1010,8 +1011,8 @@ def main():
     if args.workload == "serve" and args.impl == "ours":
         print(json.dumps(run_serve(args)), flush=True)
         return
-    if args.workload == "c2ops" and args.impl == "ours":
-        print(json.dumps(run_c2ops(args)), flush=True)
+    if args.workload == "p13n12_ops" and args.impl == "ours":
+        print(json.dumps(run_ops(args)), flush=True)
         return
     if args.workload == "h17" and args.impl == "ours":
         print(json.dumps(run_h17(args)), flush=True)

@@ -470,7 +470,7 @@ def sample_check(oracle, buf, p, N, C, seed, stripes, pairs=None):
 
 
 @pytest.mark.slow
-def test_c1_full_encode_and_every_pair(rcg, ctx, oracle):
+def test_p5n4_full_encode_and_every_pair(rcg, ctx, oracle):
     # p=5, N=4, 1 KiB rows, 1024 stripes, seed 0; all 15 erasure pairs
     p, N, C, S = 5, 4, 1024, 1024
     host = host_stripes(0, p, N, C, S)
@@ -498,7 +498,7 @@ def test_c1_full_encode_and_every_pair(rcg, ctx, oracle):
 
 
 @pytest.mark.slow
-def test_c2_full_size(rcg, ctx, oracle):
+def test_p13n12_full_size(rcg, ctx, oracle):
     # p=13, N=12, 4 KiB rows, 8192 stripes (~4.5 GiB user data), seed 1
     p, N, C, S, seed = 13, 12, 4096, 8192, 1
     sb = inputs.stripe_bytes(p, N, C)
@@ -541,7 +541,7 @@ def test_c2_full_size(rcg, ctx, oracle):
 
 
 @pytest.mark.slow
-def test_c3_full_size_double_data(rcg, ctx, oracle):
+def test_p59n58_full_size_double_data(rcg, ctx, oracle):
     # p=59, N=58, 2 KiB rows, 1024 stripes (~7 GiB), uniformly random data pairs
     p, N, C, S, seed = 59, 58, 2048, 1024, 2
     sb = inputs.stripe_bytes(p, N, C)
@@ -577,8 +577,8 @@ def test_c3_full_size_double_data(rcg, ctx, oracle):
 
 
 @pytest.mark.slow
-def test_c2_geometry_degraded_read_and_small_write(rcg, ctx, oracle):
-    # the launches bench.py --workload c2ops times: one batch job over 8192
+def test_p13n12_degraded_read_and_small_write(rcg, ctx, oracle):
+    # the launches bench.py --workload p13n12_ops times: one batch job over 8192
     # stripes each; every rebuilt byte is checked, sampled stripes by the oracle
     p, N, C, S, seed = 13, 12, 4096, 8192, 1
     buf = torch.empty((S, N + 2, p - 1, C), dtype=torch.uint8, device="cuda")
