@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--batch-jobs", type=int, default=50000)
     ap.add_argument("--arena-gb", type=float, default=100.0)
     ap.add_argument("--schedule", default="dynamic", choices=["static", "dynamic"])
+    ap.add_argument("--row-align", type=int, default=16,
+                    help="batched: bytes each row stride is rounded up to (16 = packed rows, the workload as "
+                         "specified; 128 = rows padded to whole L2 lines)")
     return ap.parse_args()
 
 
@@ -814,9 +817,13 @@ def run_batched(args):
     arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
     base = arena.data_ptr()
     align = lambda x: (x + 255) // 256 * 256
+    if args.row_align < 16 or args.row_align % 16:
+        raise SystemExit("--row-align must be a positive multiple of 16")
+    rs_of = lambda c: (c + args.row_align - 1) // args.row_align * args.row_align
+    footprint = lambda j: (j["n"] + 2) * (j["p"] - 1) * rs_of(j["c"])
     waves, cur, used = [], [], 0
     for j in jobs:
-        sz = align(inputs.stripe_bytes(j["p"], j["n"], j["c"]))
+        sz = align(footprint(j))
         if used + sz > arena_bytes and cur:
             waves.append(cur)
             cur, used = [], 0
@@ -830,9 +837,9 @@ def run_batched(args):
     tuning = None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for w in waves:
-        used = w[-1][1] + align(inputs.stripe_bytes(w[-1][0]["p"], w[-1][0]["n"], w[-1][0]["c"]))
+        used = w[-1][1] + align(footprint(w[-1][0]))
         rcg.rcg_fill_random(arena, used, 3)
-        lays = [rcg.make_layout(base + o, j["p"], j["n"], j["c"]) for j, o in w]
+        lays = [rcg.make_layout(base + o, j["p"], j["n"], j["c"], rs_of(j["c"])) for j, o in w]
         pre = [rcg.make_job(L, 0, 1, rcg.RCG_OP_ENCODE) for L, (j, _) in zip(lays, w) if j["op"] == "recover"]
         if pre:
             assert ctx.batch_wait(ctx.batch_submit(pre))
@@ -888,6 +895,8 @@ def run_batched(args):
            "config": {"workload": "batched uneven: %d single-stripe jobs, p in {5,13,29,59}, N in [3,p-1], "
                                   "rows 512 B..64 KiB log-uniform, 60%% encode / 40%% recovery" % len(jobs),
                       "waves": len(waves), "arena_bytes": arena_bytes, "user_bytes": tot["user"],
+                      "row_stride": "packed (row stride = C)" if args.row_align == 16 else
+                                    "C rounded up to a multiple of %d bytes" % args.row_align,
                       "schedule": args.schedule,
                       "hbm_bytes": tot["moved"]},
            "autotune": {"tuning": tuning, "seconds": tot.get("autotune_s"),

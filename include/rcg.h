@@ -32,7 +32,11 @@
  * base + s*stripe_stride, its strip k (data k < N, P = strip N, Q = strip
  * N+1) at + k*strip_stride, row r at + r*row_stride; each row is row_bytes
  * bytes.  A zero stride means "packed".  base, strides and row_bytes must be
- * multiples of 16 bytes.
+ * multiples of 16 bytes.  Any such layout is exact; the engine is fastest when
+ * base and row_stride are multiples of 128 bytes (one L2 line), so that the
+ * column tiles it copies start on line boundaries: with a packed layout whose
+ * row_bytes is an odd multiple of 16, p = 59 launches measured 10-15 % slower
+ * on GB300 (pad the row stride to a multiple of 128 to avoid it).
  *
  * Ownership and asynchrony.  The caller owns every stripe buffer (device
  * memory, e.g. from PyTorch) and every output buffer.  Calls enqueue work on

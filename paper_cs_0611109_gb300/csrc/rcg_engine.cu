@@ -129,9 +129,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
     return true;
 }
 
-__device__ __forceinline__ uint64_t l2_evict_first() {
+// L2 policy of the strip-tile loads: normal priority.  Measured on GB300
+// against evict-first, whole launches ran 7 % faster on rows whose stride is
+// a multiple of 128 bytes and 10-15 % faster on other strides (where two
+// neighbouring tiles read the same boundary lines).
+__device__ __forceinline__ uint64_t l2_tile_policy() {
     uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
 
@@ -343,7 +347,7 @@ template <class S>
 __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHeader *bh,
                          uint64_t total_units, uint32_t ring_bytes, uint32_t n_slots) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint64_t policy = l2_evict_first();
+    const uint64_t policy = l2_tile_policy();
     const uint64_t timeout = prm.timeout_ns;
     const uint32_t ring0 = smem_addr(sm.ring);
     // batches: work items (a run of one job's tiles); single launches: one
