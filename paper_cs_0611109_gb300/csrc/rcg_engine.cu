@@ -5,9 +5,10 @@
 //
 // Data path.  A work unit is a tile: W bytes of columns of one stripe (all
 // p-1 rows of every strip it needs).  The producer warp streams the tile's
-// strips, one strip per shared-memory ring slot, with 1-D bulk asynchronous
-// copies (cp.async.bulk global->shared, one per row, completion counted on an
-// mbarrier).  Consumer warps XOR each slot into register accumulators:
+// strips, one strip per shared-memory ring slot, each with one 4-D tensor copy
+// (cp.async.bulk.tensor: a (W/8) x (p-1) box of 8-byte elements; per-row 1-D
+// bulk copies where the driver refuses the layout), completion counted on an
+// mbarrier.  Consumer warps XOR each slot into register accumulators:
 //   accP[r]            ^= strip[r]                      (P, first equation of (znparity))
 //   accQ[(r + k) mod p] ^= strip_k[r]                   (x^k d_k in F2[x]/(x^p - 1))
 // A consumer owns fixed accumulator rows, so x^k is a read of the slot at the
@@ -18,9 +19,11 @@
 // memory and writes the results straight to global memory.
 //
 // Two-data recovery (Sections 4.3, 4.6): with z = j - i,
-//   T   = dP + x^(-i) dQ,     D_j = (1 + x^z)^(-1) T,     D_i = D_j + dP,
-// where (1 + x^z)^(-1) = sum_{t=0}^{(p-1)/2} x^(2tz) is read from a per-p
-// table precomputed on the host and kept in constant memory.
+//   T   = dP + x^(-i) dQ,     D_j = (1 + x^z)^(-1) T,     D_i = D_j + dP.
+// By default the epilogue solves (1 + x^z) D_j = T by one walk along the rows
+// p-1, p-1+z, p-1+2z, ... (mod p); the alternative multiplies by
+// (1 + x^z)^(-1) = sum_{t=0}^{(p-1)/2} x^(2tz), a per-p host table kept in
+// constant memory.
 //
 // Extended Q-parity (Section 3.3, equation qext).  For primes that satisfy
 // Theorem 3.3.3 a stripe may hold up to 2p - 1 data strips; strip k >= p is
@@ -924,7 +927,8 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
         // row whose source is the imaginary row p-1 is vrow = (p-1+rot) mod p
         const uint32_t qbase = stage - rot * pitch;  // + p*pitch for rows r < rot
         const int vrow = rot == 0 ? p - 1 : rot - 1;
-        if ((flags & (F_P | F_Q | F_Q2 | F_COPY)) == (F_P | F_Q)) {
+        const uint32_t fsel = flags & (F_P | F_Q | F_Q2 | F_COPY);
+        if (fsel == (F_P | F_Q)) {
             // a data strip feeding both accumulators: the common case
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t) {
@@ -932,7 +936,21 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
                 if (r < p - 1) accP[t] = xor4(accP[t], lds_a(stage + off[t]));
                 if (r < p && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
             }
-        } else if ((flags & (F_P | F_Q | F_Q2 | F_COPY)) == (F_P | F_Q | F_Q2) && hv.z == 0) {
+        } else if (S::kItems <= 4 && fsel == F_P) {
+            // P alone: every stage of a degraded read from P, the P strip of a
+            // recovery (not in the 6-item shape, where this path costs a
+            // register spill; there the general path below takes it)
+#pragma unroll
+            for (int t = 0; t < S::kItems; ++t)
+                if (row[t] < p - 1) accP[t] = xor4(accP[t], lds_a(stage + off[t]));
+        } else if (fsel == F_Q) {
+            // Q alone: every stage of a degraded read of Q, the Q strip of a recovery
+#pragma unroll
+            for (int t = 0; t < S::kItems; ++t) {
+                const int r = row[t];
+                if (r < p && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
+            }
+        } else if (fsel == (F_P | F_Q | F_Q2) && hv.z == 0) {
             // an extended data strip (weight 1 + x^rot) feeding both accumulators
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t) {
