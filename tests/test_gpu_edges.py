@@ -169,3 +169,40 @@ def test_recover_many_subrange(rcg, ctxs, oracle, path, p, N):
     assert np.array_equal(got[2:5], host[2:5])
     assert np.array_equal(got[:2], lost[:2]) and np.array_equal(got[5:], lost[5:])
     assert c.last_device_status() == 0
+
+
+@pytest.mark.parametrize("shape", ["wide", "pair"])
+@pytest.mark.parametrize("p,N,C", [(5, 4, 1040), (13, 12, 2064), (59, 58, 528), (13, 25, 2064)])
+def test_degraded_read_and_update_in_both_shapes(rcg, oracle, shape, p, N, C):
+    # every kind of ring slot -- P and Q together, P alone, Q alone, the small
+    # write's copied strip -- in both engine shapes, against the oracle
+    S = 3
+    host = stripes(7400 + p + N, p, N, C, S)
+    oracle.encode(p, N, C, host, S)
+    with rcg.Context(0) as c:
+        c.set_column_kernel(rcg.RCG_COLUMN_OFF)
+        c.set_engine_shape(rcg.RCG_SHAPE_WIDE if shape == "wide" else rcg.RCG_SHAPE_PAIR)
+        for j in sorted({0, N // 2, N - 1, N, N + 1}):
+            lost = host.copy()
+            lost[:, j] = POISON_I  # the strip served is never read
+            buf = dev(lost)
+            L = rcg.make_layout(buf, p, N, C)
+            out = torch.zeros((S, p - 1, C), dtype=torch.uint8, device="cuda")
+            assert c.batch_wait(c.batch_submit([rcg.make_job(L, 0, S, rcg.RCG_OP_DEGRADED_READ, 0, j, out)]))
+            assert c.last_device_status() == 0
+            assert np.array_equal(out.cpu().numpy(), host[:, j]), j
+            one = torch.zeros((p - 1, C), dtype=torch.uint8, device="cuda")
+            c.degraded_read(L, 1, j, one)
+            torch.cuda.synchronize()
+            assert np.array_equal(one.cpu().numpy(), host[1, j]), j
+            assert np.array_equal(buf.cpu().numpy(), lost)  # the stripes are not written
+        want = host.copy()
+        buf = dev(host)
+        L = rcg.make_layout(buf, p, N, C)
+        for s, i in ((0, 0), (1, N - 1), (2, N // 2)):
+            new = inputs.random_bytes(7500 + 7 * s + i, (p - 1) * C).reshape(p - 1, C)
+            c.update(L, s, i, dev(new))
+            oracle.update(p, N, C, want, s, i, new)
+        torch.cuda.synchronize()
+        assert c.last_device_status() == 0
+        assert np.array_equal(buf.cpu().numpy(), want)
