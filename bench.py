@@ -253,7 +253,7 @@ def run_ours(args):
                    "hbm_bytes_per_op_per_gpu": moved_bytes_per_op(S),
                    "l2": "inputs (5.25 GiB per op) far larger than the 129 MB L2; no flush",
                    "parallelism": "stripe-sharded x%d, no collective" % world},
-        "roofline": {"bound": "hbm", "kernel": "rcg_tile_engine_wide",
+        "roofline": {"bound": "hbm", "kernel": "rcg_tile_engine<wide>",
                      "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                      "avg_launch_ms": round(avg_launch_ms, 4),
@@ -627,7 +627,7 @@ def run_geometry(args):
                          # the launch's kernel: the column kernel for p <= 7, else the
                          # tile engine's shape for the launch's traffic (256 MB threshold)
                          "kernel": "rcg_column_kernel" if p <= 7 else
-                                   "rcg_tile_engine_wide" if moved >= (256 << 20) else "rcg_tile_engine_pair",
+                                   "rcg_tile_engine<wide>" if moved >= (256 << 20) else "rcg_tile_engine<pair>",
                          "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(achieved / peak, 4)},
             "per_op": per_op, "gpu_launches": len(ops) * args.steps, "clocks": clk,
             "small_launch_reference": ref}
@@ -705,7 +705,7 @@ def run_ops(args):
             "config": {"workload": "p=13, N=12, 12 rows x 4 KiB per strip, %d stripes: degraded read of data "
                                    "strip 3, degraded read of Q, small write of data strip 5; one launch each" % S,
                        "l2": "inputs far larger than the 129 MB L2; no flush"},
-            "roofline": {"bound": "hbm", "kernel": "rcg_tile_engine_wide", "achieved": round(achieved, 1),
+            "roofline": {"bound": "hbm", "kernel": "rcg_tile_engine<wide>", "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(achieved / peak, 4)},
             "per_op": per_op, "gpu_launches": len(ops) * args.steps, "clocks": clk}
 

@@ -936,8 +936,10 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
                 if (r < p - 1) accP[t] = xor4(accP[t], lds_a(stage + off[t]));
                 if (r < p && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
             }
-        } else if (fsel == F_P) {
-            // P alone: every stage of a degraded read from P, the P strip of a recovery
+        } else if (S::kItems <= 4 && fsel == F_P) {
+            // P alone: every stage of a degraded read from P, the P strip of a
+            // recovery (not in the 6-item shape, where this path costs a
+            // register spill; there the general path below takes it)
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t)
                 if (row[t] < p - 1) accP[t] = xor4(accP[t], lds_a(stage + off[t]));
@@ -993,7 +995,8 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
 // ------------------------------------------------------------------ kernel
 
 template <class S>
-__device__ __forceinline__ void engine_body(const LaunchParams &prm, const BatchHeader *bh) {
+__global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
+    rcg_tile_engine(const __grid_constant__ LaunchParams prm, const BatchHeader *bh) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const Smem sm = carve<S>(smem_raw);
 
@@ -1028,21 +1031,6 @@ __device__ __forceinline__ void engine_body(const LaunchParams &prm, const Batch
         producer<S>(prm, sm, bh, total, static_cast<uint32_t>(ring_bytes), n_slots);
     else
         consumer<S>(prm, sm, n_slots);
-}
-
-// The two shapes as kernels.  Wide: one 512-thread CTA per SM, registers
-// capped at 128 by its launch bounds.  Pair: two 224-thread CTAs per SM; launch
-// bounds would cap it at 128 registers too (and spill), while the register
-// file holds two CTAs at up to 144 (kMaxRegs), so the cap is given directly --
-// engine_init_attributes checks that two CTAs still fit.
-__global__ void __launch_bounds__(ShapeWide::kThreads, ShapeWide::kCtasPerSm)
-    rcg_tile_engine_wide(const __grid_constant__ LaunchParams prm, const BatchHeader *bh) {
-    engine_body<ShapeWide>(prm, bh);
-}
-
-__global__ void __maxnreg__(ShapePair::kMaxRegs)
-    rcg_tile_engine_pair(const __grid_constant__ LaunchParams prm, const BatchHeader *bh) {
-    engine_body<ShapePair>(prm, bh);
 }
 
 // --------------------------------------------------- bounded-wait self test
@@ -1136,31 +1124,19 @@ cudaError_t upload_inverse_tables() {
 }
 
 cudaError_t engine_init_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(rcg_tile_engine_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(rcg_tile_engine<ShapeWide>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(ShapeWide::kSmemLimit));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(rcg_tile_engine_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(rcg_tile_engine<ShapePair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(ShapePair::kSmemLimit));
-    // every CTA of a shape's grid must be resident at once (grid = SMs x CTAs per SM)
-    int wide = 0, pair = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wide, rcg_tile_engine_wide, ShapeWide::kThreads,
-                                                          ShapeWide::kSmemLimit);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pair, rcg_tile_engine_pair, ShapePair::kThreads,
-                                                          ShapePair::kSmemLimit);
-    if (e == cudaSuccess && (wide < ShapeWide::kCtasPerSm || pair < ShapePair::kCtasPerSm))
-        e = cudaErrorInvalidConfiguration;
     return e;
 }
 
 template <class S>
 static cudaError_t launch_shape(const LaunchParams &prm, const BatchHeader *bh, size_t smem, int grid,
                                 cudaStream_t stream) {
-    if (S::kCtasPerSm == 2)
-        rcg_tile_engine_pair<<<grid, S::kThreads, smem, stream>>>(prm, bh);
-    else
-        rcg_tile_engine_wide<<<grid, S::kThreads, smem, stream>>>(prm, bh);
+    rcg_tile_engine<S><<<grid, S::kThreads, smem, stream>>>(prm, bh);
     return cudaGetLastError();
 }
 

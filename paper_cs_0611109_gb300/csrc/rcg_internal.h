@@ -39,9 +39,6 @@ struct EngineShape {
     static constexpr int kMaxItems = IT * CW * 32;
     static constexpr int kCtasPerSm = CT;
     static constexpr int kMinSlots = MINSLOTS;  // a plan keeps at least this ring depth
-    // registers per thread that still let kCtasPerSm CTAs share the 64K-register file
-    // (allocated per warp in steps of 8 per thread)
-    static constexpr int kMaxRegs = (65536 / (CT * kThreads)) / 8 * 8;
     // 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
     static constexpr uint32_t kSmemLimit = (228 / CT - 1) * 1024;
     static constexpr uint32_t kXBytes = kMaxItems * 16;  // the p x W exchange buffer
