@@ -35,7 +35,7 @@
  * multiples of 16 bytes.  Any such layout is exact; the engine is fastest when
  * base and row_stride are multiples of 128 bytes (one L2 line), so that the
  * column tiles it copies start on line boundaries: with a packed layout whose
- * row_bytes is an odd multiple of 16, p = 59 launches measured 10-15 % slower
+ * row_bytes is an odd multiple of 16, p = 59 launches measured about 10 % slower
  * on GB300 (pad the row stride to a multiple of 128 to avoid it).
  *
  * Ownership and asynchrony.  The caller owns every stripe buffer (device
