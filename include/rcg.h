@@ -297,9 +297,10 @@ typedef struct rcg_job {
 } rcg_job;
 
 /* Run a list of jobs of mixed p, N, C and op in ONE persistent-kernel launch:
- * jobs are cut into work items of roughly equal bytes, largest jobs first, and the
- * stages of all of them share one shared-memory byte ring per CTA, so small
- * and large stripes keep the same number of bytes in flight.  The job list is validated on the
+ * jobs are cut into work items of roughly equal bytes, largest jobs first, and
+ * the stages of all of them share each CTA's shared-memory ring (by default
+ * equal slots sized for the batch's largest stage; a byte ring, where small
+ * stages take less room, is a tuning choice -- rcg_set_batch_tuning).  The job list is validated on the
  * host, copied into a context-owned device descriptor table and replayed
  * through a CUDA graph captured once per context.  Jobs must not overlap in
  * memory.  On return *ticket identifies the batch for rcg_batch_wait.  The
