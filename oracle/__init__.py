@@ -262,6 +262,10 @@ def o2() -> ctypes.CDLL:
         L.o2_recover.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _u64, _uint, _uint, _vp, ctypes.c_int]
         L.o2_inverse.restype = _u64
         L.o2_inverse.argtypes = [_uint, _u64]
+        L.o2_h_encode.restype = ctypes.c_int
+        L.o2_h_encode.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, ctypes.c_int]
+        L.o2_h_recover.restype = ctypes.c_int
+        L.o2_h_recover.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _uint, _uint, _vp, ctypes.c_int]
         _o2 = L
     return _o2
 
@@ -291,6 +295,29 @@ def o2_recover(p, N, C, buf, n_stripes, i=0, j=1, pairs=None, row_stride=None, s
     rc = o2().o2_recover(p, N, C, _ptr(buf), n_stripes, rs, ss, st, i, j, pp, _threads(threads))
     if rc:
         raise ValueError("o2_recover: invalid arguments (rc=%d)" % rc)
+
+
+def o2_h_encode(p, N, strip_bytes, buf, n_stripes, strip_stride=None, stripe_stride=None, threads=None):
+    """Word-level encode of stripes in the horizontal representation of Section 4.5, in place."""
+    _check_buf(buf)
+    ss, st = _h_strides(N, strip_bytes, strip_stride, stripe_stride)
+    rc = o2().o2_h_encode(p, N, strip_bytes, _ptr(buf), n_stripes, ss, st, _threads(threads))
+    if rc:
+        raise ValueError("o2_h_encode: invalid arguments (rc=%d)" % rc)
+
+
+def o2_h_recover(p, N, strip_bytes, buf, n_stripes, i=0, j=1, pairs=None, strip_stride=None,
+                 stripe_stride=None, threads=None):
+    """Word-level recovery (Lemma 3.1.2) of horizontal stripes, pair (i, j) or per-stripe pairs, in place."""
+    _check_buf(buf)
+    ss, st = _h_strides(N, strip_bytes, strip_stride, stripe_stride)
+    pp = None
+    if pairs is not None:
+        pairs = np.ascontiguousarray(pairs, dtype=np.uint8)
+        pp = _ptr(pairs)
+    rc = o2().o2_h_recover(p, N, strip_bytes, _ptr(buf), n_stripes, ss, st, i, j, pp, _threads(threads))
+    if rc:
+        raise ValueError("o2_h_recover: invalid arguments (rc=%d)" % rc)
 
 
 def o2_inverse(p: int, a: int) -> int:

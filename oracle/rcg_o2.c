@@ -24,7 +24,9 @@
  *
  * Layout: stripe s at buf + s*stripe_stride, strip k at + k*strip_stride, row
  * r at + r*row_stride, C bytes per row (C a multiple of 8 here: every row is
- * processed as C/8 words).  Stripes are split across threads.
+ * processed as C/8 words).  Stripes are split across threads.  Stripes in the
+ * horizontal representation of Section 4.5 (o2_h_*) are turned into this form
+ * 64 elements at a time and back.
  */
 #include <pthread.h>
 #include <stdint.h>
@@ -283,6 +285,178 @@ int o2_recover(unsigned p, unsigned N, u64 C, uint8_t *buf, u64 n_stripes, u64 r
                unsigned i, unsigned j, const uint8_t *pairs, int threads)
 {
     return run(p, N, C, buf, n_stripes, rs, ss, st, i, j, pairs, threads);
+}
+
+/* ---------------------------------------------------- horizontal strips */
+
+/* Stripes in the horizontal representation of Section 4.5: element e of a
+ * strip is bits [e(p-1), (e+1)(p-1)) of the strip (bit b = bit b%8 of byte
+ * b/8), one ring element each.  Blocks of 64 elements are turned into the
+ * bit-sliced form this file already computes on -- p-1 words, bit t of word r
+ * = coefficient of x^r of element t -- run through stripe_word, and the
+ * strips it wrote are turned back. */
+
+typedef struct {
+    uint8_t *buf;
+    unsigned p, N;
+    u64 strip_bytes, ss, st;
+} hgeo_t;
+
+/* Bits [e(p-1), (e+1)(p-1)) of a strip (p-1 <= 60): the bytes that hold
+ * them, assembled little-endian (only those bytes are touched), or bit by
+ * bit when they span nine bytes. */
+static u64 h_get(const uint8_t *strip, unsigned rows, u64 e)
+{
+    u64 b = e * rows, a = 0;
+    unsigned sh = (unsigned)(b & 7), nb = (sh + rows + 7) >> 3;
+    if (nb <= 8) {
+        for (unsigned q = 0; q < nb; q++)
+            a |= (u64)strip[(b >> 3) + q] << (8 * q);
+        return (a >> sh) & ((1ull << rows) - 1);
+    }
+    for (unsigned r = 0; r < rows; r++, b++)
+        a |= (u64)((strip[b >> 3] >> (b & 7)) & 1u) << r;
+    return a;
+}
+
+static void h_put(uint8_t *strip, unsigned rows, u64 e, u64 a)
+{
+    u64 b = e * rows;
+    unsigned sh = (unsigned)(b & 7), nb = (sh + rows + 7) >> 3;
+    if (nb <= 8) {
+        u64 v = 0, m = ((1ull << rows) - 1) << sh;
+        for (unsigned q = 0; q < nb; q++)
+            v |= (u64)strip[(b >> 3) + q] << (8 * q);
+        v = (v & ~m) | (a << sh);
+        for (unsigned q = 0; q < nb; q++)
+            strip[(b >> 3) + q] = (uint8_t)(v >> (8 * q));
+        return;
+    }
+    for (unsigned r = 0; r < rows; r++, b++) {
+        uint8_t m = (uint8_t)(1u << (b & 7));
+        if (a >> r & 1)
+            strip[b >> 3] |= m;
+        else
+            strip[b >> 3] &= (uint8_t)~m;
+    }
+}
+
+/* Elements [e0, e0 + n) (n <= 64) of stripe s: (i, j) = (N, N+1) encodes. */
+static void h_block(const hgeo_t *h, u64 s, u64 e0, unsigned n, unsigned i, unsigned j, const u64 *inv_w,
+                    const u64 (*inv_pair)[O2_MAXN])
+{
+    unsigned p = h->p, N = h->N, rows = p - 1;
+    u64 words[(O2_MAXN + 2) * (O2_MAXP - 1)];   /* strip k, row r at k*rows + r */
+    memset(words, 0, sizeof(u64) * (N + 2) * rows);
+    for (unsigned k = 0; k < N + 2; k++) {
+        if (k == i || k == j)
+            continue;
+        const uint8_t *strip = h->buf + s * h->st + (u64)k * h->ss;
+        for (unsigned t = 0; t < n; t++) {
+            u64 a = h_get(strip, rows, e0 + t);
+            for (unsigned r = 0; r < rows; r++)
+                words[k * rows + r] |= (a >> r & 1) << t;
+        }
+    }
+    /* one word per row, rows 8 bytes apart, strips rows*8 bytes apart */
+    geo_t g = {(uint8_t *)words, p, N, 8, 8, (u64)rows * 8, (u64)(N + 2) * rows * 8};
+    stripe_word(&g, 0, 0, i, j, inv_w, inv_pair);
+    for (unsigned q = 0; q < 2; q++) {
+        unsigned k = q ? j : i;
+        uint8_t *strip = h->buf + s * h->st + (u64)k * h->ss;
+        for (unsigned t = 0; t < n; t++) {
+            u64 a = 0;
+            for (unsigned r = 0; r < rows; r++)
+                a |= (words[k * rows + r] >> t & 1) << r;
+            h_put(strip, rows, e0 + t, a);
+        }
+    }
+}
+
+typedef struct {
+    const hgeo_t *h;
+    u64 s0, s1;
+    unsigned i, j;
+    const uint8_t *pairs;
+    const u64 *inv_w;
+    const u64 (*inv_pair)[O2_MAXN];
+    int bad;
+} hwork_t;
+
+static void *h_worker(void *arg)
+{
+    hwork_t *wk = (hwork_t *)arg;
+    const hgeo_t *h = wk->h;
+    u64 n_el = h->strip_bytes * 8 / (h->p - 1);
+    for (u64 s = wk->s0; s < wk->s1; s++) {
+        unsigned i = wk->pairs ? wk->pairs[2 * s] : wk->i;
+        unsigned j = wk->pairs ? wk->pairs[2 * s + 1] : wk->j;
+        if (!(i < j && j <= h->N + 1)) {
+            wk->bad = 1;
+            continue;
+        }
+        for (u64 e0 = 0; e0 < n_el; e0 += 64)
+            h_block(h, s, e0, (unsigned)(n_el - e0 < 64 ? n_el - e0 : 64), i, j, wk->inv_w, wk->inv_pair);
+    }
+    return NULL;
+}
+
+static int h_run(unsigned p, unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes, u64 ss, u64 st,
+                 unsigned i, unsigned j, const uint8_t *pairs, int threads)
+{
+    if (p < 3 || p > O2_MAXP || N < 1 || N > 2 * p - 1 || N > O2_MAXN || strip_bytes == 0 ||
+        (strip_bytes * 8) % (p - 1))
+        return -1;
+    for (unsigned t = 2; t * t <= p; t++)
+        if (p % t == 0)
+            return -1;
+    static u64 inv_w[O2_MAXN];
+    static u64 inv_pair[O2_MAXN][O2_MAXN];
+    for (unsigned a = 0; a < N; a++) {
+        inv_w[a] = inverse(p, weight(p, a));
+        for (unsigned b = a + 1; b < N; b++) {
+            inv_pair[a][b] = inverse(p, weight(p, a) ^ weight(p, b));
+            if (inv_pair[a][b] == 0)
+                return -3;
+        }
+    }
+    hgeo_t h = {buf, p, N, strip_bytes, ss, st};
+    if (threads < 1)
+        threads = 1;
+    if (threads > 256)
+        threads = 256;
+    pthread_t tid[256];
+    hwork_t wk[256];
+    for (int t = 0; t < threads; t++) {
+        wk[t].h = &h;
+        wk[t].s0 = n_stripes * t / threads;
+        wk[t].s1 = n_stripes * (t + 1) / threads;
+        wk[t].i = i;
+        wk[t].j = j;
+        wk[t].pairs = pairs;
+        wk[t].inv_w = inv_w;
+        wk[t].inv_pair = (const u64 (*)[O2_MAXN])inv_pair;
+        wk[t].bad = 0;
+        pthread_create(&tid[t], NULL, h_worker, &wk[t]);
+    }
+    int bad = 0;
+    for (int t = 0; t < threads; t++) {
+        pthread_join(tid[t], NULL);
+        bad |= wk[t].bad;
+    }
+    return bad ? -2 : 0;
+}
+
+int o2_h_encode(unsigned p, unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes, u64 ss, u64 st, int threads)
+{
+    return h_run(p, N, strip_bytes, buf, n_stripes, ss, st, N, N + 1, NULL, threads);
+}
+
+/* Recover pair (i, j), or per-stripe pairs (two bytes per stripe) when pairs != NULL. */
+int o2_h_recover(unsigned p, unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes, u64 ss, u64 st,
+                 unsigned i, unsigned j, const uint8_t *pairs, int threads)
+{
+    return h_run(p, N, strip_bytes, buf, n_stripes, ss, st, i, j, pairs, threads);
 }
 
 /* The inverse of a in R (bit mask), 0 when singular -- exposed for the tests. */

@@ -94,3 +94,69 @@ def test_o2_invalid_arguments(o2):
         o2.o2_encode(9, 4, 16, h, 1)      # not a prime
     with pytest.raises(ValueError):
         o2.o2_encode(7, 8, 16, np.zeros((1, 10, 6, 16), dtype=np.uint8), 1)  # 7 fails Theorem 3.3.3
+
+
+# ------------------------------------------------ horizontal representation
+
+H_CASES = [(3, 1, 16, 3), (3, 3, 48, 2), (5, 4, 64, 3), (5, 9, 32, 2), (17, 16, 256, 2), (17, 33, 64, 1),
+           (17, 5, 16 * 9, 2)]
+
+
+def h_stripes(seed, N, B, S):
+    return np.ascontiguousarray(inputs.random_bytes(seed, S * (N + 2) * B).reshape(S, N + 2, B))
+
+
+@pytest.mark.parametrize("p,N,B,S", H_CASES)
+def test_o2_h_encode_equals_oracle(o2, p, N, B, S):
+    h = h_stripes(6400 + p + N, N, B, S)
+    a, b = h.copy(), h.copy()
+    o2.h_encode(p, N, B, a, S)
+    o2.o2_h_encode(p, N, B, b, S, threads=2)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("p,N,B,S", H_CASES)
+@pytest.mark.parametrize("kind", ["dd", "dp", "dq", "pq", "any"])
+def test_o2_h_recover_equals_oracle(o2, p, N, B, S, kind):
+    if kind == "dd" and N < 2:
+        pytest.skip("two-data erasures need N >= 2")
+    h = h_stripes(6500 + p + N, N, B, S)
+    o2.h_encode(p, N, B, h, S)
+    pairs = inputs.random_pairs(6501 + N, N, S, kind)
+    lost = h.copy()
+    for s, (i, j) in enumerate(pairs):
+        lost[s, i] = POISON_I
+        lost[s, j] = POISON_J
+    a, b = lost.copy(), lost.copy()
+    o2.h_recover(p, N, B, a, S, pairs=pairs)
+    o2.o2_h_recover(p, N, B, b, S, pairs=pairs, threads=3)
+    assert np.array_equal(a, b)
+    assert np.array_equal(b, h)
+
+
+def test_o2_h_every_pair_and_strides(o2):
+    p, N, B, S = 17, 6, 48, 3
+    ss, st = B + 16, (N + 2) * (B + 16) + 32
+    flat = inputs.random_bytes(6600, st * S)
+    a, b = flat.copy(), flat.copy()
+    o2.h_encode(p, N, B, a, S, ss, st)
+    o2.o2_h_encode(p, N, B, b, S, ss, st, threads=2)
+    assert np.array_equal(a, b)  # padding between strips and stripes untouched too
+    for i in range(N + 2):
+        for j in range(i + 1, N + 2):
+            lost = b.copy()
+            for s in range(S):
+                lost[s * st + i * ss: s * st + i * ss + B] = POISON_I
+                lost[s * st + j * ss: s * st + j * ss + B] = POISON_J
+            o2.o2_h_recover(p, N, B, lost, S, i, j, strip_stride=ss, stripe_stride=st)
+            assert np.array_equal(lost, b), (i, j)
+
+
+def test_o2_h_invalid_arguments(o2):
+    h = np.zeros((1, 6, 64), dtype=np.uint8)
+    with pytest.raises(ValueError):
+        o2.o2_h_encode(9, 4, 64, h, 1)      # not a prime
+    with pytest.raises(ValueError):
+        o2.o2_h_encode(7, 4, 64, h, 1)      # p - 1 = 6 does not divide the 512 bits of a strip
+    with pytest.raises(ValueError):
+        o2.o2_h_recover(5, 4, 64, h, 1, 2, 2)
