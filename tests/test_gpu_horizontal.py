@@ -155,13 +155,20 @@ def test_h_validation(rcg, ctx):
 
 @pytest.mark.slow
 def test_h17_full_size(rcg, ctx, oracle):
-    # the horizontal bench geometry: p = 17, N = 16, 64 KiB strips, 4096 stripes, seed 5
+    # the horizontal bench geometry: p = 17, N = 16, 64 KiB strips, 4096 stripes, seed 5;
+    # encode checked on every byte by O2, sampled stripes by the bit-level oracle, and every
+    # recovery against the encoded stripes (the solution is unique, Lemma 3.1.2)
     p, N, B, S, seed = 17, 16, 65536, 4096, 5
     buf = torch.empty((S, N + 2, B), dtype=torch.uint8, device="cuda")
     rcg.rcg_fill_random(buf, buf.numel(), seed)
+    want = buf.cpu().numpy()
     L = rcg.make_hlayout(buf, p, N, B)
     ctx.h_encode(L, 0, S)
     clean(ctx)
+    # every byte against the word-level O2 (itself pinned to the bit-level oracle)
+    oracle.o2_h_encode(p, N, B, want, S)
+    assert np.array_equal(buf.cpu().numpy(), want)
+    del want
     sb = (N + 2) * B
     for s in (0, S - 1):
         h = np.ascontiguousarray(inputs.random_bytes(seed, sb, s * sb).reshape(1, N + 2, B))
