@@ -605,3 +605,8 @@ def test_p13n12_degraded_read_and_small_write(rcg, ctx, oracle):
         want = np.ascontiguousarray(before[n:n + 1])
         oracle.update(p, N, C, want, 0, 5, new[s].cpu().numpy())
         assert np.array_equal(buf[s].cpu().numpy(), want[0]), s
+    # every byte: P and Q after the small write equal O2's encode of the new data
+    host = buf.cpu().numpy()
+    full = host.copy()
+    oracle.o2_encode(p, N, C, full, S)
+    assert np.array_equal(host, full)
