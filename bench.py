@@ -11,6 +11,13 @@ data + Q, P + Q.  User bytes per step = 5 x N x (p-1) x C x stripes.  Every
 operation moves (N+2)(p-1)C bytes per stripe; each operation's inputs (5.25
 GiB) are far larger than the 129 MB L2, so no flush is needed.
 
+At N = 1 the line also carries the two other forms of the same code, each
+with its own clock record: `batched` -- the uneven 50k-stripe workload in
+waves, one persistent launch per wave against one launch per stripe on the
+same bytes (and a per-prime split) -- and `serve` -- a Poisson request stream
+swept from 0.1x to 2x of saturation, continuous batching against one launch
+per request (p50/p99 latency, user GB/s, kernel launches).
+
 Multi-GPU: stripes are independent codes, so each rank runs the same
 workload on its own stripes (weak scaling, no collective on the data path);
 the timing is the max over ranks.
@@ -48,6 +55,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="leave the batched sub-object out of the line")
+    ap.add_argument("--no-serve", action="store_true", help="leave the serving sub-object out of the line")
     ap.add_argument("--stripes", type=int, default=None,
                     help="stripes per GPU (default: the workload's own, 8192 for p13n12; other values are "
                          "profiling cases, not bench lines)")
@@ -271,6 +280,13 @@ def run_ours(args):
         out["e2e"] = e2e_ours(ctx, rcg, torch, dev, stream, pairs, args, world, S)
     del buf
     torch.cuda.empty_cache()
+    if world == 1:
+        # the batched and served forms of the same code, each measured against
+        # one launch per stripe / per request on the same GPU (single-GPU forms)
+        if not args.no_batched:
+            out["batched"] = measure_batched(args, ctx, rcg, torch)
+        if not args.no_serve:
+            out["serve"] = measure_serve(args, ctx, rcg, torch)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=15.0)
         out["cpu_word_level"] = cpu_word_level()
@@ -797,33 +813,11 @@ def run_h17(args):
 
 # ----------------------------------------------------------- batched form
 
-def run_batched(args):
-    """The uneven batched workload: 50k single-stripe descriptors (p over
-    {5,13,29,59}, N in [3,p-1], rows 512 B..64 KiB log-uniform, 60 % encode /
-    40 % two-erasure recovery), 390 GiB with parity, so it runs in waves that
-    fit the device arena.  Each wave is timed twice on the same bytes: as ONE
-    persistent batch launch (rcg_batch_submit, CUDA graph) and as one launch
-    per stripe (rcg_encode / rcg_recover).  Recovery stripes are encoded before
-    the timed region."""
-    import torch
-
-    from paper_cs_0611109_gb300 import build, inputs
-    build.build()
-    from paper_cs_0611109_gb300 import rcg
-
-    torch.cuda.set_device(0)
-    ctx = rcg.Context(0)
-    ctx.set_batch_schedule(rcg.RCG_SCHED_DYNAMIC if args.schedule == "dynamic" else rcg.RCG_SCHED_STATIC)
-    stream = torch.cuda.current_stream()
-    jobs = inputs.batched_jobs(3, args.batch_jobs)
-    free = torch.cuda.mem_get_info()[0]
-    arena_bytes = int(min(args.arena_gb * 1e9, 0.8 * free))
-    arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
-    base = arena.data_ptr()
+def batched_waves(jobs, arena_bytes, row_align):
+    """Cut the job list into waves whose stripes fit the device arena; each
+    entry is (job, byte offset in the arena)."""
     align = lambda x: (x + 255) // 256 * 256
-    if args.row_align < 16 or args.row_align % 16:
-        raise SystemExit("--row-align must be a positive multiple of 16")
-    rs_of = lambda c: (c + args.row_align - 1) // args.row_align * args.row_align
+    rs_of = lambda c: (c + row_align - 1) // row_align * row_align
     footprint = lambda j: (j["n"] + 2) * (j["p"] - 1) * rs_of(j["c"])
     waves, cur, used = [], [], 0
     for j in jobs:
@@ -835,14 +829,41 @@ def run_batched(args):
         used += sz
     if cur:
         waves.append(cur)
+    return waves, rs_of, lambda w: w[-1][1] + align(footprint(w[-1][0]))
+
+
+def measure_batched(args, ctx, rcg, torch):
+    """The uneven batched workload: 50k single-stripe descriptors (p over
+    {5,13,29,59}, N in [3,p-1], rows 512 B..64 KiB log-uniform, 60 % encode /
+    40 % two-erasure recovery), 390 GiB with parity, so it runs in waves that
+    fit the device arena.  Each wave is timed on the same bytes as ONE
+    persistent batch launch (autotuned layout, and the default layout) and as
+    one launch per stripe (rcg_encode / rcg_recover); each prime's jobs of the
+    wave are also timed as a batch of their own (the per-prime split).
+    Recovery stripes are encoded before the timed launches.  Clocks are
+    sampled over the whole measurement."""
+    from paper_cs_0611109_gb300 import inputs
+
+    ctx.set_batch_schedule(rcg.RCG_SCHED_DYNAMIC if args.schedule == "dynamic" else rcg.RCG_SCHED_STATIC)
+    stream = torch.cuda.current_stream()
+    jobs = inputs.batched_jobs(3, args.batch_jobs)
+    free = torch.cuda.mem_get_info()[0]
+    arena_bytes = int(min(args.arena_gb * 1e9, 0.8 * free))
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
+    base = arena.data_ptr()
+    if args.row_align < 16 or args.row_align % 16:
+        raise SystemExit("--row-align must be a positive multiple of 16")
+    waves, rs_of, wave_bytes = batched_waves(jobs, arena_bytes, args.row_align)
 
     tot = {"batched_ms": 0.0, "default_ms": 0.0, "per_stripe_ms": 0.0, "user": 0, "moved": 0,
-           "launches_per_stripe": 0}
+           "launches_per_stripe": 0, "kernel_launches": 0}
+    by_p = {}
     tuning = None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for w in waves:
-        used = w[-1][1] + align(footprint(w[-1][0]))
-        rcg.rcg_fill_random(arena, used, 3)
+        rcg.rcg_fill_random(arena, wave_bytes(w), 3)
         lays = [rcg.make_layout(base + o, j["p"], j["n"], j["c"], rs_of(j["c"])) for j, o in w]
         pre = [rcg.make_job(L, 0, 1, rcg.RCG_OP_ENCODE) for L, (j, _) in zip(lays, w) if j["op"] == "recover"]
         if pre:
@@ -855,25 +876,43 @@ def run_batched(args):
             h0 = time.perf_counter()
             tuning = ctx.batch_autotune(mix)
             tot["autotune_s"] = round(time.perf_counter() - h0, 2)
-        for mode in ("default", "tuned"):
-            ctx.set_batch_tuning(None if mode == "default" else tuning)
-            if mode == "default" and args.schedule == "static":
-                ctx.set_batch_schedule(rcg.RCG_SCHED_STATIC)
-            # host half (validation, tiling, tensor maps, work items): can overlap
-            # the previous batch on the GPU, reported separately
+
+        def time_batch(batch_jobs):
             h0 = time.perf_counter()
-            prepared = ctx.batch_prepare(mix)
-            if mode == "tuned":
-                tot["prepare_host_ms"] = tot.get("prepare_host_ms", 0.0) + (time.perf_counter() - h0) * 1e3
+            prepared = ctx.batch_prepare(batch_jobs)
+            prep_ms = (time.perf_counter() - h0) * 1e3
             for _ in range(2):  # warm-up (graph capture, descriptor caches)
                 ctx.batch_wait(ctx.batch_launch(prepared))
             torch.cuda.synchronize()
             e0.record(stream)
-            t = ctx.batch_launch(prepared)
+            ctx.batch_launch(prepared)
             e1.record(stream)
             torch.cuda.synchronize()
             rcg.rcg_batch_free(prepared)
-            tot["batched_ms" if mode == "tuned" else "default_ms"] += e0.elapsed_time(e1)
+            tot["kernel_launches"] += 1
+            return e0.elapsed_time(e1), prep_ms
+
+        for mode in ("default", "tuned"):
+            ctx.set_batch_tuning(None if mode == "default" else tuning)
+            if mode == "default" and args.schedule == "static":
+                ctx.set_batch_schedule(rcg.RCG_SCHED_STATIC)
+            ms, prep_ms = time_batch(mix)
+            tot["batched_ms" if mode == "tuned" else "default_ms"] += ms
+            if mode == "tuned":
+                # host half (validation, tiling, tensor maps, work items): can
+                # overlap the previous batch on the GPU, reported separately
+                tot["prepare_host_ms"] = tot.get("prepare_host_ms", 0.0) + prep_ms
+        # per-prime split: each prime's jobs of this wave as a batch of their own (tuned layout)
+        for pr in sorted({j["p"] for j, _ in w}):
+            sel = [job for job, (j, _) in zip(mix, w) if j["p"] == pr]
+            ms, _ = time_batch(sel)
+            d = by_p.setdefault(pr, {"ms": 0.0, "moved": 0, "user": 0, "jobs": 0})
+            d["ms"] += ms
+            d["jobs"] += len(sel)
+            for j, _ in w:
+                if j["p"] == pr:
+                    d["moved"] += (j["n"] + 2) * (j["p"] - 1) * j["c"]
+                    d["user"] += j["n"] * (j["p"] - 1) * j["c"]
         e0.record(stream)
         for L, (j, _) in zip(lays, w):
             if j["op"] == "encode":
@@ -887,60 +926,87 @@ def run_batched(args):
         for j, _ in w:
             tot["user"] += j["n"] * (j["p"] - 1) * j["c"]
             tot["moved"] += (j["n"] + 2) * (j["p"] - 1) * j["c"]
+    clk = clocks.stop()
     status = ctx.last_device_status()
     if status:
         raise RuntimeError("device status word %#x" % status)
+    del arena
+    torch.cuda.empty_cache()
     peak, kind = peak_hbm()
     gbs = lambda nbytes, ms: nbytes / (ms * 1e-3) / 1e9
-    out = {"metric": "batched uneven stripes: user GB/s, one persistent launch per wave (autotuned layout) "
-                     "vs the default layout vs one launch per stripe",
-           "value": round(gbs(tot["user"], tot["batched_ms"]), 2), "unit": "GB/s", "n_gpus": 1,
-           "higher_is_better": True, "dtype": "u8", "data": "synthetic (SplitMix64 bytes, seed 3)",
-           "config": {"workload": "batched uneven: %d single-stripe jobs, p in {5,13,29,59}, N in [3,p-1], "
-                                  "rows 512 B..64 KiB log-uniform, 60%% encode / 40%% recovery" % len(jobs),
-                      "waves": len(waves), "arena_bytes": arena_bytes, "user_bytes": tot["user"],
-                      "row_stride": "packed (row stride = C)" if args.row_align == 16 else
-                                    "C rounded up to a multiple of %d bytes" % args.row_align,
-                      "schedule": args.schedule,
-                      "hbm_bytes": tot["moved"]},
-           "autotune": {"tuning": tuning, "seconds": tot.get("autotune_s"),
-                        "default_layout_ms": round(tot["default_ms"], 3),
-                        "default_layout_user_gbs": round(gbs(tot["user"], tot["default_ms"]), 1),
-                        "default_layout_hbm_frac": round(gbs(tot["moved"], tot["default_ms"]) / peak, 4)},
-           "batched": {"ms": round(tot["batched_ms"], 3), "user_gbs": round(gbs(tot["user"], tot["batched_ms"]), 1),
-                       "hbm_gbs": round(gbs(tot["moved"], tot["batched_ms"]), 1),
-                       "hbm_frac": round(gbs(tot["moved"], tot["batched_ms"]) / peak, 4), "launches": len(waves),
-                       "prepare_host_ms": round(tot.get("prepare_host_ms", 0.0), 3),
-                       "user_gbs_with_prepare": round(gbs(tot["user"], tot["batched_ms"] + tot.get("prepare_host_ms", 0.0)), 1)},
-           "per_stripe": {"ms": round(tot["per_stripe_ms"], 3),
-                          "user_gbs": round(gbs(tot["user"], tot["per_stripe_ms"]), 1),
-                          "hbm_gbs": round(gbs(tot["moved"], tot["per_stripe_ms"]), 1),
-                          "launches": tot["launches_per_stripe"]},
-           "speedup_batched_over_per_stripe": round(tot["per_stripe_ms"] / tot["batched_ms"], 2),
-           "peak": peak, "peak_kind": kind}
+    return {
+        "workload": "batched uneven: %d single-stripe jobs, p in {5,13,29,59}, N in [3,p-1], rows 512 B..64 KiB "
+                    "log-uniform, 60%% encode / 40%% two-erasure recovery; %d waves of <= %.0f GB, each one "
+                    "persistent launch (CUDA graph) vs one launch per stripe on the same bytes"
+                    % (len(jobs), len(waves), arena_bytes / 1e9),
+        "row_stride": "packed (row stride = C)" if args.row_align == 16 else
+                      "C rounded up to a multiple of %d bytes" % args.row_align,
+        "user_bytes": tot["user"], "hbm_bytes": tot["moved"],
+        "batched": {"ms": round(tot["batched_ms"], 3), "user_gbs": round(gbs(tot["user"], tot["batched_ms"]), 1),
+                    "hbm_gbs": round(gbs(tot["moved"], tot["batched_ms"]), 1),
+                    "hbm_frac": round(gbs(tot["moved"], tot["batched_ms"]) / peak, 4), "launches": len(waves),
+                    "layout": "autotuned on the first wave", "tuning": tuning,
+                    "autotune_s": tot.get("autotune_s"),
+                    "prepare_host_ms": round(tot.get("prepare_host_ms", 0.0), 3),
+                    "user_gbs_with_prepare": round(gbs(tot["user"], tot["batched_ms"] + tot.get("prepare_host_ms", 0.0)), 1)},
+        "batched_default_layout": {"ms": round(tot["default_ms"], 3),
+                                   "user_gbs": round(gbs(tot["user"], tot["default_ms"]), 1),
+                                   "hbm_frac": round(gbs(tot["moved"], tot["default_ms"]) / peak, 4)},
+        "per_stripe": {"ms": round(tot["per_stripe_ms"], 3),
+                       "user_gbs": round(gbs(tot["user"], tot["per_stripe_ms"]), 1),
+                       "hbm_gbs": round(gbs(tot["moved"], tot["per_stripe_ms"]), 1),
+                       "hbm_frac": round(gbs(tot["moved"], tot["per_stripe_ms"]) / peak, 4),
+                       "launches": tot["launches_per_stripe"]},
+        "speedup_batched_over_per_stripe": round(tot["per_stripe_ms"] / tot["batched_ms"], 2),
+        "by_prime": {str(pr): {"jobs": d["jobs"], "ms": round(d["ms"], 3),
+                               "user_gbs": round(gbs(d["user"], d["ms"]), 1),
+                               "hbm_frac": round(gbs(d["moved"], d["ms"]) / peak, 4),
+                               "share_of_bytes": round(d["moved"] / tot["moved"], 4)}
+                     for pr, d in sorted(by_p.items())},
+        "peak": peak, "peak_kind": kind,
+        "gpu_launches": tot["kernel_launches"] + tot["launches_per_stripe"],
+        "clocks": clk,
+    }
+
+
+def run_batched(args):
+    """The batched workload on its own line."""
+    import torch
+
+    from paper_cs_0611109_gb300 import build
+    build.build()
+    from paper_cs_0611109_gb300 import rcg
+
+    torch.cuda.set_device(0)
+    ctx = rcg.Context(0)
+    m = measure_batched(args, ctx, rcg, torch)
     ctx.close()
-    return out
+    return {"metric": "batched uneven stripes: user GB/s, one persistent launch per wave (autotuned layout) "
+                      "vs the default layout vs one launch per stripe",
+            "value": m["batched"]["user_gbs"], "unit": "GB/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "u8", "data": "synthetic (SplitMix64 bytes, seed 3)",
+            "config": {"workload": m["workload"], "row_stride": m["row_stride"], "schedule": args.schedule},
+            **{k: v for k, v in m.items() if k not in ("workload", "row_stride")}}
 
 
 # ---------------------------------------------------------------- serving
 
-def run_serve(args):
+SERVE_LOADS = (0.1, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0)
+
+
+def measure_serve(args, ctx, rcg, torch):
     """Serving: a pool of device-resident stripes with the batched workload's
     geometry (encoded before the run), and a Poisson stream of requests on
     uniformly drawn stripes -- 70 % encode, 20 % degraded read of one strip,
     10 % double-erasure rebuild.  The arrival rate is swept from 10 % to 200 %
     of the measured saturation rate; at each rate the same stream is served by
     the continuous-batching server and by one launch per request.  Latency is
-    arrival to completion (as the host sees it)."""
+    arrival to completion (as the host sees it).  Clocks are sampled over the
+    whole sweep."""
     import numpy as np
-    import torch
 
-    from paper_cs_0611109_gb300 import build, inputs
-    build.build()
-    from paper_cs_0611109_gb300 import rcg
+    from paper_cs_0611109_gb300 import inputs
 
-    torch.cuda.set_device(0)
-    ctx = rcg.Context(0)
     geo = inputs.batched_jobs(4, 10 ** 6)
     align = lambda x: (x + 255) // 256 * 256
     pool_bytes = int(args.pool_gb * 1e9)
@@ -987,33 +1053,60 @@ def run_serve(args):
         rcg.rcg_serve_start(srv)
         rcg.rcg_serve_drain(srv, 600 * 10 ** 9)
         res = rcg.rcg_serve_results(srv, n)
+        st = rcg.rcg_serve_get_stats(srv)
         rcg.rcg_serve_destroy(srv)
         lat = np.array([r["complete_ns"] - r["arrival_ns"] for r in res], dtype=np.float64) / 1e6
         span = (max(r["complete_ns"] for r in res) - min(r["arrival_ns"] for r in res)) / 1e9
         return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                "user_gbs": round(user / span / 1e9, 1), "launches": max(r["batch"] for r in res)}
+                "user_gbs": round(user / span / 1e9, 1), "kernel_launches": st["kernel_launches"],
+                "max_inflight_launches": st["max_inflight_launches"],
+                "max_inflight_requests": st["max_inflight_jobs"]}
 
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     serve(0, False)  # warm-up: graph capture, caches
     sat = serve(0, False)  # everything at t = 0: the saturation throughput
+    sat_per_job = serve(0, True)
     sat_rate = sat["user_gbs"] * 1e9 / (user / n)
     points = []
-    for f in (0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.25, 1.5, 2.0):
+    launches = 0
+    for f in SERVE_LOADS:
         rate = f * sat_rate
-        points.append({"load": f, "rate_req_per_s": round(rate), "batched": serve(rate, False),
-                       "per_job": serve(rate, True)})
+        bt, pj = serve(rate, False), serve(rate, True)
+        launches += bt["kernel_launches"] + pj["kernel_launches"]
+        points.append({"load": f, "rate_req_per_s": round(rate), "batched": bt, "per_job": pj})
+    clk = clocks.stop()
     status = ctx.last_device_status()
     if status:
         raise RuntimeError("device status word %#x" % status)
+    del pool, outs
+    torch.cuda.empty_cache()
+    return {"workload": "serving: Poisson stream of %d requests on %d resident stripes (%.1f GB), batched-workload "
+                        "geometry, 70%% encode / 20%% degraded read / 10%% rebuild; rate swept 0.1x..2x of the "
+                        "saturation rate; continuous batching vs one launch per request"
+                        % (n, len(stripes), used / 1e9),
+            "requests": n, "resident_stripes": len(stripes), "pool_bytes": used,
+            "mean_user_bytes_per_request": user // n,
+            "saturation": {"batched": sat, "per_job": sat_per_job}, "sweep": points,
+            "gpu_launches": launches, "clocks": clk}
+
+
+def run_serve(args):
+    """The served workload on its own line."""
+    import torch
+
+    from paper_cs_0611109_gb300 import build
+    build.build()
+    from paper_cs_0611109_gb300 import rcg
+
+    torch.cuda.set_device(0)
+    ctx = rcg.Context(0)
+    m = measure_serve(args, ctx, rcg, torch)
     ctx.close()
     return {"metric": "serving: p50/p99 latency and user GB/s vs arrival rate, continuous batching vs per-job launches",
-            "value": sat["user_gbs"], "unit": "GB/s (saturation, batched)", "n_gpus": 1, "higher_is_better": True,
-            "dtype": "u8", "data": "synthetic (SplitMix64 bytes, seed 4)",
-            "config": {"workload": "serving: Poisson stream of %d requests on %d resident stripes (%.1f GB), "
-                                   "batched-workload geometry, 70%% encode / 20%% degraded read / 10%% rebuild"
-                                   % (n, len(stripes), used / 1e9),
-                       "requests": n, "resident_stripes": len(stripes), "pool_bytes": used,
-                       "mean_user_bytes_per_request": user // n},
-            "saturation": sat, "sweep": points}
+            "value": m["saturation"]["batched"]["user_gbs"], "unit": "GB/s (saturation, batched)", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic (SplitMix64 bytes, seed 4)",
+            "config": {"workload": m["workload"]}, **{k: v for k, v in m.items() if k != "workload"}}
 
 
 def main():

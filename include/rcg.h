@@ -379,15 +379,29 @@ rcg_status rcg_batch_wait(rcg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns);
  * in device memory), each with an arrival time and an HBM footprint.  A
  * scheduler thread, started by rcg_serve_start, owns the context until
  * rcg_serve_destroy (do not use the context from other threads meanwhile) and
- * repeats: retire launches whose completion event fired; admit requests
- * whose arrival time has passed, in arrival order, while the in-flight
- * request count and the HBM budget allow (a request on a stripe an admitted
- * request still uses waits, so two jobs on one stripe never share a launch);
- * launch everything admitted as ONE batch of the persistent engine while
- * fewer than two launches are in flight -- requests arriving meanwhile join
- * the next batch, which is prepared on the host while the GPU runs.  With
- * per_job_launches = 1 each request is launched on its own with the single-
- * operation call instead (the comparison). */
+ * repeats:
+ *  - retire launches whose completion event fired;
+ *  - admit requests whose arrival time has passed, in arrival order, while
+ *    the in-flight request count and the HBM budget allow.  Two requests
+ *    conflict when the device bytes they touch overlap: the extent of the
+ *    job's stripes ([first stripe, last byte of its last stripe]) and, for a
+ *    degraded read or a small write, the extent of its aux buffer.  A request
+ *    that conflicts with an admitted request, or with an earlier request
+ *    still waiting, waits too (requests on the same bytes run in arrival
+ *    order and never share a launch); requests behind it that do not
+ *    conflict go ahead;
+ *  - batched mode (default): launch everything admitted as ONE batch of the
+ *    persistent engine while fewer than two batches are in flight -- requests
+ *    arriving meanwhile join the next batch, which is prepared on the host
+ *    while the GPU runs;
+ *  - per-job mode (per_job_launches = 1, the comparison): launch every
+ *    admitted request at once with its own single-operation call (one kernel
+ *    launch each); the number in flight is bounded only by max_inflight_jobs.
+ *
+ * The HBM budget is a counter, not a live reading: the budget is fixed when
+ * the server is created (default min(120 GB, the device's free memory at that
+ * moment)) and every admitted request's footprint counts against it until the
+ * request completes.  The server itself allocates nothing per request. */
 typedef struct rcg_server rcg_server;
 
 typedef struct rcg_serve_config {
@@ -401,24 +415,40 @@ typedef struct rcg_serve_config {
 typedef struct rcg_serve_request {
     rcg_job job;                /* one stripe (n_stripes = 1) unless op = encode */
     uint64_t arrival_ns;        /* visible to the scheduler this long after rcg_serve_start */
-    uint64_t footprint_bytes;   /* HBM working set while in flight; 0 = the job's stripes (+ output) */
+    uint64_t footprint_bytes;   /* HBM working set while in flight; 0 = the default footprint:
+                                   (n_data + 2) x strip stride x n_stripes, plus (p - 1) x row_bytes
+                                   x n_stripes for a degraded read's output or a small write's
+                                   new strips */
 } rcg_serve_request;
 
 typedef struct rcg_serve_result {
     uint64_t id;                /* submission index */
     uint64_t arrival_ns, admit_ns, launch_ns, complete_ns;  /* since rcg_serve_start */
     uint32_t status;            /* RCG_OK, or RCG_EBUSY while not completed */
-    uint32_t batch;             /* launch number that carried the request */
+    uint32_t batch;             /* number of the launch that carried the request (1, 2, ...) */
 } rcg_serve_result;
 
+typedef struct rcg_serve_stats {
+    uint64_t kernel_launches;        /* GPU kernel launches issued (one per batch, or one per request) */
+    uint64_t completed;              /* requests completed */
+    uint64_t conflict_waits;         /* admissions put off by an overlapping request */
+    uint32_t max_inflight_launches;  /* most launches in flight at once */
+    uint32_t max_inflight_jobs;      /* most admitted, not completed requests at once */
+} rcg_serve_stats;
+
 rcg_status rcg_serve_create(rcg_ctx *ctx, const rcg_serve_config *cfg, rcg_server **out);
-/* Queue n requests (before or after rcg_serve_start); *first_id = id of the first. */
+/* Queue n requests (before or after rcg_serve_start); *first_id = id of the
+ * first.  All or nothing: when any request is invalid (an op other than
+ * encode on more than one stripe, or a footprint above the budget, which could
+ * never be admitted) none is queued and the call returns RCG_EINVAL. */
 rcg_status rcg_serve_submit(rcg_server *s, const rcg_serve_request *reqs, uint32_t n, uint64_t *first_id);
 rcg_status rcg_serve_start(rcg_server *s);
 /* Wait (at most timeout_ns) until every submitted request has completed. */
 rcg_status rcg_serve_drain(rcg_server *s, uint64_t timeout_ns);
 /* Timings of requests [0, min(max, submitted)). */
 rcg_status rcg_serve_results(rcg_server *s, rcg_serve_result *out, uint64_t max, uint64_t *n);
+/* Counters of the server so far. */
+rcg_status rcg_serve_get_stats(rcg_server *s, rcg_serve_stats *out);
 /* Stop the scheduler (after the launches in flight finish) and free the server. */
 rcg_status rcg_serve_destroy(rcg_server *s);
 

@@ -168,6 +168,15 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// A batch's tensor maps live in a device table that a copy rewrites before
+// each launch, at the same addresses as the previous batch's maps: acquire
+// the map through the tensor-map proxy before the TMA unit reads it, so no
+// descriptor cached from an earlier batch is used.
+__device__ __forceinline__ void acquire_tmap(const CUtensorMap *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }
@@ -387,6 +396,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
     uint64_t u = items ? (dynamic ? next_index() : blockIdx.x) : 0;
     uint32_t nxt = 0;
     if (items && u < total_units) nxt = fetch(u);
+    uint32_t acquired = ~0u;  // job whose tensor map this CTA last acquired
 
     for (;;) {
         // the fields of this unit, in registers
@@ -427,12 +437,22 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
         }
         const Job &J = job_ref(prm, ji);  // only its tensor map is used, in place
         const uint32_t rows = p - 1;
+        if (items && use_tmap && ji != acquired) {
+            if (lane == 0) acquire_tmap(&J.tmap);
+            acquired = ji;
+        }
 
         for (uint32_t q = 0; q < nt && ok; ++q) {
             if (q == 0 && items && u < total_units) {  // the next item's descriptor
                 const uint32_t njob = __shfl_sync(0xffffffffu, nxt, 22);
                 const uint32_t ntm = (__shfl_sync(0xffffffffu, nxt, 24) >> 8) & 0xffu;
-                if (lane == 0 && ntm) prefetch_tmap(&prm.jobs[njob].tmap);
+                if (ntm && njob != acquired) {
+                    if (lane == 0) {
+                        acquire_tmap(&prm.jobs[njob].tmap);
+                        prefetch_tmap(&prm.jobs[njob].tmap);
+                    }
+                    acquired = njob;
+                }
             }
             const uint64_t local = lt0 + q;
             const uint32_t stripe = static_cast<uint32_t>(local / tps);

@@ -6,18 +6,21 @@
 // the context while the server runs and repeats:
 //   1. retire: launches whose completion event has fired complete their
 //      requests (completion time = when the host sees the event), freeing
-//      their HBM footprint and in-flight slots;
+//      their HBM footprint, in-flight slots and device byte ranges;
 //   2. admit: requests whose arrival time has passed are admitted in arrival
-//      order while the in-flight slot count and the HBM budget allow -- a
-//      request on a stripe that an earlier admitted request still uses waits
-//      (two jobs on one stripe must not share a batch);
-//   3. launch: while fewer than two launches are in flight, everything
-//      admitted and not yet launched (up to max_batch_jobs) goes out as ONE
-//      persistent-kernel batch -- so requests that arrived while the previous
-//      batch ran join the next one (continuous batching), and the next batch
-//      is prepared on the host while the GPU runs the current one.
-// In per-job mode (the comparison) each admitted request is launched on its
-// own with the single-operation call.  Latency = completion - arrival.
+//      order while the in-flight count and the HBM budget allow.  A request
+//      whose device bytes (its stripes' extent, and its aux buffer's) overlap
+//      those of an admitted request -- or of an earlier request that is still
+//      waiting -- waits, so requests on the same bytes run in arrival order
+//      and never share a launch;
+//   3. launch: batched mode -- while fewer than two launches are in flight,
+//      everything admitted and not yet launched (up to max_batch_jobs) goes
+//      out as ONE persistent-kernel batch, so requests that arrived while the
+//      previous batch ran join the next one (continuous batching) and the next
+//      batch is prepared on the host while the GPU runs the current one;
+//      per-job mode (the comparison) -- every admitted request is launched at
+//      once with its own single-operation call and completion event.
+// Latency = completion - arrival.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -27,10 +30,10 @@
 #include <atomic>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "../../include/rcg.h"
@@ -44,10 +47,17 @@ uint64_t mono_ns() {
     return static_cast<uint64_t>(ts.tv_sec) * 1000000000ull + ts.tv_nsec;
 }
 
+// A device byte range [lo, hi) a request reads or writes.
+struct Extent {
+    uintptr_t lo = 0, hi = 0;
+};
+
 struct Request {
     rcg_serve_request req;
     uint64_t id;
     uint64_t footprint;
+    Extent ext[2];
+    uint32_t n_ext = 0;
     uint64_t admit_ns = 0, launch_ns = 0, complete_ns = 0;
     uint32_t status = RCG_OK;
     uint32_t batch = 0;
@@ -59,13 +69,55 @@ struct Launch {
     uint64_t ticket = 0;         // batch mode
 };
 
+struct Strides {
+    uint64_t rs, ss, st, ars, ass;
+};
+
+Strides strides_of(const rcg_job &j) {
+    const rcg_layout &L = j.layout;
+    Strides s;
+    s.rs = L.row_stride ? L.row_stride : L.row_bytes;
+    s.ss = L.strip_stride ? L.strip_stride : (L.p - 1ull) * s.rs;
+    s.st = L.stripe_stride ? L.stripe_stride : (L.n_data + 2ull) * s.ss;
+    s.ars = j.aux_row_stride ? j.aux_row_stride : L.row_bytes;
+    s.ass = j.aux_stripe_stride ? j.aux_stripe_stride : (L.p - 1ull) * s.ars;
+    return s;
+}
+
+bool uses_aux(const rcg_job &j) { return j.op == RCG_OP_DEGRADED_READ || j.op == RCG_OP_UPDATE; }
+
 uint64_t job_footprint(const rcg_job &j) {
     const rcg_layout &L = j.layout;
-    const uint64_t rs = L.row_stride ? L.row_stride : L.row_bytes;
-    const uint64_t ss = L.strip_stride ? L.strip_stride : (L.p - 1ull) * rs;
-    uint64_t fp = (L.n_data + 2ull) * ss * j.n_stripes;
-    if (j.op == RCG_OP_DEGRADED_READ || j.op == RCG_OP_UPDATE) fp += (L.p - 1ull) * L.row_bytes * j.n_stripes;
+    const Strides s = strides_of(j);
+    uint64_t fp = (L.n_data + 2ull) * s.ss * j.n_stripes;
+    if (uses_aux(j)) fp += (L.p - 1ull) * L.row_bytes * j.n_stripes;
     return fp;
+}
+
+// The device bytes a job touches: from its first stripe's first byte to one
+// past the last byte of row p-2 of strip N+1 of its last stripe, and the same
+// for the aux buffer of a degraded read or small write.  Overlapping extents
+// are merged.
+uint32_t job_extents(const rcg_job &j, Extent *out) {
+    const rcg_layout &L = j.layout;
+    const Strides s = strides_of(j);
+    const uint64_t n = j.n_stripes ? j.n_stripes : 1;
+    uint32_t k = 0;
+    out[k].lo = reinterpret_cast<uintptr_t>(L.base) + j.first_stripe * s.st;
+    out[k].hi = out[k].lo + (n - 1) * s.st + (L.n_data + 1ull) * s.ss + (L.p - 2ull) * s.rs + L.row_bytes;
+    ++k;
+    if (uses_aux(j) && j.aux) {
+        Extent a;
+        a.lo = reinterpret_cast<uintptr_t>(j.aux);
+        a.hi = a.lo + (n - 1) * s.ass + (L.p - 2ull) * s.ars + L.row_bytes;
+        if (a.lo < out[0].hi && out[0].lo < a.hi) {
+            out[0].lo = std::min(out[0].lo, a.lo);
+            out[0].hi = std::max(out[0].hi, a.hi);
+        } else {
+            out[k++] = a;
+        }
+    }
+    return k;
 }
 
 }  // namespace
@@ -78,16 +130,22 @@ struct rcg_server {
     std::mutex mu;
     std::condition_variable cv;
     std::vector<Request> reqs;          // by id
-    std::deque<uint64_t> pending;       // submitted, not admitted (arrival order of submission)
+    std::deque<uint64_t> pending;       // submitted, not yet examined (arrival order of submission)
+    std::deque<uint64_t> blocked;       // arrived and examined, waiting on an overlapping request
+    std::map<uintptr_t, uintptr_t> waiting;  // union of the blocked requests' extents, lo -> hi (merged)
     std::deque<uint64_t> admitted;      // admitted, not launched
     std::deque<Launch> inflight;        // launched, not retired
-    std::unordered_map<uintptr_t, uint32_t> busy;  // stripe base -> requests admitted on it
+    std::map<uintptr_t, uintptr_t> busy;  // device byte ranges of admitted requests, lo -> hi (disjoint)
     std::vector<cudaEvent_t> free_events;
     uint64_t budget_used = 0;
     uint32_t inflight_jobs = 0;
     uint64_t start_ns = 0;
     uint64_t completed = 0;
-    uint32_t batches = 0;
+    uint32_t launches = 0;              // launch numbers handed out (batches, or single jobs)
+    uint64_t kernel_launches = 0;
+    uint64_t conflict_waits = 0;
+    uint32_t max_inflight_launches = 0;
+    uint32_t max_inflight_jobs = 0;
     std::atomic<bool> stop{false};
     std::atomic<bool> running{false};
     rcg_status error = RCG_OK;
@@ -106,12 +164,23 @@ cudaEvent_t get_event(rcg_server *s) {
     return e;
 }
 
-uintptr_t stripe_key(const rcg_job &j) {
-    const rcg_layout &L = j.layout;
-    const uint64_t rs = L.row_stride ? L.row_stride : L.row_bytes;
-    const uint64_t ss = L.strip_stride ? L.strip_stride : (L.p - 1ull) * rs;
-    const uint64_t st = L.stripe_stride ? L.stripe_stride : (L.n_data + 2ull) * ss;
-    return reinterpret_cast<uintptr_t>(L.base) + j.first_stripe * st;
+// Does [e.lo, e.hi) overlap a range of the disjoint, sorted map?
+bool overlaps(const std::map<uintptr_t, uintptr_t> &m, const Extent &e) {
+    auto it = m.upper_bound(e.lo);
+    if (it != m.begin() && std::prev(it)->second > e.lo) return true;
+    return it != m.end() && it->first < e.hi;
+}
+
+// Add [e.lo, e.hi) to a disjoint, sorted map, merging the ranges it touches.
+void insert_merged(std::map<uintptr_t, uintptr_t> &m, Extent e) {
+    auto it = m.upper_bound(e.lo);
+    if (it != m.begin() && std::prev(it)->second >= e.lo) --it;
+    while (it != m.end() && it->first <= e.hi) {
+        e.lo = std::min(e.lo, it->first);
+        e.hi = std::max(e.hi, it->second);
+        it = m.erase(it);
+    }
+    m[e.lo] = e.hi;
 }
 
 rcg_status launch_single_job(rcg_ctx *ctx, const rcg_job &j, cudaStream_t s) {
@@ -132,12 +201,17 @@ rcg_status launch_single_job(rcg_ctx *ctx, const rcg_job &j, cudaStream_t s) {
     return RCG_EINVAL;
 }
 
+void note_launch(rcg_server *s) {
+    s->max_inflight_launches = std::max<uint32_t>(s->max_inflight_launches, static_cast<uint32_t>(s->inflight.size()));
+}
+
 // One pass of the scheduler; returns true when it did something.
 bool tick(rcg_server *s) {
     bool did = false;
     const uint64_t now = mono_ns() - s->start_ns;
     std::unique_lock<std::mutex> lock(s->mu);
-    // 1. retire, in launch order
+    // 1. retire, in launch order (one stream: launches finish in order)
+    bool freed = false;
     while (!s->inflight.empty()) {
         Launch &L = s->inflight.front();
         const cudaError_t q = cudaEventQuery(L.done);
@@ -148,79 +222,105 @@ bool tick(rcg_server *s) {
             if (q != cudaSuccess) r.status = RCG_ECUDA;
             s->budget_used -= r.footprint;
             --s->inflight_jobs;
-            auto it = s->busy.find(stripe_key(r.req.job));
-            if (it != s->busy.end() && --it->second == 0) s->busy.erase(it);
+            for (uint32_t k = 0; k < r.n_ext; ++k) s->busy.erase(r.ext[k].lo);
         }
         s->completed += L.ids.size();
         s->free_events.push_back(L.done);
         s->inflight.pop_front();
+        freed = true;
         did = true;
         s->cv.notify_all();
     }
+    // Blocked requests can only move once something has retired: then they
+    // are examined again, ahead of the later arrivals, and the union of
+    // waiting extents is rebuilt as they are.
+    if (freed && !s->blocked.empty()) {
+        s->pending.insert(s->pending.begin(), s->blocked.begin(), s->blocked.end());
+        s->blocked.clear();
+        s->waiting.clear();
+    }
     // 2. admit arrived requests in order while slots and HBM allow; a request
-    //    on a stripe still in use waits (without blocking the ones behind it)
-    for (auto it = s->pending.begin(); it != s->pending.end();) {
-        Request &r = s->reqs[*it];
+    //    whose bytes overlap an admitted one's, or a blocked earlier one's,
+    //    is blocked too (the ones behind it that do not overlap go ahead)
+    while (!s->pending.empty()) {
+        Request &r = s->reqs[s->pending.front()];
         if (r.req.arrival_ns > now) break;
         if (s->inflight_jobs >= s->cfg.max_inflight_jobs) break;
         if (s->budget_used + r.footprint > s->cfg.hbm_budget_bytes) break;
-        const uintptr_t key = stripe_key(r.req.job);
-        if (s->busy.count(key)) {
-            ++it;
+        bool conflict = false;
+        for (uint32_t k = 0; k < r.n_ext && !conflict; ++k)
+            conflict = overlaps(s->busy, r.ext[k]) || overlaps(s->waiting, r.ext[k]);
+        if (conflict) {
+            for (uint32_t k = 0; k < r.n_ext; ++k) insert_merged(s->waiting, r.ext[k]);
+            ++s->conflict_waits;
+            s->blocked.push_back(s->pending.front());
+            s->pending.pop_front();
             continue;
         }
-        s->busy[key] = 1;
+        for (uint32_t k = 0; k < r.n_ext; ++k) s->busy[r.ext[k].lo] = r.ext[k].hi;
         s->budget_used += r.footprint;
         ++s->inflight_jobs;
+        s->max_inflight_jobs = std::max(s->max_inflight_jobs, s->inflight_jobs);
         r.admit_ns = now;
-        s->admitted.push_back(*it);
-        it = s->pending.erase(it);
+        s->admitted.push_back(s->pending.front());
+        s->pending.pop_front();
         did = true;
     }
-    // 3. launch what is admitted, keeping at most two launches in flight
+    // 3a. per-job mode: every admitted request goes out at once, on its own
+    if (s->cfg.per_job_launches) {
+        while (!s->admitted.empty()) {
+            const uint64_t id = s->admitted.front();
+            s->admitted.pop_front();
+            const rcg_job job = s->reqs[id].req.job;
+            const uint32_t launch_no = ++s->launches;
+            lock.unlock();
+            const uint64_t t_launch = mono_ns() - s->start_ns;
+            const rcg_status st = launch_single_job(s->ctx, job, s->stream);
+            Launch one;
+            one.ids.push_back(id);
+            one.done = get_event(s);
+            cudaEventRecord(one.done, s->stream);
+            lock.lock();
+            Request &r = s->reqs[id];
+            r.launch_ns = t_launch;
+            r.batch = launch_no;
+            if (st != RCG_OK) {
+                r.status = st;
+                if (s->error == RCG_OK) s->error = st;
+            } else {
+                ++s->kernel_launches;
+            }
+            s->inflight.push_back(std::move(one));
+            note_launch(s);
+            did = true;
+        }
+        return did;
+    }
+    // 3b. batched mode: what is admitted goes out as one batch, keeping at
+    //     most two batches in flight
     if (!s->admitted.empty() && s->inflight.size() < 2) {
         const uint32_t n = static_cast<uint32_t>(std::min<size_t>(s->admitted.size(), s->cfg.max_batch_jobs));
         std::vector<uint64_t> ids(s->admitted.begin(), s->admitted.begin() + n);
         s->admitted.erase(s->admitted.begin(), s->admitted.begin() + n);
         std::vector<rcg_job> jobs(n);
         for (uint32_t k = 0; k < n; ++k) jobs[k] = s->reqs[ids[k]].req.job;
-        const uint32_t batch_no = ++s->batches;
+        const uint32_t launch_no = ++s->launches;
         lock.unlock();  // host preparation runs without the lock
         const uint64_t t_launch = mono_ns() - s->start_ns;
-        rcg_status st = RCG_OK;
         Launch L;
-        if (s->cfg.per_job_launches) {
-            for (uint32_t k = 0; k < n && st == RCG_OK; ++k) {
-                st = launch_single_job(s->ctx, jobs[k], s->stream);
-                if (st == RCG_OK && k + 1 < n) {  // one completion event per job
-                    Launch one;
-                    one.ids.push_back(ids[k]);
-                    one.done = get_event(s);
-                    cudaEventRecord(one.done, s->stream);
-                    lock.lock();
-                    s->reqs[ids[k]].launch_ns = t_launch;
-                    s->reqs[ids[k]].batch = batch_no;
-                    s->inflight.push_back(std::move(one));
-                    lock.unlock();
-                    ids[k] = ~0ull;
-                }
-            }
-        } else {
-            st = rcg_batch_submit(s->ctx, jobs.data(), n, s->stream, &L.ticket);
-        }
+        const rcg_status st = rcg_batch_submit(s->ctx, jobs.data(), n, s->stream, &L.ticket);
+        L.done = get_event(s);
+        cudaEventRecord(L.done, s->stream);
         lock.lock();
-        for (uint64_t id : ids)
-            if (id != ~0ull) {
-                L.ids.push_back(id);
-                s->reqs[id].launch_ns = t_launch;
-                s->reqs[id].batch = batch_no;
-                if (st != RCG_OK) s->reqs[id].status = st;
-            }
-        if (!L.ids.empty()) {
-            L.done = get_event(s);
-            cudaEventRecord(L.done, s->stream);
-            s->inflight.push_back(std::move(L));
+        L.ids = ids;
+        for (uint64_t id : ids) {
+            s->reqs[id].launch_ns = t_launch;
+            s->reqs[id].batch = launch_no;
+            if (st != RCG_OK) s->reqs[id].status = st;
         }
+        if (st == RCG_OK) ++s->kernel_launches;
+        s->inflight.push_back(std::move(L));
+        note_launch(s);
         if (st != RCG_OK && s->error == RCG_OK) s->error = st;
         did = true;
     }
@@ -270,18 +370,24 @@ rcg_status rcg_serve_create(rcg_ctx *ctx, const rcg_serve_config *cfg, rcg_serve
 
 rcg_status rcg_serve_submit(rcg_server *s, const rcg_serve_request *reqs, uint32_t n, uint64_t *first_id) {
     if (!s || (n && !reqs)) return RCG_EINVAL;
+    // validate every request before queueing any (all or nothing)
+    std::vector<Request> batch(n);
+    for (uint32_t k = 0; k < n; ++k) {
+        const rcg_job &j = reqs[k].job;
+        if (j.n_stripes == 0 || (j.n_stripes != 1 && j.op != RCG_OP_ENCODE)) return RCG_EINVAL;
+        if (!j.layout.base || j.layout.p < 3 || j.layout.n_data < 1 || j.layout.row_bytes == 0) return RCG_EINVAL;
+        Request &r = batch[k];
+        r.req = reqs[k];
+        r.footprint = reqs[k].footprint_bytes ? reqs[k].footprint_bytes : job_footprint(j);
+        if (r.footprint > s->cfg.hbm_budget_bytes) return RCG_EINVAL;  // could never be admitted
+        r.n_ext = job_extents(j, r.ext);
+    }
     std::lock_guard<std::mutex> lock(s->mu);
     const uint64_t first = s->reqs.size();
     for (uint32_t k = 0; k < n; ++k) {
-        const rcg_job &j = reqs[k].job;
-        if (j.n_stripes != 1 && j.op != RCG_OP_ENCODE) return RCG_EINVAL;
-        Request r;
-        r.req = reqs[k];
-        r.id = first + k;
-        r.footprint = reqs[k].footprint_bytes ? reqs[k].footprint_bytes : job_footprint(j);
-        if (r.footprint > s->cfg.hbm_budget_bytes) return RCG_EINVAL;  // could never be admitted
-        s->reqs.push_back(r);
-        s->pending.push_back(r.id);
+        batch[k].id = first + k;
+        s->reqs.push_back(batch[k]);
+        s->pending.push_back(first + k);
     }
     if (first_id) *first_id = first;
     return RCG_OK;
@@ -322,6 +428,17 @@ rcg_status rcg_serve_results(rcg_server *s, rcg_serve_result *out, uint64_t max,
         out[k].batch = r.batch;
     }
     *n = m;
+    return RCG_OK;
+}
+
+rcg_status rcg_serve_get_stats(rcg_server *s, rcg_serve_stats *out) {
+    if (!s || !out) return RCG_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    out->kernel_launches = s->kernel_launches;
+    out->completed = s->completed;
+    out->conflict_waits = s->conflict_waits;
+    out->max_inflight_launches = s->max_inflight_launches;
+    out->max_inflight_jobs = s->max_inflight_jobs;
     return RCG_OK;
 }
 

@@ -62,6 +62,11 @@ class rcg_serve_result(ctypes.Structure):
                 ("complete_ns", _u64), ("status", _u32), ("batch", _u32)]
 
 
+class rcg_serve_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", _u64), ("completed", _u64), ("conflict_waits", _u64),
+                ("max_inflight_launches", _u32), ("max_inflight_jobs", _u32)]
+
+
 class rcg_plan_info(ctypes.Structure):
     _fields_ = [("tile_bytes", _u32), ("tiles_per_stripe", _u32), ("slot_bytes", _u32), ("n_slots", _u32),
                 ("max_items", _u32), ("smem_bytes", _u32), ("ctas_per_sm", _u32), ("shape", _u32)]
@@ -111,6 +116,7 @@ EXPORTS = {
     "rcg_serve_start": (_int, [_vp]),
     "rcg_serve_drain": (_int, [_vp, _u64]),
     "rcg_serve_results": (_int, [_vp, ctypes.POINTER(rcg_serve_result), _u64, ctypes.POINTER(_u64)]),
+    "rcg_serve_get_stats": (_int, [_vp, ctypes.POINTER(rcg_serve_stats)]),
     "rcg_serve_destroy": (_int, [_vp]),
     "rcg_batch_submit_noalloc": (_int, [ctypes.POINTER(rcg_job), _u32, _vp, _vp]),
     "rcg_fill_random": (_int, [_vp, _u64, _u64, _u64, _vp]),
@@ -406,6 +412,14 @@ def rcg_serve_results(server: int, n: int):
     got = _u64(0)
     _check(lib().rcg_serve_results(server, arr, n, ctypes.byref(got)), "rcg_serve_results")
     return [{f: int(getattr(arr[k], f)) for f, _ in rcg_serve_result._fields_} for k in range(int(got.value))]
+
+
+def rcg_serve_get_stats(server: int) -> dict:
+    """Kernel launches issued, requests completed, conflict waits, and the most
+    launches / requests in flight at once."""
+    st = rcg_serve_stats()
+    _check(lib().rcg_serve_get_stats(server, ctypes.byref(st)), "rcg_serve_get_stats")
+    return {f: int(getattr(st, f)) for f, _ in rcg_serve_stats._fields_}
 
 
 def rcg_serve_destroy(server: int):

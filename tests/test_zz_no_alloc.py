@@ -2,9 +2,11 @@
 allocate device memory (a framework whose allocator owns the whole GPU, or a
 submit path that cannot take cudaMalloc's implicit synchronisation).
 
-It must give exactly the bytes rcg_batch_submit gives for the same jobs --
-the code is XOR over GF(2), so the tolerance is zero -- on two calls in a row,
-the second reusing the scratch the first one left behind.  This file is
+It must give exactly the bytes rcg_batch_submit gives for the same jobs, and
+the bytes of the CPU oracle -- the code is XOR over GF(2), so the tolerance is
+zero -- on two calls in a row, the second reusing the scratch the first one
+left behind.  Recoveries, degraded reads and small writes run on stripes the
+oracle encoded (codewords), so the bytes they check are the code's.  This file is
 collected last so that a failure here does not hide the rest of the suite.
 """
 import numpy as np
@@ -26,55 +28,84 @@ def rcg():
     return R
 
 
-def make_batch(rcg, seed, specs):
-    """Device buffers and jobs for a mixed batch; returns (buffers, jobs, outs)."""
-    bufs, jobs, outs = [], [], []
+def make_batch(rcg, oracle, seed, specs):
+    """Device buffers and jobs for a mixed batch, and the oracle's expected
+    bytes.  Recoveries, degraded reads and small writes run on stripes the
+    oracle encoded first (codewords); a recovery's erased strips are poisoned.
+    Returns (buffers, jobs, outs, expected buffers, expected outs)."""
+    bufs, jobs, outs, want_bufs, want_outs = [], [], [], [], []
     for n, (p, N, C, S, kind) in enumerate(specs):
         host = np.ascontiguousarray(inputs.random_stripes(seed + n, p, N, C, S))
+        if kind != "enc":
+            oracle.encode(p, N, C, host, S)
+        want = host.copy()
+        if kind == "enc":
+            oracle.encode(p, N, C, want, S)
+        elif kind == "rec":
+            i, j = 1, min(3, N + 1)
+            host[:, i] = 0xA5
+            host[:, j] = 0x5A
         buf = torch.from_numpy(host).cuda()
         L = rcg.make_layout(buf, p, N, C)
         if kind == "enc":
             jobs.append(rcg.make_job(L, 0, S, rcg.RCG_OP_ENCODE))
         elif kind == "rec":
-            jobs.append(rcg.make_job(L, 0, S, rcg.RCG_OP_RECOVER, 1, min(3, N + 1)))
+            jobs.append(rcg.make_job(L, 0, S, rcg.RCG_OP_RECOVER, i, j))
         elif kind == "deg":
             out = torch.zeros((S, p - 1, C), dtype=torch.uint8, device="cuda")
             outs.append(out)
+            want_outs.append(np.stack([oracle.degraded_read(p, N, C, want, s, 0) for s in range(S)]))
             jobs.append(rcg.make_job(L, 0, S, rcg.RCG_OP_DEGRADED_READ, 0, 0, out))
         elif kind == "upd":
-            new = torch.from_numpy(inputs.random_bytes(seed + 99, S * (p - 1) * C).reshape(S, p - 1, C)).cuda()
-            outs.append(new)
-            jobs.append(rcg.make_job(L, 0, S, rcg.RCG_OP_UPDATE, N - 1, 0, new))
+            new = inputs.random_bytes(seed + 99, S * (p - 1) * C).reshape(S, p - 1, C)
+            for s in range(S):
+                oracle.update(p, N, C, want, s, N - 1, new[s])
+            new_dev = torch.from_numpy(np.ascontiguousarray(new)).cuda()
+            outs.append(new_dev)
+            want_outs.append(new)
+            jobs.append(rcg.make_job(L, 0, S, rcg.RCG_OP_UPDATE, N - 1, 0, new_dev))
         bufs.append(buf)
-    return bufs, jobs, outs
+        want_bufs.append(want)
+    return bufs, jobs, outs, want_bufs, want_outs
 
 
-def run_both(rcg, seed, specs):
+def run_both(rcg, oracle, seed, specs, with_status=True):
     # reference: the existing context-based batch entry point
-    ref_bufs, ref_jobs, ref_outs = make_batch(rcg, seed, specs)
+    ref_bufs, ref_jobs, ref_outs, _, _ = make_batch(rcg, oracle, seed, specs)
     with rcg.Context(0) as ctx:
         t = ctx.batch_submit(ref_jobs)
         assert ctx.batch_wait(t)
         assert ctx.last_device_status() == 0
     # the same jobs through the no-allocation entry point
-    bufs, jobs, outs = make_batch(rcg, seed, specs)
-    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    bufs, jobs, outs, want_bufs, want_outs = make_batch(rcg, oracle, seed, specs)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda") if with_status else None
     rcg.rcg_batch_submit_noalloc(jobs, status)
     torch.cuda.synchronize()
-    assert int(status.item()) == 0
-    for a, b in zip(ref_bufs, bufs):
+    if with_status:
+        assert int(status.item()) == 0
+    for a, b, w in zip(ref_bufs, bufs, want_bufs):
         assert torch.equal(a, b)
-    for a, b in zip(ref_outs, outs):
+        assert np.array_equal(b.cpu().numpy(), w)  # and the oracle's bytes
+    for a, b, w in zip(ref_outs, outs, want_outs):
         assert torch.equal(a, b)
+        assert np.array_equal(b.cpu().numpy(), w)
 
 
-def test_noalloc_matches_batch_submit_twice_in_a_row(rcg):
-    first = [(13, 12, 4096, 6, "enc"), (5, 4, 1024, 9, "rec"), (59, 58, 528, 2, "rec"),
-             (29, 7, 1040, 3, "deg"), (13, 6, 256, 4, "upd"), (3, 2, 16, 5, "enc")]
-    second = [(59, 58, 2048, 3, "enc"), (13, 12, 1024, 40, "rec"), (61, 60, 64, 2, "deg"),
-              (5, 4, 64, 17, "upd")]
-    run_both(rcg, 1000, first)
-    run_both(rcg, 2000, second)
+FIRST = [(13, 12, 4096, 6, "enc"), (5, 4, 1024, 9, "rec"), (59, 58, 528, 2, "rec"),
+         (29, 7, 1040, 3, "deg"), (13, 6, 256, 4, "upd"), (3, 2, 16, 5, "enc")]
+SECOND = [(59, 58, 2048, 3, "enc"), (13, 12, 1024, 40, "rec"), (61, 60, 64, 2, "deg"),
+          (5, 4, 64, 17, "upd")]
+
+
+def test_noalloc_matches_batch_submit_twice_in_a_row(rcg, oracle):
+    run_both(rcg, oracle, 1000, FIRST)
+    run_both(rcg, oracle, 2000, SECOND)
+
+
+def test_noalloc_without_a_status_word(rcg, oracle):
+    # with status_dev = NULL device-side errors go unreported, but a valid
+    # batch still gives the oracle's bytes
+    run_both(rcg, oracle, 3000, SECOND, with_status=False)
 
 
 def test_noalloc_rejects_too_many_jobs(rcg):
