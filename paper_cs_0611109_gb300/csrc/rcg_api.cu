@@ -33,6 +33,9 @@ struct BatchSlot {
     cudaGraph_t graph = nullptr;       // kept alive: exec updates name its nodes
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t copy_node = nullptr;
+    cudaGraphNode_t col_nodes[kColVariants] = {};  // column kernels of the p <= 7 jobs
+    cudaGraphNode_t engine_node = nullptr;         // the tile engine
+    int enabled = -1;  // bit v: column variant v enabled; bit 4: tile engine; -1 unknown
     cudaEvent_t done = nullptr;
     uint32_t shape = 0;  // engine shape the graph's kernel node was captured with
     uint64_t ticket = 0;
@@ -207,16 +210,33 @@ rcg_status launch_single(rcg_ctx *ctx, const Job &J, const Plan &pl, cudaStream_
     return from_cuda(launch_engine(prm, pl.shape, static_cast<int>(grid), stream));
 }
 
-// The column kernel serves single-operation encode and recovery launches of
-// p <= 7 unless the context asks for the tile engine.
+// The column kernel serves single-operation launches of p <= 7 unless the
+// context asks for the tile engine.
 bool use_column(const rcg_ctx *ctx, const Geo &g) { return ctx->column == RCG_COLUMN_AUTO && g.p <= 7; }
 
-rcg_status launch_column_op(rcg_ctx *ctx, const rcg_layout *L, const Geo &g, uint64_t first, uint64_t n,
-                            uint32_t i, uint32_t j, const uint8_t *pairs, cudaStream_t stream) {
+ColJob column_job(const rcg_layout *L, const Geo &g, uint64_t first, uint32_t op, uint32_t i, uint32_t j,
+                  const uint8_t *pairs, void *aux = nullptr, uint64_t ars = 0) {
+    ColJob J;
+    memset(&J, 0, sizeof(J));
+    J.base = static_cast<uint8_t *>(L->base) + first * g.st;
+    J.pairs = pairs;
+    J.aux = static_cast<uint8_t *>(aux);
+    J.rs = g.rs;
+    J.ss = g.ss;
+    J.st = g.st;
+    J.ars = ars;
+    J.ass = (g.p - 1) * ars;
+    J.vps = static_cast<uint32_t>(g.C / 16);
+    J.N = g.N;
+    J.i = i;
+    J.j = j;
+    J.op = op;
+    return J;
+}
+
+rcg_status launch_column_op(rcg_ctx *ctx, const ColJob &J, const Geo &g, uint64_t n, cudaStream_t stream) {
     DeviceGuard guard(ctx->device);
-    return from_cuda(launch_column(static_cast<uint8_t *>(L->base) + first * g.st, g.p, g.N, g.C, g.rs, g.ss, g.st, n,
-                                   i, j, pairs, ctx->status, ctx->sm_count, stream),
-                     "column kernel launch");
+    return from_cuda(launch_column(J, g.p, n, ctx->status, ctx->sm_count, stream), "column kernel launch");
 }
 
 uint64_t now_ns() {
@@ -466,7 +486,7 @@ rcg_status rcg_encode(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_stripe, 
     if (n_stripes == 0) return RCG_OK;
     if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
     if (use_column(ctx, g))
-        return launch_column_op(ctx, L, g, first_stripe, n_stripes, g.N, g.N + 1, nullptr,
+        return launch_column_op(ctx, column_job(L, g, first_stripe, OP_ENCODE, 0, 0, nullptr), g, n_stripes,
                                 static_cast<cudaStream_t>(stream));
     Plan pl;
     if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, n_stripes)), &pl)) return RCG_EINVAL;
@@ -484,7 +504,8 @@ rcg_status rcg_recover(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint3
     if (st) return st;
     if (!(i < j && j <= g.N + 1)) return RCG_EINVAL;
     if (use_column(ctx, g))
-        return launch_column_op(ctx, L, g, stripe, 1, i, j, nullptr, static_cast<cudaStream_t>(stream));
+        return launch_column_op(ctx, column_job(L, g, stripe, OP_RECOVER, i, j, nullptr), g, 1,
+                                static_cast<cudaStream_t>(stream));
     Plan pl;
     if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, 1)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, stripe, 1, pl);
@@ -504,7 +525,8 @@ rcg_status rcg_recover_many(rcg_ctx *ctx, const rcg_layout *L, uint64_t first_st
     if (n_stripes == 0) return RCG_OK;
     if (n_stripes > 0x7fffffffull) return RCG_EINVAL;
     if (use_column(ctx, g))
-        return launch_column_op(ctx, L, g, first_stripe, n_stripes, 0, 0, pairs, static_cast<cudaStream_t>(stream));
+        return launch_column_op(ctx, column_job(L, g, first_stripe, OP_RECOVER, 0, 0, pairs), g, n_stripes,
+                                static_cast<cudaStream_t>(stream));
     Plan pl;
     if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, n_stripes)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, first_stripe, n_stripes, pl);
@@ -523,6 +545,9 @@ rcg_status rcg_update(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe, uint32
     if (i >= g.N) return RCG_EINVAL;
     const uint64_t ars = new_row_stride ? new_row_stride : g.C;
     if (ars < g.C || (ars & 15)) return RCG_EINVAL;
+    if (use_column(ctx, g))
+        return launch_column_op(ctx, column_job(L, g, stripe, OP_UPDATE, i, 0, nullptr, const_cast<void *>(new_strip), ars),
+                                g, 1, static_cast<cudaStream_t>(stream));
     Plan pl;
     if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, 1)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, stripe, 1, pl);
@@ -544,6 +569,9 @@ rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe,
     if (j > g.N + 1) return RCG_EINVAL;
     const uint64_t ors = out_row_stride ? out_row_stride : g.C;
     if (ors < g.C || (ors & 15)) return RCG_EINVAL;
+    if (use_column(ctx, g))
+        return launch_column_op(ctx, column_job(L, g, stripe, OP_DEGRADED, 0, j, nullptr, out, ors), g, 1,
+                                static_cast<cudaStream_t>(stream));
     Plan pl;
     if (!make_plan(g.p, g.C, choose_shape(ctx, launch_bytes(g, 1)), &pl)) return RCG_EINVAL;
     Job J = base_job(ctx, L, g, stripe, 1, pl);
@@ -640,13 +668,17 @@ static rcg_status build_job(const rcg_ctx *ctx, const rcg_job &in, uint32_t shap
 }
 
 // Capture the slot's graph: descriptor-table copy -> tile-counter reset ->
-// persistent kernel of the given engine shape.
+// the column kernels of the four p <= 7 variants -> persistent tile engine of
+// the given shape.  A launch enables only the kernels its table has work for.
 static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
     if (s.exec) cudaGraphExecDestroy(s.exec);
     if (s.graph) cudaGraphDestroy(s.graph);
     s.exec = nullptr;
     s.graph = nullptr;
     s.copy_node = nullptr;
+    s.engine_node = nullptr;
+    for (auto &n : s.col_nodes) n = nullptr;
+    s.enabled = -1;
     const size_t bytes = s.cap_bytes;
     s.bytes = bytes;
     cudaGraph_t graph = nullptr;
@@ -655,9 +687,12 @@ static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
     if (e == cudaSuccess) {
         cudaError_t e1 = cudaMemcpyAsync(s.dev, s.host, bytes, cudaMemcpyHostToDevice, s.capture);
         cudaError_t e2 = cudaMemsetAsync(s.counter, 0, sizeof(unsigned long long), s.capture);
-        cudaError_t e3 = launch_batch(s.dev, ctx->status, s.counter, ctx->timeout_ns, shape,
-                                      ctx->sm_count * static_cast<int>(shape_info(shape).ctas_per_sm),
-                                      s.capture);
+        cudaError_t e3 = cudaSuccess;
+        for (int v = 0; v < kColVariants && e3 == cudaSuccess; ++v)
+            e3 = launch_column_batch(v, s.dev, ctx->status, ctx->sm_count, s.capture);
+        if (e3 == cudaSuccess)
+            e3 = launch_batch(s.dev, ctx->status, s.counter, ctx->timeout_ns, shape,
+                              ctx->sm_count * static_cast<int>(shape_info(shape).ctas_per_sm), s.capture);
         e = cudaStreamEndCapture(s.capture, &graph);
         if (e1 != cudaSuccess) { e = e1; where = "captured table copy"; }
         else if (e2 != cudaSuccess) { e = e2; where = "captured counter reset"; }
@@ -674,9 +709,23 @@ static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
         cudaGraphGetNodes(graph, nodes.data(), &n);
         for (auto nd : nodes) {
             cudaGraphNodeType t;
-            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeMemcpy) s.copy_node = nd;
+            if (cudaGraphNodeGetType(nd, &t) != cudaSuccess) continue;
+            if (t == cudaGraphNodeTypeMemcpy) s.copy_node = nd;
+            if (t != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+            bool col = false;
+            for (int v = 0; v < kColVariants; ++v)
+                if (kp.func == column_batch_function(v)) {
+                    s.col_nodes[v] = nd;
+                    col = true;
+                }
+            if (!col) s.engine_node = nd;
         }
-        if (!s.copy_node) e = cudaErrorUnknown;
+        bool all = s.copy_node && s.engine_node;
+        for (auto nd : s.col_nodes) all = all && nd;
+        if (!all) e = cudaErrorUnknown;
+        where = "graph nodes";
     }
     s.graph = graph;
     if (e != cudaSuccess) {
@@ -685,6 +734,25 @@ static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
     }
     s.shape = shape;
     return RCG_OK;
+}
+
+// Enable the graph's kernels that the table has work for (bit v: column
+// variant v; bit 4: the tile engine).
+static cudaError_t set_enabled(BatchSlot &s, int mask) {
+    if (mask == s.enabled) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < kColVariants && e == cudaSuccess; ++v)
+        e = cudaGraphNodeSetEnabled(s.exec, s.col_nodes[v], (mask >> v) & 1);
+    if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(s.exec, s.engine_node, (mask >> 4) & 1);
+    s.enabled = e == cudaSuccess ? mask : -1;
+    return e;
+}
+
+static int work_mask(const BatchHeader &h) {
+    int m = h.n_items ? 16 : 0;
+    for (int v = 0; v < kColVariants; ++v)
+        if (h.col_count[v]) m |= 1 << v;
+    return m;
 }
 
 // (Re)allocate a batch slot for a table of `bytes`; recapture its graph when
@@ -721,18 +789,28 @@ static uint32_t batch_shape(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_
 }
 
 // The descriptor table of a batch for one engine shape, built in `out`:
-// header, jobs, then work items (runs of tiles of one job of roughly equal
-// bytes); the items of larger jobs come first so the batch ends on small items.
+// header, jobs, work items of the tile engine (runs of tiles of one job of
+// roughly equal bytes; the items of larger jobs come first so the batch ends
+// on small items), then the column items of the p <= 7 jobs (when the
+// context uses the column kernel), grouped by variant.  max_items (0: no
+// limit) coarsens the work items to fit a fixed table; more column items
+// than max_col_items (0: no limit) is RCG_EINVAL.
 static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, uint32_t shape,
-                              uint64_t max_items, std::vector<uint8_t> &out) {
+                              uint64_t max_items, std::vector<uint8_t> &out, uint64_t max_col_items = 0) {
     std::vector<Job> table(n_jobs);
     std::vector<uint64_t> tiles(n_jobs);
+    std::vector<int> variant(n_jobs, -1);
     uint64_t total = 0;
     uint32_t slot_bytes = 0;
     for (uint32_t k = 0; k < n_jobs; ++k) {
         Plan pl;
         rcg_status st = build_job(ctx, jobs[k], shape, &table[k], &pl);
         if (st) return st;
+        if (ctx->column == RCG_COLUMN_AUTO) variant[k] = column_variant(table[k].p, table[k].n);
+        if (variant[k] >= 0) {
+            tiles[k] = 0;
+            continue;
+        }
         tiles[k] = static_cast<uint64_t>(table[k].n_stripes) * table[k].tiles_per_stripe;
         table[k].tile_begin = total;
         total += tiles[k];
@@ -743,14 +821,16 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     // alone at the end; max_items (the no-allocation table) can only raise it.
     uint64_t batch_bytes = 0;
     for (uint32_t k = 0; k < n_jobs; ++k)
-        batch_bytes += static_cast<uint64_t>(table[k].n_stripes) * (table[k].n + 2u) * (table[k].p - 1u) * table[k].C;
+        if (variant[k] < 0)
+            batch_bytes += static_cast<uint64_t>(table[k].n_stripes) * (table[k].n + 2u) * (table[k].p - 1u) * table[k].C;
     const uint64_t ctas = static_cast<uint64_t>(ctx->sm_count ? ctx->sm_count : 152) * shape_info(shape).ctas_per_sm;
     const uint64_t target = ctx->tune_item_bytes
                                 ? ctx->tune_item_bytes
                                 : std::min<uint64_t>(2ull << 20, std::max<uint64_t>(256ull << 10, batch_bytes / (ctas * 16)));
-    std::vector<uint64_t> per(n_jobs);
+    std::vector<uint64_t> per(n_jobs, 1);
     uint64_t n_items_est = 0;
     for (uint32_t k = 0; k < n_jobs; ++k) {
+        if (variant[k] >= 0) continue;
         const uint64_t tile_bytes = (table[k].n + 2ull) * (table[k].p - 1u) * table[k].W;
         per[k] = std::max<uint64_t>(1, target / tile_bytes);
         n_items_est += (tiles[k] + per[k] - 1) / per[k];
@@ -767,6 +847,7 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     });
     std::vector<WorkItem> items;
     for (uint32_t k : order) {
+        if (variant[k] >= 0) continue;
         const Job &J = table[k];
         WorkItem w;
         memset(&w, 0, sizeof(w));
@@ -799,10 +880,32 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     for (uint32_t k = 0; k < n_jobs; ++k)
         if (tiles[k] > 0xffffffffull) return RCG_EINVAL;
     if (items.size() > 0xffffffffull) return RCG_EINVAL;
+    // column items: one per p <= 7 job, grouped by variant, numbering the
+    // variant's 32-column chunks
+    std::vector<ColItem> col_items;
+    uint32_t col_begin[kColVariants] = {}, col_count[kColVariants] = {}, col_chunks[kColVariants] = {};
+    for (int v = 0; v < kColVariants; ++v) {
+        col_begin[v] = static_cast<uint32_t>(col_items.size());
+        uint64_t chunks = 0;
+        for (uint32_t k = 0; k < n_jobs; ++k) {
+            if (variant[k] != v) continue;
+            ColItem ci;
+            ci.job = k;
+            ci.pad = 0;
+            ci.chunk0 = chunks;
+            col_items.push_back(ci);
+            chunks += (static_cast<uint64_t>(table[k].n_stripes) * (table[k].C / 16) + kColChunk - 1) / kColChunk;
+        }
+        if (chunks > 0xffffffffull) return RCG_EINVAL;
+        col_count[v] = static_cast<uint32_t>(col_items.size()) - col_begin[v];
+        col_chunks[v] = static_cast<uint32_t>(chunks);
+    }
+    if (max_col_items && col_items.size() > max_col_items) return RCG_EINVAL;
     BatchHeader hdr;
     memset(&hdr, 0, sizeof(hdr));
     hdr.total_tiles = total;
     hdr.n_jobs = n_jobs;
+    if (slot_bytes == 0) slot_bytes = 128;  // no tile-engine job
     hdr.slot_bytes = slot_bytes;  // the largest stage
     if (ctx->tune_ring == RCG_RING_FIXED) {
         // equal slots of the largest stage, as many as the ring holds (the
@@ -820,10 +923,17 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     hdr.shape = shape;
     hdr.n_items = static_cast<uint32_t>(items.size());
     hdr.items_offset = sizeof(BatchHeader) + static_cast<uint64_t>(n_jobs) * sizeof(Job);
-    out.resize(hdr.items_offset + items.size() * sizeof(WorkItem));
+    hdr.col_items_offset = hdr.items_offset + items.size() * sizeof(WorkItem);
+    for (int v = 0; v < kColVariants; ++v) {
+        hdr.col_begin[v] = col_begin[v];
+        hdr.col_count[v] = col_count[v];
+        hdr.col_chunks[v] = col_chunks[v];
+    }
+    out.resize(hdr.col_items_offset + col_items.size() * sizeof(ColItem));
     memcpy(out.data(), &hdr, sizeof(hdr));
     memcpy(out.data() + sizeof(hdr), table.data(), static_cast<size_t>(n_jobs) * sizeof(Job));
     memcpy(out.data() + hdr.items_offset, items.data(), items.size() * sizeof(WorkItem));
+    memcpy(out.data() + hdr.col_items_offset, col_items.data(), col_items.size() * sizeof(ColItem));
     return RCG_OK;
 }
 
@@ -889,6 +999,10 @@ rcg_status rcg_batch_launch(rcg_ctx *ctx, const rcg_batch *b, void *stream, uint
             cudaGetLastError();
             e = cudaSuccess;
         }
+    }
+    if (e == cudaSuccess) {
+        e = set_enabled(s, work_mask(*reinterpret_cast<const BatchHeader *>(b->image.data())));
+        where = "graph node enable";
     }
     if (e == cudaSuccess) {
         e = cudaGraphLaunch(s.exec, static_cast<cudaStream_t>(stream));
@@ -1083,20 +1197,36 @@ rcg_status rcg_fill_random(void *dev, uint64_t nbytes, uint64_t seed, uint64_t b
 
 }  // extern "C"
 
-// Descriptor table for rcg_batch_submit_noalloc (default copy mode, solve and
-// shape; no context), written into `table` of `capacity` bytes with at most
-// kNoallocItems work items.  Returns the engine shape through *shape.
+// Descriptor table for rcg_batch_submit_noalloc (default copy mode, solve,
+// shape and column kernel; no context), written into `table` of `capacity`
+// bytes, of which col_capacity bytes are kept for column items.  Returns the
+// engine shape through *shape.
 bool rcg::noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, uint8_t *table, size_t capacity,
-                              size_t *bytes, uint32_t *shape) {
+                              size_t col_capacity, size_t *bytes, uint32_t *shape) {
     static const rcg_ctx defaults;
     *shape = batch_shape(&defaults, jobs, n_jobs);
-    const uint64_t max_items = (capacity - sizeof(BatchHeader) - n_jobs * sizeof(Job)) / sizeof(WorkItem) - n_jobs;
+    const uint64_t max_items =
+        (capacity - col_capacity - sizeof(BatchHeader) - n_jobs * sizeof(Job)) / sizeof(WorkItem) - n_jobs;
     std::vector<uint8_t> image;
-    if (build_table(&defaults, jobs, n_jobs, *shape, max_items, image) != RCG_OK || image.size() > capacity)
+    if (build_table(&defaults, jobs, n_jobs, *shape, max_items, image, col_capacity / sizeof(ColItem)) != RCG_OK ||
+        image.size() > capacity)
         return false;
     memcpy(table, image.data(), image.size());
     *bytes = image.size();
     return true;
+}
+
+cudaError_t rcg::launch_batch_all(const uint8_t *table_dev, const uint8_t *table_host, uint32_t *status,
+                                  unsigned long long *counter, uint64_t timeout_ns, uint32_t shape, int sm_count,
+                                  cudaStream_t stream) {
+    const auto &h = *reinterpret_cast<const BatchHeader *>(table_host);
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < kColVariants && e == cudaSuccess; ++v)
+        if (h.col_count[v]) e = launch_column_batch(v, table_dev, status, sm_count, stream);
+    if (e == cudaSuccess && h.n_items)
+        e = launch_batch(table_dev, status, counter, timeout_ns, shape,
+                         sm_count * static_cast<int>(shape_info(shape).ctas_per_sm), stream);
+    return e;
 }
 
 int rcg::ctx_device(const rcg_ctx *ctx) { return ctx ? ctx->device : 0; }

@@ -12,12 +12,17 @@
 // f = 1 + ... + x^(p-1) folds row p-1 into every other row (Lemma 3.4.1's
 // conditional all-ones fold).  Recovery follows Lemma 3.1.2's four cases with
 // one multiplication by an inverse -- of w_i (data + P) or of w_i + w_j (two
-// data strips) -- from a host-computed table of exponent masks.
+// data strips) -- from a host-computed table of exponent masks.  The degraded
+// read is the recovery of the strip alone, written to the caller's buffer;
+// the small write adds (old + new) to P and w_i (old + new) to Q.
 //
 // Why a second kernel: the tile engine streams one strip tile per pipeline
 // stage, and at p = 5 with 1 KiB rows a stage is 4 KB, so its fixed cost per
-// stage and per tile dominates small launches.  Here a launch is one DRAM
-// round trip per thread.
+// stage and per tile dominates small stripes.  Here a column is one DRAM round
+// trip per thread.  Single-operation launches stride the columns of one job
+// over the grid; batches give each warp a contiguous range of 32-column
+// chunks of their jobs (persistent grid, one kernel per variant: p = 3, 5, 5
+// with extended strips, 7).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -37,16 +42,6 @@ constexpr int kColMaxN = 9;    // 2p - 1 for p = 5
 
 __constant__ uint32_t c_col_inv_w[kColPrimes][kColMaxN];
 __constant__ uint32_t c_col_inv_pair[kColPrimes][kColMaxN][kColMaxN];
-
-struct ColParams {
-    uint8_t *base;
-    const uint8_t *pairs;  // per-stripe (i, j), or nullptr: use i, j
-    uint64_t row_stride, strip_stride, stripe_stride;
-    uint64_t n_stripes;
-    uint32_t vps;          // 16-byte columns per row
-    uint32_t N, i, j;
-    uint32_t *status;
-};
 
 __device__ __forceinline__ uint4 xr(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
@@ -135,119 +130,301 @@ __device__ __forceinline__ void lift(const uint4 (&a)[P - 1], uint4 (&out)[P]) {
     out[P - 1] = zero4();
 }
 
-// Registers: two 256-thread CTAs per SM where the accumulators fit 128
-// registers without spilling (p = 3, 5), one otherwise.
-template <int P, bool EXT>
-__global__ void __launch_bounds__(256, (P == 7 || EXT) ? 1 : 2) rcg_column_kernel(const ColParams prm) {
+template <int P>
+__host__ __device__ constexpr int table_slot() {
+    return P == 3 ? 0 : P == 5 ? 1 : 2;
+}
+
+// The small write on column v of stripe s: with D = old d_i + new d_i,
+// P += D, Q += w_i D (reduced), d_i = new.
+template <int P>
+__device__ __forceinline__ void column_update(const ColJob &J, uint64_t s, uint32_t v) {
     constexpr int R = P - 1;
-    constexpr int KB = P == 3 ? 4 : 2;  // strips per batch of loads
-    constexpr int slot = P == 3 ? 0 : P == 5 ? 1 : 2;
-    const uint32_t N = prm.N;
-    const uint64_t rs = prm.row_stride, ss = prm.strip_stride;
-    const uint64_t total = prm.n_stripes * prm.vps;
-    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-    for (uint64_t u = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; u < total; u += stride) {
-        const uint64_t s = u / prm.vps;
-        const uint32_t v = static_cast<uint32_t>(u - s * prm.vps);
-        uint32_t a = prm.i, b = prm.j;
-        if (prm.pairs) {
-            a = prm.pairs[2 * s];
-            b = prm.pairs[2 * s + 1];
+    uint8_t *const col = J.base + s * J.st + v * 16ull;
+    const uint8_t *const nw = J.aux + s * J.ass + v * 16ull;
+    const uint32_t N = J.N, a = J.i;
+    const uint64_t rs = J.rs, ss = J.ss;
+    uint4 od[R], nv[R], pv[R], qv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        od[r] = ld_col(col + a * ss + r * rs);
+        nv[r] = ld_col(nw + r * J.ars);
+        pv[r] = ld_col(col + N * ss + r * rs);
+        qv[r] = ld_col(col + (N + 1) * ss + r * rs);
+    }
+    uint4 dl[P], t[P];
+#pragma unroll
+    for (int r = 0; r < R; ++r) dl[r] = xr(od[r], nv[r]);
+    dl[R] = zero4();
+    mul_w<P>(dl, a, t);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        st_col(col + a * ss + r * rs, nv[r]);
+        st_col(col + N * ss + r * rs, xr(pv[r], dl[r]));
+        st_col(col + (N + 1) * ss + r * rs, xr(qv[r], xr(t[r], t[R])));
+    }
+}
+
+// One 16-byte column v of stripe s of a job: every operation but the small write.
+template <int P, bool EXT>
+__device__ __forceinline__ void column_unit(const ColJob &J, uint64_t s, uint32_t v, uint32_t *status) {
+    constexpr int R = P - 1;
+    constexpr int KB = P == 7 ? 2 : 4;  // strips per batch of loads
+    constexpr int slot = table_slot<P>();
+    if (J.op == OP_UPDATE) {
+        column_update<P>(J, s, v);
+        return;
+    }
+    const uint32_t N = J.N;
+    const uint64_t rs = J.rs, ss = J.ss;
+    const bool deg = J.op == OP_DEGRADED;
+    // strips a < b that are not read: the erased pair; (N, N+1) for encode;
+    // a degraded read of data strip j is the recovery of (j, Q) without the
+    // writes, of P or Q the encode without them
+    uint32_t a, b;
+    if (J.op == OP_ENCODE) {
+        a = N;
+        b = N + 1;
+    } else if (deg) {
+        a = J.j < N ? J.j : N;
+        b = N + 1;
+    } else {
+        a = J.i;
+        b = J.j;
+        if (J.pairs) {
+            a = J.pairs[2 * s];
+            b = J.pairs[2 * s + 1];
         }
         if (!(a < b && b <= N + 1)) {
-            if (v == 0 && prm.status) atomicOr(prm.status, RCG_DEV_BADPAIR);
-            continue;
+            if (v == 0 && status) atomicOr(status, RCG_DEV_BADPAIR);
+            return;
         }
-        uint8_t *const col = prm.base + s * prm.stripe_stride + v * 16ull;
-        const bool read_p = a != N && b != N, read_q = a != N + 1 && b != N + 1;
-        uint4 pv[R], qv[R];
+    }
+    uint8_t *const col = J.base + s * J.st + v * 16ull;
+    const bool read_p = a != N && b != N, read_q = a != N + 1 && b != N + 1;
+    // dP starts as P (when read).  The Horner sum of the data strips starts
+    // as x^(-h) Q, h = the number of Horner steps it takes (N, or p when the
+    // extended strips have their own sum; x^p = 1 in the lift), so that it
+    // ends as Q + sum of x^k d_k.  x^(-h) is applied to the load addresses:
+    // lifted row t of x^(-h) Q is row t + h (mod p) of Q, the imaginary row 0.
+    // Every load of a column is issued before any of them is used.
+    uint4 dp[R], hl[P];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            pv[r] = read_p ? ld_col(col + N * ss + r * rs) : zero4();
-            qv[r] = read_q ? ld_col(col + (N + 1) * ss + r * rs) : zero4();
-        }
-        // Horner from the last data strip down (erased strips count as zero)
-        uint4 dp[R], hl[P], hx[P], ex[R];
+    for (int r = 0; r < R; ++r) dp[r] = read_p ? ld_col(col + N * ss + r * rs) : zero4();
+    const uint32_t h = (EXT ? static_cast<uint32_t>(P) : N) % static_cast<uint32_t>(P);
 #pragma unroll
-        for (int r = 0; r < P; ++r) hl[r] = hx[r] = zero4();
+    for (int t = 0; t < P; ++t) {
+        uint32_t row = static_cast<uint32_t>(t) + h;
+        if (row >= static_cast<uint32_t>(P)) row -= P;
+        hl[t] = (read_q && row < static_cast<uint32_t>(R)) ? ld_col(col + (N + 1) * ss + row * rs) : zero4();
+    }
+    // Horner from the last data strip down (erased strips count as zero)
+    uint4 hx[P], ex[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) dp[r] = ex[r] = zero4();
-        for (int k0 = static_cast<int>(N); k0 > 0; k0 -= KB) {
-            uint4 d[KB][R];  // a batch of strips, every row, loads in flight together
+    for (int r = 0; r < P; ++r) hx[r] = zero4();
 #pragma unroll
-            for (int q = 0; q < KB; ++q) {
-                const int k = k0 - 1 - q;
-                const bool live = k >= 0 && static_cast<uint32_t>(k) != a && static_cast<uint32_t>(k) != b;
+    for (int r = 0; r < R; ++r) ex[r] = zero4();
+    for (int k0 = static_cast<int>(N); k0 > 0; k0 -= KB) {
+        uint4 d[KB][R];  // a batch of strips, every row, loads in flight together
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    d[q][r] = live ? ld_col(col + static_cast<uint64_t>(k) * ss + r * rs) : zero4();
-            }
+        for (int q = 0; q < KB; ++q) {
+            const int k = k0 - 1 - q;
+            const bool live = k >= 0 && static_cast<uint32_t>(k) != a && static_cast<uint32_t>(k) != b;
 #pragma unroll
-            for (int q = 0; q < KB; ++q) {
-                const int k = k0 - 1 - q;
-                if (k < 0) break;
-#pragma unroll
-                for (int r = 0; r < R; ++r) dp[r] = xr(dp[r], d[q][r]);
-                if (EXT && static_cast<uint32_t>(k) >= static_cast<uint32_t>(P)) {
-                    horner_step<P>(hx, d[q]);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) ex[r] = xr(ex[r], d[q][r]);
-                } else {
-                    horner_step<P>(hl, d[q]);
-                }
-            }
-        }
-        // dq (lifted) = sum of w_k d_k over the surviving data strips + Q
-        uint4 dq[P];
-#pragma unroll
-        for (int r = 0; r < P; ++r) dq[r] = hl[r];
-        if (EXT) {
-            const uint4 top = hx[P - 1];  // x hx: rotate by one
-#pragma unroll
-            for (int r = P - 1; r >= 1; --r) dq[r] = xr(dq[r], hx[r - 1]);
-            dq[0] = xr(dq[0], top);
-#pragma unroll
-            for (int r = 0; r < R; ++r) dq[r] = xr(dq[r], ex[r]);
+            for (int r = 0; r < R; ++r)
+                d[q][r] = live ? ld_col(col + static_cast<uint64_t>(k) * ss + r * rs) : zero4();
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            dp[r] = xr(dp[r], pv[r]);
-            dq[r] = xr(dq[r], qv[r]);
-        }
-
-        uint4 lp[P], t[P], o[P];
-        if (a == N) {                     // P and Q (encode)
-            store_rows<P>(col + N * ss, rs, dp);
-            store_folded<P>(col + (N + 1) * ss, rs, dq);
-        } else if (b == N + 1) {          // data a and Q: RAID-5, then Q
-            store_rows<P>(col + a * ss, rs, dp);
-            lift<P>(dp, lp);
-            mul_w<P>(lp, a, t);
+        for (int q = 0; q < KB; ++q) {
+            const int k = k0 - 1 - q;
+            if (k < 0) break;
 #pragma unroll
-            for (int r = 0; r < P; ++r) t[r] = xr(t[r], dq[r]);
-            store_folded<P>(col + (N + 1) * ss, rs, t);
-        } else if (b == N) {              // data a and P: w_a D_a = dQ
-            mul_mask<P>(dq, c_col_inv_w[slot][a], o);
+            for (int r = 0; r < R; ++r) dp[r] = xr(dp[r], d[q][r]);
+            if (EXT && static_cast<uint32_t>(k) >= static_cast<uint32_t>(P)) {
+                horner_step<P>(hx, d[q]);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint4 da = xr(o[r], o[P - 1]);
-                st_col(col + a * ss + r * rs, da);
-                st_col(col + N * ss + r * rs, xr(dp[r], da));
-            }
-        } else {                          // two data: (w_a + w_b) D_b = w_a dP + dQ
-            lift<P>(dp, lp);
-            mul_w<P>(lp, a, t);
-#pragma unroll
-            for (int r = 0; r < P; ++r) t[r] = xr(t[r], dq[r]);
-            mul_mask<P>(t, c_col_inv_pair[slot][a][b], o);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint4 db = xr(o[r], o[P - 1]);
-                st_col(col + b * ss + r * rs, db);
-                st_col(col + a * ss + r * rs, xr(db, dp[r]));
+                for (int r = 0; r < R; ++r) ex[r] = xr(ex[r], d[q][r]);
+            } else {
+                horner_step<P>(hl, d[q]);
             }
         }
     }
+    // dq (lifted) = Q + sum of w_k d_k over the surviving data strips
+    uint4 dq[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) dq[r] = hl[r];
+    if (EXT) {
+        const uint4 top = hx[P - 1];  // x hx: rotate by one
+#pragma unroll
+        for (int r = P - 1; r >= 1; --r) dq[r] = xr(dq[r], hx[r - 1]);
+        dq[0] = xr(dq[0], top);
+#pragma unroll
+        for (int r = 0; r < R; ++r) dq[r] = xr(dq[r], ex[r]);
+    }
+
+    if (deg) {  // the strip alone, to the caller's buffer
+        uint8_t *const out = J.aux + s * J.ass + v * 16ull;
+        if (J.j == N + 1)
+            store_folded<P>(out, J.ars, dq);
+        else
+            store_rows<P>(out, J.ars, dp);
+        return;
+    }
+    uint4 lp[P], t[P], o[P];
+    if (a == N) {                     // P and Q (encode)
+        store_rows<P>(col + N * ss, rs, dp);
+        store_folded<P>(col + (N + 1) * ss, rs, dq);
+    } else if (b == N + 1) {          // data a and Q: RAID-5, then Q
+        store_rows<P>(col + a * ss, rs, dp);
+        lift<P>(dp, lp);
+        mul_w<P>(lp, a, t);
+#pragma unroll
+        for (int r = 0; r < P; ++r) t[r] = xr(t[r], dq[r]);
+        store_folded<P>(col + (N + 1) * ss, rs, t);
+    } else if (b == N) {              // data a and P: w_a D_a = dQ
+        mul_mask<P>(dq, c_col_inv_w[slot][a], o);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint4 da = xr(o[r], o[P - 1]);
+            st_col(col + a * ss + r * rs, da);
+            st_col(col + N * ss + r * rs, xr(dp[r], da));
+        }
+    } else {                          // two data: (w_a + w_b) D_b = w_a dP + dQ
+        lift<P>(dp, lp);
+        mul_w<P>(lp, a, t);
+#pragma unroll
+        for (int r = 0; r < P; ++r) t[r] = xr(t[r], dq[r]);
+        mul_mask<P>(t, c_col_inv_pair[slot][a][b], o);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint4 db = xr(o[r], o[P - 1]);
+            st_col(col + b * ss + r * rs, db);
+            st_col(col + a * ss + r * rs, xr(db, dp[r]));
+        }
+    }
+}
+
+// Registers: two 256-thread CTAs per SM where the accumulators fit 128
+// registers without spilling (p = 3, 5), one otherwise.
+template <int P, bool EXT>
+__host__ __device__ constexpr int col_ctas_per_sm() {
+    return (P == 7 || EXT) ? 1 : 2;
+}
+
+// One operation over n_stripes stripes of one job: columns strided over the grid.
+template <int P, bool EXT>
+__global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
+    rcg_column_kernel(const ColJob J, uint64_t n_stripes, uint32_t *status) {
+    const uint64_t total = n_stripes * J.vps;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t u = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; u < total; u += stride) {
+        const uint64_t s = u / J.vps;
+        const uint32_t v = static_cast<uint32_t>(u - s * J.vps);
+        column_unit<P, EXT>(J, s, v, status);
+    }
+}
+
+template <int P, bool EXT>
+__host__ __device__ constexpr int variant_of() {
+    return P == 3 ? 0 : P == 5 ? (EXT ? 2 : 1) : 3;
+}
+
+// A batch's columns of one variant: warp w of W takes the contiguous range
+// [T w / W, T (w+1) / W) of the variant's T chunks (one column per lane), so
+// every warp has the same work give or take one chunk.  The job of the first
+// chunk is found by binary search over the variant's ColItems; the job's
+// fields go to a per-warp copy in shared memory.
+template <int P, bool EXT>
+__global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
+    rcg_column_batch(const uint8_t *__restrict__ table, uint32_t *status) {
+    const auto *bh = reinterpret_cast<const BatchHeader *>(table);
+    constexpr int g = variant_of<P, EXT>();
+    const uint32_t n_runs = bh->col_count[g];
+    const uint64_t total = bh->col_chunks[g];
+    const auto *runs = reinterpret_cast<const ColItem *>(table + bh->col_items_offset) + bh->col_begin[g];
+    const auto *jobs = reinterpret_cast<const Job *>(table + sizeof(BatchHeader));
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
+    const uint64_t w = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint64_t c0 = total * w / warps, c1 = total * (w + 1) / warps;
+    if (c0 >= c1 || n_runs == 0) return;
+    // the last job whose first chunk is <= c0 (the first job's is 0)
+    uint32_t lo = 0, hi = n_runs;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (runs[mid].chunk0 <= c0) lo = mid; else hi = mid;
+    }
+    // the job's fields and the warp's position, one copy per warp in shared
+    // memory (re-read by the loop; kept out of registers, which the column needs)
+    struct WarpState {
+        ColJob J;
+        uint64_t first, next, units, c1;
+        uint32_t r, valid;
+    };
+    __shared__ WarpState ws_all[8];
+    WarpState &ws = ws_all[threadIdx.x >> 5];
+    auto load_job = [&](uint32_t r) {
+        __syncwarp();
+        if (lane == 0) {
+            const ColItem ci = runs[r];
+            ws.r = r;
+            ws.first = ci.chunk0;
+            ws.next = r + 1 < n_runs ? runs[r + 1].chunk0 : total;
+            bool valid = ci.job < bh->n_jobs;
+            if (valid) {
+                const Job &jb = jobs[ci.job];
+                ColJob &J = ws.J;
+                J.base = jb.base;
+                J.pairs = jb.pairs;
+                J.aux = jb.aux;
+                J.rs = jb.row_stride;
+                J.ss = jb.strip_stride;
+                J.st = jb.stripe_stride;
+                J.ars = jb.aux_row_stride;
+                J.ass = jb.aux_stripe_stride;
+                J.vps = jb.C >> 4;
+                J.N = jb.n;
+                J.i = jb.i;
+                J.j = jb.j;
+                J.op = jb.op;
+                ws.units = static_cast<uint64_t>(jb.n_stripes) * (jb.C >> 4);
+                // device-side guard: the job is this variant's and its chunks cover it
+                valid = jb.p == P && (jb.n > static_cast<uint32_t>(P)) == EXT && jb.n >= 1 && ws.units > 0 &&
+                        ws.next - ws.first == (ws.units + kColChunk - 1) / kColChunk;
+            }
+            ws.valid = valid;
+            if (!valid && status) atomicOr(status, RCG_DEV_BADJOB);
+        }
+        __syncwarp();
+    };
+    if (lane == 0) ws.c1 = c1;
+    load_job(lo);
+#pragma unroll 1
+    for (uint64_t c = c0; c < ws.c1; ++c) {
+        if (c >= ws.next) {
+            // the job holding chunk c (bounded by the number of jobs)
+            uint32_t r = ws.r;
+            uint64_t next = ws.next;
+            while (c >= next && r + 1 < n_runs) {
+                ++r;
+                next = r + 1 < n_runs ? runs[r + 1].chunk0 : total;
+            }
+            load_job(r);
+        }
+        if (!ws.valid) continue;
+        const uint64_t u = (c - ws.first) * kColChunk + lane;
+        if (u >= ws.units) continue;
+        const uint32_t vps = ws.J.vps;
+        const uint64_t s = u / vps;
+        column_unit<P, EXT>(ws.J, s, static_cast<uint32_t>(u - s * vps), status);
+    }
+}
+
+template <class K>
+int resident_ctas(K kernel, int sm_count) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess) per_sm = 1;
+    return sm_count * std::max(per_sm, 1);
 }
 
 }  // namespace
@@ -278,37 +455,46 @@ cudaError_t upload_column_tables() {
     return e;
 }
 
-cudaError_t launch_column(uint8_t *base, uint32_t p, uint32_t N, uint64_t C, uint64_t row_stride,
-                          uint64_t strip_stride, uint64_t stripe_stride, uint64_t n_stripes, uint32_t i, uint32_t j,
-                          const uint8_t *pairs, uint32_t *status, int sm_count, cudaStream_t stream) {
-    ColParams prm;
-    prm.base = base;
-    prm.pairs = pairs;
-    prm.row_stride = row_stride;
-    prm.strip_stride = strip_stride;
-    prm.stripe_stride = stripe_stride;
-    prm.n_stripes = n_stripes;
-    prm.vps = static_cast<uint32_t>(C / 16);
-    prm.N = N;
-    prm.i = i;
-    prm.j = j;
-    prm.status = status;
-    const uint64_t total = n_stripes * prm.vps;
+cudaError_t launch_column(const ColJob &job, uint32_t p, uint64_t n_stripes, uint32_t *status, int sm_count,
+                          cudaStream_t stream) {
+    const uint64_t total = n_stripes * job.vps;
     if (total == 0) return cudaSuccess;
     auto go = [&](auto kernel) -> cudaError_t {
-        int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
-        if (e != cudaSuccess) return e;
-        const uint64_t resident = static_cast<uint64_t>(sm_count) * static_cast<uint64_t>(std::max(per_sm, 1));
+        const uint64_t resident = static_cast<uint64_t>(resident_ctas(kernel, sm_count));
         const unsigned g = static_cast<unsigned>(std::min<uint64_t>((total + 255) / 256, resident));
-        kernel<<<g, 256, 0, stream>>>(prm);
+        kernel<<<g, 256, 0, stream>>>(job, n_stripes, status);
         return cudaGetLastError();
     };
-    const bool ext = N > p;
+    const bool ext = job.N > p;
     switch (p) {
         case 3: return go(rcg_column_kernel<3, false>);
         case 5: return ext ? go(rcg_column_kernel<5, true>) : go(rcg_column_kernel<5, false>);
         case 7: return go(rcg_column_kernel<7, false>);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+const void *column_batch_function(int variant) {
+    switch (variant) {
+        case 0: return reinterpret_cast<const void *>(rcg_column_batch<3, false>);
+        case 1: return reinterpret_cast<const void *>(rcg_column_batch<5, false>);
+        case 2: return reinterpret_cast<const void *>(rcg_column_batch<5, true>);
+        case 3: return reinterpret_cast<const void *>(rcg_column_batch<7, false>);
+        default: return nullptr;
+    }
+}
+
+cudaError_t launch_column_batch(int variant, const uint8_t *table_dev, uint32_t *status, int sm_count,
+                                cudaStream_t stream) {
+    auto go = [&](auto kernel) -> cudaError_t {
+        kernel<<<resident_ctas(kernel, sm_count), 256, 0, stream>>>(table_dev, status);
+        return cudaGetLastError();
+    };
+    switch (variant) {
+        case 0: return go(rcg_column_batch<3, false>);
+        case 1: return go(rcg_column_batch<5, false>);
+        case 2: return go(rcg_column_batch<5, true>);
+        case 3: return go(rcg_column_batch<7, false>);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -139,9 +139,38 @@ struct alignas(128) BatchHeader {
     uint64_t items_offset;  // bytes from the header to the first WorkItem
     uint32_t dynamic;       // 0: items dealt round-robin; 1: taken from the global counter
     uint32_t fixed_slots;   // 1: n_slots equal slots of slot_bytes (as single launches); 0: byte ring
-    uint32_t pad[20];
+    // jobs of p <= 7 run in the column kernel: ColItems (one per job) from
+    // col_items_offset, grouped by kernel variant (p = 3; p = 5; p = 5 with
+    // extended strips; p = 7); col_chunks: the variant's 32-column chunks
+    uint64_t col_items_offset;
+    uint32_t col_begin[4];
+    uint32_t col_count[4];
+    uint32_t col_chunks[4];
+    uint32_t pad[6];
 };
 static_assert(sizeof(BatchHeader) == 128, "the job table after the header stays 128-byte aligned");
+
+// A job of the column kernel in a batch: its columns (unit = stripe * (C/16)
+// + 16-byte column) are cut into chunks of 32, one column per lane; the
+// variant's chunks are numbered across its jobs, this job's from chunk0.
+// Warps take contiguous ranges of chunks.
+struct ColItem {
+    uint32_t job;
+    uint32_t pad;
+    uint64_t chunk0;
+};
+static_assert(sizeof(ColItem) == 16, "column items are 16 bytes");
+constexpr uint32_t kColChunk = 32;  // columns per chunk: one per lane
+constexpr int kColVariants = 4;
+
+// The column-kernel variant of a geometry (index into col_begin / col_count),
+// or -1 when p > 7.
+inline int column_variant(uint32_t p, uint32_t N) {
+    if (p == 3) return 0;
+    if (p == 5) return N > 5 ? 2 : 1;
+    if (p == 7) return 3;
+    return -1;
+}
 static_assert(sizeof(Job) % 128 == 0, "jobs keep their tensor maps 128-byte aligned");
 
 struct Plan {
@@ -186,20 +215,42 @@ cudaError_t launch_h(uint8_t *base, uint32_t p, uint32_t N, uint64_t strip_bytes
                      uint32_t *status, int sm_count, cudaStream_t stream);
 
 // Column kernel (rcg_column.cu): bit-sliced stripes of p <= 7 without shared
-// memory; same pair convention as launch_h.
+// memory.  One launch over n_stripes stripes of one job: op OP_ENCODE,
+// OP_RECOVER (pair i < j, or per-stripe pairs), OP_DEGRADED (strip j into aux)
+// or OP_UPDATE (data strip i replaced by aux).
+struct ColJob {
+    uint8_t *base;         // stripe 0 of the job
+    const uint8_t *pairs;  // recovery: per-stripe (i, j) bytes, or nullptr
+    uint8_t *aux;          // degraded read: output; small write: the new strips
+    uint64_t rs, ss, st;   // row, strip and stripe strides
+    uint64_t ars, ass;     // aux row and stripe strides
+    uint32_t vps;          // 16-byte columns per row, C / 16
+    uint32_t N, i, j, op;
+};
 cudaError_t upload_column_tables();
-cudaError_t launch_column(uint8_t *base, uint32_t p, uint32_t N, uint64_t C, uint64_t row_stride,
-                          uint64_t strip_stride, uint64_t stripe_stride, uint64_t n_stripes, uint32_t i, uint32_t j,
-                          const uint8_t *pairs, uint32_t *status, int sm_count, cudaStream_t stream);
+cudaError_t launch_column(const ColJob &job, uint32_t p, uint64_t n_stripes, uint32_t *status, int sm_count,
+                          cudaStream_t stream);
+// Batches: the column kernel of one variant over the table's ColItems of that
+// variant (persistent grid); the variant's kernel function for graph nodes.
+cudaError_t launch_column_batch(int variant, const uint8_t *table_dev, uint32_t *status, int sm_count,
+                                cudaStream_t stream);
+const void *column_batch_function(int variant);
+// Every kernel of a batch table on `stream`, skipping kernels with no work:
+// the column kernels of its p <= 7 jobs, then the tile engine (the path of
+// rcg_batch_submit_noalloc; context batches replay the same in a graph).
+cudaError_t launch_batch_all(const uint8_t *table_dev, const uint8_t *table_host, uint32_t *status,
+                             unsigned long long *counter, uint64_t timeout_ns, uint32_t shape, int sm_count,
+                             cudaStream_t stream);
 
 // Host: the CUDA device of a context.
 int ctx_device(const rcg_ctx *ctx);
 
 // Host: validate public jobs and build the batch descriptor table with the
-// default copy mode, two-data solve and engine shape (used by
-// rcg_batch_submit_noalloc); *shape receives the shape to launch.
+// default copy mode, two-data solve, engine shape and column kernel (used by
+// rcg_batch_submit_noalloc), keeping col_capacity bytes of the table for
+// column items; *shape receives the shape to launch.
 bool noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, uint8_t *table, size_t capacity,
-                         size_t *bytes, uint32_t *shape);
+                         size_t col_capacity, size_t *bytes, uint32_t *shape);
 
 
 

@@ -28,9 +28,11 @@ namespace {
 
 using namespace rcg;
 
-// header, up to RCG_NOALLOC_MAX_JOBS jobs and 2 x RCG_NOALLOC_MAX_JOBS work items (~130 KB)
-constexpr uint32_t kTableBytes =
-    sizeof(BatchHeader) + RCG_NOALLOC_MAX_JOBS * sizeof(Job) + 2 * RCG_NOALLOC_MAX_JOBS * sizeof(WorkItem);
+// header, up to RCG_NOALLOC_MAX_JOBS jobs, 2 x RCG_NOALLOC_MAX_JOBS work items
+// of the tile engine and one column-kernel item per job (~134 KB)
+constexpr uint32_t kColTableBytes = RCG_NOALLOC_MAX_JOBS * sizeof(ColItem);
+constexpr uint32_t kTableBytes = sizeof(BatchHeader) + RCG_NOALLOC_MAX_JOBS * sizeof(Job) +
+                                 2 * RCG_NOALLOC_MAX_JOBS * sizeof(WorkItem) + kColTableBytes;
 constexpr uint32_t kCounterOff = (kTableBytes + 255) / 256 * 256;
 constexpr uint32_t kStatusOff = kCounterOff + 256;
 constexpr uint32_t kScratchBytes = kStatusOff + 256;
@@ -52,8 +54,8 @@ std::mutex g_setup_lock;
 alignas(128) uint8_t g_host_table[kTableBytes];
 
 // Once per device, with that device current: the scratch address, the
-// per-p inverse tables in constant memory and the kernel's shared-memory
-// attribute.  None of these allocates.
+// per-p inverse tables of the tile engine and the column kernel in constant
+// memory and the engine's shared-memory attribute.  None of these allocates.
 rcg_status setup_device(int dev, DeviceState **out) {
     if (dev < 0 || dev >= kMaxDevices) return RCG_EUNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_setup_lock);
@@ -65,6 +67,7 @@ rcg_status setup_device(int dev, DeviceState **out) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return RCG_ECUDA;
         if (upload_inverse_tables() != cudaSuccess) return RCG_ECUDA;
+        if (upload_column_tables() != cudaSuccess) return RCG_ECUDA;
         if (engine_init_attributes() != cudaSuccess) return RCG_ECUDA;
         d.scratch = static_cast<uint8_t *>(ptr);
         d.sm_count = prop.multiProcessorCount;
@@ -84,7 +87,8 @@ extern "C" rcg_status rcg_batch_submit_noalloc(const rcg_job *jobs, uint32_t n_j
 
     uint32_t shape = SHAPE_WIDE;
     size_t bytes = 0;
-    if (!noalloc_build_table(jobs, n_jobs, g_host_table, kTableBytes, &bytes, &shape)) return RCG_EINVAL;
+    if (!noalloc_build_table(jobs, n_jobs, g_host_table, kTableBytes, kColTableBytes, &bytes, &shape))
+        return RCG_EINVAL;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RCG_ECUDA;
@@ -100,7 +104,6 @@ extern "C" rcg_status rcg_batch_submit_noalloc(const rcg_job *jobs, uint32_t n_j
     cudaError_t e = cudaMemcpyAsync(table_dev, g_host_table, bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
-        e = launch_batch(table_dev, status, counter, 2000000000ull, shape,
-                         d->sm_count * static_cast<int>(shape_info(shape).ctas_per_sm), s);
+        e = launch_batch_all(table_dev, g_host_table, status, counter, 2000000000ull, shape, d->sm_count, s);
     return e == cudaSuccess ? RCG_OK : RCG_ECUDA;
 }

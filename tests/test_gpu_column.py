@@ -145,3 +145,137 @@ def test_column_kernel_setting_is_validated(rcg, ctxs):
     col, _ = ctxs
     with pytest.raises(rcg.RcgError):
         col.set_column_kernel(7)
+
+
+# ------------------------------------------------ degraded read, small write
+
+@pytest.mark.parametrize("p,N,C,S", [(3, 3, 48, 2), (5, 4, 1024, 2), (5, 9, 256, 2), (7, 6, 1040, 2)])
+def test_column_degraded_read_every_strip(rcg, ctxs, oracle, p, N, C, S):
+    col, eng = ctxs
+    host = stripes(4500 + p + N, p, N, C, S)
+    oracle.encode(p, N, C, host, S)
+    buf = dev(host)
+    L = rcg.make_layout(buf, p, N, C)
+    for j in range(N + 2):
+        for s in range(S):
+            want = oracle.degraded_read(p, N, C, host, s, j)
+            assert np.array_equal(want, host[s, j])  # a codeword: the strip itself
+            for c in (col, eng):
+                out = torch.zeros((p - 1, C), dtype=torch.uint8, device="cuda")
+                c.degraded_read(L, s, j, out)
+                assert c.last_device_status() == 0
+                assert np.array_equal(out.cpu().numpy(), want), (j, s)
+    assert np.array_equal(buf.cpu().numpy(), host)  # the stripe is not touched
+
+
+@pytest.mark.parametrize("p,N,C", [(3, 2, 32), (5, 4, 1024), (5, 9, 64), (7, 7, 528)])
+def test_column_small_write_matches_oracle(rcg, ctxs, oracle, p, N, C):
+    col, _ = ctxs
+    S = 3
+    host = stripes(4600 + p + N, p, N, C, S)
+    oracle.encode(p, N, C, host, S)
+    want = host.copy()
+    buf = dev(host)
+    L = rcg.make_layout(buf, p, N, C)
+    for s, i in enumerate([0, N - 1, N // 2]):
+        new = inputs.random_bytes(4601 + s, (p - 1) * C).reshape(p - 1, C)
+        oracle.update(p, N, C, want, s, i, new)
+        col.update(L, s, i, dev(new))
+    assert col.last_device_status() == 0
+    assert np.array_equal(buf.cpu().numpy(), want)
+
+
+# ------------------------------------------------------------ batches
+
+def mixed_batch(rcg, oracle, seed, specs):
+    """Jobs of every op on separate buffers (codewords for all but encode);
+    returns (device buffers, jobs, outputs, expected buffers, expected outputs)."""
+    bufs, jobs, outs, want_bufs, want_outs = [], [], [], [], []
+    for n, (p, N, C, S, kind) in enumerate(specs):
+        host = stripes(seed + n, p, N, C, S)
+        if kind != "enc":
+            oracle.encode(p, N, C, host, S)
+        want = host.copy()
+        aux = None
+        if kind == "enc":
+            oracle.encode(p, N, C, want, S)
+            job = lambda L: rcg.make_job(L, 0, S, rcg.RCG_OP_ENCODE)
+        elif kind.startswith("rec"):
+            i, j = {"rec_dd": (0, N - 1), "rec_dp": (N - 1, N), "rec_dq": (0, N + 1), "rec_pq": (N, N + 1)}[kind]
+            host[:, i] = POISON_I
+            host[:, j] = POISON_J
+            job = lambda L, i=i, j=j: rcg.make_job(L, 0, S, rcg.RCG_OP_RECOVER, i, j)
+        elif kind.startswith("deg"):
+            jj = {"deg_d": N // 2, "deg_p": N, "deg_q": N + 1}[kind]
+            aux = torch.zeros((S, p - 1, C), dtype=torch.uint8, device="cuda")
+            want_outs.append(np.stack([oracle.degraded_read(p, N, C, want, s, jj) for s in range(S)]))
+            job = lambda L, jj=jj, aux=aux: rcg.make_job(L, 0, S, rcg.RCG_OP_DEGRADED_READ, 0, jj, aux)
+        else:  # small write of strip N - 1
+            new = inputs.random_bytes(seed + 500 + n, S * (p - 1) * C).reshape(S, p - 1, C)
+            for s in range(S):
+                oracle.update(p, N, C, want, s, N - 1, new[s])
+            aux = dev(new)
+            want_outs.append(new)
+            job = lambda L, aux=aux: rcg.make_job(L, 0, S, rcg.RCG_OP_UPDATE, N - 1, 0, aux)
+        buf = dev(host)
+        jobs.append(job(rcg.make_layout(buf, p, N, C)))
+        bufs.append(buf)
+        if aux is not None:
+            outs.append(aux)
+        want_bufs.append(want)
+    return bufs, jobs, outs, want_bufs, want_outs
+
+
+SMALL = [(3, 2, 32, 3, "enc"), (3, 3, 1040, 2, "rec_dd"), (5, 4, 1024, 40, "enc"), (5, 4, 1024, 7, "rec_dd"),
+         (5, 4, 512, 3, "rec_dp"), (5, 3, 2048, 2, "rec_dq"), (5, 4, 64, 5, "rec_pq"), (5, 9, 256, 3, "rec_dd"),
+         (5, 8, 96, 2, "deg_d"), (5, 4, 1040, 2, "deg_q"), (7, 6, 4096, 2, "deg_p"), (7, 7, 528, 3, "upd"),
+         (5, 4, 16, 9, "upd"), (7, 5, 1024, 3, "enc")]
+LARGE = [(13, 12, 1024, 3, "enc"), (29, 8, 512, 2, "rec_dd"), (59, 20, 2048, 1, "deg_d"), (13, 6, 4096, 2, "upd")]
+
+
+@pytest.mark.parametrize("mix", ["small", "large", "both"])
+def test_batch_with_column_jobs_matches_oracle(rcg, ctxs, oracle, mix):
+    # p <= 7 jobs run in the column kernels of the batch, the others in the
+    # tile engine; the same slot is launched with only one kind, then both
+    col, eng = ctxs
+    specs = SMALL if mix == "small" else LARGE if mix == "large" else SMALL + LARGE
+    for c in (col, eng):  # column kernels in the batch, and the tile engine alone
+        for rep in range(2):
+            bufs, jobs, outs, want_bufs, want_outs = mixed_batch(rcg, oracle, 4700 + 10 * rep, specs)
+            assert c.batch_wait(c.batch_submit(jobs))
+            assert c.last_device_status() == 0
+            for k, (b, w) in enumerate(zip(bufs, want_bufs)):
+                assert np.array_equal(b.cpu().numpy(), w), (specs[k], rep)
+            for o, w in zip(outs, want_outs):
+                assert np.array_equal(o.cpu().numpy(), w)
+
+
+def test_p5n4_sixteen_operations_in_one_batch(rcg, oracle):
+    # the p = 5, N = 4, 1 KiB-row geometry (1024 stripes): encode and the 15
+    # erasure pairs, each on a copy of its own, as ONE batch (384 MB) -- the
+    # form in which this small geometry can fill HBM; every byte against O2,
+    # sampled stripes against the bit-level oracle
+    p, N, C, S = 5, 4, 1024, 1024
+    host = stripes(0, p, N, C, S)
+    enc = host.copy()
+    oracle.o2_encode(p, N, C, enc, S)
+    pairs = [(i, j) for i in range(N + 2) for j in range(i + 1, N + 2)]
+    copies = torch.empty((16, S, N + 2, p - 1, C), dtype=torch.uint8, device="cuda")
+    copies[0] = dev(host)
+    for k, (i, j) in enumerate(pairs, 1):
+        lost = enc.copy()
+        lost[:, i] = POISON_I
+        lost[:, j] = POISON_J
+        copies[k] = dev(lost)
+    jobs = [rcg.make_job(rcg.make_layout(copies[0], p, N, C), 0, S, rcg.RCG_OP_ENCODE)]
+    for k, (i, j) in enumerate(pairs, 1):
+        jobs.append(rcg.make_job(rcg.make_layout(copies[k], p, N, C), 0, S, rcg.RCG_OP_RECOVER, i, j))
+    with rcg.Context(0) as c:
+        assert c.batch_wait(c.batch_submit(jobs))
+        assert c.last_device_status() == 0
+    got = copies.cpu().numpy()
+    for k in range(16):
+        assert np.array_equal(got[k], enc), k
+    sample = stripes(0, p, N, C, S)[:8].copy()
+    oracle.encode(p, N, C, sample, 8)
+    assert np.array_equal(got[0, :8], sample)
