@@ -78,6 +78,17 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.oracle_h_encode.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64]
     lib.oracle_h_recover.restype = ctypes.c_int
     lib.oracle_h_recover.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _uint, _uint, _vp]
+    for name in ("oracle_big_ring_mul",):
+        getattr(lib, name).restype = ctypes.c_int
+        getattr(lib, name).argtypes = [_uint, _vp, _vp, _vp]
+    lib.oracle_big_ring_xpow.restype = ctypes.c_int
+    lib.oracle_big_ring_xpow.argtypes = [_uint, _uint, _vp]
+    lib.oracle_big_ring_inv.restype = ctypes.c_int
+    lib.oracle_big_ring_inv.argtypes = [_uint, _vp, _vp]
+    lib.oracle_hbig_encode.restype = ctypes.c_int
+    lib.oracle_hbig_encode.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64]
+    lib.oracle_hbig_recover.restype = ctypes.c_int
+    lib.oracle_hbig_recover.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _uint, _uint, _vp]
     return lib
 
 
@@ -236,6 +247,69 @@ def h_recover(p, N, strip_bytes, buf, n_stripes, i=0, j=1, pairs=None, strip_str
         raise ValueError("oracle_h_recover: invalid arguments (rc=%d)" % rc)
 
 
+# ------------------------------------------- large primes (p up to 257)
+
+def _big_bytes(p: int) -> int:
+    return (p - 1 + 7) // 8
+
+
+def _to_bits(p: int, a: int) -> np.ndarray:
+    return np.frombuffer(int(a).to_bytes(_big_bytes(p), "little"), dtype=np.uint8).copy()
+
+
+def _from_bits(b: np.ndarray) -> int:
+    return int.from_bytes(bytes(b), "little")
+
+
+def big_ring_mul(p: int, a: int, b: int) -> int:
+    """a * b in R for any odd prime p <= 257 (bit m = coefficient of x^m):
+    coefficient arrays, schoolbook product, long division by f."""
+    x, y, out = _to_bits(p, a), _to_bits(p, b), np.zeros(_big_bytes(p), np.uint8)
+    if lib().oracle_big_ring_mul(p, _ptr(x), _ptr(y), _ptr(out)):
+        raise ValueError("oracle_big_ring_mul: invalid p")
+    return _from_bits(out)
+
+
+def big_ring_xpow(p: int, k: int) -> int:
+    out = np.zeros(_big_bytes(p), np.uint8)
+    if lib().oracle_big_ring_xpow(p, k, _ptr(out)):
+        raise ValueError("oracle_big_ring_xpow: invalid arguments")
+    return _from_bits(out)
+
+
+def big_ring_inv(p: int, a: int) -> int:
+    """Inverse in R by the extended Euclidean algorithm; 0 when a is not a unit."""
+    x, out = _to_bits(p, a), np.zeros(_big_bytes(p), np.uint8)
+    rc = lib().oracle_big_ring_inv(p, _ptr(x), _ptr(out))
+    if rc < 0:
+        raise ValueError("oracle_big_ring_inv: invalid p")
+    return _from_bits(out) if rc else 0
+
+
+def hbig_encode(p, N, strip_bytes, buf, n_stripes, strip_stride=None, stripe_stride=None):
+    """Encode horizontal stripes (element e = bits [e(p-1), (e+1)(p-1)) of a
+    strip) for any odd prime p <= 257, N <= p: the coefficient-array code."""
+    _check_buf(buf)
+    ss, st = _h_strides(N, strip_bytes, strip_stride, stripe_stride)
+    if lib().oracle_hbig_encode(p, N, strip_bytes, _ptr(buf), n_stripes, ss, st):
+        raise ValueError("oracle_hbig_encode: invalid arguments")
+
+
+def hbig_recover(p, N, strip_bytes, buf, n_stripes, i=0, j=1, pairs=None, strip_stride=None,
+                 stripe_stride=None):
+    """Rebuild strips i < j (or per-stripe pairs) of horizontal stripes of any
+    odd prime p <= 257 in place (Lemma 3.1.2, inverses by Euclid)."""
+    _check_buf(buf)
+    ss, st = _h_strides(N, strip_bytes, strip_stride, stripe_stride)
+    pp = None
+    if pairs is not None:
+        pairs = np.ascontiguousarray(pairs, dtype=np.uint8)
+        pp = _ptr(pairs)
+    rc = lib().oracle_hbig_recover(p, N, strip_bytes, _ptr(buf), n_stripes, ss, st, i, j, pp)
+    if rc:
+        raise ValueError("oracle_hbig_recover: invalid arguments (rc=%d)" % rc)
+
+
 # ------------------------------------------------------- O2 (word-level)
 
 _O2_SRC = os.path.join(_HERE, "rcg_o2.c")
@@ -266,6 +340,12 @@ def o2() -> ctypes.CDLL:
         L.o2_h_encode.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, ctypes.c_int]
         L.o2_h_recover.restype = ctypes.c_int
         L.o2_h_recover.argtypes = [_uint, _uint, _u64, _vp, _u64, _u64, _u64, _uint, _uint, _vp, ctypes.c_int]
+        L.o2_h257_encode.restype = ctypes.c_int
+        L.o2_h257_encode.argtypes = [_uint, _u64, _vp, _u64, _u64, _u64, ctypes.c_int]
+        L.o2_h257_recover.restype = ctypes.c_int
+        L.o2_h257_recover.argtypes = [_uint, _u64, _vp, _u64, _u64, _u64, _uint, _uint, _vp, ctypes.c_int]
+        L.o2_h257_inverse.restype = ctypes.c_int
+        L.o2_h257_inverse.argtypes = [_vp, _vp]
         _o2 = L
     return _o2
 
@@ -318,6 +398,36 @@ def o2_h_recover(p, N, strip_bytes, buf, n_stripes, i=0, j=1, pairs=None, strip_
     rc = o2().o2_h_recover(p, N, strip_bytes, _ptr(buf), n_stripes, ss, st, i, j, pp, _threads(threads))
     if rc:
         raise ValueError("o2_h_recover: invalid arguments (rc=%d)" % rc)
+
+
+def o2_h257_encode(N, strip_bytes, buf, n_stripes, strip_stride=None, stripe_stride=None, threads=None):
+    """Word-level encode of Z_257 stripes in the horizontal representation
+    (element e = bytes [32e, 32e + 32)), N <= 257."""
+    _check_buf(buf)
+    ss, st = _h_strides(N, strip_bytes, strip_stride, stripe_stride)
+    rc = o2().o2_h257_encode(N, strip_bytes, _ptr(buf), n_stripes, ss, st, _threads(threads))
+    if rc:
+        raise ValueError("o2_h257_encode: invalid arguments (rc=%d)" % rc)
+
+
+def o2_h257_recover(N, strip_bytes, buf, n_stripes, i=0, j=1, pairs=None, strip_stride=None,
+                    stripe_stride=None, threads=None):
+    _check_buf(buf)
+    ss, st = _h_strides(N, strip_bytes, strip_stride, stripe_stride)
+    pp = None
+    if pairs is not None:
+        pairs = np.ascontiguousarray(pairs, dtype=np.uint8)
+        pp = _ptr(pairs)
+    rc = o2().o2_h257_recover(N, strip_bytes, _ptr(buf), n_stripes, ss, st, i, j, pp, _threads(threads))
+    if rc:
+        raise ValueError("o2_h257_recover: invalid arguments (rc=%d)" % rc)
+
+
+def o2_h257_inverse(a: int) -> int:
+    """Inverse in R (p = 257) by Gaussian elimination; 0 when singular."""
+    x = np.frombuffer(int(a).to_bytes(32, "little"), dtype=np.uint8).copy()
+    out = np.zeros(32, np.uint8)
+    return int.from_bytes(bytes(out), "little") if o2().o2_h257_inverse(_ptr(x), _ptr(out)) else 0
 
 
 def o2_inverse(p: int, a: int) -> int:

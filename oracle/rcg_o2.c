@@ -26,7 +26,8 @@
  * r at + r*row_stride, C bytes per row (C a multiple of 8 here: every row is
  * processed as C/8 words).  Stripes are split across threads.  Stripes in the
  * horizontal representation of Section 4.5 (o2_h_*) are turned into this form
- * 64 elements at a time and back.
+ * 64 elements at a time and back.  Z_257 (o2_h257_*, at the end) has 256-bit
+ * elements and its own word-level code on them.
  */
 #include <pthread.h>
 #include <stdint.h>
@@ -463,4 +464,281 @@ int o2_h_recover(unsigned p, unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_st
 u64 o2_inverse(unsigned p, u64 a)
 {
     return inverse(p, a);
+}
+
+/* ======================================= Z_257: 256-bit elements, word level
+ *
+ * p = 257 (Section 3.4's Z_257): an element is 256 bits, too wide for the
+ * bit masks above, and in the horizontal representation it is exactly 32
+ * bytes (four 64-bit words, little-endian).  Elements are held lifted to
+ * F2[x]/(x^257 - 1) in five words (bit 256 = bit 0 of word 4, the imaginary
+ * row); x^k is a cyclic rotation of the 257 bits, and the residue modulo f
+ * flips bits 0..255 when bit 256 is set.  Inverses are solved by Gaussian
+ * elimination on the 256 x 256 matrix of multiplication by the element, one
+ * per stripe (per erasure pair).  Base code only: N <= 257. */
+
+#define Z_P 257u
+#define Z_BITS 256u
+
+typedef struct {
+    u64 w[5];
+} l257;
+
+static void l257_load(const uint8_t *src, l257 *a)
+{
+    for (unsigned q = 0; q < 4; q++) {
+        u64 v = 0;
+        for (unsigned b = 0; b < 8; b++)
+            v |= (u64)src[8 * q + b] << (8 * b);
+        a->w[q] = v;
+    }
+    a->w[4] = 0;
+}
+
+static void l257_store(uint8_t *dst, const l257 *a)
+{
+    for (unsigned q = 0; q < 4; q++)
+        for (unsigned b = 0; b < 8; b++)
+            dst[8 * q + b] = (uint8_t)(a->w[q] >> (8 * b));
+}
+
+static void l257_xor(l257 *a, const l257 *b)
+{
+    for (unsigned q = 0; q < 5; q++)
+        a->w[q] ^= b->w[q];
+}
+
+/* x^k a in the lift, 0 <= k < 257: bit t moves to bit (t + k) mod 257. */
+static void l257_rot(const l257 *a, unsigned k, l257 *out)
+{
+    if (k == 0) {
+        *out = *a;
+        return;
+    }
+    l257 hi = {{0}}, lo = {{0}};
+    const unsigned qk = k / 64, rk = k % 64;
+    for (int t = 4; t >= 0; t--) {          /* hi = a << k */
+        const int s0 = t - (int)qk, s1 = s0 - 1;
+        u64 v = s0 >= 0 ? a->w[s0] << rk : 0;
+        if (rk && s1 >= 0)
+            v |= a->w[s1] >> (64 - rk);
+        hi.w[t] = v;
+    }
+    hi.w[4] &= 1;                            /* keep 257 bits */
+    const unsigned m = Z_P - k, qm = m / 64, rm = m % 64;
+    for (unsigned t = 0; t < 5; t++) {       /* lo = a >> (257 - k) */
+        const unsigned s0 = t + qm, s1 = s0 + 1;
+        u64 v = s0 <= 4 ? a->w[s0] >> rm : 0;
+        if (rm && s1 <= 4)
+            v |= a->w[s1] << (64 - rm);
+        lo.w[t] = v;
+    }
+    for (unsigned q = 0; q < 5; q++)
+        out->w[q] = hi.w[q] | lo.w[q];
+}
+
+/* residue modulo f = 1 + ... + x^256 */
+static void l257_reduce(l257 *a)
+{
+    if (a->w[4] & 1)
+        for (unsigned q = 0; q < 4; q++)
+            a->w[q] = ~a->w[q];
+    a->w[4] = 0;
+}
+
+/* c * t in R, c reduced (256 bits): sum over the set bits m of c of x^m t. */
+static void l257_mul(const l257 *c, const l257 *t, l257 *out)
+{
+    l257 acc = {{0}}, r;
+    for (unsigned m = 0; m < Z_BITS; m++)
+        if (c->w[m / 64] >> (m % 64) & 1) {
+            l257_rot(t, m, &r);
+            l257_xor(&acc, &r);
+        }
+    l257_reduce(&acc);
+    *out = acc;
+}
+
+/* The inverse of u (reduced) by Gauss-Jordan elimination on [M | e_0], M the
+ * matrix of multiplication by u (column c = u x^c): the solution v of
+ * u v = 1.  Returns 0 when u is singular. */
+static int l257_inverse(const l257 *u, l257 *out)
+{
+    static __thread u64 row[Z_BITS][5];      /* words 0..3: M's row, bit 0 of word 4: the right side */
+    memset(row, 0, sizeof(row));
+    for (unsigned c = 0; c < Z_BITS; c++) {
+        l257 col;
+        l257_rot(u, c, &col);
+        l257_reduce(&col);
+        for (unsigned i = 0; i < Z_BITS; i++)
+            if (col.w[i / 64] >> (i % 64) & 1)
+                row[i][c / 64] |= 1ull << (c % 64);
+    }
+    row[0][4] = 1;
+    for (unsigned c = 0; c < Z_BITS; c++) {
+        unsigned piv = c;
+        while (piv < Z_BITS && !(row[piv][c / 64] >> (c % 64) & 1))
+            piv++;
+        if (piv == Z_BITS)
+            return 0;
+        if (piv != c)
+            for (unsigned q = 0; q < 5; q++) {
+                u64 t = row[c][q];
+                row[c][q] = row[piv][q];
+                row[piv][q] = t;
+            }
+        for (unsigned i = 0; i < Z_BITS; i++)
+            if (i != c && (row[i][c / 64] >> (c % 64) & 1))
+                for (unsigned q = 0; q < 5; q++)
+                    row[i][q] ^= row[c][q];
+    }
+    memset(out, 0, sizeof(*out));
+    for (unsigned i = 0; i < Z_BITS; i++)
+        if (row[i][4] & 1)
+            out->w[i / 64] |= 1ull << (i % 64);
+    return 1;
+}
+
+static void l257_xpow(unsigned k, l257 *out)
+{
+    l257 one = {{1, 0, 0, 0, 0}};
+    l257_rot(&one, k % Z_P, out);
+    l257_reduce(out);
+}
+
+typedef struct {
+    uint8_t *buf;
+    unsigned N;
+    u64 n_el, ss, st;
+    u64 s0, s1;
+    unsigned i, j;
+    const uint8_t *pairs;
+    int bad;
+} zwork_t;
+
+/* Every element of stripe s, lost pair a < b ((N, N+1) encodes), by the four
+ * cases of Lemma 3.1.2 on the lifted elements. */
+static int z_stripe(const zwork_t *z, u64 s, unsigned a, unsigned b)
+{
+    const unsigned N = z->N;
+    l257 inv = {{0}};
+    if (b <= N && a < N) {
+        l257 u, t;
+        l257_xpow(a, &u);                         /* g_a (data + P) */
+        if (b < N) {                              /* g_a + g_b (two data) */
+            l257_xpow(b, &t);
+            l257_xor(&u, &t);
+        }
+        if (!l257_inverse(&u, &inv))
+            return -3;
+    }
+    const int read_p = a != N && b != N, read_q = a != N + 1 && b != N + 1;
+    uint8_t *const stripe = z->buf + s * z->st;
+    for (u64 e = 0; e < z->n_el; e++) {
+        uint8_t *const el = stripe + e * 32;
+        l257 dP = {{0}}, dQ = {{0}}, d, r;
+        if (read_p)
+            l257_load(el + (u64)N * z->ss, &dP);
+        if (read_q)
+            l257_load(el + (u64)(N + 1) * z->ss, &dQ);
+        for (unsigned k = 0; k < N; k++) {
+            if (k == a || k == b)
+                continue;
+            l257_load(el + (u64)k * z->ss, &d);
+            l257_xor(&dP, &d);
+            l257_rot(&d, k, &r);
+            l257_xor(&dQ, &r);
+        }
+        if (a == N) {                             /* P and Q */
+            l257_reduce(&dQ);
+            l257_store(el + (u64)N * z->ss, &dP);
+            l257_store(el + (u64)(N + 1) * z->ss, &dQ);
+        } else if (b == N + 1) {                  /* d_a = dP, then Q */
+            l257_rot(&dP, a, &r);
+            l257_xor(&dQ, &r);
+            l257_reduce(&dQ);
+            l257_store(el + (u64)a * z->ss, &dP);
+            l257_store(el + (u64)(N + 1) * z->ss, &dQ);
+        } else if (b == N) {                      /* g_a d_a = dQ, then P */
+            l257 da;
+            l257_reduce(&dQ);
+            l257_mul(&inv, &dQ, &da);
+            l257_store(el + (u64)a * z->ss, &da);
+            l257_xor(&dP, &da);
+            l257_store(el + (u64)N * z->ss, &dP);
+        } else {                                  /* (g_a + g_b) d_b = g_a dP + dQ */
+            l257 t, db;
+            l257_rot(&dP, a, &t);
+            l257_xor(&t, &dQ);
+            l257_reduce(&t);
+            l257_mul(&inv, &t, &db);
+            l257_store(el + (u64)b * z->ss, &db);
+            l257_xor(&dP, &db);
+            l257_store(el + (u64)a * z->ss, &dP);
+        }
+    }
+    return 0;
+}
+
+static void *z_worker(void *arg)
+{
+    zwork_t *wk = (zwork_t *)arg;
+    for (u64 s = wk->s0; s < wk->s1; s++) {
+        const unsigned a = wk->pairs ? wk->pairs[2 * s] : wk->i;
+        const unsigned b = wk->pairs ? wk->pairs[2 * s + 1] : wk->j;
+        if (!(a < b && b <= wk->N + 1) || z_stripe(wk, s, a, b))
+            wk->bad = 1;
+    }
+    return NULL;
+}
+
+static int z_run(unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes, u64 ss, u64 st, unsigned i,
+                 unsigned j, const uint8_t *pairs, int threads)
+{
+    if (N < 1 || N > Z_P || strip_bytes == 0 || strip_bytes % 32)
+        return -1;
+    if (threads < 1)
+        threads = 1;
+    if (threads > 256)
+        threads = 256;
+    pthread_t tid[256];
+    zwork_t wk[256];
+    for (int t = 0; t < threads; t++) {
+        zwork_t w = {buf, N, strip_bytes / 32, ss, st, n_stripes * t / threads, n_stripes * (t + 1) / threads,
+                     i, j, pairs, 0};
+        wk[t] = w;
+        pthread_create(&tid[t], NULL, z_worker, &wk[t]);
+    }
+    int bad = 0;
+    for (int t = 0; t < threads; t++) {
+        pthread_join(tid[t], NULL);
+        bad |= wk[t].bad;
+    }
+    return bad ? -2 : 0;
+}
+
+/* Z_257 stripes in the horizontal representation: strips of strip_bytes (a
+ * multiple of 32), element e = bytes [32e, 32e + 32) little-endian. */
+int o2_h257_encode(unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes, u64 ss, u64 st, int threads)
+{
+    return z_run(N, strip_bytes, buf, n_stripes, ss, st, N, N + 1, NULL, threads);
+}
+
+/* Recover pair (i, j), or per-stripe pairs (two bytes per stripe) when pairs != NULL. */
+int o2_h257_recover(unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes, u64 ss, u64 st, unsigned i,
+                    unsigned j, const uint8_t *pairs, int threads)
+{
+    return z_run(N, strip_bytes, buf, n_stripes, ss, st, i, j, pairs, threads);
+}
+
+/* The inverse in R (p = 257) of the 32-byte element a, for the tests;
+ * returns 0 when a is singular. */
+int o2_h257_inverse(const uint8_t *a, uint8_t *out)
+{
+    l257 u, v;
+    l257_load(a, &u);
+    if (!l257_inverse(&u, &v))
+        return 0;
+    l257_store(out, &v);
+    return 1;
 }

@@ -46,6 +46,13 @@
  * bit t%8 of byte t/8), bit r of it the coefficient of x^r; for p = 17 that is
  * the 16-bit little-endian word e.  The arithmetic is the same; only gather
  * and scatter differ.
+ *
+ * Large primes (the oracle_big_* and oracle_hbig_* functions, at the end):
+ * Section 3.4 names Z_257 beside Z_17, whose elements (256 bits) do not fit
+ * the 128-bit polynomials above.  That part holds polynomials as arrays of
+ * coefficients and works for any odd prime p <= 257 (base code, N <= p), in
+ * the horizontal representation; it shares nothing with the 128-bit code, and
+ * the tests require both to agree on every prime both accept.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -498,6 +505,375 @@ int oracle_degraded_read(unsigned p, unsigned N, u64 C, const uint8_t *buf, u64 
                     v ^= gather(&L, stripe, k, b);
         }
         scatter(&O, 0, 0, b, v);
+    }
+    return 0;
+}
+
+/* ============================================== large primes (p <= 257)
+ *
+ * The same definitions for primes whose strips do not fit a machine word --
+ * Section 3.4 names Z_257 (256-bit elements) beside Z_17 -- on polynomials
+ * held as arrays of coefficients, one byte per coefficient (0 or 1), and
+ * stripes in the horizontal representation.  Nothing here is shared with the
+ * 128-bit code above: multiplication is schoolbook, reduction is long
+ * division by f, inverses come from the extended Euclidean algorithm.  The
+ * tests run both on the primes both accept and require equal results. */
+
+#define BP_MAXP 257
+#define BP_CAP (2 * BP_MAXP + 2) /* room for a product of two residues */
+
+typedef struct {
+    int deg;               /* -1 for the zero polynomial */
+    uint8_t c[BP_CAP];     /* c[t] = coefficient of x^t */
+} bpoly;
+
+static void bp_zero(bpoly *a)
+{
+    memset(a->c, 0, sizeof(a->c));
+    a->deg = -1;
+}
+
+static void bp_fix_deg(bpoly *a)
+{
+    int d = BP_CAP - 1;
+    while (d >= 0 && a->c[d] == 0)
+        d--;
+    a->deg = d;
+}
+
+static void bp_add(const bpoly *a, const bpoly *b, bpoly *out)
+{
+    for (int t = 0; t < BP_CAP; t++)
+        out->c[t] = a->c[t] ^ b->c[t];
+    bp_fix_deg(out);
+}
+
+/* Carry-less product; deg(a) + deg(b) < BP_CAP. */
+static void bp_mul(const bpoly *a, const bpoly *b, bpoly *out)
+{
+    bpoly r;
+    bp_zero(&r);
+    for (int i = 0; i <= a->deg; i++) {
+        if (!a->c[i])
+            continue;
+        for (int j = 0; j <= b->deg; j++)
+            r.c[i + j] ^= b->c[j];
+    }
+    bp_fix_deg(&r);
+    *out = r;
+}
+
+/* Long division a = q*m + r, m nonzero.  q may be NULL. */
+static void bp_divmod(const bpoly *a, const bpoly *m, bpoly *q, bpoly *r)
+{
+    bpoly rem = *a, quo;
+    bp_zero(&quo);
+    while (rem.deg >= m->deg) {
+        const int shift = rem.deg - m->deg;
+        quo.c[shift] ^= 1;
+        for (int t = 0; t <= m->deg; t++)
+            rem.c[t + shift] ^= m->c[t];
+        bp_fix_deg(&rem);
+    }
+    bp_fix_deg(&quo);
+    if (q)
+        *q = quo;
+    *r = rem;
+}
+
+/* f = 1 + x + ... + x^(p-1) */
+static void bp_f(unsigned p, bpoly *f)
+{
+    bp_zero(f);
+    for (unsigned t = 0; t < p; t++)
+        f->c[t] = 1;
+    f->deg = (int)p - 1;
+}
+
+static void bp_ring_mul(unsigned p, const bpoly *a, const bpoly *b, bpoly *out)
+{
+    bpoly f, prod;
+    bp_f(p, &f);
+    bp_mul(a, b, &prod);
+    bp_divmod(&prod, &f, NULL, out);
+}
+
+/* x^k reduced modulo f, k < BP_CAP. */
+static void bp_xpow(unsigned p, unsigned k, bpoly *out)
+{
+    bpoly f, m;
+    bp_f(p, &f);
+    bp_zero(&m);
+    m.c[k] = 1;
+    m.deg = (int)k;
+    bp_divmod(&m, &f, NULL, out);
+}
+
+/* Inverse in R by the extended Euclidean algorithm; returns 0 (and leaves
+ * out zero) when gcd(a, f) != 1. */
+static int bp_ring_inv(unsigned p, const bpoly *a, bpoly *out)
+{
+    bpoly f, r0, r1, s0, s1;
+    bp_f(p, &f);
+    bp_divmod(a, &f, NULL, &r1);
+    bp_zero(out);
+    if (r1.deg < 0)
+        return 0;
+    r0 = f;
+    bp_zero(&s0);
+    bp_zero(&s1);
+    s1.c[0] = 1;
+    s1.deg = 0;
+    while (r1.deg >= 0) {
+        bpoly q, rem, qs, s2;
+        bp_divmod(&r0, &r1, &q, &rem);
+        bp_mul(&q, &s1, &qs);
+        bp_add(&s0, &qs, &s2);
+        r0 = r1;
+        r1 = rem;
+        s0 = s1;
+        s1 = s2;
+    }
+    if (r0.deg != 0)
+        return 0;
+    bp_divmod(&s0, &f, NULL, out);
+    return 1;
+}
+
+/* Weight of data strip k < p in Q: x^k (Corollary 3.2.4). */
+static void bp_weight(unsigned p, unsigned k, bpoly *out)
+{
+    bp_xpow(p, k, out);
+}
+
+/* Residues to and from packed bit strings: bit t (bit t%8 of byte t/8) is
+ * the coefficient of x^t, t < p-1. */
+static void bp_from_bits(unsigned p, const uint8_t *bits, bpoly *a)
+{
+    bp_zero(a);
+    for (unsigned t = 0; t + 1 < p; t++)
+        a->c[t] = (bits[t >> 3] >> (t & 7)) & 1u;
+    bp_fix_deg(a);
+}
+
+static void bp_to_bits(unsigned p, const bpoly *a, uint8_t *bits)
+{
+    memset(bits, 0, (p - 1 + 7) / 8);
+    for (unsigned t = 0; t + 1 < p; t++)
+        bits[t >> 3] |= (uint8_t)(a->c[t] << (t & 7));
+}
+
+static int bp_check_prime(unsigned p)
+{
+    if (p < 3 || p > BP_MAXP || (p % 2) == 0)
+        return -1;
+    for (unsigned t = 3; t * t <= p; t += 2)
+        if (p % t == 0)
+            return -1;
+    return 0;
+}
+
+/* Ring operations on packed residues (bits of (p-1+7)/8 bytes), for the tests. */
+int oracle_big_ring_mul(unsigned p, const uint8_t *a, const uint8_t *b, uint8_t *out)
+{
+    bpoly x, y, z;
+    if (bp_check_prime(p))
+        return -1;
+    bp_from_bits(p, a, &x);
+    bp_from_bits(p, b, &y);
+    bp_ring_mul(p, &x, &y, &z);
+    bp_to_bits(p, &z, out);
+    return 0;
+}
+
+int oracle_big_ring_xpow(unsigned p, unsigned k, uint8_t *out)
+{
+    bpoly z;
+    if (bp_check_prime(p) || k >= BP_CAP)
+        return -1;
+    bp_xpow(p, k, &z);
+    bp_to_bits(p, &z, out);
+    return 0;
+}
+
+/* Returns 1 and the inverse when a is a unit, 0 otherwise. */
+int oracle_big_ring_inv(unsigned p, const uint8_t *a, uint8_t *out)
+{
+    bpoly x, z;
+    if (bp_check_prime(p))
+        return -1;
+    bp_from_bits(p, a, &x);
+    const int ok = bp_ring_inv(p, &x, &z);
+    bp_to_bits(p, &z, out);
+    return ok;
+}
+
+/* Element e of strip k of stripe s of a horizontal layout: bits
+ * [e(p-1), (e+1)(p-1)) of the strip, little-endian. */
+static void bp_gather(unsigned p, const uint8_t *buf, u64 ss, u64 st, u64 s, unsigned k, u64 e, bpoly *a)
+{
+    const uint8_t *strip = buf + s * st + (u64)k * ss;
+    bp_zero(a);
+    for (unsigned r = 0; r + 1 < p; r++) {
+        const u64 t = e * (p - 1) + r;
+        a->c[r] = (strip[t >> 3] >> (t & 7)) & 1u;
+    }
+    bp_fix_deg(a);
+}
+
+static void bp_scatter(unsigned p, uint8_t *buf, u64 ss, u64 st, u64 s, unsigned k, u64 e, const bpoly *a)
+{
+    uint8_t *strip = buf + s * st + (u64)k * ss;
+    for (unsigned r = 0; r + 1 < p; r++) {
+        const u64 t = e * (p - 1) + r;
+        const uint8_t m = (uint8_t)(1u << (t & 7));
+        if (a->c[r])
+            strip[t >> 3] |= m;
+        else
+            strip[t >> 3] &= (uint8_t)~m;
+    }
+}
+
+static int bp_check_args(unsigned p, unsigned N, u64 strip_bytes)
+{
+    if (bp_check_prime(p) || N < 1 || N > p || (strip_bytes * 8) % (p - 1))
+        return -1;
+    return 0;
+}
+
+/* Equation (znparity): P = sum d_k, Q = sum x^k d_k, on horizontal stripes of
+ * any odd prime p <= 257 (base code, N <= p). */
+int oracle_hbig_encode(unsigned p, unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes,
+                       u64 strip_stride, u64 stripe_stride)
+{
+    if (bp_check_args(p, N, strip_bytes))
+        return -1;
+    static bpoly g[BP_MAXP];
+    for (unsigned k = 0; k < N; k++)
+        bp_weight(p, k, &g[k]);
+    const u64 n_el = strip_bytes * 8 / (p - 1);
+    for (u64 s = 0; s < n_stripes; s++)
+        for (u64 e = 0; e < n_el; e++) {
+            bpoly P, Q, d, t;
+            bp_zero(&P);
+            bp_zero(&Q);
+            for (unsigned k = 0; k < N; k++) {
+                bp_gather(p, buf, strip_stride, stripe_stride, s, k, e, &d);
+                bp_add(&P, &d, &P);
+                bp_ring_mul(p, &g[k], &d, &t);
+                bp_add(&Q, &t, &Q);
+            }
+            bp_scatter(p, buf, strip_stride, stripe_stride, s, N, e, &P);
+            bp_scatter(p, buf, strip_stride, stripe_stride, s, N + 1, e, &Q);
+        }
+    return 0;
+}
+
+/* Lemma 3.1.2's four cases for the lost pair i < j (strip N = P, N+1 = Q),
+ * with inverses by the extended Euclidean algorithm, on horizontal stripes of
+ * any odd prime p <= 257.  pairs, when not NULL, gives (i, j) per stripe. */
+int oracle_hbig_recover(unsigned p, unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes,
+                        u64 strip_stride, u64 stripe_stride, unsigned i, unsigned j, const uint8_t *pairs)
+{
+    if (bp_check_args(p, N, strip_bytes))
+        return -1;
+    static bpoly g[BP_MAXP];
+    for (unsigned k = 0; k < N; k++)
+        bp_weight(p, k, &g[k]);
+    const u64 n_el = strip_bytes * 8 / (p - 1);
+    const u64 ss = strip_stride, st = stripe_stride;
+    for (u64 s = 0; s < n_stripes; s++) {
+        const unsigned a = pairs ? pairs[2 * s] : i;
+        const unsigned b = pairs ? pairs[2 * s + 1] : j;
+        if (!(a < b && b < N + 2))
+            return -2;
+        /* the inverse this pair needs: of g_a (data + P), of g_a + g_b (two data) */
+        bpoly inv;
+        bp_zero(&inv);
+        if (b == N) {
+            if (!bp_ring_inv(p, &g[a], &inv))
+                return -3;
+        } else if (b < N) {
+            bpoly sum;
+            bp_add(&g[a], &g[b], &sum);
+            if (!bp_ring_inv(p, &sum, &inv))
+                return -3;
+        }
+        for (u64 e = 0; e < n_el; e++) {
+            bpoly d, t, acc, P, Q;
+            if (a == N) { /* P and Q: encode */
+                bp_zero(&P);
+                bp_zero(&Q);
+                for (unsigned k = 0; k < N; k++) {
+                    bp_gather(p, buf, ss, st, s, k, e, &d);
+                    bp_add(&P, &d, &P);
+                    bp_ring_mul(p, &g[k], &d, &t);
+                    bp_add(&Q, &t, &Q);
+                }
+                bp_scatter(p, buf, ss, st, s, N, e, &P);
+                bp_scatter(p, buf, ss, st, s, N + 1, e, &Q);
+            } else if (b == N) { /* d_a and P: d_a = g_a^{-1}(Q + sum_{k != a} g_k d_k), then P */
+                bpoly da;
+                bp_gather(p, buf, ss, st, s, N + 1, e, &acc);
+                for (unsigned k = 0; k < N; k++) {
+                    if (k == a)
+                        continue;
+                    bp_gather(p, buf, ss, st, s, k, e, &d);
+                    bp_ring_mul(p, &g[k], &d, &t);
+                    bp_add(&acc, &t, &acc);
+                }
+                bp_ring_mul(p, &inv, &acc, &da);
+                P = da;
+                for (unsigned k = 0; k < N; k++) {
+                    if (k == a)
+                        continue;
+                    bp_gather(p, buf, ss, st, s, k, e, &d);
+                    bp_add(&P, &d, &P);
+                }
+                bp_scatter(p, buf, ss, st, s, a, e, &da);
+                bp_scatter(p, buf, ss, st, s, N, e, &P);
+            } else if (b == N + 1) { /* d_a and Q: RAID-5, then Q */
+                bpoly da;
+                bp_gather(p, buf, ss, st, s, N, e, &da);
+                for (unsigned k = 0; k < N; k++) {
+                    if (k == a)
+                        continue;
+                    bp_gather(p, buf, ss, st, s, k, e, &d);
+                    bp_add(&da, &d, &da);
+                }
+                bp_zero(&Q);
+                for (unsigned k = 0; k < N; k++) {
+                    if (k == a)
+                        d = da;
+                    else
+                        bp_gather(p, buf, ss, st, s, k, e, &d);
+                    bp_ring_mul(p, &g[k], &d, &t);
+                    bp_add(&Q, &t, &Q);
+                }
+                bp_scatter(p, buf, ss, st, s, a, e, &da);
+                bp_scatter(p, buf, ss, st, s, N + 1, e, &Q);
+            } else { /* two data: d_b = (g_a + g_b)^{-1}(g_a P + Q + sum_{k != a,b} (g_k + g_a) d_k) */
+                bpoly db, da, w;
+                bp_gather(p, buf, ss, st, s, N, e, &P);
+                bp_gather(p, buf, ss, st, s, N + 1, e, &Q);
+                bp_ring_mul(p, &g[a], &P, &acc);
+                bp_add(&acc, &Q, &acc);
+                da = P;
+                for (unsigned k = 0; k < N; k++) {
+                    if (k == a || k == b)
+                        continue;
+                    bp_gather(p, buf, ss, st, s, k, e, &d);
+                    bp_add(&g[k], &g[a], &w);
+                    bp_ring_mul(p, &w, &d, &t);
+                    bp_add(&acc, &t, &acc);
+                    bp_add(&da, &d, &da);
+                }
+                bp_ring_mul(p, &inv, &acc, &db);
+                bp_add(&da, &db, &da);
+                bp_scatter(p, buf, ss, st, s, a, e, &da);
+                bp_scatter(p, buf, ss, st, s, b, e, &db);
+            }
+        }
     }
     return 0;
 }

@@ -41,6 +41,18 @@ MUTANTS = {
                          "        for (unsigned r = 0; r < L->rows; r++) {\n            u64 t = b * L->rows + r;",
                          "const uint8_t *strip = L->base + s * L->stripe_stride + (u64)k * L->strip_stride;\n"
                          "        for (unsigned r = 0; r < L->rows; r++) {\n            u64 t = b * (L->rows + 1) + r;"),
+    # the coefficient-array path for large primes (Z_257)
+    "big_mul_drops_top_term": ("        for (int j = 0; j <= b->deg; j++)\n            r.c[i + j] ^= b->c[j];",
+                               "        for (int j = 0; j < b->deg; j++)\n            r.c[i + j] ^= b->c[j];"),
+    "big_f_one_term_short": ("    for (unsigned t = 0; t < p; t++)\n        f->c[t] = 1;",
+                             "    for (unsigned t = 1; t < p; t++)\n        f->c[t] = 1;"),
+    "big_euclid_swapped_cofactors": ("    s1.c[0] = 1;\n    s1.deg = 0;", "    s0.c[0] = 1;\n    s0.deg = 0;"),
+    "big_weight_off_by_one": ("    bp_xpow(p, k, out);\n}", "    bp_xpow(p, k + 1, out);\n}"),
+    "big_gather_element_stride": ("        const u64 t = e * (p - 1) + r;\n        a->c[r]",
+                                  "        const u64 t = e * p + r;\n        a->c[r]"),
+    "big_dd_wrong_cofactor": ("bp_add(&g[k], &g[a], &w);", "bp_add(&g[k], &g[b], &w);"),
+    "big_dp_without_inverse": ("bp_ring_mul(p, &inv, &acc, &da);", "da = acc;"),
+    "big_dq_forgets_p": ("bp_gather(p, buf, ss, st, s, N, e, &da);", "bp_zero(&da);"),
 }
 
 
@@ -59,6 +71,7 @@ def test_pins_catch_planted_mistake(name):
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                             os.path.join(ROOT, "tests", "test_oracle_qext_pins.py"),
-                            os.path.join(ROOT, "tests", "test_oracle_horizontal_pins.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_horizontal_pins.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_p257_pins.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, "planted mistake %r passed every pin:\n%s" % (name, r.stdout[-2000:])

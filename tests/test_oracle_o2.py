@@ -160,3 +160,54 @@ def test_o2_h_invalid_arguments(o2):
         o2.o2_h_encode(7, 4, 64, h, 1)      # p - 1 = 6 does not divide the 512 bits of a strip
     with pytest.raises(ValueError):
         o2.o2_h_recover(5, 4, 64, h, 1, 2, 2)
+
+
+# ------------------------------------------------- Z_257 (256-bit elements)
+
+def test_o2_h257_inverse_equals_the_oracle(oracle):
+    import random
+    rnd = random.Random(257)
+    for z in list(range(1, 12)) + [128, 255, 256]:
+        u = 1 ^ oracle.big_ring_xpow(257, z)
+        assert oracle.o2_h257_inverse(u) == oracle.big_ring_inv(257, u)
+    for _ in range(6):
+        a = rnd.getrandbits(256)
+        assert oracle.o2_h257_inverse(a) == oracle.big_ring_inv(257, a)
+
+
+@pytest.mark.parametrize("N,B,S", [(1, 32, 2), (4, 64, 3), (17, 96, 2), (257, 32, 2)])
+def test_o2_h257_equals_the_oracle(oracle, N, B, S):
+    rng = np.random.default_rng(2570 + N)
+    h = rng.integers(0, 256, size=(S, N + 2, B), dtype=np.uint8)
+    a, b = h.copy(), h.copy()
+    oracle.hbig_encode(257, N, B, a, S)
+    oracle.o2_h257_encode(N, B, b, S, threads=3)
+    assert np.array_equal(a, b)
+    pairs = [(i, j) for i in range(N + 2) for j in range(i + 1, N + 2)]
+    for t in rng.choice(len(pairs), min(10, len(pairs)), replace=False):
+        i, j = pairs[t]
+        x, y = a.copy(), a.copy()
+        for z in (x, y):
+            z[:, i] = 0xA5
+            z[:, j] = 0x5A
+        oracle.hbig_recover(257, N, B, x, S, i, j)
+        oracle.o2_h257_recover(N, B, y, S, i, j, threads=2)
+        assert np.array_equal(x, y), (i, j)
+        assert np.array_equal(y, a), (i, j)
+
+
+def test_o2_h257_per_stripe_pairs_and_strides(oracle):
+    N, B, S = 9, 64, 5
+    ss, st = 96, 96 * (N + 2) + 32
+    rng = np.random.default_rng(2571)
+    flat = rng.integers(0, 256, size=st * S, dtype=np.uint8)
+    a, b = flat.copy(), flat.copy()
+    oracle.hbig_encode(257, N, B, a, S, ss, st)
+    oracle.o2_h257_encode(N, B, b, S, ss, st)
+    assert np.array_equal(a, b)
+    pairs = np.array([[0, 1], [3, N], [2, N + 1], [N, N + 1], [4, 8]], dtype=np.uint8)
+    x, y = a.copy(), a.copy()
+    oracle.hbig_recover(257, N, B, x, S, pairs=pairs, strip_stride=ss, stripe_stride=st)
+    oracle.o2_h257_recover(N, B, y, S, pairs=pairs, strip_stride=ss, stripe_stride=st)
+    assert np.array_equal(x, y)
+    assert np.array_equal(y, a)
