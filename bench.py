@@ -61,10 +61,12 @@ def parse():
                     help="stripes per GPU (default: the workload's own, 8192 for p13n12; other values are "
                          "profiling cases, not bench lines)")
     ap.add_argument("--workload", default="p13n12",
-                    choices=["p13n12", "p5n4", "p59n58", "qext", "h17", "p13n12_ops", "batched", "serve"],
+                    choices=["p13n12", "p5n4", "p59n58", "qext", "h17", "h257", "h257n16", "p13n12_ops",
+                             "batched", "serve"],
                     help="p13n12: the bench line; p5n4 / p59n58: the p=5 and p=59 plain geometries; "
                          "qext: extended Q-parity, p=59 with 117 data strips; "
                          "h17: the horizontal Z_17 representation (one element per 16-bit word); "
+                         "h257 / h257n16: Z_257 (256-bit elements), N=256 / N=16; "
                          "p13n12_ops: degraded read and small write on the bench line's geometry; "
                          "batched: the uneven 50k-stripe batch vs per-stripe launches; "
                          "serve: Poisson request stream, continuous batching vs per-job launches")
@@ -795,23 +797,31 @@ def run_ops(args):
 
 # ------------------------------------------------ horizontal representation
 
-H17 = (17, 16, 65536, 4096, 5)  # p, N, strip bytes, stripes, seed
+# name: (p, N, strip bytes, stripes, seed, description)
+HGEOMETRIES = {
+    "h17": (17, 16, 65536, 4096, 5, "horizontal Z_17 (Section 4.5): p=17, N=16 data strips + P + Q of 64 KiB "
+                                    "(32768 16-bit elements), %d stripes; encode + DD/DP/DQ/PQ, one launch per op"),
+    "h257": (257, 256, 65536, 256, 8, "horizontal Z_257 (Section 3.4): p=257, N=256 data strips + P + Q of 64 KiB "
+                                      "(2048 256-bit elements), %d stripes; encode + DD/DP/DQ/PQ, one launch per op"),
+    "h257n16": (257, 16, 65536, 4096, 9, "horizontal Z_257: p=257, N=16 data strips + P + Q of 64 KiB, %d stripes; "
+                                         "encode + DD/DP/DQ/PQ, one launch per op (recovery arithmetic per byte "
+                                         "16x that of N=256)"),
+}
 
 
-def run_h17(args):
-    """The horizontal representation of Section 4.5 (one Z_17 element per
-    16-bit word): p = 17, N = 16 data strips + P + Q of 64 KiB, 4096 stripes
-    (4.3 GB of user data, 4.8 GB moved per op); encode and one launch per
-    recovery class with a uniformly drawn pair per stripe."""
+def run_h(args):
+    """The horizontal representation of Section 4.5 (one ring element per
+    (p-1)-bit field): Z_17 (16-bit words) or Z_257 (256-bit elements); encode
+    and one launch per recovery class with a uniformly drawn pair per stripe
+    (16-bit pairs at p = 257)."""
+    import numpy as np
     import torch
 
     from paper_cs_0611109_gb300 import build, inputs
     build.build()
     from paper_cs_0611109_gb300 import rcg
 
-    p, n, B, S, seed = H17
-    desc = ("horizontal Z_17 (Section 4.5): p=17, N=16 data strips + P + Q of 64 KiB "
-            "(32768 16-bit elements), %d stripes; encode + DD/DP/DQ/PQ, one launch per op")
+    p, n, B, S, seed, desc = HGEOMETRIES[args.workload]
     if args.stripes and args.stripes != S:
         S = args.stripes
         desc = "profiling case: " + desc
@@ -824,8 +834,13 @@ def run_h17(args):
     rcg.rcg_fill_random(buf, buf.numel(), seed)
     L = rcg.make_hlayout(buf, p, n, B)
     ctx.h_encode(L, 0, S)
-    ops = [("encode", None)] + [(k, torch.from_numpy(inputs.random_pairs(3500 + m, n, S, k)).to(dev))
-                                for m, k in enumerate(CLASSES)]
+    wide = np.uint16 if p == 257 else np.uint8
+
+    def pairs_of(m, k):
+        pr = inputs.random_pairs(3500 + m, n, S, k, dtype=wide)
+        return torch.from_numpy(pr.view(np.int16) if p == 257 else pr).to(dev)
+
+    ops = [("encode", None)] + [(k, pairs_of(m, k)) for m, k in enumerate(CLASSES)]
     moved = (n + 2) * B * S
     user = n * B * S
 
@@ -866,19 +881,16 @@ def run_h17(args):
                         "hbm_gbs": round(moved / (ms * 1e-3) / 1e9, 1),
                         "hbm_frac": round(moved / (ms * 1e-3) / 1e9 / peak, 4)}
     achieved = moved * len(ops) / (total_ms * 1e-3) / 1e9
-    batched = None
-    if args.workload == "p5n4":
-        batched = p5n4_sixteen_in_one_batch(args, ctx, rcg, torch, buf, ops, flush, stream)
     ctx.close()
-    line_gbs = user * len(ops) / (total_ms * 1e-3) / 1e9
-    out = {"metric": METRIC, "value": round(line_gbs, 2), "unit": "GB/s",
+    return {"metric": METRIC, "value": round(user * len(ops) / (total_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms, 4),
-            "higher_is_better": True, "dtype": "u16 lanes",
+            "higher_is_better": True, "dtype": "u16 lanes" if p == 17 else "u256 elements",
             "data": "synthetic (SplitMix64 bytes generated on the device, seed %d)" % seed,
             "config": {"workload": desc, "p": p, "n_data": n, "strip_bytes": B, "stripes": S,
                        "hbm_bytes_per_op": moved, "l2": "inputs far larger than the 129 MB L2; no flush"},
-            "roofline": {"bound": "hbm", "kernel": "rcg_h_kernel<16>", "achieved": round(achieved, 1),
-                         "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(achieved / peak, 4)},
+            "roofline": {"bound": "hbm", "kernel": "rcg_h_kernel<16>" if p == 17 else "rcg_h257_kernel",
+                         "achieved": round(achieved, 1), "peak": peak, "peak_kind": kind, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4)},
             "per_op": per_op, "gpu_launches": len(ops) * args.steps, "clocks": clk}
 
 
@@ -1191,8 +1203,8 @@ def main():
     if args.workload == "p13n12_ops" and args.impl == "ours":
         print(json.dumps(run_ops(args)), flush=True)
         return
-    if args.workload == "h17" and args.impl == "ours":
-        print(json.dumps(run_h17(args)), flush=True)
+    if args.workload in HGEOMETRIES and args.impl == "ours":
+        print(json.dumps(run_h(args)), flush=True)
         return
     if args.workload in GEOMETRIES and args.impl == "ours":
         print(json.dumps(run_geometry(args)), flush=True)

@@ -220,12 +220,21 @@ rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe,
  * bit-sliced calls; results are identical to encoding the transposed stripe.
  * Layout: stripe s at base + s*stripe_stride, strip k at + k*strip_stride,
  * strip_bytes bytes per strip.  base, strides and strip_bytes are multiples of
- * 16; zero strides mean packed. */
+ * 16; zero strides mean packed.
+ *
+ * p = 257 (Z_257, named in Section 3.4 beside Z_17): an element is 256 bits,
+ * the 32 little-endian bytes [32e, 32e + 32) of the strip.  base, strides and
+ * strip_bytes are multiples of 32, N <= 257 (the base code: no extended
+ * strips), and the per-stripe pairs of rcg_h_recover_many are two 16-bit
+ * numbers per stripe (strip indices reach 258).  A recovery's inverse is not
+ * tabulated: (1 + x^z)^(-1) = x^z (1 + x^(2z)) (1 + x^(4z)) ... (1 + x^(128z)),
+ * because squaring has order 16 in R (Lemma 3.3.1: 2^16 = 1 and 2^8 = -1
+ * modulo 257). */
 typedef struct rcg_hlayout {
     void *base;             /* device address of stripe 0 */
-    uint32_t p;             /* 3, 5 or 17 */
+    uint32_t p;             /* 3, 5, 17 or 257 */
     uint32_t n_data;        /* N, 1 <= N <= p (or 2p - 1 for p = 5, 17) */
-    uint64_t strip_bytes;   /* bytes per strip, a positive multiple of 16 */
+    uint64_t strip_bytes;   /* bytes per strip, a positive multiple of 16 (32 for p = 257) */
     uint64_t strip_stride;  /* bytes between strips; 0 = strip_bytes */
     uint64_t stripe_stride; /* bytes between stripes; 0 = (N+2)*strip_stride */
 } rcg_hlayout;
@@ -245,7 +254,8 @@ rcg_status rcg_h_recover(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t stripe, ui
                          void *stream);
 
 /* rcg_h_recover for a per-stripe pair: pairs is a DEVICE array of
- * 2*n_stripes bytes, as in rcg_recover_many; an invalid pair leaves its
+ * 2*n_stripes bytes, as in rcg_recover_many (for p = 257: 2*n_stripes
+ * little-endian 16-bit numbers, 4-byte aligned); an invalid pair leaves its
  * stripe untouched and sets RCG_DEV_BADPAIR. */
 rcg_status rcg_h_recover_many(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t first_stripe, uint64_t n_stripes,
                               const uint8_t *pairs, void *stream);

@@ -297,13 +297,14 @@ def hbig_encode(p, N, strip_bytes, buf, n_stripes, strip_stride=None, stripe_str
 
 def hbig_recover(p, N, strip_bytes, buf, n_stripes, i=0, j=1, pairs=None, strip_stride=None,
                  stripe_stride=None):
-    """Rebuild strips i < j (or per-stripe pairs) of horizontal stripes of any
-    odd prime p <= 257 in place (Lemma 3.1.2, inverses by Euclid)."""
+    """Rebuild strips i < j (or per-stripe pairs, [n_stripes, 2] of 16-bit
+    numbers) of horizontal stripes of any odd prime p <= 257 in place
+    (Lemma 3.1.2, inverses by Euclid)."""
     _check_buf(buf)
     ss, st = _h_strides(N, strip_bytes, strip_stride, stripe_stride)
     pp = None
     if pairs is not None:
-        pairs = np.ascontiguousarray(pairs, dtype=np.uint8)
+        pairs = np.ascontiguousarray(pairs, dtype=np.uint16)
         pp = _ptr(pairs)
     rc = lib().oracle_hbig_recover(p, N, strip_bytes, _ptr(buf), n_stripes, ss, st, i, j, pp)
     if rc:
@@ -416,7 +417,7 @@ def o2_h257_recover(N, strip_bytes, buf, n_stripes, i=0, j=1, pairs=None, strip_
     ss, st = _h_strides(N, strip_bytes, strip_stride, stripe_stride)
     pp = None
     if pairs is not None:
-        pairs = np.ascontiguousarray(pairs, dtype=np.uint8)
+        pairs = np.ascontiguousarray(pairs, dtype=np.uint16)  # strip indices reach 258
         pp = _ptr(pairs)
     rc = o2().o2_h257_recover(N, strip_bytes, _ptr(buf), n_stripes, ss, st, i, j, pp, _threads(threads))
     if rc:

@@ -612,7 +612,7 @@ typedef struct {
     u64 n_el, ss, st;
     u64 s0, s1;
     unsigned i, j;
-    const uint8_t *pairs;
+    const uint16_t *pairs;
     int bad;
 } zwork_t;
 
@@ -693,7 +693,7 @@ static void *z_worker(void *arg)
 }
 
 static int z_run(unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes, u64 ss, u64 st, unsigned i,
-                 unsigned j, const uint8_t *pairs, int threads)
+                 unsigned j, const uint16_t *pairs, int threads)
 {
     if (N < 1 || N > Z_P || strip_bytes == 0 || strip_bytes % 32)
         return -1;
@@ -724,9 +724,10 @@ int o2_h257_encode(unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes, u64
     return z_run(N, strip_bytes, buf, n_stripes, ss, st, N, N + 1, NULL, threads);
 }
 
-/* Recover pair (i, j), or per-stripe pairs (two bytes per stripe) when pairs != NULL. */
+/* Recover pair (i, j), or per-stripe pairs (two 16-bit numbers per stripe:
+ * strip indices reach 258) when pairs != NULL. */
 int o2_h257_recover(unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes, u64 ss, u64 st, unsigned i,
-                    unsigned j, const uint8_t *pairs, int threads)
+                    unsigned j, const uint16_t *pairs, int threads)
 {
     return z_run(N, strip_bytes, buf, n_stripes, ss, st, i, j, pairs, threads);
 }

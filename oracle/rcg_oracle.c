@@ -771,9 +771,10 @@ int oracle_hbig_encode(unsigned p, unsigned N, u64 strip_bytes, uint8_t *buf, u6
 
 /* Lemma 3.1.2's four cases for the lost pair i < j (strip N = P, N+1 = Q),
  * with inverses by the extended Euclidean algorithm, on horizontal stripes of
- * any odd prime p <= 257.  pairs, when not NULL, gives (i, j) per stripe. */
+ * any odd prime p <= 257.  pairs, when not NULL, gives (i, j) per stripe as
+ * two 16-bit numbers (strip indices reach 258 at p = 257). */
 int oracle_hbig_recover(unsigned p, unsigned N, u64 strip_bytes, uint8_t *buf, u64 n_stripes,
-                        u64 strip_stride, u64 stripe_stride, unsigned i, unsigned j, const uint8_t *pairs)
+                        u64 strip_stride, u64 stripe_stride, unsigned i, unsigned j, const uint16_t *pairs)
 {
     if (bp_check_args(p, N, strip_bytes))
         return -1;

@@ -588,7 +588,16 @@ rcg_status rcg_degraded_read(rcg_ctx *ctx, const rcg_layout *L, uint64_t stripe,
 
 static rcg_status check_hlayout(const rcg_hlayout *L, uint64_t *ss, uint64_t *st) {
     if (!L || !L->base || !aligned16(L->base)) return RCG_EINVAL;
-    if (L->p != 3 && L->p != 5 && L->p != 17) return RCG_EINVAL;
+    if (L->p != 3 && L->p != 5 && L->p != 17 && L->p != 257) return RCG_EINVAL;
+    if (L->p == 257) {  // 32-byte elements, base code
+        if ((reinterpret_cast<uintptr_t>(L->base) & 31) || L->n_data < 1 || L->n_data > 257 ||
+            L->strip_bytes == 0 || (L->strip_bytes & 31) || L->strip_bytes / 32 > 0xffffffffull)
+            return RCG_EINVAL;
+        *ss = L->strip_stride ? L->strip_stride : L->strip_bytes;
+        *st = L->stripe_stride ? L->stripe_stride : (L->n_data + 2ull) * *ss;
+        if (*ss < L->strip_bytes || (*ss & 31) || (*st & 31)) return RCG_EINVAL;
+        return RCG_OK;
+    }
     if (L->n_data < 1 || L->n_data > max_data_strips(L->p)) return RCG_EINVAL;
     if (L->strip_bytes == 0 || (L->strip_bytes & 15) || L->strip_bytes / 16 > 0xffffffffull) return RCG_EINVAL;
     *ss = L->strip_stride ? L->strip_stride : L->strip_bytes;
@@ -605,6 +614,11 @@ static rcg_status h_launch(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t first, u
     if (s) return s;
     if (n == 0) return RCG_OK;
     DeviceGuard guard(ctx->device);
+    if (L->p == 257)
+        return from_cuda(launch_h257(static_cast<uint8_t *>(L->base) + first * st, L->n_data, L->strip_bytes, ss, st,
+                                     n, i, j, reinterpret_cast<const uint16_t *>(pairs), ctx->status, ctx->sm_count,
+                                     static_cast<cudaStream_t>(stream)),
+                         "Z_257 kernel launch");
     return from_cuda(launch_h(static_cast<uint8_t *>(L->base) + first * st, L->p, L->n_data, L->strip_bytes, ss, st,
                               n, i, j, pairs, ctx->status, ctx->sm_count, static_cast<cudaStream_t>(stream)),
                      "horizontal kernel launch");
@@ -625,6 +639,7 @@ rcg_status rcg_h_recover(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t stripe, ui
 rcg_status rcg_h_recover_many(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t first_stripe, uint64_t n_stripes,
                               const uint8_t *pairs, void *stream) {
     if (!L || !pairs) return RCG_EINVAL;
+    if (L->p == 257 && (reinterpret_cast<uintptr_t>(pairs) & 3)) return RCG_EINVAL;  // 16-bit pairs
     return h_launch(ctx, L, first_stripe, n_stripes, 0, 0, pairs, stream);
 }
 

@@ -214,6 +214,12 @@ cudaError_t launch_h(uint8_t *base, uint32_t p, uint32_t N, uint64_t strip_bytes
                      uint64_t stripe_stride, uint64_t n_stripes, uint32_t i, uint32_t j, const uint8_t *pairs,
                      uint32_t *status, int sm_count, cudaStream_t stream);
 
+// Z_257 in the horizontal representation (rcg_h257.cu): 32-byte elements,
+// base code (N <= 257); per-stripe pairs are 16-bit; i = N, j = N+1 encodes.
+cudaError_t launch_h257(uint8_t *base, uint32_t N, uint64_t strip_bytes, uint64_t strip_stride,
+                        uint64_t stripe_stride, uint64_t n_stripes, uint32_t i, uint32_t j, const uint16_t *pairs,
+                        uint32_t *status, int sm_count, cudaStream_t stream);
+
 // Column kernel (rcg_column.cu): bit-sliced stripes of p <= 7 without shared
 // memory.  One launch over n_stripes stripes of one job: op OP_ENCODE,
 // OP_RECOVER (pair i < j, or per-stripe pairs), OP_DEGRADED (strip j into aux)

@@ -65,14 +65,17 @@ def random_stripes(seed: int, p: int, n_data: int, C: int, n_stripes: int,
     return flat.reshape(n_stripes, n_data + 2, p - 1, C)
 
 
-def random_pairs(seed: int, n_data: int, n: int, kind: str = "any") -> np.ndarray:
-    """n erasure pairs (i < j) as uint8 [n, 2], drawn uniformly within a class.
+def random_pairs(seed: int, n_data: int, n: int, kind: str = "any", dtype=np.uint8) -> np.ndarray:
+    """n erasure pairs (i < j) as [n, 2] of `dtype` (uint8, or uint16 where
+    strip indices pass 255), drawn uniformly within a class.
 
     kind: "any" (i < j among all N+2 strips), "dd" (two data strips),
     "dp" (data + P), "dq" (data + Q), "pq" (both parities)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     N = n_data
-    out = np.empty((n, 2), dtype=np.uint8)
+    if N + 1 > np.iinfo(dtype).max:
+        raise ValueError("strip indices up to %d do not fit %s" % (N + 1, np.dtype(dtype).name))
+    out = np.empty((n, 2), dtype=dtype)
     if kind == "any":
         a = rng.integers(0, N + 2, size=n)
         b = rng.integers(0, N + 1, size=n)

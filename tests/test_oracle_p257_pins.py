@@ -266,7 +266,7 @@ def test_z257_wide_array_sampled_pairs(oracle):
     h = h_random(901, N, B, 2)
     oracle.hbig_encode(P, N, B, h, 2)
     rnd = random.Random(901)
-    pairs = np.array([sorted(rnd.sample(range(N + 2), 2)) for _ in range(2)], dtype=np.uint8)
+    pairs = np.array([[256, 258], sorted(rnd.sample(range(N + 2), 2))], dtype=np.uint16)
     for extra in [(0, 256), (255, 256), (256, 257), (257, 258), (3, 258)]:
         lost = h.copy()
         lost[:, extra[0]] = POISON
