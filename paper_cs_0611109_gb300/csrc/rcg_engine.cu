@@ -948,18 +948,20 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
         const uint32_t qbase = stage - rot * pitch;  // + p*pitch for rows r < rot
         const int vrow = rot == 0 ? p - 1 : rot - 1;
         const uint32_t fsel = flags & (F_P | F_Q | F_Q2 | F_COPY);
-        if (fsel == (F_P | F_Q)) {
-            // a data strip feeding both accumulators: the common case
+        if (fsel == (F_P | F_Q) || (S::kItems > 4 && fsel == F_P)) {
+            // a data strip feeding both accumulators: the common case; in the
+            // 6-item shape also P alone (a separate loop there costs a spill)
+            const bool with_q = fsel & F_Q;
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t) {
                 const int r = row[t];  // invalid items carry a row >= p
                 if (r < p - 1) accP[t] = xor4(accP[t], lds_a(stage + off[t]));
-                if (r < p && r != vrow) accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
+                if (with_q && r < p && r != vrow)
+                    accQ[t] = xor4(accQ[t], lds_a(qbase + off[t] + (r < rot ? pw : 0u)));
             }
-        } else if (S::kItems <= 4 && fsel == F_P) {
+        } else if (fsel == F_P) {
             // P alone: every stage of a degraded read from P, the P strip of a
-            // recovery (not in the 6-item shape, where this path costs a
-            // register spill; there the general path below takes it)
+            // recovery (the 4-item shape)
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t)
                 if (row[t] < p - 1) accP[t] = xor4(accP[t], lds_a(stage + off[t]));

@@ -34,6 +34,7 @@
 #include <mutex>
 #include <new>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/rcg.h"
@@ -133,6 +134,11 @@ struct rcg_server {
     std::deque<uint64_t> pending;       // submitted, not yet examined (arrival order of submission)
     std::deque<uint64_t> blocked;       // arrived and examined, waiting on an overlapping request
     std::map<uintptr_t, uintptr_t> waiting;  // union of the blocked requests' extents, lo -> hi (merged)
+    // Exact extents, keyed by their first byte: the common conflict (requests
+    // on the same stripe) is one hash lookup; an extent identical to one
+    // already here needs no ordered-map work
+    std::unordered_map<uintptr_t, uintptr_t> busy_exact;
+    std::unordered_map<uintptr_t, uintptr_t> waiting_exact;
     std::deque<uint64_t> admitted;      // admitted, not launched
     std::deque<Launch> inflight;        // launched, not retired
     std::map<uintptr_t, uintptr_t> busy;  // device byte ranges of admitted requests, lo -> hi (disjoint)
@@ -222,7 +228,10 @@ bool tick(rcg_server *s) {
             if (q != cudaSuccess) r.status = RCG_ECUDA;
             s->budget_used -= r.footprint;
             --s->inflight_jobs;
-            for (uint32_t k = 0; k < r.n_ext; ++k) s->busy.erase(r.ext[k].lo);
+            for (uint32_t k = 0; k < r.n_ext; ++k) {
+                s->busy.erase(r.ext[k].lo);
+                s->busy_exact.erase(r.ext[k].lo);
+            }
         }
         s->completed += L.ids.size();
         s->free_events.push_back(L.done);
@@ -238,6 +247,7 @@ bool tick(rcg_server *s) {
         s->pending.insert(s->pending.begin(), s->blocked.begin(), s->blocked.end());
         s->blocked.clear();
         s->waiting.clear();
+        s->waiting_exact.clear();
     }
     // 2. admit arrived requests in order while slots and HBM allow; a request
     //    whose bytes overlap an admitted one's, or a blocked earlier one's,
@@ -248,16 +258,34 @@ bool tick(rcg_server *s) {
         if (s->inflight_jobs >= s->cfg.max_inflight_jobs) break;
         if (s->budget_used + r.footprint > s->cfg.hbm_budget_bytes) break;
         bool conflict = false;
-        for (uint32_t k = 0; k < r.n_ext && !conflict; ++k)
-            conflict = overlaps(s->busy, r.ext[k]) || overlaps(s->waiting, r.ext[k]);
+        for (uint32_t k = 0; k < r.n_ext && !conflict; ++k) {
+            const Extent &e = r.ext[k];
+            // two extents with the same first byte overlap
+            conflict = s->busy_exact.count(e.lo) || s->waiting_exact.count(e.lo) || overlaps(s->busy, e) ||
+                       overlaps(s->waiting, e);
+        }
         if (conflict) {
-            for (uint32_t k = 0; k < r.n_ext; ++k) insert_merged(s->waiting, r.ext[k]);
+            for (uint32_t k = 0; k < r.n_ext; ++k) {
+                const Extent &e = r.ext[k];
+                // the union already covers an extent identical to a busy or waiting one
+                auto b = s->busy_exact.find(e.lo);
+                auto w = s->waiting_exact.find(e.lo);
+                const bool known = (b != s->busy_exact.end() && b->second == e.hi) ||
+                                   (w != s->waiting_exact.end() && w->second == e.hi);
+                if (!known) {
+                    insert_merged(s->waiting, e);
+                    if (w == s->waiting_exact.end() || w->second < e.hi) s->waiting_exact[e.lo] = e.hi;
+                }
+            }
             ++s->conflict_waits;
             s->blocked.push_back(s->pending.front());
             s->pending.pop_front();
             continue;
         }
-        for (uint32_t k = 0; k < r.n_ext; ++k) s->busy[r.ext[k].lo] = r.ext[k].hi;
+        for (uint32_t k = 0; k < r.n_ext; ++k) {
+            s->busy[r.ext[k].lo] = r.ext[k].hi;
+            s->busy_exact[r.ext[k].lo] = r.ext[k].hi;
+        }
         s->budget_used += r.footprint;
         ++s->inflight_jobs;
         s->max_inflight_jobs = std::max(s->max_inflight_jobs, s->inflight_jobs);
