@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--batch-jobs", type=int, default=50000)
     ap.add_argument("--arena-gb", type=float, default=100.0)
     ap.add_argument("--schedule", default="dynamic", choices=["static", "dynamic"])
+    ap.add_argument("--tuning", default="autotune", choices=["autotune", "default"],
+                    help="batched: autotune the layout on the first wave (the bench line), or keep the default "
+                         "layout (profiling captures)")
     ap.add_argument("--row-align", type=int, default=16,
                     help="batched: bytes each row stride is rounded up to (16 = packed rows, the workload as "
                          "specified; 128 = rows padded to whole L2 lines)")
@@ -969,7 +972,7 @@ def measure_batched(args, ctx, rcg, torch):
             assert ctx.batch_wait(ctx.batch_submit(pre))
         mix = [rcg.make_job(L, 0, 1, rcg.RCG_OP_ENCODE) if j["op"] == "encode" else
                rcg.make_job(L, 0, 1, rcg.RCG_OP_RECOVER, j["i"], j["j"]) for L, (j, _) in zip(lays, w)]
-        if tuning is None:
+        if tuning is None and args.tuning == "autotune":
             # autotune the layout once, on the first wave (the batch itself runs
             # repeatedly: every op is idempotent on non-overlapping jobs)
             h0 = time.perf_counter()
@@ -1044,7 +1047,8 @@ def measure_batched(args, ctx, rcg, torch):
         "batched": {"ms": round(tot["batched_ms"], 3), "user_gbs": round(gbs(tot["user"], tot["batched_ms"]), 1),
                     "hbm_gbs": round(gbs(tot["moved"], tot["batched_ms"]), 1),
                     "hbm_frac": round(gbs(tot["moved"], tot["batched_ms"]) / peak, 4), "launches": len(waves),
-                    "layout": "autotuned on the first wave", "tuning": tuning,
+                    "layout": "autotuned on the first wave" if args.tuning == "autotune" else "default",
+                    "tuning": tuning,
                     "autotune_s": tot.get("autotune_s"),
                     "prepare_host_ms": round(tot.get("prepare_host_ms", 0.0), 3),
                     "user_gbs_with_prepare": round(gbs(tot["user"], tot["batched_ms"] + tot.get("prepare_host_ms", 0.0)), 1)},

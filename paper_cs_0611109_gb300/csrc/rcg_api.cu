@@ -35,8 +35,7 @@ struct BatchSlot {
     cudaGraphNode_t copy_node = nullptr;
     cudaGraphNode_t col_nodes[kColVariants] = {};  // column kernels of the p <= 7 jobs
     cudaGraphNode_t engine_node = nullptr;         // the tile engine
-    cudaGraphNode_t reset_node = nullptr;          // the tile counter reset (the engine's only)
-    int enabled = -1;  // bit v: column variant v enabled; bit 4: tile engine and its reset; -1 unknown
+    int enabled = -1;  // bit v: column variant v enabled; bit 4: tile engine; -1 unknown
     cudaEvent_t done = nullptr;
     uint32_t shape = 0;  // engine shape the graph's kernel node was captured with
     uint64_t ticket = 0;
@@ -693,7 +692,6 @@ static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
     s.graph = nullptr;
     s.copy_node = nullptr;
     s.engine_node = nullptr;
-    s.reset_node = nullptr;
     for (auto &n : s.col_nodes) n = nullptr;
     s.enabled = -1;
     const size_t bytes = s.cap_bytes;
@@ -728,7 +726,6 @@ static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
             cudaGraphNodeType t;
             if (cudaGraphNodeGetType(nd, &t) != cudaSuccess) continue;
             if (t == cudaGraphNodeTypeMemcpy) s.copy_node = nd;
-            if (t == cudaGraphNodeTypeMemset) s.reset_node = nd;
             if (t != cudaGraphNodeTypeKernel) continue;
             cudaKernelNodeParams kp;
             if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
@@ -740,7 +737,7 @@ static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
                 }
             if (!col) s.engine_node = nd;
         }
-        bool all = s.copy_node && s.engine_node && s.reset_node;
+        bool all = s.copy_node && s.engine_node;
         for (auto nd : s.col_nodes) all = all && nd;
         if (!all) e = cudaErrorUnknown;
         where = "graph nodes";
@@ -755,14 +752,17 @@ static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
 }
 
 // Enable the graph's kernels that the table has work for (bit v: column
-// variant v; bit 4: the tile engine and its counter reset).
+// variant v; bit 4: the tile engine).  Only kernel nodes are switched: the
+// table copy and the counter reset always run.  Measured on GB300: with the
+// counter reset (the memset between the copy and the kernels) disabled, a
+// kernel of a back-to-back batch could start before its table copy had
+// landed (1 to 4 of 400 column-only batches read the previous table).
 static cudaError_t set_enabled(BatchSlot &s, int mask) {
     if (mask == s.enabled) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     for (int v = 0; v < kColVariants && e == cudaSuccess; ++v)
         e = cudaGraphNodeSetEnabled(s.exec, s.col_nodes[v], (mask >> v) & 1);
     if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(s.exec, s.engine_node, (mask >> 4) & 1);
-    if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(s.exec, s.reset_node, (mask >> 4) & 1);
     s.enabled = e == cudaSuccess ? mask : -1;
     return e;
 }

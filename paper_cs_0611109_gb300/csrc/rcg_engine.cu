@@ -177,6 +177,12 @@ __device__ __forceinline__ void acquire_tmap(const CUtensorMap *map) {
                  : "memory");
 }
 
+// Bit e of m moved to bit (p - e) mod p, for exponent sets of p bits: the
+// exponents of x^(-e).
+__device__ __forceinline__ uint64_t reflect_exponents(uint64_t m, uint32_t p) {
+    return (m & 1ull) | (__brevll(m & ~1ull) >> (63 - p));
+}
+
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }
@@ -257,6 +263,7 @@ struct Smem {
     uint64_t *full;   // [kMaxSlots] producer -> consumers (tx-counted)
     uint64_t *empty;  // [kMaxSlots] consumers -> producer
     uint64_t *ep;     // epilogue barrier among consumer warps
+    uint8_t *terms;   // table solves: the inverse's reflected exponents, listed (64 bytes)
     SlotHdr *hdr;     // [kMaxSlots]
     uint8_t *xb;      // exchange buffer [p][nvec] x 16 B
     uint8_t *fold;    // two rows [2][nvec] x 16 B, used alternately by successive tiles
@@ -269,6 +276,7 @@ __device__ __forceinline__ Smem carve(uint8_t *smem) {
     s.full = reinterpret_cast<uint64_t *>(smem);
     s.empty = s.full + kMaxSlots;
     s.ep = s.empty + kMaxSlots;
+    s.terms = smem + 640;  // after the barriers (520 bytes), before the slot headers at 1 KB
     s.hdr = reinterpret_cast<SlotHdr *>(smem + 1024);
     s.xb = smem + kCtlBytes;
     s.fold = s.xb + S::kXBytes;
@@ -639,7 +647,9 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                         h.base = reinterpret_cast<uint64_t>(stripe_base);
                         h.strip_stride = strip_stride;
                         h.row_stride = row_stride;
-                        h.out = (cls == E_DD || cls == E_DPX) ? mask : reinterpret_cast<uint64_t>(aux_base);
+                        // table solves: the inverse's exponents reflected (see the epilogue)
+                        h.out = (cls == E_DD || cls == E_DPX) ? reflect_exponents(mask, p)
+                                                              : reinterpret_cast<uint64_t>(aux_base);
                         h.out_row_stride = aux_rs;
                     }
                     mbar_arrive_tx(full, tensor ? tx_tensor : tx_rows);
@@ -846,33 +856,41 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[S::k
         case E_DPX: {
             // accQ = x^(-s) dQ (lifted), so T = dP + x^(-s) dQ is formed in place
             // (row p-1 of dP is zero), or T = accQ (extended data strip + P);
-            // D_b = c^(-1) T needs every row of T.  The exponent mask of c^(-1)
+            // D_b = c^(-1) T needs every row of T.  The exponent set of c^(-1)
             // -- (1 + x^z)^(-1) of Section 4.6, or a trinomial's inverse --
-            // comes in the tile header.
+            // comes in the tile header reflected (e -> p - e): row r of D_b is
+            // the XOR of rows (e' + r) mod p of T over the reflected exponents
+            // e'.  The consumers list those exponents once per tile; each thread
+            // then walks the list once for all its items.
             const uint4 zero = make_uint4(0, 0, 0, 0);
             const bool tp = T.cls == E_DD;
+            const uint64_t mref = reinterpret_cast<uint64_t>(T.out) & ((1ull << p) - 1);  // exponents < p
+            if (ctid < p && ((mref >> ctid) & 1ull))
+                sm.terms[__popcll(mref & ((1ull << ctid) - 1))] = static_cast<uint8_t>(ctid);
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t)
                 if (row[t] < p)
                     sts(X(sm.xb, row[t], col[t]), (tp && row[t] < p - 1) ? xor4(accP[t], accQ[t]) : accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
-            // D_b (lifted) = sum over the mask's exponent set of x^m T
-            const uint64_t mask = reinterpret_cast<uint64_t>(T.out) & ((1ull << p) - 1);  // exponents < p
+            const int n_terms = __popcll(mref);
+            const uint32_t row_bytes = nv * 16;
+            const uint32_t xb0 = smem_addr(sm.xb);
 #pragma unroll
-            for (int t = 0; t < S::kItems; ++t) {
-                if (row[t] >= p) continue;
-                uint4 d = zero;
-                uint64_t m = mask;
-                while (m) {
-                    const int e = __ffsll(static_cast<long long>(m)) - 1;
-                    m &= m - 1;
-                    int s = row[t] - e;
-                    if (s < 0) s += p;
-                    d = xor4(d, lds(X(sm.xb, s, col[t])));
+            for (int t = 0; t < S::kItems; ++t) accQ[t] = zero;
+            for (int k = 0; k < n_terms; ++k) {
+                const int e = sm.terms[k];  // the same in every thread
+#pragma unroll
+                for (int t = 0; t < S::kItems; ++t) {
+                    const int r = row[t];
+                    if (r >= p) continue;
+                    int j = e + r;
+                    if (j >= p) j -= p;
+                    accQ[t] = xor4(accQ[t], lds_a(xb0 + j * row_bytes + col[t] * 16));
                 }
-                accQ[t] = d;
-                if (row[t] == p - 1) sts(fold + col[t] * 16, d);
             }
+#pragma unroll
+            for (int t = 0; t < S::kItems; ++t)
+                if (row[t] == p - 1) sts(fold + col[t] * 16, accQ[t]);
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t) {

@@ -279,3 +279,30 @@ def test_p5n4_sixteen_operations_in_one_batch(rcg, oracle):
     sample = stripes(0, p, N, C, S)[:8].copy()
     oracle.encode(p, N, C, sample, 8)
     assert np.array_equal(got[0, :8], sample)
+
+
+def test_back_to_back_batches_switching_kernels(rcg, oracle):
+    # batches launched without waiting, alternating column-kernel-only, tile-
+    # engine-only and mixed tables, so each replayed graph switches its kernel
+    # nodes on and off while the previous batches still run: every batch must
+    # run on its own table
+    kinds = ["p5", "p13", "mix", "p5", "p5"] * 60
+    bufs = []
+    for k, kind in enumerate(kinds):
+        geos = {"p5": [(5, 4, 544)], "p13": [(13, 6, 512)], "mix": [(13, 6, 512), (5, 4, 544)]}[kind]
+        entry = []
+        for g, (p, N, C) in enumerate(geos):
+            host = stripes(7000 + 2 * k + g, p, N, C, 1)
+            entry.append((p, N, C, host, dev(host)))
+        bufs.append(entry)
+    with rcg.Context(0) as c:
+        for entry in bufs:
+            c.batch_submit([rcg.make_job(rcg.make_layout(d, p, N, C), 0, 1, rcg.RCG_OP_ENCODE)
+                            for p, N, C, _, d in entry])
+        torch.cuda.synchronize()
+        assert c.last_device_status() == 0
+    for k, entry in enumerate(bufs):
+        for p, N, C, host, d in entry:
+            want = host.copy()
+            oracle.encode(p, N, C, want, 1)
+            assert np.array_equal(d.cpu().numpy(), want), (k, kinds[k], p)
