@@ -683,8 +683,10 @@ static rcg_status build_job(const rcg_ctx *ctx, const rcg_job &in, uint32_t shap
 }
 
 // Capture the slot's graph: descriptor-table copy -> tile-counter reset ->
-// the column kernels of the four p <= 7 variants -> persistent tile engine of
-// the given shape.  A launch enables only the kernels its table has work for.
+// {the column kernels of the four p <= 7 variants, the persistent tile engine
+// of the given shape}, each kernel depending on the reset directly (they work
+// on different jobs).  A launch enables only the kernels its table has work
+// for.
 static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
     if (s.exec) cudaGraphExecDestroy(s.exec);
     if (s.graph) cudaGraphDestroy(s.graph);
@@ -697,22 +699,42 @@ static rcg_status capture_slot(rcg_ctx *ctx, BatchSlot &s, uint32_t shape) {
     const size_t bytes = s.cap_bytes;
     s.bytes = bytes;
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(s.capture, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaSuccess;
     const char *where = "graph capture";
+    // fan-out: every kernel node depends on the counter reset (which follows
+    // the table copy) directly, never through a node a launch may disable
+    cudaStream_t side[kColVariants] = {};
+    cudaEvent_t fork = nullptr, join[kColVariants] = {};
+    for (int v = 0; v < kColVariants && e == cudaSuccess; ++v) {
+        e = cudaStreamCreateWithFlags(&side[v], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[v], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(s.capture, cudaStreamCaptureModeThreadLocal);
+    else where = "capture streams";
     if (e == cudaSuccess) {
         cudaError_t e1 = cudaMemcpyAsync(s.dev, s.host, bytes, cudaMemcpyHostToDevice, s.capture);
         cudaError_t e2 = cudaMemsetAsync(s.counter, 0, sizeof(unsigned long long), s.capture);
-        cudaError_t e3 = cudaSuccess;
-        for (int v = 0; v < kColVariants && e3 == cudaSuccess; ++v)
-            e3 = launch_column_batch(v, s.dev, ctx->status, ctx->sm_count, s.capture);
+        cudaError_t e3 = cudaEventRecord(fork, s.capture);
+        for (int v = 0; v < kColVariants && e3 == cudaSuccess; ++v) {
+            e3 = cudaStreamWaitEvent(side[v], fork, 0);
+            if (e3 == cudaSuccess) e3 = launch_column_batch(v, s.dev, ctx->status, ctx->sm_count, side[v]);
+            if (e3 == cudaSuccess) e3 = cudaEventRecord(join[v], side[v]);
+        }
         if (e3 == cudaSuccess)
             e3 = launch_batch(s.dev, ctx->status, s.counter, ctx->timeout_ns, shape,
                               ctx->sm_count * static_cast<int>(shape_info(shape).ctas_per_sm), s.capture);
+        for (int v = 0; v < kColVariants && e3 == cudaSuccess; ++v) e3 = cudaStreamWaitEvent(s.capture, join[v], 0);
         e = cudaStreamEndCapture(s.capture, &graph);
         if (e1 != cudaSuccess) { e = e1; where = "captured table copy"; }
         else if (e2 != cudaSuccess) { e = e2; where = "captured counter reset"; }
         else if (e3 != cudaSuccess) { e = e3; where = "captured kernel launch"; }
     }
+    for (int v = 0; v < kColVariants; ++v) {
+        if (join[v]) cudaEventDestroy(join[v]);
+        if (side[v]) cudaStreamDestroy(side[v]);
+    }
+    if (fork) cudaEventDestroy(fork);
     if (e == cudaSuccess) {
         e = cudaGraphInstantiate(&s.exec, graph, 0);
         where = "graph instantiate";
