@@ -164,7 +164,7 @@ __device__ __forceinline__ El rot(const El &y, uint32_t m) {
 
 // Blocks of 256 elements of one strip position of one stripe, interleaved
 // over a resident grid.
-__global__ void __launch_bounds__(256, 2) rcg_h257_kernel(const H257Params prm) {
+__global__ void __launch_bounds__(256, 3) rcg_h257_kernel(const H257Params prm) {
     const uint32_t N = prm.N;
     const uint32_t bps = (prm.eps + 255) / 256;  // blocks of 256 elements per strip
     const uint64_t blocks = prm.n_stripes * bps;
