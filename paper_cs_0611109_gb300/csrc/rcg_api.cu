@@ -174,7 +174,7 @@ void attach_tensor_map(Job &J, const Geo &g) {
 }
 
 Job base_job(const rcg_ctx *ctx, const rcg_layout *L, const Geo &g, uint64_t first_stripe,
-             uint64_t n_stripes, const Plan &pl) {
+             uint64_t n_stripes, const Plan &pl, bool want_tmap = true) {
     Job J;
     memset(&J, 0, sizeof(J));
     J.base = static_cast<uint8_t *>(L->base) + first_stripe * g.st;
@@ -187,7 +187,7 @@ Job base_job(const rcg_ctx *ctx, const rcg_layout *L, const Geo &g, uint64_t fir
     J.tiles_per_stripe = pl.tiles_per_stripe;
     J.p = static_cast<uint8_t>(g.p);
     J.n = static_cast<uint8_t>(g.N);
-    if (ctx->copy_mode == RCG_COPY_AUTO) attach_tensor_map(J, g);
+    if (want_tmap && ctx->copy_mode == RCG_COPY_AUTO) attach_tensor_map(J, g);
     J.dd_solve = ctx->dd_solve == RCG_SOLVE_TABLE ? 1 : 0;
     return J;
 }
@@ -231,6 +231,7 @@ ColJob column_job(const rcg_layout *L, const Geo &g, uint64_t first, uint32_t op
     J.i = i;
     J.j = j;
     J.op = op;
+    J.p = g.p;
     return J;
 }
 
@@ -645,13 +646,15 @@ rcg_status rcg_h_recover_many(rcg_ctx *ctx, const rcg_hlayout *L, uint64_t first
 
 // ================================================================= batches
 
-static rcg_status build_job(const rcg_ctx *ctx, const rcg_job &in, uint32_t shape, Job *out, Plan *pl) {
+// want_tmap = false: the job runs in the column kernel, which needs no tensor map.
+static rcg_status build_job(const rcg_ctx *ctx, const rcg_job &in, uint32_t shape, Job *out, Plan *pl,
+                            bool want_tmap = true) {
     Geo g;
     rcg_status st = check_layout(&in.layout, &g);
     if (st) return st;
     if (in.n_stripes == 0 || in.n_stripes > 0x7fffffffull) return RCG_EINVAL;
     if (!make_plan(g.p, g.C, shape, pl, ctx->tune_tile_div)) return RCG_EINVAL;
-    Job J = base_job(ctx, &in.layout, g, in.first_stripe, in.n_stripes, *pl);
+    Job J = base_job(ctx, &in.layout, g, in.first_stripe, in.n_stripes, *pl, want_tmap);
     const uint64_t ars = in.aux_row_stride ? in.aux_row_stride : g.C;
     const uint64_t ass = in.aux_stripe_stride ? in.aux_stripe_stride : (g.p - 1) * ars;
     switch (in.op) {
@@ -830,7 +833,8 @@ static uint32_t batch_shape(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_
 }
 
 // The descriptor table of a batch for one engine shape, built in `out`:
-// header, jobs, work items of the tile engine (runs of tiles of one job of
+// header, the tile-engine jobs (with their tensor maps), work items of the
+// tile engine (runs of tiles of one job of
 // roughly equal bytes; the items of larger jobs come first so the batch ends
 // on small items), then the column items of the p <= 7 jobs (when the
 // context uses the column kernel), grouped by variant.  max_items (0: no
@@ -845,9 +849,9 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     uint32_t slot_bytes = 0;
     for (uint32_t k = 0; k < n_jobs; ++k) {
         Plan pl;
-        rcg_status st = build_job(ctx, jobs[k], shape, &table[k], &pl);
+        if (ctx->column == RCG_COLUMN_AUTO) variant[k] = column_variant(jobs[k].layout.p, jobs[k].layout.n_data);
+        rcg_status st = build_job(ctx, jobs[k], shape, &table[k], &pl, variant[k] < 0);
         if (st) return st;
-        if (ctx->column == RCG_COLUMN_AUTO) variant[k] = column_variant(table[k].p, table[k].n);
         if (variant[k] >= 0) {
             tiles[k] = 0;
             continue;
@@ -886,6 +890,14 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
         return table[x].n_stripes * static_cast<uint64_t>(table[x].p - 1) * table[x].C * (table[x].n + 2u) >
                table[y].n_stripes * static_cast<uint64_t>(table[y].p - 1) * table[y].C * (table[y].n + 2u);
     });
+    // the Job entries (tensor maps) of tile-engine jobs only, in job order
+    std::vector<uint32_t> tile_index(n_jobs, 0);
+    std::vector<Job> tile_jobs;
+    for (uint32_t k = 0; k < n_jobs; ++k)
+        if (variant[k] < 0) {
+            tile_index[k] = static_cast<uint32_t>(tile_jobs.size());
+            tile_jobs.push_back(table[k]);
+        }
     std::vector<WorkItem> items;
     for (uint32_t k : order) {
         if (variant[k] >= 0) continue;
@@ -904,7 +916,7 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
         w.W = J.W;
         w.C = J.C;
         w.n_stripes = J.n_stripes;
-        w.job = k;
+        w.job = tile_index[k];
         w.p = J.p;
         w.n = J.n;
         w.op = J.op;
@@ -921,21 +933,36 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     for (uint32_t k = 0; k < n_jobs; ++k)
         if (tiles[k] > 0xffffffffull) return RCG_EINVAL;
     if (items.size() > 0xffffffffull) return RCG_EINVAL;
-    // column items: one per p <= 7 job, grouped by variant, numbering the
-    // variant's 32-column chunks
-    std::vector<ColItem> col_items;
+    // column items: one self-contained record per p <= 7 job, grouped by
+    // variant, numbering the variant's 32-column chunks
+    std::vector<ColJob> col_items;
     uint32_t col_begin[kColVariants] = {}, col_count[kColVariants] = {}, col_chunks[kColVariants] = {};
     for (int v = 0; v < kColVariants; ++v) {
         col_begin[v] = static_cast<uint32_t>(col_items.size());
         uint64_t chunks = 0;
         for (uint32_t k = 0; k < n_jobs; ++k) {
             if (variant[k] != v) continue;
-            ColItem ci;
-            ci.job = k;
-            ci.pad = 0;
-            ci.chunk0 = chunks;
-            col_items.push_back(ci);
-            chunks += (static_cast<uint64_t>(table[k].n_stripes) * (table[k].C / 16) + kColChunk - 1) / kColChunk;
+            const Job &J = table[k];
+            ColJob cj;
+            memset(&cj, 0, sizeof(cj));
+            cj.base = J.base;
+            cj.pairs = J.pairs;
+            cj.aux = J.aux;
+            cj.rs = J.row_stride;
+            cj.ss = J.strip_stride;
+            cj.st = J.stripe_stride;
+            cj.ars = J.aux_row_stride;
+            cj.ass = J.aux_stripe_stride;
+            cj.chunk0 = chunks;
+            cj.n_stripes = J.n_stripes;
+            cj.vps = J.C / 16;
+            cj.N = J.n;
+            cj.i = J.i;
+            cj.j = J.j;
+            cj.op = J.op;
+            cj.p = J.p;
+            col_items.push_back(cj);
+            chunks += (static_cast<uint64_t>(J.n_stripes) * (J.C / 16) + kColChunk - 1) / kColChunk;
         }
         if (chunks > 0xffffffffull) return RCG_EINVAL;
         col_count[v] = static_cast<uint32_t>(col_items.size()) - col_begin[v];
@@ -945,7 +972,7 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     BatchHeader hdr;
     memset(&hdr, 0, sizeof(hdr));
     hdr.total_tiles = total;
-    hdr.n_jobs = n_jobs;
+    hdr.n_jobs = static_cast<uint32_t>(tile_jobs.size());  // the Job entries (tile-engine jobs)
     if (slot_bytes == 0) slot_bytes = 128;  // no tile-engine job
     hdr.slot_bytes = slot_bytes;  // the largest stage
     if (ctx->tune_ring == RCG_RING_FIXED) {
@@ -963,18 +990,18 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     hdr.dynamic = ctx->batch_schedule == RCG_SCHED_DYNAMIC ? 1u : 0u;
     hdr.shape = shape;
     hdr.n_items = static_cast<uint32_t>(items.size());
-    hdr.items_offset = sizeof(BatchHeader) + static_cast<uint64_t>(n_jobs) * sizeof(Job);
-    hdr.col_items_offset = hdr.items_offset + items.size() * sizeof(WorkItem);
+    hdr.items_offset = sizeof(BatchHeader) + static_cast<uint64_t>(tile_jobs.size()) * sizeof(Job);
+    hdr.col_items_offset = hdr.items_offset + items.size() * sizeof(WorkItem);  // 128-byte aligned
     for (int v = 0; v < kColVariants; ++v) {
         hdr.col_begin[v] = col_begin[v];
         hdr.col_count[v] = col_count[v];
         hdr.col_chunks[v] = col_chunks[v];
     }
-    out.resize(hdr.col_items_offset + col_items.size() * sizeof(ColItem));
+    out.resize(hdr.col_items_offset + col_items.size() * sizeof(ColJob));
     memcpy(out.data(), &hdr, sizeof(hdr));
-    memcpy(out.data() + sizeof(hdr), table.data(), static_cast<size_t>(n_jobs) * sizeof(Job));
+    memcpy(out.data() + sizeof(hdr), tile_jobs.data(), tile_jobs.size() * sizeof(Job));
     memcpy(out.data() + hdr.items_offset, items.data(), items.size() * sizeof(WorkItem));
-    memcpy(out.data() + hdr.col_items_offset, col_items.data(), col_items.size() * sizeof(ColItem));
+    memcpy(out.data() + hdr.col_items_offset, col_items.data(), col_items.size() * sizeof(ColJob));
     return RCG_OK;
 }
 
@@ -1249,7 +1276,7 @@ bool rcg::noalloc_build_table(const rcg_job *jobs, uint32_t n_jobs, uint8_t *tab
     const uint64_t max_items =
         (capacity - col_capacity - sizeof(BatchHeader) - n_jobs * sizeof(Job)) / sizeof(WorkItem) - n_jobs;
     std::vector<uint8_t> image;
-    if (build_table(&defaults, jobs, n_jobs, *shape, max_items, image, col_capacity / sizeof(ColItem)) != RCG_OK ||
+    if (build_table(&defaults, jobs, n_jobs, *shape, max_items, image, col_capacity / sizeof(ColJob)) != RCG_OK ||
         image.size() > capacity)
         return false;
     memcpy(table, image.data(), image.size());

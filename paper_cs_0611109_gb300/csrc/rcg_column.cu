@@ -21,8 +21,9 @@
 // stage and per tile dominates small stripes.  Here a column is one DRAM round
 // trip per thread.  Single-operation launches stride the columns of one job
 // over the grid; batches give each warp a contiguous range of 32-column
-// chunks of their jobs (persistent grid, one kernel per variant: p = 3, 5, 5
-// with extended strips, 7).
+// chunks of their jobs, each job a self-contained 128-byte record
+// (persistent grid, one kernel per variant: p = 3, 5, 5 with extended
+// strips, 7).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -43,13 +44,23 @@ constexpr int kColMaxN = 9;    // 2p - 1 for p = 5
 __constant__ uint32_t c_col_inv_w[kColPrimes][kColMaxN];
 __constant__ uint32_t c_col_inv_pair[kColPrimes][kColMaxN][kColMaxN];
 
+// A lane's column is 16 bytes (a uint4; the helpers take the vector type
+// as a template parameter).  8-byte columns (half the registers, three CTAs
+// per SM) measured slower on GB300: the p = 5 geometry's 16-operation batch
+// 0.68 against 0.69 of peak, p = 5 jobs in the uneven batches 0.49 against 0.53.
 __device__ __forceinline__ uint4 xr(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }
 
-__device__ __forceinline__ uint4 zero4() { return make_uint4(0, 0, 0, 0); }
+template <class V>
+__device__ __forceinline__ V vzero();
+template <>
+__device__ __forceinline__ uint4 vzero<uint4>() { return make_uint4(0, 0, 0, 0); }
 
-__device__ __forceinline__ uint4 ld_col(const uint8_t *p) {
+template <class V>
+__device__ __forceinline__ V ld_col(const uint8_t *p);
+template <>
+__device__ __forceinline__ uint4 ld_col<uint4>(const uint8_t *p) {
     uint4 v;
     asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
@@ -63,9 +74,9 @@ __device__ __forceinline__ void st_col(uint8_t *p, uint4 v) {
 }
 
 // acc <- x acc + d in the lift (d has p-1 rows; its row p-1 is zero)
-template <int P>
-__device__ __forceinline__ void horner_step(uint4 (&acc)[P], const uint4 (&d)[P - 1]) {
-    const uint4 top = acc[P - 1];
+template <int P, class V>
+__device__ __forceinline__ void horner_step(V (&acc)[P], const V (&d)[P - 1]) {
+    const V top = acc[P - 1];
     acc[P - 1] = acc[P - 2];
 #pragma unroll
     for (int r = P - 2; r >= 1; --r) acc[r] = xr(acc[r - 1], d[r]);
@@ -73,8 +84,8 @@ __device__ __forceinline__ void horner_step(uint4 (&acc)[P], const uint4 (&d)[P 
 }
 
 // out += x^m a in the lift, m in [0, p): a rotation of the rows
-template <int P, int M = 0>
-__device__ __forceinline__ void add_rot(const uint4 (&a)[P], uint32_t m, uint4 (&out)[P]) {
+template <int P, int M = 0, class V>
+__device__ __forceinline__ void add_rot(const V (&a)[P], uint32_t m, V (&out)[P]) {
     if constexpr (M < P) {
         if (m == M) {
 #pragma unroll
@@ -86,10 +97,10 @@ __device__ __forceinline__ void add_rot(const uint4 (&a)[P], uint32_t m, uint4 (
 }
 
 // out = w_k a (weight of data strip k: x^k, or 1 + x^(k-p+1) when k >= p)
-template <int P>
-__device__ __forceinline__ void mul_w(const uint4 (&a)[P], uint32_t k, uint4 (&out)[P]) {
+template <int P, class V>
+__device__ __forceinline__ void mul_w(const V (&a)[P], uint32_t k, V (&out)[P]) {
 #pragma unroll
-    for (int r = 0; r < P; ++r) out[r] = zero4();
+    for (int r = 0; r < P; ++r) out[r] = vzero<V>();
     if (k < static_cast<uint32_t>(P)) {
         add_rot<P>(a, k, out);
     } else {
@@ -100,10 +111,10 @@ __device__ __forceinline__ void mul_w(const uint4 (&a)[P], uint32_t k, uint4 (&o
 }
 
 // out = (sum over the mask's exponents m of x^m) a
-template <int P>
-__device__ __forceinline__ void mul_mask(const uint4 (&a)[P], uint32_t mask, uint4 (&out)[P]) {
+template <int P, class V>
+__device__ __forceinline__ void mul_mask(const V (&a)[P], uint32_t mask, V (&out)[P]) {
 #pragma unroll
-    for (int r = 0; r < P; ++r) out[r] = zero4();
+    for (int r = 0; r < P; ++r) out[r] = vzero<V>();
     while (mask) {
         const uint32_t m = __ffs(mask) - 1;
         mask &= mask - 1;
@@ -111,23 +122,23 @@ __device__ __forceinline__ void mul_mask(const uint4 (&a)[P], uint32_t mask, uin
     }
 }
 
-template <int P>
-__device__ __forceinline__ void store_folded(uint8_t *strip, uint64_t rs, const uint4 (&a)[P]) {
+template <int P, class V>
+__device__ __forceinline__ void store_folded(uint8_t *strip, uint64_t rs, const V (&a)[P]) {
 #pragma unroll
     for (int r = 0; r < P - 1; ++r) st_col(strip + r * rs, xr(a[r], a[P - 1]));
 }
 
-template <int P>
-__device__ __forceinline__ void store_rows(uint8_t *strip, uint64_t rs, const uint4 (&a)[P - 1]) {
+template <int P, class V>
+__device__ __forceinline__ void store_rows(uint8_t *strip, uint64_t rs, const V (&a)[P - 1]) {
 #pragma unroll
     for (int r = 0; r < P - 1; ++r) st_col(strip + r * rs, a[r]);
 }
 
-template <int P>
-__device__ __forceinline__ void lift(const uint4 (&a)[P - 1], uint4 (&out)[P]) {
+template <int P, class V>
+__device__ __forceinline__ void lift(const V (&a)[P - 1], V (&out)[P]) {
 #pragma unroll
     for (int r = 0; r < P - 1; ++r) out[r] = a[r];
-    out[P - 1] = zero4();
+    out[P - 1] = vzero<V>();
 }
 
 template <int P>
@@ -135,27 +146,27 @@ __host__ __device__ constexpr int table_slot() {
     return P == 3 ? 0 : P == 5 ? 1 : 2;
 }
 
-// The small write on column v of stripe s: with D = old d_i + new d_i,
+// The small write on column v (sizeof(V) bytes) of stripe s: with D = old d_i + new d_i,
 // P += D, Q += w_i D (reduced), d_i = new.
-template <int P>
+template <int P, class V>
 __device__ __forceinline__ void column_update(const ColJob &J, uint64_t s, uint32_t v) {
     constexpr int R = P - 1;
-    uint8_t *const col = J.base + s * J.st + v * 16ull;
-    const uint8_t *const nw = J.aux + s * J.ass + v * 16ull;
+    uint8_t *const col = J.base + s * J.st + v * static_cast<uint64_t>(sizeof(V));
+    const uint8_t *const nw = J.aux + s * J.ass + v * static_cast<uint64_t>(sizeof(V));
     const uint32_t N = J.N, a = J.i;
     const uint64_t rs = J.rs, ss = J.ss;
-    uint4 od[R], nv[R], pv[R], qv[R];
+    V od[R], nv[R], pv[R], qv[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        od[r] = ld_col(col + a * ss + r * rs);
-        nv[r] = ld_col(nw + r * J.ars);
-        pv[r] = ld_col(col + N * ss + r * rs);
-        qv[r] = ld_col(col + (N + 1) * ss + r * rs);
+        od[r] = ld_col<V>(col + a * ss + r * rs);
+        nv[r] = ld_col<V>(nw + r * J.ars);
+        pv[r] = ld_col<V>(col + N * ss + r * rs);
+        qv[r] = ld_col<V>(col + (N + 1) * ss + r * rs);
     }
-    uint4 dl[P], t[P];
+    V dl[P], t[P];
 #pragma unroll
     for (int r = 0; r < R; ++r) dl[r] = xr(od[r], nv[r]);
-    dl[R] = zero4();
+    dl[R] = vzero<V>();
     mul_w<P>(dl, a, t);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -165,14 +176,14 @@ __device__ __forceinline__ void column_update(const ColJob &J, uint64_t s, uint3
     }
 }
 
-// One 16-byte column v of stripe s of a job: every operation but the small write.
-template <int P, bool EXT>
+// One column v (sizeof(V) bytes) of stripe s of a job: every operation but the small write.
+template <int P, bool EXT, class V>
 __device__ __forceinline__ void column_unit(const ColJob &J, uint64_t s, uint32_t v, uint32_t *status) {
     constexpr int R = P - 1;
     constexpr int KB = P == 7 ? 2 : 4;  // strips per batch of loads
     constexpr int slot = table_slot<P>();
     if (J.op == OP_UPDATE) {
-        column_update<P>(J, s, v);
+        column_update<P, V>(J, s, v);
         return;
     }
     const uint32_t N = J.N;
@@ -200,7 +211,7 @@ __device__ __forceinline__ void column_unit(const ColJob &J, uint64_t s, uint32_
             return;
         }
     }
-    uint8_t *const col = J.base + s * J.st + v * 16ull;
+    uint8_t *const col = J.base + s * J.st + v * static_cast<uint64_t>(sizeof(V));
     const bool read_p = a != N && b != N, read_q = a != N + 1 && b != N + 1;
     // dP starts as P (when read).  The Horner sum of the data strips starts
     // as x^(-h) Q, h = the number of Horner steps it takes (N, or p when the
@@ -208,31 +219,31 @@ __device__ __forceinline__ void column_unit(const ColJob &J, uint64_t s, uint32_
     // ends as Q + sum of x^k d_k.  x^(-h) is applied to the load addresses:
     // lifted row t of x^(-h) Q is row t + h (mod p) of Q, the imaginary row 0.
     // Every load of a column is issued before any of them is used.
-    uint4 dp[R], hl[P];
+    V dp[R], hl[P];
 #pragma unroll
-    for (int r = 0; r < R; ++r) dp[r] = read_p ? ld_col(col + N * ss + r * rs) : zero4();
+    for (int r = 0; r < R; ++r) dp[r] = read_p ? ld_col<V>(col + N * ss + r * rs) : vzero<V>();
     const uint32_t h = (EXT ? static_cast<uint32_t>(P) : N) % static_cast<uint32_t>(P);
 #pragma unroll
     for (int t = 0; t < P; ++t) {
         uint32_t row = static_cast<uint32_t>(t) + h;
         if (row >= static_cast<uint32_t>(P)) row -= P;
-        hl[t] = (read_q && row < static_cast<uint32_t>(R)) ? ld_col(col + (N + 1) * ss + row * rs) : zero4();
+        hl[t] = (read_q && row < static_cast<uint32_t>(R)) ? ld_col<V>(col + (N + 1) * ss + row * rs) : vzero<V>();
     }
     // Horner from the last data strip down (erased strips count as zero)
-    uint4 hx[P], ex[R];
+    V hx[P], ex[R];
 #pragma unroll
-    for (int r = 0; r < P; ++r) hx[r] = zero4();
+    for (int r = 0; r < P; ++r) hx[r] = vzero<V>();
 #pragma unroll
-    for (int r = 0; r < R; ++r) ex[r] = zero4();
+    for (int r = 0; r < R; ++r) ex[r] = vzero<V>();
     for (int k0 = static_cast<int>(N); k0 > 0; k0 -= KB) {
-        uint4 d[KB][R];  // a batch of strips, every row, loads in flight together
+        V d[KB][R];  // a batch of strips, every row, loads in flight together
 #pragma unroll
         for (int q = 0; q < KB; ++q) {
             const int k = k0 - 1 - q;
             const bool live = k >= 0 && static_cast<uint32_t>(k) != a && static_cast<uint32_t>(k) != b;
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                d[q][r] = live ? ld_col(col + static_cast<uint64_t>(k) * ss + r * rs) : zero4();
+                d[q][r] = live ? ld_col<V>(col + static_cast<uint64_t>(k) * ss + r * rs) : vzero<V>();
         }
 #pragma unroll
         for (int q = 0; q < KB; ++q) {
@@ -250,11 +261,11 @@ __device__ __forceinline__ void column_unit(const ColJob &J, uint64_t s, uint32_
         }
     }
     // dq (lifted) = Q + sum of w_k d_k over the surviving data strips
-    uint4 dq[P];
+    V dq[P];
 #pragma unroll
     for (int r = 0; r < P; ++r) dq[r] = hl[r];
     if (EXT) {
-        const uint4 top = hx[P - 1];  // x hx: rotate by one
+        const V top = hx[P - 1];  // x hx: rotate by one
 #pragma unroll
         for (int r = P - 1; r >= 1; --r) dq[r] = xr(dq[r], hx[r - 1]);
         dq[0] = xr(dq[0], top);
@@ -263,14 +274,14 @@ __device__ __forceinline__ void column_unit(const ColJob &J, uint64_t s, uint32_
     }
 
     if (deg) {  // the strip alone, to the caller's buffer
-        uint8_t *const out = J.aux + s * J.ass + v * 16ull;
+        uint8_t *const out = J.aux + s * J.ass + v * static_cast<uint64_t>(sizeof(V));
         if (J.j == N + 1)
             store_folded<P>(out, J.ars, dq);
         else
             store_rows<P>(out, J.ars, dp);
         return;
     }
-    uint4 lp[P], t[P], o[P];
+    V lp[P], t[P], o[P];
     if (a == N) {                     // P and Q (encode)
         store_rows<P>(col + N * ss, rs, dp);
         store_folded<P>(col + (N + 1) * ss, rs, dq);
@@ -285,7 +296,7 @@ __device__ __forceinline__ void column_unit(const ColJob &J, uint64_t s, uint32_
         mul_mask<P>(dq, c_col_inv_w[slot][a], o);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const uint4 da = xr(o[r], o[P - 1]);
+            const V da = xr(o[r], o[P - 1]);
             st_col(col + a * ss + r * rs, da);
             st_col(col + N * ss + r * rs, xr(dp[r], da));
         }
@@ -297,15 +308,23 @@ __device__ __forceinline__ void column_unit(const ColJob &J, uint64_t s, uint32_
         mul_mask<P>(t, c_col_inv_pair[slot][a][b], o);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const uint4 db = xr(o[r], o[P - 1]);
+            const V db = xr(o[r], o[P - 1]);
             st_col(col + b * ss + r * rs, db);
             st_col(col + a * ss + r * rs, xr(db, dp[r]));
         }
     }
 }
 
+template <int P, bool EXT>
+__host__ __device__ constexpr int variant_of() {
+    return P == 3 ? 0 : P == 5 ? (EXT ? 2 : 1) : 3;
+}
+
+template <int P, bool EXT>
+using ColVec = uint4;
+
 // Registers: two 256-thread CTAs per SM where the accumulators fit 128
-// registers without spilling (p = 3, 5), one otherwise.
+// registers (p = 3, 5), one otherwise.
 template <int P, bool EXT>
 __host__ __device__ constexpr int col_ctas_per_sm() {
     return (P == 7 || EXT) ? 1 : 2;
@@ -315,34 +334,34 @@ __host__ __device__ constexpr int col_ctas_per_sm() {
 template <int P, bool EXT>
 __global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
     rcg_column_kernel(const ColJob J, uint64_t n_stripes, uint32_t *status) {
-    const uint64_t total = n_stripes * J.vps;
+    using V = ColVec<P, EXT>;
+    const uint32_t cols = J.vps * static_cast<uint32_t>(16 / sizeof(V));  // lane columns per row
+    const uint64_t total = n_stripes * cols;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     for (uint64_t u = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; u < total; u += stride) {
-        const uint64_t s = u / J.vps;
-        const uint32_t v = static_cast<uint32_t>(u - s * J.vps);
-        column_unit<P, EXT>(J, s, v, status);
+        const uint64_t s = u / cols;
+        const uint32_t v = static_cast<uint32_t>(u - s * cols);
+        column_unit<P, EXT, V>(J, s, v, status);
     }
 }
 
-template <int P, bool EXT>
-__host__ __device__ constexpr int variant_of() {
-    return P == 3 ? 0 : P == 5 ? (EXT ? 2 : 1) : 3;
-}
-
 // A batch's columns of one variant: warp w of W takes the contiguous range
-// [T w / W, T (w+1) / W) of the variant's T chunks (one column per lane), so
+// [T w / W, T (w+1) / W) of the variant's T chunks (one lane column per lane), so
 // every warp has the same work give or take one chunk.  The job of the first
-// chunk is found by binary search over the variant's ColItems; the job's
-// fields go to a per-warp copy in shared memory.
+// chunk is found by binary search over the variant's ColJob records.  A job's
+// 128-byte record is read by the warp in one coalesced load (a word per lane)
+// into a per-warp copy in shared memory (kept out of registers, which the
+// column needs), and the next record is prefetched into L1 meanwhile, so a
+// switch between small jobs costs no dependent global round trips.
 template <int P, bool EXT>
 __global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
     rcg_column_batch(const uint8_t *__restrict__ table, uint32_t *status) {
+    using V = ColVec<P, EXT>;
     const auto *bh = reinterpret_cast<const BatchHeader *>(table);
     constexpr int g = variant_of<P, EXT>();
     const uint32_t n_runs = bh->col_count[g];
     const uint64_t total = bh->col_chunks[g];
-    const auto *runs = reinterpret_cast<const ColItem *>(table + bh->col_items_offset) + bh->col_begin[g];
-    const auto *jobs = reinterpret_cast<const Job *>(table + sizeof(BatchHeader));
+    const auto *runs = reinterpret_cast<const ColJob *>(table + bh->col_items_offset) + bh->col_begin[g];
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
     const uint64_t w = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -354,44 +373,29 @@ __global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
         const uint32_t mid = (lo + hi) >> 1;
         if (runs[mid].chunk0 <= c0) lo = mid; else hi = mid;
     }
-    // the job's fields and the warp's position, one copy per warp in shared
-    // memory (re-read by the loop; kept out of registers, which the column needs)
     struct WarpState {
         ColJob J;
-        uint64_t first, next, units, c1;
+        uint64_t next, units, c1;
         uint32_t r, valid;
     };
     __shared__ WarpState ws_all[8];
     WarpState &ws = ws_all[threadIdx.x >> 5];
     auto load_job = [&](uint32_t r) {
+        const uint32_t word = reinterpret_cast<const uint32_t *>(runs + r)[lane];
+        if (lane == 0 && r + 1 < n_runs)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<uint64_t>(runs + r + 1)));
+        __syncwarp();
+        reinterpret_cast<uint32_t *>(&ws.J)[lane] = word;
         __syncwarp();
         if (lane == 0) {
-            const ColItem ci = runs[r];
+            const ColJob &J = ws.J;
             ws.r = r;
-            ws.first = ci.chunk0;
             ws.next = r + 1 < n_runs ? runs[r + 1].chunk0 : total;
-            bool valid = ci.job < bh->n_jobs;
-            if (valid) {
-                const Job &jb = jobs[ci.job];
-                ColJob &J = ws.J;
-                J.base = jb.base;
-                J.pairs = jb.pairs;
-                J.aux = jb.aux;
-                J.rs = jb.row_stride;
-                J.ss = jb.strip_stride;
-                J.st = jb.stripe_stride;
-                J.ars = jb.aux_row_stride;
-                J.ass = jb.aux_stripe_stride;
-                J.vps = jb.C >> 4;
-                J.N = jb.n;
-                J.i = jb.i;
-                J.j = jb.j;
-                J.op = jb.op;
-                ws.units = static_cast<uint64_t>(jb.n_stripes) * (jb.C >> 4);
-                // device-side guard: the job is this variant's and its chunks cover it
-                valid = jb.p == P && (jb.n > static_cast<uint32_t>(P)) == EXT && jb.n >= 1 && ws.units > 0 &&
-                        ws.next - ws.first == (ws.units + kColChunk - 1) / kColChunk;
-            }
+            ws.units = J.n_stripes * J.vps * (16 / sizeof(V));  // lane columns of the job
+            // device-side guard: the job is this variant's and its chunks cover it
+            const bool valid = J.p == static_cast<uint32_t>(P) && (J.N > static_cast<uint32_t>(P)) == EXT &&
+                               J.N >= 1 && ws.units > 0 && J.op <= OP_UPDATE &&
+                               ws.next - J.chunk0 == (ws.units + kColChunk - 1) / kColChunk;
             ws.valid = valid;
             if (!valid && status) atomicOr(status, RCG_DEV_BADJOB);
         }
@@ -412,11 +416,11 @@ __global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
             load_job(r);
         }
         if (!ws.valid) continue;
-        const uint64_t u = (c - ws.first) * kColChunk + lane;
+        const uint64_t u = (c - ws.J.chunk0) * kColChunk + lane;
         if (u >= ws.units) continue;
-        const uint32_t vps = ws.J.vps;
-        const uint64_t s = u / vps;
-        column_unit<P, EXT>(ws.J, s, static_cast<uint32_t>(u - s * vps), status);
+        const uint32_t cols = ws.J.vps * static_cast<uint32_t>(16 / sizeof(V));
+        const uint64_t s = u / cols;
+        column_unit<P, EXT, V>(ws.J, s, static_cast<uint32_t>(u - s * cols), status);
     }
 }
 

@@ -139,7 +139,7 @@ struct alignas(128) BatchHeader {
     uint64_t items_offset;  // bytes from the header to the first WorkItem
     uint32_t dynamic;       // 0: items dealt round-robin; 1: taken from the global counter
     uint32_t fixed_slots;   // 1: n_slots equal slots of slot_bytes (as single launches); 0: byte ring
-    // jobs of p <= 7 run in the column kernel: ColItems (one per job) from
+    // jobs of p <= 7 run in the column kernel: one ColJob record per job from
     // col_items_offset, grouped by kernel variant (p = 3; p = 5; p = 5 with
     // extended strips; p = 7); col_chunks: the variant's 32-column chunks
     uint64_t col_items_offset;
@@ -150,16 +150,6 @@ struct alignas(128) BatchHeader {
 };
 static_assert(sizeof(BatchHeader) == 128, "the job table after the header stays 128-byte aligned");
 
-// A job of the column kernel in a batch: its columns (unit = stripe * (C/16)
-// + 16-byte column) are cut into chunks of 32, one column per lane; the
-// variant's chunks are numbered across its jobs, this job's from chunk0.
-// Warps take contiguous ranges of chunks.
-struct ColItem {
-    uint32_t job;
-    uint32_t pad;
-    uint64_t chunk0;
-};
-static_assert(sizeof(ColItem) == 16, "column items are 16 bytes");
 constexpr uint32_t kColChunk = 32;  // columns per chunk: one per lane
 constexpr int kColVariants = 4;
 
@@ -221,22 +211,30 @@ cudaError_t launch_h257(uint8_t *base, uint32_t N, uint64_t strip_bytes, uint64_
                         uint32_t *status, int sm_count, cudaStream_t stream);
 
 // Column kernel (rcg_column.cu): bit-sliced stripes of p <= 7 without shared
-// memory.  One launch over n_stripes stripes of one job: op OP_ENCODE,
-// OP_RECOVER (pair i < j, or per-stripe pairs), OP_DEGRADED (strip j into aux)
-// or OP_UPDATE (data strip i replaced by aux).
-struct ColJob {
+// memory.  One job: op OP_ENCODE, OP_RECOVER (pair i < j, or per-stripe
+// pairs), OP_DEGRADED (strip j into aux) or OP_UPDATE (data strip i replaced
+// by aux).  The record is the kernel parameter of a single launch and, in a
+// batch table, the self-contained description of one job: its columns
+// (unit = stripe * vps + 16-byte column) are cut into chunks of 32, one column
+// per lane, numbered across the variant's jobs from chunk0; a warp loads the
+// 128 bytes with one coalesced read.
+struct alignas(128) ColJob {
     uint8_t *base;         // stripe 0 of the job
     const uint8_t *pairs;  // recovery: per-stripe (i, j) bytes, or nullptr
     uint8_t *aux;          // degraded read: output; small write: the new strips
     uint64_t rs, ss, st;   // row, strip and stripe strides
     uint64_t ars, ass;     // aux row and stripe strides
+    uint64_t chunk0;       // batches: the job's first chunk in its variant's numbering
+    uint64_t n_stripes;
     uint32_t vps;          // 16-byte columns per row, C / 16
-    uint32_t N, i, j, op;
+    uint32_t N, i, j, op, p;
+    uint32_t pad[6];
 };
+static_assert(sizeof(ColJob) == 128, "a column job is one 128-byte record");
 cudaError_t upload_column_tables();
 cudaError_t launch_column(const ColJob &job, uint32_t p, uint64_t n_stripes, uint32_t *status, int sm_count,
                           cudaStream_t stream);
-// Batches: the column kernel of one variant over the table's ColItems of that
+// Batches: the column kernel of one variant over the table's ColJob records of that
 // variant (persistent grid); the variant's kernel function for graph nodes.
 cudaError_t launch_column_batch(int variant, const uint8_t *table_dev, uint32_t *status, int sm_count,
                                 cudaStream_t stream);

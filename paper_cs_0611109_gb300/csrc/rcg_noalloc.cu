@@ -29,8 +29,8 @@ namespace {
 using namespace rcg;
 
 // header, up to RCG_NOALLOC_MAX_JOBS jobs, 2 x RCG_NOALLOC_MAX_JOBS work items
-// of the tile engine and one column-kernel item per job (~134 KB)
-constexpr uint32_t kColTableBytes = RCG_NOALLOC_MAX_JOBS * sizeof(ColItem);
+// of the tile engine and one 128-byte column-kernel record per job (~162 KB)
+constexpr uint32_t kColTableBytes = RCG_NOALLOC_MAX_JOBS * sizeof(ColJob);
 constexpr uint32_t kTableBytes = sizeof(BatchHeader) + RCG_NOALLOC_MAX_JOBS * sizeof(Job) +
                                  2 * RCG_NOALLOC_MAX_JOBS * sizeof(WorkItem) + kColTableBytes;
 constexpr uint32_t kCounterOff = (kTableBytes + 255) / 256 * 256;
