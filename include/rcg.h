@@ -472,7 +472,7 @@ rcg_status rcg_serve_destroy(rcg_server *s);
  * Runs jobs exactly as rcg_batch_submit does (one persistent launch, same
  * kernel, same results), but needs no rcg_ctx and allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine.  Its scratch (the
- * descriptor table, the tile counter and a fallback status word, about 134 KB)
+ * descriptor table, the tile counter and a fallback status word, about 165 KB)
  * is one file-scope device array that every GPU loading librcg holds until
  * the process exits.  The caller passes the inputs and outputs as in
  * rcg_job, plus optionally status_dev: a caller-owned device word that

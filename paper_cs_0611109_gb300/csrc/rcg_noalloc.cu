@@ -29,7 +29,7 @@ namespace {
 using namespace rcg;
 
 // header, up to RCG_NOALLOC_MAX_JOBS jobs, 2 x RCG_NOALLOC_MAX_JOBS work items
-// of the tile engine and one 128-byte column-kernel record per job (~162 KB)
+// of the tile engine and one 128-byte column-kernel record per job (~165 KB)
 constexpr uint32_t kColTableBytes = RCG_NOALLOC_MAX_JOBS * sizeof(ColJob);
 constexpr uint32_t kTableBytes = sizeof(BatchHeader) + RCG_NOALLOC_MAX_JOBS * sizeof(Job) +
                                  2 * RCG_NOALLOC_MAX_JOBS * sizeof(WorkItem) + kColTableBytes;
