@@ -139,14 +139,14 @@ rcg_status rcg_set_dd_solve(rcg_ctx *ctx, int solve);
 #define RCG_SHAPE_PAIR 2
 rcg_status rcg_set_engine_shape(rcg_ctx *ctx, int shape);
 
-/* Kernel for single-operation encode and recovery calls (rcg_encode,
- * rcg_recover, rcg_recover_many and the host-memory calls built on them) of
- * small primes.  RCG_COLUMN_AUTO (default): for p <= 7 a column kernel -- a
- * thread owns a 16-byte column of all p-1 rows of a stripe in registers, Q by
- * Horner's rule, no shared memory -- whose launches cost one DRAM round trip,
- * where the tile engine's stages would be tiny (p = 5, 1 KiB rows: 4 KB).
- * RCG_COLUMN_OFF: always the tile engine.  Results are identical; batches,
- * the small write and the degraded read always use the tile engine. */
+/* Kernel for stripes of small primes.  RCG_COLUMN_AUTO (default): every
+ * operation on p <= 7 -- single calls (encode, recover, recover_many, update,
+ * degraded read, the host-memory calls) and the p <= 7 jobs of batches and of
+ * the server -- runs in a column kernel: a thread owns a 16-byte column of
+ * all p-1 rows of a stripe in registers, Q by Horner's rule, no shared memory,
+ * one DRAM round trip per column, where the tile engine's stages would be
+ * tiny (p = 5, 1 KiB rows: 4 KB).  RCG_COLUMN_OFF: always the tile engine.
+ * Results are identical. */
 #define RCG_COLUMN_AUTO 0
 #define RCG_COLUMN_OFF 1
 rcg_status rcg_set_column_kernel(rcg_ctx *ctx, int mode);
