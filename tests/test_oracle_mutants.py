@@ -36,7 +36,8 @@ MUTANTS = {
                             "return oracle_encode(p, N, C, buf, 1,"),
     "h_bits_reversed": ("a |= (u64)((strip[t >> 3] >> (t & 7)) & 1u) << r;",
                         "a |= (u64)((strip[t >> 3] >> (t & 7)) & 1u) << (L->rows - 1 - r);"),
-    "h_scatter_toggles": ("strip[t >> 3] |= m;", "strip[t >> 3] ^= m;"),
+    "h_scatter_toggles": ("if ((a >> r) & 1u)\n                strip[t >> 3] |= m;",
+                          "if ((a >> r) & 1u)\n                strip[t >> 3] ^= m;"),
     "h_element_stride": ("const uint8_t *strip = L->base + s * L->stripe_stride + (u64)k * L->strip_stride;\n"
                          "        for (unsigned r = 0; r < L->rows; r++) {\n            u64 t = b * L->rows + r;",
                          "const uint8_t *strip = L->base + s * L->stripe_stride + (u64)k * L->strip_stride;\n"
