@@ -30,14 +30,14 @@
 #include <atomic>
 #include <condition_variable>
 #include <deque>
-#include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "../../include/rcg.h"
+#include "rcg_admission.h"
 #include "rcg_internal.h"
 
 namespace {
@@ -48,10 +48,7 @@ uint64_t mono_ns() {
     return static_cast<uint64_t>(ts.tv_sec) * 1000000000ull + ts.tv_nsec;
 }
 
-// A device byte range [lo, hi) a request reads or writes.
-struct Extent {
-    uintptr_t lo = 0, hi = 0;
-};
+using rcg::Extent;
 
 struct Request {
     rcg_serve_request req;
@@ -108,15 +105,10 @@ uint32_t job_extents(const rcg_job &j, Extent *out) {
     out[k].hi = out[k].lo + (n - 1) * s.st + (L.n_data + 1ull) * s.ss + (L.p - 2ull) * s.rs + L.row_bytes;
     ++k;
     if (uses_aux(j) && j.aux) {
-        Extent a;
-        a.lo = reinterpret_cast<uintptr_t>(j.aux);
-        a.hi = a.lo + (n - 1) * s.ass + (L.p - 2ull) * s.ars + L.row_bytes;
-        if (a.lo < out[0].hi && out[0].lo < a.hi) {
-            out[0].lo = std::min(out[0].lo, a.lo);
-            out[0].hi = std::max(out[0].hi, a.hi);
-        } else {
-            out[k++] = a;
-        }
+        // an aux extent overlapping the stripes is merged by Admission::add
+        out[k].lo = reinterpret_cast<uintptr_t>(j.aux);
+        out[k].hi = out[k].lo + (n - 1) * s.ass + (L.p - 2ull) * s.ars + L.row_bytes;
+        ++k;
     }
     return k;
 }
@@ -131,27 +123,15 @@ struct rcg_server {
     std::mutex mu;
     std::condition_variable cv;
     std::vector<Request> reqs;          // by id
-    std::deque<uint64_t> pending;       // submitted, not yet examined (arrival order of submission)
-    std::deque<uint64_t> blocked;       // arrived and examined, waiting on an overlapping request
-    std::map<uintptr_t, uintptr_t> waiting;  // union of the blocked requests' extents, lo -> hi (merged)
-    // Exact extents, keyed by their first byte: the common conflict (requests
-    // on the same stripe) is one hash lookup; an extent identical to one
-    // already here needs no ordered-map work
-    std::unordered_map<uintptr_t, uintptr_t> busy_exact;
-    std::unordered_map<uintptr_t, uintptr_t> waiting_exact;
+    std::unique_ptr<rcg::Admission> adm;  // which requests may start (rcg_admission.h)
     std::deque<uint64_t> admitted;      // admitted, not launched
     std::deque<Launch> inflight;        // launched, not retired
-    std::map<uintptr_t, uintptr_t> busy;  // device byte ranges of admitted requests, lo -> hi (disjoint)
     std::vector<cudaEvent_t> free_events;
-    uint64_t budget_used = 0;
-    uint32_t inflight_jobs = 0;
     uint64_t start_ns = 0;
     uint64_t completed = 0;
     uint32_t launches = 0;              // launch numbers handed out (batches, or single jobs)
     uint64_t kernel_launches = 0;
-    uint64_t conflict_waits = 0;
     uint32_t max_inflight_launches = 0;
-    uint32_t max_inflight_jobs = 0;
     std::atomic<bool> stop{false};
     std::atomic<bool> running{false};
     rcg_status error = RCG_OK;
@@ -168,25 +148,6 @@ cudaEvent_t get_event(rcg_server *s) {
     cudaEvent_t e = nullptr;
     cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
     return e;
-}
-
-// Does [e.lo, e.hi) overlap a range of the disjoint, sorted map?
-bool overlaps(const std::map<uintptr_t, uintptr_t> &m, const Extent &e) {
-    auto it = m.upper_bound(e.lo);
-    if (it != m.begin() && std::prev(it)->second > e.lo) return true;
-    return it != m.end() && it->first < e.hi;
-}
-
-// Add [e.lo, e.hi) to a disjoint, sorted map, merging the ranges it touches.
-void insert_merged(std::map<uintptr_t, uintptr_t> &m, Extent e) {
-    auto it = m.upper_bound(e.lo);
-    if (it != m.begin() && std::prev(it)->second >= e.lo) --it;
-    while (it != m.end() && it->first <= e.hi) {
-        e.lo = std::min(e.lo, it->first);
-        e.hi = std::max(e.hi, it->second);
-        it = m.erase(it);
-    }
-    m[e.lo] = e.hi;
 }
 
 rcg_status launch_single_job(rcg_ctx *ctx, const rcg_job &j, cudaStream_t s) {
@@ -217,7 +178,6 @@ bool tick(rcg_server *s) {
     const uint64_t now = mono_ns() - s->start_ns;
     std::unique_lock<std::mutex> lock(s->mu);
     // 1. retire, in launch order (one stream: launches finish in order)
-    bool freed = false;
     while (!s->inflight.empty()) {
         Launch &L = s->inflight.front();
         const cudaError_t q = cudaEventQuery(L.done);
@@ -226,74 +186,22 @@ bool tick(rcg_server *s) {
             Request &r = s->reqs[id];
             r.complete_ns = now;  // the tick's clock: frees precede this tick's admissions
             if (q != cudaSuccess) r.status = RCG_ECUDA;
-            s->budget_used -= r.footprint;
-            --s->inflight_jobs;
-            for (uint32_t k = 0; k < r.n_ext; ++k) {
-                s->busy.erase(r.ext[k].lo);
-                s->busy_exact.erase(r.ext[k].lo);
-            }
+            s->adm->retire(id);
         }
         s->completed += L.ids.size();
         s->free_events.push_back(L.done);
         s->inflight.pop_front();
-        freed = true;
         did = true;
         s->cv.notify_all();
     }
-    // Blocked requests can only move once something has retired: then they
-    // are examined again, ahead of the later arrivals, and the union of
-    // waiting extents is rebuilt as they are.
-    if (freed && !s->blocked.empty()) {
-        s->pending.insert(s->pending.begin(), s->blocked.begin(), s->blocked.end());
-        s->blocked.clear();
-        s->waiting.clear();
-        s->waiting_exact.clear();
-    }
     // 2. admit arrived requests in order while slots and HBM allow; a request
-    //    whose bytes overlap an admitted one's, or a blocked earlier one's,
-    //    is blocked too (the ones behind it that do not overlap go ahead)
-    while (!s->pending.empty()) {
-        Request &r = s->reqs[s->pending.front()];
-        if (r.req.arrival_ns > now) break;
-        if (s->inflight_jobs >= s->cfg.max_inflight_jobs) break;
-        if (s->budget_used + r.footprint > s->cfg.hbm_budget_bytes) break;
-        bool conflict = false;
-        for (uint32_t k = 0; k < r.n_ext && !conflict; ++k) {
-            const Extent &e = r.ext[k];
-            // two extents with the same first byte overlap
-            conflict = s->busy_exact.count(e.lo) || s->waiting_exact.count(e.lo) || overlaps(s->busy, e) ||
-                       overlaps(s->waiting, e);
-        }
-        if (conflict) {
-            for (uint32_t k = 0; k < r.n_ext; ++k) {
-                const Extent &e = r.ext[k];
-                // the union already covers an extent identical to a busy or waiting one
-                auto b = s->busy_exact.find(e.lo);
-                auto w = s->waiting_exact.find(e.lo);
-                const bool known = (b != s->busy_exact.end() && b->second == e.hi) ||
-                                   (w != s->waiting_exact.end() && w->second == e.hi);
-                if (!known) {
-                    insert_merged(s->waiting, e);
-                    if (w == s->waiting_exact.end() || w->second < e.hi) s->waiting_exact[e.lo] = e.hi;
-                }
-            }
-            ++s->conflict_waits;
-            s->blocked.push_back(s->pending.front());
-            s->pending.pop_front();
-            continue;
-        }
-        for (uint32_t k = 0; k < r.n_ext; ++k) {
-            s->busy[r.ext[k].lo] = r.ext[k].hi;
-            s->busy_exact[r.ext[k].lo] = r.ext[k].hi;
-        }
-        s->budget_used += r.footprint;
-        ++s->inflight_jobs;
-        s->max_inflight_jobs = std::max(s->max_inflight_jobs, s->inflight_jobs);
-        r.admit_ns = now;
-        s->admitted.push_back(s->pending.front());
-        s->pending.pop_front();
+    //    whose bytes overlap an admitted one's, or an earlier waiting one's,
+    //    waits (the ones behind it that do not overlap go ahead)
+    if (s->adm->admit(now, [&](uint64_t id) {
+            s->reqs[id].admit_ns = now;
+            s->admitted.push_back(id);
+        }))
         did = true;
-    }
     // 3a. per-job mode: every admitted request goes out at once, on its own
     if (s->cfg.per_job_launches) {
         while (!s->admitted.empty()) {
@@ -386,6 +294,12 @@ rcg_status rcg_serve_create(rcg_ctx *ctx, const rcg_serve_config *cfg, rcg_serve
     if (s->cfg.max_batch_jobs == 0) s->cfg.max_batch_jobs = 2048;
     // room for two full batches in flight, so the next one is prepared while one runs
     if (s->cfg.max_inflight_jobs == 0) s->cfg.max_inflight_jobs = 4 * s->cfg.max_batch_jobs;
+    s->adm.reset(new (std::nothrow) rcg::Admission(s->cfg.hbm_budget_bytes, s->cfg.max_inflight_jobs));
+    if (!s->adm) {
+        if (prev >= 0) cudaSetDevice(prev);
+        delete s;
+        return RCG_ENOMEM;
+    }
     const cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess) {
@@ -415,7 +329,12 @@ rcg_status rcg_serve_submit(rcg_server *s, const rcg_serve_request *reqs, uint32
     for (uint32_t k = 0; k < n; ++k) {
         batch[k].id = first + k;
         s->reqs.push_back(batch[k]);
-        s->pending.push_back(first + k);
+        rcg::Admission::Item it;
+        it.arrival_ns = batch[k].req.arrival_ns;
+        it.footprint = batch[k].footprint;
+        it.n_ext = batch[k].n_ext;
+        for (uint32_t e = 0; e < batch[k].n_ext; ++e) it.ext[e] = batch[k].ext[e];
+        s->adm->add(it);  // the same id
     }
     if (first_id) *first_id = first;
     return RCG_OK;
@@ -464,9 +383,9 @@ rcg_status rcg_serve_get_stats(rcg_server *s, rcg_serve_stats *out) {
     std::lock_guard<std::mutex> lock(s->mu);
     out->kernel_launches = s->kernel_launches;
     out->completed = s->completed;
-    out->conflict_waits = s->conflict_waits;
+    out->conflict_waits = s->adm->conflict_waits();
     out->max_inflight_launches = s->max_inflight_launches;
-    out->max_inflight_jobs = s->max_inflight_jobs;
+    out->max_inflight_jobs = s->adm->max_inflight_seen();
     return RCG_OK;
 }
 
