@@ -151,6 +151,18 @@ rcg_status rcg_set_engine_shape(rcg_ctx *ctx, int shape);
 #define RCG_COLUMN_OFF 1
 rcg_status rcg_set_column_kernel(rcg_ctx *ctx, int mode);
 
+/* Where a batch's descriptor table travels (rcg_batch_launch, rcg_batch_submit
+ * and the server's batches).  RCG_TABLES_AUTO (default): a table of at most
+ * 31 744 bytes (about 240 column jobs, or a few dozen engine jobs with their
+ * work items) is passed in the kernels' own parameter blocks -- no
+ * host-to-device copy and no graph before the kernels start, the engine's
+ * work items dealt round-robin -- and a larger one is copied to a device
+ * buffer by a replayed CUDA graph.  RCG_TABLES_DEVICE: always the device
+ * buffer and the graph.  Results are identical. */
+#define RCG_TABLES_AUTO 0
+#define RCG_TABLES_DEVICE 1
+rcg_status rcg_set_batch_tables(rcg_ctx *ctx, int mode);
+
 /* Synchronise the device and read, then clear, the device status word.
  * Returns RCG_EDEVICE when any bit was set (then *code holds the bits). */
 rcg_status rcg_last_device_status(rcg_ctx *ctx, uint32_t *code);
@@ -486,6 +498,9 @@ rcg_status rcg_serve_destroy(rcg_server *s);
  *    scratch array's device address, uploads the inverse tables, sets the
  *    kernel's shared-memory limit); make that first call before any stream
  *    capture;
+ *  - a descriptor table of at most 31 744 bytes (as for rcg_batch_submit with
+ *    RCG_TABLES_AUTO) travels in the kernels' parameter blocks and leaves the
+ *    scratch untouched; a larger one is copied into the scratch;
  *  - every call reuses the same scratch, which keeps the previous call's
  *    contents (the tile counter is cleared on the stream before each launch):
  *    calls whose work overlaps on the GPU race on it, so keep them ordered

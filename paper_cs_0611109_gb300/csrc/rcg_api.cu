@@ -71,6 +71,11 @@ struct rcg_ctx {
     int shape = RCG_SHAPE_AUTO;
     int batch_schedule = RCG_SCHED_DYNAMIC;
     int column = RCG_COLUMN_AUTO;
+    int batch_tables = RCG_TABLES_AUTO;
+    // small-table batches with column and engine work: the column kernels on a
+    // side stream beside the engine (created on first use)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     // batch tuning (rcg_batch_autotune / rcg_set_batch_tuning)
     int tune_shape = RCG_SHAPE_AUTO;  // engine shape of batches; AUTO = the size rule
     uint64_t tune_item_bytes = 0;     // work-item size; 0 = the rule in build_table
@@ -195,7 +200,6 @@ Job base_job(const rcg_ctx *ctx, const rcg_layout *L, const Geo &g, uint64_t fir
 rcg_status launch_single(rcg_ctx *ctx, const Job &J, const Plan &pl, cudaStream_t stream) {
     LaunchParams prm;
     memset(&prm, 0, sizeof(prm));
-    prm.jobs = nullptr;
     prm.job0 = J;
     prm.n_jobs = 1;
     prm.slot_bytes = pl.slot_bytes;
@@ -417,6 +421,10 @@ rcg_status rcg_destroy(rcg_ctx *ctx) {
         free_slot(s);
     }
     host_staging_destroy(ctx->host);
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->status) cudaFree(ctx->status);
     delete ctx;
     return RCG_OK;
@@ -444,6 +452,12 @@ rcg_status rcg_set_engine_shape(rcg_ctx *ctx, int shape) {
 rcg_status rcg_set_column_kernel(rcg_ctx *ctx, int mode) {
     if (!ctx || (mode != RCG_COLUMN_AUTO && mode != RCG_COLUMN_OFF)) return RCG_EINVAL;
     ctx->column = mode;
+    return RCG_OK;
+}
+
+rcg_status rcg_set_batch_tables(rcg_ctx *ctx, int mode) {
+    if (!ctx || (mode != RCG_TABLES_AUTO && mode != RCG_TABLES_DEVICE)) return RCG_EINVAL;
+    ctx->batch_tables = mode;
     return RCG_OK;
 }
 
@@ -1043,41 +1057,62 @@ rcg_status rcg_batch_launch(rcg_ctx *ctx, const rcg_batch *b, void *stream, uint
         if (st) return st;
     }
     const size_t bytes = b->image.size();
-    rcg_status st = prepare_slot(ctx, s, bytes, b->shape);
-    if (st) return st;
-    memcpy(s.host, b->image.data(), bytes);
+    const auto &hdr = *reinterpret_cast<const BatchHeader *>(b->image.data());
+    cudaStream_t st_user = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    const char *where = "graph copy-size update";
-    if (bytes != s.bytes) {
-        // copy only the live part of the table: update the captured node
-        cudaMemcpy3DParms mp;
-        e = cudaGraphMemcpyNodeGetParams(s.copy_node, &mp);
-        if (e == cudaSuccess) {
-            mp.extent.width = bytes;
-            mp.srcPtr.pitch = bytes;
-            mp.srcPtr.xsize = bytes;
-            mp.dstPtr.pitch = bytes;
-            mp.dstPtr.xsize = bytes;
-            e = cudaGraphExecMemcpyNodeSetParams(s.exec, s.copy_node, &mp);
+    const char *where = "batch event";
+    if (ctx->batch_tables == RCG_TABLES_AUTO && bytes <= kParamTableLarge) {
+        // a small table travels in the kernels' parameter blocks: no table
+        // copy, no graph, no counter reset before the kernels
+        if (!s.done) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+        const int mask = work_mask(hdr);
+        if (e == cudaSuccess && (mask & 15) && (mask & 16) && !ctx->side) {
+            where = "side stream";
+            e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming);
         }
         if (e == cudaSuccess) {
-            s.bytes = bytes;
-        } else {
-            // keep copying the whole table (the kernel reads n_jobs entries)
-            cudaGetLastError();
-            e = cudaSuccess;
+            e = launch_batch_all_param(b->image.data(), bytes, ctx->status, ctx->timeout_ns, b->shape,
+                                       ctx->sm_count, st_user, ctx->side, ctx->fork, ctx->join);
+            where = "batch launch";
+        }
+    } else {
+        rcg_status st = prepare_slot(ctx, s, bytes, b->shape);
+        if (st) return st;
+        memcpy(s.host, b->image.data(), bytes);
+        where = "graph copy-size update";
+        if (bytes != s.bytes) {
+            // copy only the live part of the table: update the captured node
+            cudaMemcpy3DParms mp;
+            e = cudaGraphMemcpyNodeGetParams(s.copy_node, &mp);
+            if (e == cudaSuccess) {
+                mp.extent.width = bytes;
+                mp.srcPtr.pitch = bytes;
+                mp.srcPtr.xsize = bytes;
+                mp.dstPtr.pitch = bytes;
+                mp.dstPtr.xsize = bytes;
+                e = cudaGraphExecMemcpyNodeSetParams(s.exec, s.copy_node, &mp);
+            }
+            if (e == cudaSuccess) {
+                s.bytes = bytes;
+            } else {
+                // keep copying the whole table (the kernel reads n_jobs entries)
+                cudaGetLastError();
+                e = cudaSuccess;
+            }
+        }
+        if (e == cudaSuccess) {
+            e = set_enabled(s, work_mask(hdr));
+            where = "graph node enable";
+        }
+        if (e == cudaSuccess) {
+            e = cudaGraphLaunch(s.exec, st_user);
+            where = "graph launch";
         }
     }
     if (e == cudaSuccess) {
-        e = set_enabled(s, work_mask(*reinterpret_cast<const BatchHeader *>(b->image.data())));
-        where = "graph node enable";
-    }
-    if (e == cudaSuccess) {
-        e = cudaGraphLaunch(s.exec, static_cast<cudaStream_t>(stream));
-        where = "graph launch";
-    }
-    if (e == cudaSuccess) {
-        e = cudaEventRecord(s.done, static_cast<cudaStream_t>(stream));
+        e = cudaEventRecord(s.done, st_user);
         where = "event record";
     }
     if (e != cudaSuccess) return from_cuda(e, where);
@@ -1294,6 +1329,32 @@ cudaError_t rcg::launch_batch_all(const uint8_t *table_dev, const uint8_t *table
     if (e == cudaSuccess && h.n_items)
         e = launch_batch(table_dev, status, counter, timeout_ns, shape,
                          sm_count * static_cast<int>(shape_info(shape).ctas_per_sm), stream);
+    return e;
+}
+
+cudaError_t rcg::launch_batch_all_param(const uint8_t *table_host, size_t bytes, uint32_t *status,
+                                        uint64_t timeout_ns, uint32_t shape, int sm_count, cudaStream_t stream,
+                                        cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+    if (bytes < sizeof(BatchHeader) || bytes > kParamTableLarge) return cudaErrorInvalidValue;
+    const auto &h = *reinterpret_cast<const BatchHeader *>(table_host);
+    bool cols = false;
+    for (int v = 0; v < kColVariants; ++v) cols = cols || h.col_count[v] != 0;
+    const bool beside = cols && h.n_items && side && fork && join;
+    cudaStream_t cs = beside ? side : stream;
+    cudaError_t e = cudaSuccess;
+    if (beside) {
+        e = cudaEventRecord(fork, stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+    }
+    for (int v = 0; v < kColVariants && e == cudaSuccess; ++v)
+        if (h.col_count[v]) e = launch_column_batch_param(v, table_host, bytes, status, sm_count, cs);
+    if (e == cudaSuccess && h.n_items)
+        e = launch_batch_param(table_host, bytes, status, timeout_ns, shape,
+                               sm_count * static_cast<int>(shape_info(shape).ctas_per_sm), stream);
+    if (e == cudaSuccess && beside) {
+        e = cudaEventRecord(join, side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, join, 0);
+    }
     return e;
 }
 

@@ -30,6 +30,8 @@
 
 #include <algorithm>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "../../include/rcg.h"
 #include "rcg_internal.h"
@@ -352,10 +354,11 @@ __global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
 // 128-byte record is read by the warp in one coalesced load (a word per lane)
 // into a per-warp copy in shared memory (kept out of registers, which the
 // column needs), and the next record is prefetched into L1 meanwhile, so a
-// switch between small jobs costs no dependent global round trips.
-template <int P, bool EXT>
-__global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
-    rcg_column_batch(const uint8_t *__restrict__ table, uint32_t *status) {
+// switch between small jobs costs no dependent global round trips.  The
+// table is a device buffer, or (IN_PARAMS) the launch's own parameter block,
+// which is read through the same generic pointer and needs no prefetch.
+template <int P, bool EXT, bool IN_PARAMS>
+__device__ __forceinline__ void column_batch_body(const uint8_t *__restrict__ table, uint32_t *status) {
     using V = ColVec<P, EXT>;
     const auto *bh = reinterpret_cast<const BatchHeader *>(table);
     constexpr int g = variant_of<P, EXT>();
@@ -373,24 +376,37 @@ __global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
         const uint32_t mid = (lo + hi) >> 1;
         if (runs[mid].chunk0 <= c0) lo = mid; else hi = mid;
     }
+    // the warp's job, its bookkeeping and the table's run list, in shared
+    // memory: only the job switch reads them, and the column needs the registers
     struct WarpState {
         ColJob J;
-        uint64_t next, units, c1;
-        uint32_t r, valid;
+        const ColJob *runs;
+        uint64_t next, units, c1, total;
+        uint32_t r, valid, n_runs;
     };
     __shared__ WarpState ws_all[8];
     WarpState &ws = ws_all[threadIdx.x >> 5];
+    if (lane == 0) {
+        ws.c1 = c1;
+        ws.runs = runs;
+        ws.total = total;
+        ws.n_runs = n_runs;
+    }
+    __syncwarp();
     auto load_job = [&](uint32_t r) {
-        const uint32_t word = reinterpret_cast<const uint32_t *>(runs + r)[lane];
-        if (lane == 0 && r + 1 < n_runs)
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<uint64_t>(runs + r + 1)));
+        const ColJob *const rl = ws.runs;
+        const uint32_t word = reinterpret_cast<const uint32_t *>(rl + r)[lane];
+        if constexpr (!IN_PARAMS) {
+            if (lane == 0 && r + 1 < ws.n_runs)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<uint64_t>(rl + r + 1)));
+        }
         __syncwarp();
         reinterpret_cast<uint32_t *>(&ws.J)[lane] = word;
         __syncwarp();
         if (lane == 0) {
             const ColJob &J = ws.J;
             ws.r = r;
-            ws.next = r + 1 < n_runs ? runs[r + 1].chunk0 : total;
+            ws.next = r + 1 < ws.n_runs ? rl[r + 1].chunk0 : ws.total;
             ws.units = J.n_stripes * J.vps * (16 / sizeof(V));  // lane columns of the job
             // device-side guard: the job is this variant's and its chunks cover it
             const bool valid = J.p == static_cast<uint32_t>(P) && (J.N > static_cast<uint32_t>(P)) == EXT &&
@@ -401,7 +417,6 @@ __global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
         }
         __syncwarp();
     };
-    if (lane == 0) ws.c1 = c1;
     load_job(lo);
 #pragma unroll 1
     for (uint64_t c = c0; c < ws.c1; ++c) {
@@ -409,9 +424,9 @@ __global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
             // the job holding chunk c (bounded by the number of jobs)
             uint32_t r = ws.r;
             uint64_t next = ws.next;
-            while (c >= next && r + 1 < n_runs) {
+            while (c >= next && r + 1 < ws.n_runs) {
                 ++r;
-                next = r + 1 < n_runs ? runs[r + 1].chunk0 : total;
+                next = r + 1 < ws.n_runs ? ws.runs[r + 1].chunk0 : ws.total;
             }
             load_job(r);
         }
@@ -424,11 +439,39 @@ __global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
     }
 }
 
+template <int P, bool EXT>
+__global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
+    rcg_column_batch(const uint8_t *__restrict__ table, uint32_t *status) {
+    column_batch_body<P, EXT, false>(table, status);
+}
+
+template <int P, bool EXT, uint32_t SZ>
+__global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
+    rcg_column_batch_param(uint32_t *status, const __grid_constant__ ParamTable<SZ> t) {
+    column_batch_body<P, EXT, true>(t.bytes, status);
+}
+
 template <class K>
 int resident_ctas(K kernel, int sm_count) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess) per_sm = 1;
     return sm_count * std::max(per_sm, 1);
+}
+
+// Launches made per call ask the occupancy once per kernel (the answer
+// depends on the kernel only), keyed by the kernel's address: kernels of the
+// same signature share a function-pointer type.
+template <class K>
+int resident_ctas_cached(K kernel, int sm_count) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> known;
+    const void *key = reinterpret_cast<const void *>(kernel);
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &k : known)
+        if (k.first == key) return sm_count * k.second;
+    const int per_sm = resident_ctas(kernel, 1);
+    known.emplace_back(key, per_sm);
+    return sm_count * per_sm;
 }
 
 }  // namespace
@@ -464,7 +507,7 @@ cudaError_t launch_column(const ColJob &job, uint32_t p, uint64_t n_stripes, uin
     const uint64_t total = n_stripes * job.vps;
     if (total == 0) return cudaSuccess;
     auto go = [&](auto kernel) -> cudaError_t {
-        const uint64_t resident = static_cast<uint64_t>(resident_ctas(kernel, sm_count));
+        const uint64_t resident = static_cast<uint64_t>(resident_ctas_cached(kernel, sm_count));
         const unsigned g = static_cast<unsigned>(std::min<uint64_t>((total + 255) / 256, resident));
         kernel<<<g, 256, 0, stream>>>(job, n_stripes, status);
         return cudaGetLastError();
@@ -486,6 +529,34 @@ const void *column_batch_function(int variant) {
         case 3: return reinterpret_cast<const void *>(rcg_column_batch<7, false>);
         default: return nullptr;
     }
+}
+
+template <uint32_t SZ>
+static cudaError_t column_batch_param_sized(int variant, const uint8_t *table_host, size_t bytes, uint32_t *status,
+                                           int sm_count, cudaStream_t stream) {
+    ParamTable<SZ> t;
+    memcpy(t.bytes, table_host, bytes);
+    memset(t.bytes + bytes, 0, SZ - bytes);
+    auto go = [&](auto kernel) -> cudaError_t {
+        kernel<<<resident_ctas_cached(kernel, sm_count), 256, 0, stream>>>(status, t);
+        return cudaGetLastError();
+    };
+    switch (variant) {
+        case 0: return go(rcg_column_batch_param<3, false, SZ>);
+        case 1: return go(rcg_column_batch_param<5, false, SZ>);
+        case 2: return go(rcg_column_batch_param<5, true, SZ>);
+        case 3: return go(rcg_column_batch_param<7, false, SZ>);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_column_batch_param(int variant, const uint8_t *table_host, size_t bytes, uint32_t *status,
+                                      int sm_count, cudaStream_t stream) {
+    if (bytes <= kParamTableSmall)
+        return column_batch_param_sized<kParamTableSmall>(variant, table_host, bytes, status, sm_count, stream);
+    if (bytes <= kParamTableLarge)
+        return column_batch_param_sized<kParamTableLarge>(variant, table_host, bytes, status, sm_count, stream);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_column_batch(int variant, const uint8_t *table_dev, uint32_t *status, int sm_count,

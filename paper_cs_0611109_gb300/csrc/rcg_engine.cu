@@ -39,6 +39,7 @@
 // the copies it issued have landed.  No trap, no unbounded spin.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <mutex>
 
@@ -346,8 +347,9 @@ __device__ __forceinline__ uint32_t strip_role(uint8_t cls, bool update, uint32_
     return 0;
 }
 
-__device__ __forceinline__ const Job &job_ref(const LaunchParams &prm, uint32_t idx) {
-    return prm.jobs ? prm.jobs[idx] : prm.job0;
+// A batch's jobs follow its table header; a single launch has job0.
+__device__ __forceinline__ const Job &job_ref(const LaunchParams &prm, const Job *jobs, uint32_t idx) {
+    return jobs ? jobs[idx] : prm.job0;
 }
 
 // ---------------------------------------------------------------- producer
@@ -363,8 +365,12 @@ struct RingPos {
     }
 };
 
+// bh: the batch table (null for single launches), in device memory or, when
+// in_params, in the launch's parameter block -- whose tensor maps need no
+// acquire (nothing rewrites them while the grid runs) and whose items are
+// dealt round-robin (no counter).
 template <class S>
-__device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHeader *bh,
+__device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHeader *bh, bool in_params,
                          uint64_t total_units, uint32_t ring_bytes, uint32_t n_slots) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t policy = l2_tile_policy();
@@ -375,6 +381,8 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
     const WorkItem *items =
         bh ? reinterpret_cast<const WorkItem *>(reinterpret_cast<const uint8_t *>(bh) + bh->items_offset)
            : nullptr;
+    const Job *jobs = bh ? reinterpret_cast<const Job *>(reinterpret_cast<const uint8_t *>(bh) + sizeof(BatchHeader))
+                         : nullptr;
     RingPos pos;
     uint32_t issued = 0;    // stages handed to the consumers
     uint32_t released = 0;  // stages known to be released (all earlier ones are)
@@ -390,7 +398,7 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
     // Batches, static: items u = blockIdx.x, blockIdx.x + grid, ...; dynamic:
     // the next item index comes from the global counter.  Either way the next
     // item's 128 bytes are requested while the current one streams.
-    const bool dynamic = bh && bh->dynamic;
+    const bool dynamic = bh && bh->dynamic && !in_params;
     auto next_index = [&]() -> uint64_t {
         unsigned long long v = 0;
         if (lane == 0) v = atomicAdd(prm.tile_counter, 1ull);
@@ -402,6 +410,16 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
         return reinterpret_cast<const uint32_t *>(items + idx)[lane];
     };
     uint64_t u = items ? (dynamic ? next_index() : blockIdx.x) : 0;
+    // Static batches with fewer items than CTAs (small batches): the CTAs
+    // b = u, u + n, u + 2n, ... (n items) share item u, each taking every
+    // share-th of its tiles, so a small batch still spreads over the grid.
+    uint32_t share = 1, share_idx = 0;
+    if (items && !dynamic && total_units > 0 && total_units < gridDim.x) {
+        const uint32_t n = static_cast<uint32_t>(total_units);
+        u = blockIdx.x % n;
+        share_idx = blockIdx.x / n;
+        share = (gridDim.x - 1 - static_cast<uint32_t>(u)) / n + 1;
+    }
     uint32_t nxt = 0;
     if (items && u < total_units) nxt = fetch(u);
     uint32_t acquired = ~0u;  // job whose tensor map this CTA last acquired
@@ -443,21 +461,21 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
             strip_stride = J0.strip_stride; row_stride = J0.row_stride; stripe_stride = J0.stripe_stride;
             aux_rs = J0.aux_row_stride; aux_ss = J0.aux_stripe_stride;
         }
-        const Job &J = job_ref(prm, ji);  // only its tensor map is used, in place
+        const Job &J = job_ref(prm, jobs, ji);  // only its tensor map is used, in place
         const uint32_t rows = p - 1;
         if (items && use_tmap && ji != acquired) {
-            if (lane == 0) acquire_tmap(&J.tmap);
+            if (lane == 0 && !in_params) acquire_tmap(&J.tmap);
             acquired = ji;
         }
 
-        for (uint32_t q = 0; q < nt && ok; ++q) {
-            if (q == 0 && items && u < total_units) {  // the next item's descriptor
+        for (uint32_t q = share_idx; q < nt && ok; q += share) {
+            if (q == share_idx && items && u < total_units) {  // the next item's descriptor
                 const uint32_t njob = __shfl_sync(0xffffffffu, nxt, 22);
                 const uint32_t ntm = (__shfl_sync(0xffffffffu, nxt, 24) >> 8) & 0xffu;
                 if (ntm && njob != acquired) {
-                    if (lane == 0) {
-                        acquire_tmap(&prm.jobs[njob].tmap);
-                        prefetch_tmap(&prm.jobs[njob].tmap);
+                    if (lane == 0 && !in_params) {
+                        acquire_tmap(&jobs[njob].tmap);
+                        prefetch_tmap(&jobs[njob].tmap);
                     }
                     acquired = njob;
                 }
@@ -1035,8 +1053,7 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
 // ------------------------------------------------------------------ kernel
 
 template <class S>
-__global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
-    rcg_tile_engine(const __grid_constant__ LaunchParams prm, const BatchHeader *bh) {
+__device__ __forceinline__ void engine_body(const LaunchParams &prm, const BatchHeader *bh, bool in_params) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const Smem sm = carve<S>(smem_raw);
 
@@ -1068,9 +1085,23 @@ __global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
     __syncthreads();
 
     if (threadIdx.x < 32)
-        producer<S>(prm, sm, bh, total, static_cast<uint32_t>(ring_bytes), n_slots);
+        producer<S>(prm, sm, bh, in_params, total, static_cast<uint32_t>(ring_bytes), n_slots);
     else
         consumer<S>(prm, sm, n_slots);
+}
+
+// Single launches (bh null) and batches with a device table.
+template <class S>
+__global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
+    rcg_tile_engine(const __grid_constant__ LaunchParams prm, const BatchHeader *bh) {
+    engine_body<S>(prm, bh, false);
+}
+
+// Batches whose table travels in the parameter block.
+template <class S, uint32_t SZ>
+__global__ void __launch_bounds__(S::kThreads, S::kCtasPerSm)
+    rcg_tile_engine_param(const __grid_constant__ LaunchParams prm, const __grid_constant__ ParamTable<SZ> t) {
+    engine_body<S>(prm, reinterpret_cast<const BatchHeader *>(t.bytes), true);
 }
 
 // --------------------------------------------------- bounded-wait self test
@@ -1164,12 +1195,14 @@ cudaError_t upload_inverse_tables() {
 }
 
 cudaError_t engine_init_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(rcg_tile_engine<ShapeWide>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(ShapeWide::kSmemLimit));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(rcg_tile_engine<ShapePair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(ShapePair::kSmemLimit));
+    const int wide = static_cast<int>(ShapeWide::kSmemLimit), pair = static_cast<int>(ShapePair::kSmemLimit);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(rcg_tile_engine<ShapeWide>, attr, wide);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rcg_tile_engine<ShapePair>, attr, pair);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rcg_tile_engine_param<ShapeWide, kParamTableSmall>, attr, wide);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rcg_tile_engine_param<ShapePair, kParamTableSmall>, attr, pair);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rcg_tile_engine_param<ShapeWide, kParamTableLarge>, attr, wide);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rcg_tile_engine_param<ShapePair, kParamTableLarge>, attr, pair);
     return e;
 }
 
@@ -1190,7 +1223,6 @@ cudaError_t launch_engine(const LaunchParams &prm, uint32_t shape, int grid, cud
 cudaError_t launch_batch(const uint8_t *table_dev, uint32_t *status, unsigned long long *counter,
                          uint64_t timeout_ns, uint32_t shape, int grid, cudaStream_t stream) {
     LaunchParams prm = {};
-    prm.jobs = reinterpret_cast<const Job *>(table_dev + sizeof(BatchHeader));
     prm.dynamic_sched = 1;
     prm.tile_counter = counter;
     prm.status = status;
@@ -1199,6 +1231,33 @@ cudaError_t launch_batch(const uint8_t *table_dev, uint32_t *status, unsigned lo
     const ShapeInfo si = shape_info(shape);
     return shape == SHAPE_PAIR ? launch_shape<ShapePair>(prm, bh, si.smem_limit, grid, stream)
                                : launch_shape<ShapeWide>(prm, bh, si.smem_limit, grid, stream);
+}
+
+template <class S, uint32_t SZ>
+static cudaError_t launch_param_sized(const uint8_t *table_host, size_t bytes, const LaunchParams &prm, size_t smem,
+                                     int grid, cudaStream_t stream) {
+    ParamTable<SZ> t;
+    memcpy(t.bytes, table_host, bytes);
+    memset(t.bytes + bytes, 0, SZ - bytes);
+    rcg_tile_engine_param<S, SZ><<<grid, S::kThreads, smem, stream>>>(prm, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_param(const uint8_t *table_host, size_t bytes, uint32_t *status, uint64_t timeout_ns,
+                               uint32_t shape, int grid, cudaStream_t stream) {
+    if (bytes > kParamTableLarge || bytes < sizeof(BatchHeader)) return cudaErrorInvalidValue;
+    LaunchParams prm = {};
+    prm.dynamic_sched = 0;
+    prm.tile_counter = nullptr;
+    prm.status = status;
+    prm.timeout_ns = timeout_ns;
+    const size_t smem = shape_info(shape).smem_limit;
+    const bool small = bytes <= kParamTableSmall;
+    if (shape == SHAPE_PAIR)
+        return small ? launch_param_sized<ShapePair, kParamTableSmall>(table_host, bytes, prm, smem, grid, stream)
+                     : launch_param_sized<ShapePair, kParamTableLarge>(table_host, bytes, prm, smem, grid, stream);
+    return small ? launch_param_sized<ShapeWide, kParamTableSmall>(table_host, bytes, prm, smem, grid, stream)
+                 : launch_param_sized<ShapeWide, kParamTableLarge>(table_host, bytes, prm, smem, grid, stream);
 }
 
 cudaError_t launch_wait_probe(uint32_t *status, uint64_t timeout_ns, cudaStream_t stream) {

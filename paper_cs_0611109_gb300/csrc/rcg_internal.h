@@ -86,8 +86,7 @@ struct alignas(128) Job {
 };
 
 struct LaunchParams {
-    const Job *jobs;                 // device table, or nullptr: use job0
-    Job job0;
+    Job job0;                        // single launches; batches read their jobs after the table header
     uint32_t n_jobs;
     uint32_t slot_bytes;
     uint32_t n_slots;
@@ -153,6 +152,19 @@ static_assert(sizeof(BatchHeader) == 128, "the job table after the header stays 
 constexpr uint32_t kColChunk = 32;  // columns per chunk: one per lane
 constexpr int kColVariants = 4;
 
+// A small batch table travels in the launch's own parameter block instead of
+// a device buffer: no host-to-device copy before the kernels, no graph, no
+// counter reset.  Two size classes (a launch copies its whole parameter
+// block); the larger leaves room for the engine's LaunchParams within the
+// 32764 bytes a kernel's parameters may take.
+constexpr uint32_t kParamTableSmall = 8192;
+constexpr uint32_t kParamTableLarge = 31744;
+template <uint32_t SZ>
+struct alignas(128) ParamTable {
+    uint8_t bytes[SZ];
+};
+static_assert(sizeof(LaunchParams) + 128 + kParamTableLarge <= 32764, "kernel parameter block limit");
+
 // The column-kernel variant of a geometry (index into col_begin / col_count),
 // or -1 when p > 7.
 inline int column_variant(uint32_t p, uint32_t N) {
@@ -179,6 +191,10 @@ cudaError_t upload_inverse_tables();
 cudaError_t launch_engine(const LaunchParams &prm, uint32_t shape, int grid, cudaStream_t stream);
 cudaError_t launch_batch(const uint8_t *table_dev, uint32_t *status, unsigned long long *counter,
                          uint64_t timeout_ns, uint32_t shape, int grid, cudaStream_t stream);
+// The tile engine over a small batch table passed as a kernel parameter
+// (bytes <= kParamTableLarge): items dealt round-robin, no counter.
+cudaError_t launch_batch_param(const uint8_t *table_host, size_t bytes, uint32_t *status, uint64_t timeout_ns,
+                               uint32_t shape, int grid, cudaStream_t stream);
 cudaError_t engine_init_attributes();
 cudaError_t launch_fill(void *dev, uint64_t nbytes, uint64_t seed, uint64_t byte_offset,
                         cudaStream_t stream);
@@ -239,12 +255,23 @@ cudaError_t launch_column(const ColJob &job, uint32_t p, uint64_t n_stripes, uin
 cudaError_t launch_column_batch(int variant, const uint8_t *table_dev, uint32_t *status, int sm_count,
                                 cudaStream_t stream);
 const void *column_batch_function(int variant);
+// The same over a small table passed as a kernel parameter (bytes <= kParamTableLarge).
+cudaError_t launch_column_batch_param(int variant, const uint8_t *table_host, size_t bytes, uint32_t *status,
+                                      int sm_count, cudaStream_t stream);
 // Every kernel of a batch table on `stream`, skipping kernels with no work:
 // the column kernels of its p <= 7 jobs, then the tile engine (the path of
 // rcg_batch_submit_noalloc; context batches replay the same in a graph).
 cudaError_t launch_batch_all(const uint8_t *table_dev, const uint8_t *table_host, uint32_t *status,
                              unsigned long long *counter, uint64_t timeout_ns, uint32_t shape, int sm_count,
                              cudaStream_t stream);
+// Every kernel of a small table (bytes <= kParamTableLarge), the table passed
+// as a kernel parameter.  With both column and engine work, the column
+// kernels run on `side` (forked from and joined back to `stream` by the two
+// events) beside the engine, as in the batch graph; side may be null when the
+// table has one kind of work.
+cudaError_t launch_batch_all_param(const uint8_t *table_host, size_t bytes, uint32_t *status, uint64_t timeout_ns,
+                                   uint32_t shape, int sm_count, cudaStream_t stream, cudaStream_t side,
+                                   cudaEvent_t fork, cudaEvent_t join);
 
 // Host: the CUDA device of a context.
 int ctx_device(const rcg_ctx *ctx);

@@ -100,10 +100,18 @@ extern "C" rcg_status rcg_batch_submit_noalloc(const rcg_job *jobs, uint32_t n_j
     uint8_t *table_dev = d->scratch;
     auto *counter = reinterpret_cast<unsigned long long *>(d->scratch + kCounterOff);
     uint32_t *status = status_dev ? status_dev : reinterpret_cast<uint32_t *>(d->scratch + kStatusOff);
-    // The host table is pageable: the copy has left it by the time the call returns.
-    cudaError_t e = cudaMemcpyAsync(table_dev, g_host_table, bytes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess)
-        e = launch_batch_all(table_dev, g_host_table, status, counter, 2000000000ull, shape, d->sm_count, s);
+    cudaError_t e = cudaSuccess;
+    if (bytes <= kParamTableLarge) {
+        // a small table travels in the kernels' parameter blocks: no copy into
+        // the scratch, no counter
+        e = launch_batch_all_param(g_host_table, bytes, status, 2000000000ull, shape, d->sm_count, s, nullptr,
+                                   nullptr, nullptr);
+    } else {
+        // The host table is pageable: the copy has left it by the time the call returns.
+        e = cudaMemcpyAsync(table_dev, g_host_table, bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+        if (e == cudaSuccess)
+            e = launch_batch_all(table_dev, g_host_table, status, counter, 2000000000ull, shape, d->sm_count, s);
+    }
     return e == cudaSuccess ? RCG_OK : RCG_ECUDA;
 }

@@ -22,6 +22,9 @@
 //      once with its own single-operation call and completion event.
 // Latency = completion - arrival.
 #include <cuda_runtime.h>
+#if defined(__linux__)
+#include <sys/prctl.h>
+#endif
 #include <stdint.h>
 #include <string.h>
 #include <time.h>
@@ -265,6 +268,12 @@ bool tick(rcg_server *s) {
 
 void worker_main(rcg_server *s) {
     cudaSetDevice(rcg::ctx_device(s->ctx));
+#if defined(__linux__)
+    // The idle poll below sleeps 2 us; with the default timer slack (50 us)
+    // the kernel may stretch each sleep to about 50 us, which then delays
+    // every admission and completion.  The slack is this thread's own.
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
+#endif
     while (!s->stop.load()) {
         if (tick(s)) continue;
         // idle: nothing retired, admitted or launched; poll again shortly

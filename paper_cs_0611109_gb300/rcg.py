@@ -23,6 +23,7 @@ RCG_NOALLOC_MAX_JOBS = 256
 RCG_SHAPE_AUTO, RCG_SHAPE_WIDE, RCG_SHAPE_PAIR = 0, 1, 2
 RCG_SCHED_STATIC, RCG_SCHED_DYNAMIC = 0, 1
 RCG_COLUMN_AUTO, RCG_COLUMN_OFF = 0, 1
+RCG_TABLES_AUTO, RCG_TABLES_DEVICE = 0, 1
 RCG_RING_FIXED, RCG_RING_BYTES = 0, 1
 
 _u32, _u64, _vp, _int = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
@@ -125,6 +126,7 @@ EXPORTS = {
     "rcg_plan": (_int, [_u32, _u64, ctypes.POINTER(rcg_plan_info)]),
     "rcg_prime_info": (_int, [_u32, ctypes.POINTER(rcg_prime_info_t)]),
     "rcg_set_column_kernel": (_int, [_vp, _int]),
+    "rcg_set_batch_tables": (_int, [_vp, _int]),
     "rcg_batch_autotune": (_int, [_vp, _vp, _u32, _vp, ctypes.POINTER(rcg_batch_tuning)]),
     "rcg_set_batch_tuning": (_int, [_vp, ctypes.POINTER(rcg_batch_tuning)]),
     "rcg_h_encode": (_int, [_vp, ctypes.POINTER(rcg_hlayout), _u64, _u64, _vp]),
@@ -283,6 +285,10 @@ def load_tuning(path: str, device: int = 0) -> dict | None:
 
 def rcg_set_column_kernel(ctx: int, mode: int):
     _check(lib().rcg_set_column_kernel(ctx, mode), "rcg_set_column_kernel")
+
+
+def rcg_set_batch_tables(ctx: int, mode: int):
+    _check(lib().rcg_set_batch_tables(ctx, mode), "rcg_set_batch_tables")
 
 
 def rcg_set_host_chunk(ctx: int, nbytes: int):
@@ -580,6 +586,9 @@ class Context:
 
     def set_column_kernel(self, mode):
         rcg_set_column_kernel(self.handle, mode)
+
+    def set_batch_tables(self, mode):
+        rcg_set_batch_tables(self.handle, mode)
 
     def set_batch_schedule(self, schedule):
         rcg_set_batch_schedule(self.handle, schedule)

@@ -233,13 +233,24 @@ SMALL = [(3, 2, 32, 3, "enc"), (3, 3, 1040, 2, "rec_dd"), (5, 4, 1024, 40, "enc"
 LARGE = [(13, 12, 1024, 3, "enc"), (29, 8, 512, 2, "rec_dd"), (59, 20, 2048, 1, "deg_d"), (13, 6, 4096, 2, "upd")]
 
 
+TABLES = ["params", "device"]
+
+
+def set_tables(rcg, c, tables):
+    c.set_batch_tables(rcg.RCG_TABLES_AUTO if tables == "params" else rcg.RCG_TABLES_DEVICE)
+
+
+@pytest.mark.parametrize("tables", TABLES)
 @pytest.mark.parametrize("mix", ["small", "large", "both"])
-def test_batch_with_column_jobs_matches_oracle(rcg, ctxs, oracle, mix):
+def test_batch_with_column_jobs_matches_oracle(rcg, ctxs, oracle, mix, tables):
     # p <= 7 jobs run in the column kernels of the batch, the others in the
-    # tile engine; the same slot is launched with only one kind, then both
+    # tile engine; the same slot is launched with only one kind, then both.
+    # These tables are small: "params" passes them in the kernels' parameter
+    # blocks, "device" copies them to a device buffer in the batch graph.
     col, eng = ctxs
     specs = SMALL if mix == "small" else LARGE if mix == "large" else SMALL + LARGE
     for c in (col, eng):  # column kernels in the batch, and the tile engine alone
+        set_tables(rcg, c, tables)
         for rep in range(2):
             bufs, jobs, outs, want_bufs, want_outs = mixed_batch(rcg, oracle, 4700 + 10 * rep, specs)
             assert c.batch_wait(c.batch_submit(jobs))
@@ -248,6 +259,42 @@ def test_batch_with_column_jobs_matches_oracle(rcg, ctxs, oracle, mix):
                 assert np.array_equal(b.cpu().numpy(), w), (specs[k], rep)
             for o, w in zip(outs, want_outs):
                 assert np.array_equal(o.cpu().numpy(), w)
+        set_tables(rcg, c, "params")
+
+
+# (column jobs, engine jobs): tables of about 2.2 KB, 15 KB and 39 KB -- the
+# parameter block's small and large classes, and one over its 31 744 bytes
+# that goes to a device buffer even when parameter tables are allowed
+SIZE_CLASSES = [(4, 4), (60, 20), (300, 4)]
+
+
+@pytest.mark.parametrize("n_col,n_eng", SIZE_CLASSES)
+def test_batch_table_size_classes(rcg, oracle, n_col, n_eng):
+    kinds = ["enc", "rec_dd", "rec_dp", "rec_dq", "rec_pq", "deg_d", "deg_q", "upd"]
+    specs = [(5, 4, 64 + 16 * (k % 5), 1 + k % 2, kinds[k % len(kinds)]) for k in range(n_col)]
+    specs += [(13, 6, 512, 1, kinds[k % len(kinds)]) for k in range(n_eng)]
+    results = []
+    with rcg.Context(0) as c:
+        for tables in TABLES:
+            set_tables(rcg, c, tables)
+            bufs, jobs, outs, want_bufs, want_outs = mixed_batch(rcg, oracle, 5200, specs)
+            assert c.batch_wait(c.batch_submit(jobs))
+            assert c.last_device_status() == 0
+            for k, (b, w) in enumerate(zip(bufs, want_bufs)):
+                assert np.array_equal(b.cpu().numpy(), w), (tables, specs[k])
+            for o, w in zip(outs, want_outs):
+                assert np.array_equal(o.cpu().numpy(), w), tables
+            results.append([b.cpu().numpy() for b in bufs])
+    for a, b in zip(*results):
+        assert np.array_equal(a, b)
+
+
+def test_batch_tables_setting_is_validated(rcg):
+    with rcg.Context(0) as c:
+        with pytest.raises(rcg.RcgError):
+            c.set_batch_tables(2)
+        c.set_batch_tables(rcg.RCG_TABLES_DEVICE)
+        c.set_batch_tables(rcg.RCG_TABLES_AUTO)
 
 
 def test_p5n4_sixteen_operations_in_one_batch(rcg, oracle):
@@ -281,11 +328,13 @@ def test_p5n4_sixteen_operations_in_one_batch(rcg, oracle):
     assert np.array_equal(got[0, :8], sample)
 
 
-def test_back_to_back_batches_switching_kernels(rcg, oracle):
+@pytest.mark.parametrize("tables", TABLES + ["alternating"])
+def test_back_to_back_batches_switching_kernels(rcg, oracle, tables):
     # batches launched without waiting, alternating column-kernel-only, tile-
     # engine-only and mixed tables, so each replayed graph switches its kernel
-    # nodes on and off while the previous batches still run: every batch must
-    # run on its own table
+    # nodes on and off while the previous batches still run (and, alternating,
+    # parameter-block and device tables follow each other on the stream):
+    # every batch must run on its own table
     kinds = ["p5", "p13", "mix", "p5", "p5"] * 60
     bufs = []
     for k, kind in enumerate(kinds):
@@ -296,7 +345,8 @@ def test_back_to_back_batches_switching_kernels(rcg, oracle):
             entry.append((p, N, C, host, dev(host)))
         bufs.append(entry)
     with rcg.Context(0) as c:
-        for entry in bufs:
+        for k, entry in enumerate(bufs):
+            set_tables(rcg, c, TABLES[k % 2] if tables == "alternating" else tables)
             c.batch_submit([rcg.make_job(rcg.make_layout(d, p, N, C), 0, 1, rcg.RCG_OP_ENCODE)
                             for p, N, C, _, d in entry])
         torch.cuda.synchronize()

@@ -102,6 +102,21 @@ def test_noalloc_matches_batch_submit_twice_in_a_row(rcg, oracle):
     run_both(rcg, oracle, 2000, SECOND)
 
 
+# 120 engine jobs (their tensor-map entries and work items: about 46 KB of
+# table) and 40 column jobs: over the 31 744 bytes a kernel parameter block
+# holds, so this table goes through the scratch; FIRST and SECOND are small
+# and travel in the kernels' parameter blocks
+KINDS = ["enc", "rec", "deg", "upd"]
+LARGE_TABLE = [(13, 6, 256, 1, KINDS[k % 4]) for k in range(120)] + \
+              [(5, 4, 64, 1 + k % 3, KINDS[k % 4]) for k in range(40)]
+
+
+def test_noalloc_large_table_between_small_ones(rcg, oracle):
+    run_both(rcg, oracle, 4000, LARGE_TABLE)
+    run_both(rcg, oracle, 5000, FIRST)
+    run_both(rcg, oracle, 6000, LARGE_TABLE)
+
+
 def test_noalloc_without_a_status_word(rcg, oracle):
     # with status_dev = NULL device-side errors go unreported, but a valid
     # batch still gives the oracle's bytes
