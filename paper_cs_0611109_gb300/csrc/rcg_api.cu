@@ -953,7 +953,7 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
     uint32_t col_begin[kColVariants] = {}, col_count[kColVariants] = {}, col_chunks[kColVariants] = {};
     for (int v = 0; v < kColVariants; ++v) {
         col_begin[v] = static_cast<uint32_t>(col_items.size());
-        uint64_t chunks = 0;
+        uint64_t chunks = 0, cost = 0;
         for (uint32_t k = 0; k < n_jobs; ++k) {
             if (variant[k] != v) continue;
             const Job &J = table[k];
@@ -975,8 +975,12 @@ static rcg_status build_table(const rcg_ctx *ctx, const rcg_job *jobs, uint32_t 
             cj.j = J.j;
             cj.op = J.op;
             cj.p = J.p;
+            cj.cost0 = cost;
+            const uint64_t n_chunks = (static_cast<uint64_t>(J.n_stripes) * (J.C / 16) + kColChunk - 1) / kColChunk;
+            chunks += n_chunks;
+            cost += n_chunks * (J.n + 2ull) * (J.p - 1u);
+            cj.chunk_end = chunks;
             col_items.push_back(cj);
-            chunks += (static_cast<uint64_t>(J.n_stripes) * (J.C / 16) + kColChunk - 1) / kColChunk;
         }
         if (chunks > 0xffffffffull) return RCG_EINVAL;
         col_count[v] = static_cast<uint32_t>(col_items.size()) - col_begin[v];

@@ -347,14 +347,17 @@ __global__ void __launch_bounds__(256, col_ctas_per_sm<P, EXT>())
     }
 }
 
-// A batch's columns of one variant: warp w of W takes the contiguous range
-// [T w / W, T (w+1) / W) of the variant's T chunks (one lane column per lane), so
-// every warp has the same work give or take one chunk.  The job of the first
-// chunk is found by binary search over the variant's ColJob records.  A job's
+// A batch's columns of one variant: warp w of W takes the contiguous chunks
+// (one lane column per lane) whose start falls in [Ct w / W, Ct (w+1) / W) of
+// the variant's total cost Ct (rows moved), so every warp moves about the same
+// bytes.  The job of its first chunk is found by binary search over the
+// variant's ColJob records.  A job's
 // 128-byte record is read by the warp in one coalesced load (a word per lane)
 // into a per-warp copy in shared memory (kept out of registers, which the
-// column needs), and the next record is prefetched into L1 meanwhile, so a
-// switch between small jobs costs no dependent global round trips.  The
+// column needs), and the next two records are prefetched into L1 meanwhile;
+// each record holds its job's end chunk, so a switch between small jobs reads
+// only records already on their way and makes no dependent global round
+// trip.  The
 // table is a device buffer, or (IN_PARAMS) the launch's own parameter block,
 // which is read through the same generic pointer and needs no prefetch.
 template <int P, bool EXT, bool IN_PARAMS>
@@ -366,39 +369,47 @@ __device__ __forceinline__ void column_batch_body(const uint8_t *__restrict__ ta
     const uint64_t total = bh->col_chunks[g];
     const auto *runs = reinterpret_cast<const ColJob *>(table + bh->col_items_offset) + bh->col_begin[g];
     const uint32_t lane = threadIdx.x & 31;
+    if (n_runs == 0 || total == 0) return;
     const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
     const uint64_t w = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const uint64_t c0 = total * w / warps, c1 = total * (w + 1) / warps;
-    if (c0 >= c1 || n_runs == 0) return;
-    // the last job whose first chunk is <= c0 (the first job's is 0)
+    // Warps split the variant's cost evenly -- the rows its chunks move,
+    // (N+2)(p-1) per chunk -- rather than its chunk count: chunk c of job r
+    // starts at cost0_r + (c - chunk0_r) (N_r+2)(p-1) and belongs to the warp
+    // whose range [A, B) holds that start.  (Equal chunk counts left the
+    // busiest warp 13 % above the mean on jobs of N = 3 and 4.)
+    const ColJob &last = runs[n_runs - 1];
+    const uint64_t cost_total = last.cost0 + (last.chunk_end - last.chunk0) * (last.N + 2ull) * (P - 1);
+    const uint64_t A = cost_total * w / warps, B = cost_total * (w + 1) / warps;
+    if (A >= B) return;
+    // the last job whose cost0 <= A (the first job's is 0)
     uint32_t lo = 0, hi = n_runs;
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (runs[mid].chunk0 <= c0) lo = mid; else hi = mid;
+        if (runs[mid].cost0 <= A) lo = mid; else hi = mid;
     }
     // the warp's job, its bookkeeping and the table's run list, in shared
     // memory: only the job switch reads them, and the column needs the registers
     struct WarpState {
         ColJob J;
         const ColJob *runs;
-        uint64_t next, units, c1, total;
+        uint64_t next, units, total, B, rows;
         uint32_t r, valid, n_runs;
     };
     __shared__ WarpState ws_all[8];
     WarpState &ws = ws_all[threadIdx.x >> 5];
     if (lane == 0) {
-        ws.c1 = c1;
         ws.runs = runs;
         ws.total = total;
         ws.n_runs = n_runs;
+        ws.B = B;
     }
     __syncwarp();
     auto load_job = [&](uint32_t r) {
         const ColJob *const rl = ws.runs;
         const uint32_t word = reinterpret_cast<const uint32_t *>(rl + r)[lane];
-        if constexpr (!IN_PARAMS) {
-            if (lane == 0 && r + 1 < ws.n_runs)
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<uint64_t>(rl + r + 1)));
+        if constexpr (!IN_PARAMS) {  // the next two records into L1
+            if (lane < 2 && r + 1 + lane < ws.n_runs)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<uint64_t>(rl + r + 1 + lane)));
         }
         __syncwarp();
         reinterpret_cast<uint32_t *>(&ws.J)[lane] = word;
@@ -406,30 +417,37 @@ __device__ __forceinline__ void column_batch_body(const uint8_t *__restrict__ ta
         if (lane == 0) {
             const ColJob &J = ws.J;
             ws.r = r;
-            ws.next = r + 1 < ws.n_runs ? rl[r + 1].chunk0 : ws.total;
+            ws.next = J.chunk_end;
+            ws.rows = (J.N + 2ull) * (P - 1);
             ws.units = J.n_stripes * J.vps * (16 / sizeof(V));  // lane columns of the job
             // device-side guard: the job is this variant's and its chunks cover it
             const bool valid = J.p == static_cast<uint32_t>(P) && (J.N > static_cast<uint32_t>(P)) == EXT &&
-                               J.N >= 1 && ws.units > 0 && J.op <= OP_UPDATE &&
-                               ws.next - J.chunk0 == (ws.units + kColChunk - 1) / kColChunk;
+                               J.N >= 1 && ws.units > 0 && J.op <= OP_UPDATE && J.chunk_end > J.chunk0 &&
+                               J.chunk_end <= ws.total &&
+                               J.chunk_end - J.chunk0 == (ws.units + kColChunk - 1) / kColChunk;
             ws.valid = valid;
             if (!valid && status) atomicOr(status, RCG_DEV_BADJOB);
         }
         __syncwarp();
     };
     load_job(lo);
+    // the job's first chunk that starts at or after A
+    uint64_t c = ws.J.chunk0 + (A > ws.J.cost0 ? (A - ws.J.cost0 + ws.rows - 1) / ws.rows : 0);
 #pragma unroll 1
-    for (uint64_t c = c0; c < ws.c1; ++c) {
+    for (;; ++c) {
+        if (c >= ws.total) break;  // a hard bound, whatever the records hold
         if (c >= ws.next) {
             // the job holding chunk c (bounded by the number of jobs)
             uint32_t r = ws.r;
             uint64_t next = ws.next;
             while (c >= next && r + 1 < ws.n_runs) {
                 ++r;
-                next = r + 1 < ws.n_runs ? ws.runs[r + 1].chunk0 : ws.total;
+                next = ws.runs[r].chunk_end;  // the record prefetched at the last switch
             }
+            if (c >= next) break;
             load_job(r);
         }
+        if (c < ws.J.chunk0 || ws.J.cost0 + (c - ws.J.chunk0) * ws.rows >= ws.B) break;  // the next warp's
         if (!ws.valid) continue;
         const uint64_t u = (c - ws.J.chunk0) * kColChunk + lane;
         if (u >= ws.units) continue;

@@ -241,10 +241,12 @@ struct alignas(128) ColJob {
     uint64_t rs, ss, st;   // row, strip and stripe strides
     uint64_t ars, ass;     // aux row and stripe strides
     uint64_t chunk0;       // batches: the job's first chunk in its variant's numbering
+    uint64_t chunk_end;    // batches: one past its last chunk (the next job's chunk0)
+    uint64_t cost0;        // batches: rows the variant's earlier jobs move, (N+2)(p-1) per chunk
     uint64_t n_stripes;
     uint32_t vps;          // 16-byte columns per row, C / 16
     uint32_t N, i, j, op, p;
-    uint32_t pad[6];
+    uint32_t pad[2];
 };
 static_assert(sizeof(ColJob) == 128, "a column job is one 128-byte record");
 cudaError_t upload_column_tables();
