@@ -716,7 +716,7 @@ def p5n4_sixteen_in_one_batch(args, ctx, rcg, torch, buf, ops, flush, stream):
     return {"ms": round(ms, 4), "user_gbs": round(user / (ms * 1e-3) / 1e9, 1), "hbm_gbs": round(achieved, 1),
             "hbm_frac": round(achieved / peak, 4), "bytes_per_launch": moved, "launches": args.steps,
             "l2": "256 MB buffer read between launches", "clocks": clk,
-            "roofline": {"bound": "hbm", "kernel": "rcg_column_batch<5>", "achieved": round(achieved, 1),
+            "roofline": {"bound": "hbm", "kernel": "rcg_column_batch_param<5> (table in the parameter block)", "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "avg_launch_ms": round(ms, 4), "bytes_per_launch": moved}}
 
