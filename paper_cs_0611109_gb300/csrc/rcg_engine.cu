@@ -188,6 +188,10 @@ __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }
 
+__device__ __forceinline__ uint4 xor3(uint4 a, uint4 b, uint4 c) {
+    return make_uint4(a.x ^ b.x ^ c.x, a.y ^ b.y ^ c.y, a.z ^ b.z ^ c.z, a.w ^ b.w ^ c.w);
+}
+
 __device__ __forceinline__ uint4 lds(const uint8_t *p) {
     return *reinterpret_cast<const uint4 *>(p);
 }
@@ -895,8 +899,24 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[S::k
             const uint32_t xb0 = smem_addr(sm.xb);
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t) accQ[t] = zero;
-            for (int k = 0; k < n_terms; ++k) {
-                const int e = sm.terms[k];  // the same in every thread
+            // two exponents per pass: each word takes one three-input XOR for
+            // both rows (the product is instruction-bound)
+            int k = 0;
+            for (; k + 1 < n_terms; k += 2) {
+                const int e0 = sm.terms[k], e1 = sm.terms[k + 1];  // the same in every thread
+#pragma unroll
+                for (int t = 0; t < S::kItems; ++t) {
+                    const int r = row[t];
+                    if (r >= p) continue;
+                    int j0 = e0 + r, j1 = e1 + r;
+                    if (j0 >= p) j0 -= p;
+                    if (j1 >= p) j1 -= p;
+                    accQ[t] = xor3(accQ[t], lds_a(xb0 + j0 * row_bytes + col[t] * 16),
+                                   lds_a(xb0 + j1 * row_bytes + col[t] * 16));
+                }
+            }
+            if (k < n_terms) {
+                const int e = sm.terms[k];
 #pragma unroll
                 for (int t = 0; t < S::kItems; ++t) {
                     const int r = row[t];
