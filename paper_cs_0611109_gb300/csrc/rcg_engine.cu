@@ -188,6 +188,13 @@ __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }
 
+// Rows per block of the chain solve's walk (loads in flight together): as
+// many as the shape's registers hold without spilling (wide 8, pair 2).
+template <class S>
+__host__ __device__ constexpr int chain_block() {
+    return S::kCtasPerSm == 1 ? 8 : 2;
+}
+
 __device__ __forceinline__ uint4 xor3(uint4 a, uint4 b, uint4 c) {
     return make_uint4(a.x ^ b.x ^ c.x, a.y ^ b.y ^ c.y, a.z ^ b.z ^ c.z, a.w ^ b.w ^ c.w);
 }
@@ -206,6 +213,11 @@ __device__ __forceinline__ uint4 lds_a(uint32_t addr) {
 }
 
 __device__ __forceinline__ void sts(uint8_t *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
+
+__device__ __forceinline__ void sts_a(uint32_t addr, uint4 v) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
 
 __device__ __forceinline__ void stg(uint8_t *p, uint4 v) {
     asm volatile("st.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
@@ -253,7 +265,7 @@ struct SlotHdr {
     uint8_t p;
     uint8_t a, b;     // strips the epilogue writes (the erased pair, or i / j of the op)
     uint16_t pitch;   // bytes between rows in the slot (the job's tile width W)
-    uint8_t zinv;     // chain solves: z^(-1) mod p
+    uint8_t spare;
     uint8_t z;        // chain solves: the z of (1 + x^z); data + Q: the rotation of D_i's weight
     uint64_t base;            // the tile's column c0 of strip 0 of its stripe
     uint64_t strip_stride;
@@ -574,11 +586,17 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
             }
             if (cls == E_ENC) ob = N;
 
-            uint32_t zinv = 0;
-            if (cls == E_DDC || cls == E_DPXC) {  // z^(p-2) mod p, the inverse in Z/p
+            // chain solves: the rows r_t = p-1 + t z (mod p) at odd positions t
+            // of the walk, as a mask (the epilogue adds c to those rows)
+            uint64_t odd_rows = 0;
+            if (cls == E_DDC || cls == E_DPXC) {
                 const uint32_t zz = z % p;
-                zinv = 1;
-                for (uint32_t e = 0; e + 2 < p; ++e) zinv = zinv * zz % p;
+                uint32_t r = p - 1;
+                for (uint32_t t = 1; t < p; ++t) {
+                    r += zz;
+                    if (r >= p) r -= p;
+                    if (t & 1u) odd_rows |= 1ull << r;
+                }
             }
 
             // strips streamed per tile: N for every class (the other N survivors,
@@ -664,14 +682,15 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
                         h.a = static_cast<uint8_t>(oa);
                         h.b = static_cast<uint8_t>(ob);
                         h.pitch = static_cast<uint16_t>(W);
-                        h.zinv = static_cast<uint8_t>(zinv);
                         h.z = static_cast<uint8_t>(z);
                         h.base = reinterpret_cast<uint64_t>(stripe_base);
                         h.strip_stride = strip_stride;
                         h.row_stride = row_stride;
-                        // table solves: the inverse's exponents reflected (see the epilogue)
-                        h.out = (cls == E_DD || cls == E_DPX) ? reflect_exponents(mask, p)
-                                                              : reinterpret_cast<uint64_t>(aux_base);
+                        // table solves: the inverse's exponents reflected (see the
+                        // epilogue); chain solves: the odd positions' rows
+                        h.out = (cls == E_DD || cls == E_DPX)     ? reflect_exponents(mask, p)
+                                : (cls == E_DDC || cls == E_DPXC) ? odd_rows
+                                                                  : reinterpret_cast<uint64_t>(aux_base);
                         h.out_row_stride = aux_rs;
                     }
                     mbar_arrive_tx(full, tensor ? tx_tensor : tx_rows);
@@ -726,10 +745,11 @@ __device__ void producer(const LaunchParams &prm, const Smem &sm, const BatchHea
 
 struct Tile {
     uint8_t *base;      // stripe base + c0
-    uint8_t *out;       // degraded read output + c0 (stripe applied); table solves: the mask
+    uint8_t *out;       // degraded read output + c0 (stripe applied); table solves: the mask;
+                        // chain solves: the rows of odd walk positions
     uint64_t strip_stride, row_stride, out_row_stride;
     uint32_t p, nvec, w;
-    uint8_t cls, a, b, zinv, z;
+    uint8_t cls, a, b, z;
 };
 
 // Epilogue barrier among the consumer warps (bounded).
@@ -849,26 +869,47 @@ __device__ bool epilogue(const Smem &sm, const Tile &T, const uint4 (&accP)[S::k
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
             const int z = T.z;
             if (ctid < static_cast<int>(nv)) {
+                // the walk in blocks of kB rows: a block's loads are
+                // issued together (they never alias its stores), so the walk
+                // pays one shared-memory latency per block, not per row
+                const uint32_t cell0 = smem_addr(sm.xb) + ctid * 16, row_bytes = nv * 16;
                 uint4 e = zero;
                 int r = p - 1;
-                for (int t = 1; t < p; ++t) {
+                int t = 1;
+                constexpr int kB = chain_block<S>();
+                for (; t + kB <= p; t += kB) {
+                    uint32_t a[kB];
+                    uint4 v[kB];
+#pragma unroll
+                    for (int q = 0; q < kB; ++q) {
+                        r += z;
+                        if (r >= p) r -= p;
+                        a[q] = cell0 + r * row_bytes;
+                        v[q] = lds_a(a[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < kB; ++q) {
+                        e = xor4(e, v[q]);
+                        sts_a(a[q], e);
+                    }
+                }
+                for (; t < p; ++t) {
                     r += z;
                     if (r >= p) r -= p;
-                    uint8_t *cell = X(sm.xb, r, ctid);
-                    e = xor4(e, lds(cell));
-                    sts(cell, e);
+                    const uint32_t a = cell0 + r * row_bytes;
+                    e = xor4(e, lds_a(a));
+                    sts_a(a, e);
                 }
                 sts(fold + ctid * 16, xor4(e, lds(X(sm.xb, p - 1, ctid))));  // c
             }
             if (!ep_sync(sm, ep_phase, timeout_ns)) return false;
-            // chain position of row r: r = p-1 + t z (mod p)  =>  t = (r+1) z^-1 (mod p)
-            const int zinv = T.zinv;
+            // D[r_t] = E_t, plus c where the walk position t of the row is odd
+            const uint64_t odd_rows = reinterpret_cast<uint64_t>(T.out);
 #pragma unroll
             for (int t = 0; t < S::kItems; ++t) {
                 if (row[t] >= p - 1) continue;
-                const int pos = ((row[t] + 1) * zinv) % p;
                 uint4 dj = lds(X(sm.xb, row[t], col[t]));
-                if (pos & 1) dj = xor4(dj, lds(fold + col[t] * 16));
+                if ((odd_rows >> row[t]) & 1ull) dj = xor4(dj, lds(fold + col[t] * 16));
                 stg(strip_row(T.b, row[t], col[t]), dj);
                 stg(strip_row(T.a, row[t], col[t]), xor4(dj, accP[t]));
             }
@@ -985,7 +1026,6 @@ __device__ void consumer(const LaunchParams &prm, const Smem &sm, uint32_t n_slo
             copy_dst = T.base + static_cast<uint64_t>(T.a) * T.strip_stride;
             p = static_cast<int>(T.p);
             pitch = tv.y & 0xffffu;
-            T.zinv = static_cast<uint8_t>(tv.y >> 16);
             T.z = static_cast<uint8_t>(tv.y >> 24);
             pw = p * pitch;
             for (int t = 0; t < S::kItems; ++t) {
