@@ -1207,7 +1207,8 @@ def measure_serve(args, ctx, rcg, torch):
     torch.cuda.empty_cache()
     return {"workload": "serving: Poisson stream of %d requests on %d resident stripes (%.1f GB), batched-workload "
                         "geometry, 70%% encode / 20%% degraded read / 10%% rebuild; rate swept 0.1x..2x of the "
-                        "saturation rate; continuous batching vs one launch per request"
+                        "saturation rate; continuous batching (up to 8 batches in flight, round-robin over "
+                        "the server's 8 streams) vs one launch per request (round-robin over the same 8 streams)"
                         % (n, len(stripes), used / 1e9),
             "requests": n, "resident_stripes": len(stripes), "pool_bytes": used,
             "mean_user_bytes_per_request": user // n,

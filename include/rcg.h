@@ -324,10 +324,12 @@ typedef struct rcg_job {
  * equal slots sized for the batch's largest stage; a byte ring, where small
  * stages take less room, is a tuning choice -- rcg_set_batch_tuning).  The job list is validated on the
  * host, copied into a context-owned device descriptor table and replayed
- * through a CUDA graph captured once per context.  Jobs must not overlap in
- * memory.  On return *ticket identifies the batch for rcg_batch_wait.  The
- * context keeps no pointer into `jobs`.  Up to 4 batches may be in flight;
- * a fifth waits (bounded) for the oldest, or returns RCG_EBUSY. */
+ * through a CUDA graph captured once per context -- or, for a table of at
+ * most 31 744 bytes, passed in the kernels' parameter blocks (see
+ * rcg_set_batch_tables).  Jobs must not overlap in memory.  On return *ticket
+ * identifies the batch for rcg_batch_wait.  The context keeps no pointer into
+ * `jobs`.  Up to 16 batches may be in flight; a seventeenth waits (bounded)
+ * for the oldest, or returns RCG_EBUSY. */
 rcg_status rcg_batch_submit(rcg_ctx *ctx, const rcg_job *jobs, uint32_t n_jobs, void *stream,
                             uint64_t *ticket);
 
@@ -413,12 +415,16 @@ rcg_status rcg_batch_wait(rcg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns);
  *    order and never share a launch); requests behind it that do not
  *    conflict go ahead;
  *  - batched mode (default): launch everything admitted as ONE batch of the
- *    persistent engine while fewer than two batches are in flight -- requests
- *    arriving meanwhile join the next batch, which is prepared on the host
- *    while the GPU runs;
+ *    persistent engine while fewer than max_inflight_batches batches are in
+ *    flight -- requests arriving meanwhile join the next batch, which is
+ *    prepared on the host while the GPU runs;
  *  - per-job mode (per_job_launches = 1, the comparison): launch every
  *    admitted request at once with its own single-operation call (one kernel
  *    launch each); the number in flight is bounded only by max_inflight_jobs.
+ *  Launches of both modes go round-robin over eight streams of the server's
+ *  own, so small launches run at once and one batch's tail overlaps the next
+ *  one's start; requests on the same bytes are never in flight together, so
+ *  launches on different streams never touch the same bytes.
  *
  * The HBM budget is a counter, not a live reading: the budget is fixed when
  * the server is created (default min(120 GB, the device's free memory at that
@@ -431,7 +437,7 @@ typedef struct rcg_serve_config {
     uint32_t max_inflight_jobs;  /* admitted but not completed; 0 = 4 x max_batch_jobs */
     uint32_t max_batch_jobs;     /* requests per launch; 0 = 2048 */
     uint32_t per_job_launches;   /* 1: one single-operation launch per request */
-    uint32_t reserved;
+    uint32_t max_inflight_batches; /* batched mode: batches in flight at once, 1..8; 0 = 8 */
 } rcg_serve_config;
 
 typedef struct rcg_serve_request {

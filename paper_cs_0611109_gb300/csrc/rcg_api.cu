@@ -21,7 +21,9 @@ using namespace rcg;
 
 namespace {
 
-constexpr int kBatchRing = 4;
+// Batches in flight per context before a launch waits for the oldest (a
+// served stream keeps up to eight batches in flight on its own streams).
+constexpr int kBatchRing = 16;
 
 struct BatchSlot {
     uint8_t *host = nullptr;  // pinned descriptor table (header + jobs)

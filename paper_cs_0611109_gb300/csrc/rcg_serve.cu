@@ -13,13 +13,14 @@
 //      those of an admitted request -- or of an earlier request that is still
 //      waiting -- waits, so requests on the same bytes run in arrival order
 //      and never share a launch;
-//   3. launch: batched mode -- while fewer than two launches are in flight,
-//      everything admitted and not yet launched (up to max_batch_jobs) goes
-//      out as ONE persistent-kernel batch, so requests that arrived while the
-//      previous batch ran join the next one (continuous batching) and the next
-//      batch is prepared on the host while the GPU runs the current one;
-//      per-job mode (the comparison) -- every admitted request is launched at
-//      once with its own single-operation call and completion event.
+//   3. launch: batched mode -- while fewer than max_inflight_batches launches
+//      are in flight, everything admitted and not yet launched (up to
+//      max_batch_jobs) goes out as ONE persistent-kernel batch, so requests
+//      that arrived while the previous batch ran join the next one (continuous
+//      batching) and the next batch is prepared on the host while the GPU runs
+//      the current one; per-job mode (the comparison) -- every admitted
+//      request is launched at once with its own single-operation call and
+//      completion event.  Launches go round-robin over the server's streams.
 // Latency = completion - arrival.
 #include <cuda_runtime.h>
 #if defined(__linux__)
@@ -69,6 +70,14 @@ struct Launch {
     cudaEvent_t done = nullptr;
     uint64_t ticket = 0;         // batch mode
 };
+
+// The server's streams.  Launches go round-robin over them -- per-job
+// launches (a request's single-stripe kernel fills a fraction of the GPU, so
+// several run at once) and batches alike (a small batch at low load starts
+// at once, and one batch's tail overlaps the next one's start).  Admission
+// keeps requests on the same bytes from being in flight together, so
+// launches on different streams never touch the same bytes.
+constexpr int kServeStreams = 8;
 
 struct Strides {
     uint64_t rs, ss, st, ars, ass;
@@ -121,14 +130,15 @@ uint32_t job_extents(const rcg_job &j, Extent *out) {
 struct rcg_server {
     rcg_ctx *ctx = nullptr;
     rcg_serve_config cfg;
-    cudaStream_t stream = nullptr;
+    cudaStream_t streams[kServeStreams] = {};
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv;
     std::vector<Request> reqs;          // by id
     std::unique_ptr<rcg::Admission> adm;  // which requests may start (rcg_admission.h)
     std::deque<uint64_t> admitted;      // admitted, not launched
-    std::deque<Launch> inflight;        // launched, not retired
+    std::deque<Launch> inflight[kServeStreams];  // launched, not retired, per stream (in launch order)
+    uint32_t n_inflight = 0;
     std::vector<cudaEvent_t> free_events;
     uint64_t start_ns = 0;
     uint64_t completed = 0;
@@ -172,7 +182,7 @@ rcg_status launch_single_job(rcg_ctx *ctx, const rcg_job &j, cudaStream_t s) {
 }
 
 void note_launch(rcg_server *s) {
-    s->max_inflight_launches = std::max<uint32_t>(s->max_inflight_launches, static_cast<uint32_t>(s->inflight.size()));
+    s->max_inflight_launches = std::max<uint32_t>(s->max_inflight_launches, s->n_inflight);
 }
 
 // One pass of the scheduler; returns true when it did something.
@@ -180,22 +190,25 @@ bool tick(rcg_server *s) {
     bool did = false;
     const uint64_t now = mono_ns() - s->start_ns;
     std::unique_lock<std::mutex> lock(s->mu);
-    // 1. retire, in launch order (one stream: launches finish in order)
-    while (!s->inflight.empty()) {
-        Launch &L = s->inflight.front();
-        const cudaError_t q = cudaEventQuery(L.done);
-        if (q == cudaErrorNotReady) break;
-        for (uint64_t id : L.ids) {
-            Request &r = s->reqs[id];
-            r.complete_ns = now;  // the tick's clock: frees precede this tick's admissions
-            if (q != cudaSuccess) r.status = RCG_ECUDA;
-            s->adm->retire(id);
+    // 1. retire: each stream's launches finish in their launch order
+    for (auto &queue : s->inflight) {
+        while (!queue.empty()) {
+            Launch &L = queue.front();
+            const cudaError_t q = cudaEventQuery(L.done);
+            if (q == cudaErrorNotReady) break;
+            for (uint64_t id : L.ids) {
+                Request &r = s->reqs[id];
+                r.complete_ns = now;  // the tick's clock: frees precede this tick's admissions
+                if (q != cudaSuccess) r.status = RCG_ECUDA;
+                s->adm->retire(id);
+            }
+            s->completed += L.ids.size();
+            s->free_events.push_back(L.done);
+            queue.pop_front();
+            --s->n_inflight;
+            did = true;
+            s->cv.notify_all();
         }
-        s->completed += L.ids.size();
-        s->free_events.push_back(L.done);
-        s->inflight.pop_front();
-        did = true;
-        s->cv.notify_all();
     }
     // 2. admit arrived requests in order while slots and HBM allow; a request
     //    whose bytes overlap an admitted one's, or an earlier waiting one's,
@@ -212,13 +225,14 @@ bool tick(rcg_server *s) {
             s->admitted.pop_front();
             const rcg_job job = s->reqs[id].req.job;
             const uint32_t launch_no = ++s->launches;
+            const int q = static_cast<int>(launch_no % kServeStreams);
             lock.unlock();
             const uint64_t t_launch = mono_ns() - s->start_ns;
-            const rcg_status st = launch_single_job(s->ctx, job, s->stream);
+            const rcg_status st = launch_single_job(s->ctx, job, s->streams[q]);
             Launch one;
             one.ids.push_back(id);
             one.done = get_event(s);
-            cudaEventRecord(one.done, s->stream);
+            cudaEventRecord(one.done, s->streams[q]);
             lock.lock();
             Request &r = s->reqs[id];
             r.launch_ns = t_launch;
@@ -229,27 +243,29 @@ bool tick(rcg_server *s) {
             } else {
                 ++s->kernel_launches;
             }
-            s->inflight.push_back(std::move(one));
+            s->inflight[q].push_back(std::move(one));
+            ++s->n_inflight;
             note_launch(s);
             did = true;
         }
         return did;
     }
-    // 3b. batched mode: what is admitted goes out as one batch, keeping at
-    //     most two batches in flight
-    if (!s->admitted.empty() && s->inflight.size() < 2) {
+    // 3b. batched mode: what is admitted goes out as one batch while fewer
+    //     than max_inflight_batches are in flight
+    if (!s->admitted.empty() && s->n_inflight < s->cfg.max_inflight_batches) {
         const uint32_t n = static_cast<uint32_t>(std::min<size_t>(s->admitted.size(), s->cfg.max_batch_jobs));
         std::vector<uint64_t> ids(s->admitted.begin(), s->admitted.begin() + n);
         s->admitted.erase(s->admitted.begin(), s->admitted.begin() + n);
         std::vector<rcg_job> jobs(n);
         for (uint32_t k = 0; k < n; ++k) jobs[k] = s->reqs[ids[k]].req.job;
         const uint32_t launch_no = ++s->launches;
+        const int q = static_cast<int>(launch_no % kServeStreams);
         lock.unlock();  // host preparation runs without the lock
         const uint64_t t_launch = mono_ns() - s->start_ns;
         Launch L;
-        const rcg_status st = rcg_batch_submit(s->ctx, jobs.data(), n, s->stream, &L.ticket);
+        const rcg_status st = rcg_batch_submit(s->ctx, jobs.data(), n, s->streams[q], &L.ticket);
         L.done = get_event(s);
-        cudaEventRecord(L.done, s->stream);
+        cudaEventRecord(L.done, s->streams[q]);
         lock.lock();
         L.ids = ids;
         for (uint64_t id : ids) {
@@ -258,7 +274,8 @@ bool tick(rcg_server *s) {
             if (st != RCG_OK) s->reqs[id].status = st;
         }
         if (st == RCG_OK) ++s->kernel_launches;
-        s->inflight.push_back(std::move(L));
+        s->inflight[q].push_back(std::move(L));
+        ++s->n_inflight;
         note_launch(s);
         if (st != RCG_OK && s->error == RCG_OK) s->error = st;
         did = true;
@@ -301,7 +318,13 @@ rcg_status rcg_serve_create(rcg_ctx *ctx, const rcg_serve_config *cfg, rcg_serve
     cudaMemGetInfo(&free_b, &total_b);
     if (s->cfg.hbm_budget_bytes == 0) s->cfg.hbm_budget_bytes = std::min<uint64_t>(120000000000ull, free_b);
     if (s->cfg.max_batch_jobs == 0) s->cfg.max_batch_jobs = 2048;
-    // room for two full batches in flight, so the next one is prepared while one runs
+    if (s->cfg.max_inflight_batches == 0) s->cfg.max_inflight_batches = kServeStreams;
+    if (s->cfg.max_inflight_batches > static_cast<uint32_t>(kServeStreams)) {
+        if (prev >= 0) cudaSetDevice(prev);
+        delete s;
+        return RCG_EINVAL;
+    }
+    // room for four full batches admitted at once, so the next ones are prepared while one runs
     if (s->cfg.max_inflight_jobs == 0) s->cfg.max_inflight_jobs = 4 * s->cfg.max_batch_jobs;
     s->adm.reset(new (std::nothrow) rcg::Admission(s->cfg.hbm_budget_bytes, s->cfg.max_inflight_jobs));
     if (!s->adm) {
@@ -309,7 +332,13 @@ rcg_status rcg_serve_create(rcg_ctx *ctx, const rcg_serve_config *cfg, rcg_serve
         delete s;
         return RCG_ENOMEM;
     }
-    const cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < kServeStreams && e == cudaSuccess; ++q)
+        e = cudaStreamCreateWithFlags(&s->streams[q], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        for (auto st : s->streams)
+            if (st) cudaStreamDestroy(st);
+    }
     if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess) {
         delete s;
@@ -403,11 +432,12 @@ rcg_status rcg_serve_destroy(rcg_server *s) {
     s->stop = true;
     if (s->worker.joinable()) s->worker.join();
     s->running = false;
-    cudaStreamSynchronize(s->stream);
-    for (auto &L : s->inflight)
-        if (L.done) cudaEventDestroy(L.done);
+    for (auto st : s->streams) cudaStreamSynchronize(st);
+    for (auto &queue : s->inflight)
+        for (auto &L : queue)
+            if (L.done) cudaEventDestroy(L.done);
     for (auto e : s->free_events) cudaEventDestroy(e);
-    cudaStreamDestroy(s->stream);
+    for (auto st : s->streams) cudaStreamDestroy(st);
     delete s;
     return RCG_OK;
 }

@@ -51,7 +51,7 @@ class rcg_job(ctypes.Structure):
 
 class rcg_serve_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", _u64), ("max_inflight_jobs", _u32), ("max_batch_jobs", _u32),
-                ("per_job_launches", _u32), ("reserved", _u32)]
+                ("per_job_launches", _u32), ("max_inflight_batches", _u32)]
 
 
 class rcg_serve_request(ctypes.Structure):
@@ -387,8 +387,9 @@ def rcg_batch_free(batch: int):
 
 
 def rcg_serve_create(ctx: int, hbm_budget_bytes=0, max_inflight_jobs=0, max_batch_jobs=0,
-                     per_job_launches=False) -> int:
-    cfg = rcg_serve_config(hbm_budget_bytes, max_inflight_jobs, max_batch_jobs, 1 if per_job_launches else 0, 0)
+                     per_job_launches=False, max_inflight_batches=0) -> int:
+    cfg = rcg_serve_config(hbm_budget_bytes, max_inflight_jobs, max_batch_jobs, 1 if per_job_launches else 0,
+                           max_inflight_batches)
     h = _vp()
     _check(lib().rcg_serve_create(ctx, ctypes.byref(cfg), ctypes.byref(h)), "rcg_serve_create")
     return h.value

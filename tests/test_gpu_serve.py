@@ -69,14 +69,16 @@ def prepare_state(rcg, arena, reqs):
                 arena[o + k * sb: o + (k + 1) * sb] = 0xA5
 
 
-@pytest.mark.parametrize("per_job", [False, True])
-def test_served_results_equal_alone(rcg, oracle, per_job):
+# batched with the default of up to eight batches in flight, batched with two,
+# and one launch per request
+@pytest.mark.parametrize("per_job,batches", [(False, 0), (False, 2), (True, 0)])
+def test_served_results_equal_alone(rcg, oracle, per_job, batches):
     arena, outs, reqs, arrivals, offs = make_stream(rcg, 31, 600, rate_per_s=200000)
     prepare_state(rcg, arena, reqs)
     initial = arena.clone()
     with rcg.Context(0) as c:
         srv = rcg.rcg_serve_create(c.handle, max_inflight_jobs=256, max_batch_jobs=128,
-                                   per_job_launches=per_job)
+                                   per_job_launches=per_job, max_inflight_batches=batches)
         rcg.rcg_serve_submit(srv, [r[3] for r in reqs], arrivals)
         rcg.rcg_serve_start(srv)
         rcg.rcg_serve_drain(srv, 60 * 10 ** 9)
@@ -96,7 +98,7 @@ def test_served_results_equal_alone(rcg, oracle, per_job):
     else:
         assert max(r["batch"] for r in res) < len(reqs)  # requests were batched together
         assert stats["kernel_launches"] == len({r["batch"] for r in res})
-        assert stats["max_inflight_launches"] <= 2
+        assert stats["max_inflight_launches"] <= (batches or 8)
     # alone: the same requests one at a time on the initial state
     arena.copy_(initial)
     outs.zero_()
@@ -135,6 +137,27 @@ def test_served_results_equal_alone(rcg, oracle, per_job):
             assert np.array_equal(got_outs[out_offs[k]:out_offs[k] + n_out].reshape(g["p"] - 1, g["c"]), strip), k
         assert np.array_equal(got[o:o + b], want), k
     assert min(checked.values()) > 0
+
+
+def test_batched_mode_keeps_several_batches_in_flight(rcg):
+    # every request arrives at once, one request per batch: batches go out on
+    # the server's streams without waiting for one another, up to the limit
+    arena, outs, reqs, arrivals, offs = make_stream(rcg, 34, 200, rate_per_s=10 ** 9)
+    prepare_state(rcg, arena, reqs)
+    with rcg.Context(0) as c:
+        with pytest.raises(rcg.RcgError):
+            rcg.rcg_serve_create(c.handle, max_inflight_batches=9)
+        srv = rcg.rcg_serve_create(c.handle, max_inflight_jobs=512, max_batch_jobs=1)
+        rcg.rcg_serve_submit(srv, [r[3] for r in reqs], np.zeros(len(reqs), np.int64))
+        rcg.rcg_serve_start(srv)
+        rcg.rcg_serve_drain(srv, 60 * 10 ** 9)
+        res = rcg.rcg_serve_results(srv, len(reqs))
+        stats = rcg.rcg_serve_get_stats(srv)
+        rcg.rcg_serve_destroy(srv)
+        assert c.last_device_status() == 0
+    assert all(r["status"] == 0 for r in res)
+    assert stats["kernel_launches"] == len(reqs)
+    assert 2 < stats["max_inflight_launches"] <= 8
 
 
 def test_per_job_mode_keeps_many_launches_in_flight(rcg):
