@@ -263,7 +263,10 @@ bool tick(rcg_server *s) {
         lock.unlock();  // host preparation runs without the lock
         const uint64_t t_launch = mono_ns() - s->start_ns;
         Launch L;
-        const rcg_status st = rcg_batch_submit(s->ctx, jobs.data(), n, s->streams[q], &L.ticket);
+        // a batch of one request gains nothing from the batch tables: it goes
+        // out as that request's single-operation call
+        const rcg_status st = n == 1 ? launch_single_job(s->ctx, jobs[0], s->streams[q])
+                                     : rcg_batch_submit(s->ctx, jobs.data(), n, s->streams[q], &L.ticket);
         L.done = get_event(s);
         cudaEventRecord(L.done, s->streams[q]);
         lock.lock();
